@@ -1,0 +1,19 @@
+"""GB300-native parallel ADMM for robust quadratic resource allocation.
+
+The solver is a C-ABI CUDA library (``libadmm.so``, declared in
+``include/admm.h``); :mod:`paper_1903_10041_gb300.capi` is its thin ctypes
+binding.  :mod:`paper_1903_10041_gb300.workloads` generates seeded inputs.
+The binding is imported lazily so that the input generators can be used on
+machines where the library has not been built.
+"""
+__all__ = ["capi", "workloads"]
+
+
+def __getattr__(name):
+    if name == "capi":
+        from . import capi
+        return capi
+    if name == "workloads":
+        from . import workloads
+        return workloads
+    raise AttributeError(name)
