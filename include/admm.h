@@ -1,0 +1,175 @@
+/*
+ * admm.h -- C ABI of the GB300 (sm_103a) parallel ADMM solver for robust
+ * quadratic resource allocation (Qureshi, East, Cannon, "Parallel ADMM for
+ * robust quadratic optimal resource allocation problems").
+ *
+ * The problem is eq. (2) of Sec. II:
+ *
+ *   min_{x_1^(i), x_k^(i,j) in [lo_k^(i), hi_k^(i)]}  (1/q) sum_{j,i,k} f_k^(i,j)(x_k^(i,j))
+ *   s.t.  sum_i x_k^(i,j) >= y_k^(j)              (demand, every k, j)
+ *         sum_k g_k^(i,j)(x_k^(i,j)) <= c^(i)      (capacity, every i, j)
+ *         x_1^(i,j) = x_1^(i)                      (shared first move)
+ *
+ * with quadratic f and g (Assumption 3):
+ *   f_k^(i,j)(x) = f2 x^2 + f1 x + f0,  g_k^(i,j)(x) = g2 x^2 + g1 x + g0.
+ * q = 1 is the nominal problem (1).  It is solved by the ADMM iteration
+ * (a)-(i) of App. A, whose step (a) minimises one quartic per element with
+ * Algorithm 1 (Sec. III-B), until the residuals r and sigma of App. A fall
+ * below r_tol and s_tol (Alg. 2 step 3), checked every `check_every`
+ * iterations (Sec. IV-B).
+ *
+ * Array layout (all row-major, k fastest; indices 0-based, so the paper's
+ * k = 1 is k = 0 here):
+ *   element arrays  f2 f1 f0 g2 g1 g0 x      [m][q][n]   index (i*q + j)*n + k
+ *   bound arrays    x_lo x_hi                [m][n]      index i*n + k
+ *   column arrays   y s mu                   [q][n]      index j*n + k
+ *   pair arrays     lam zeta h p nu          [m][q]      index i*q + j
+ *   source arrays   c x1                     [m]
+ *
+ * Errors: every call returns an admm_status; admm_last_error() gives a
+ * thread-local message for the last failing call on the calling thread.
+ * No call aborts the process.  Device waits inside the kernels are bounded:
+ * a wait that runs out returns ADMM_ETIMEOUT instead of hanging.
+ */
+#ifndef ADMM_H
+#define ADMM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum admm_status {
+    ADMM_OK = 0,
+    ADMM_EINVAL = 1,         /* bad argument or problem data (see admm_create) */
+    ADMM_ENOMEM = 2,         /* a device or pinned-host allocation failed */
+    ADMM_ECUDA = 3,          /* a CUDA runtime call failed */
+    ADMM_ETIMEOUT = 4,       /* a bounded device-side wait gave up */
+    ADMM_ENOTCONVERGED = 5,  /* max_iter reached; the result is still filled */
+    ADMM_EUNSUPPORTED = 6    /* sizes beyond this build's limits */
+} admm_status;
+
+/* Arithmetic of the per-element work (the stored state follows it). */
+enum {
+    ADMM_FP64 = 0,          /* everything in FP64 */
+    ADMM_MIXED = 1,         /* FP32 storage and element work; FP64 k-sums, pair
+                               scalars and residuals; the cubic's branch is
+                               decided in FP64 whenever FP32 cannot certify it */
+    ADMM_MIXED_FP64CUBIC = 2 /* as ADMM_MIXED, but the whole cubic step
+                               (b, c, d, Q, R, Delta, roots, delta-f) in FP64 */
+};
+/* x-update of step (a) */
+enum {
+    ADMM_XMIN_EXACT = 0,    /* constrained minimiser: both local minima clamped, better kept */
+    ADMM_XMIN_PAPER = 1     /* Pi(global unconstrained minimiser), as printed */
+};
+/* order of the sources in step (a) */
+enum { ADMM_GAUSS_SEIDEL = 0, ADMM_JACOBI = 1 };
+
+#define ADMM_MAX_M 8          /* sources per instance */
+#define ADMM_MAX_PAIRS 1024   /* m*q per single instance */
+
+typedef struct admm_problem {
+    int32_t n, m, q;                 /* steps, sources, scenarios; all >= 1 */
+    const double *f2, *f1, *f0;      /* alpha_{k,2..0}^(i,j)  [m][q][n]; f2 >= 0 */
+    const double *g2, *g1, *g0;      /* beta_{k,2..0}^(i,j)   [m][q][n]; g2 >= 0 */
+    const double *x_lo, *x_hi;       /* [m][n]; x_lo <= x_hi, finite */
+    const double *y;                 /* [q][n] */
+    const double *c;                 /* [m]; +INFINITY = no capacity limit */
+    int32_t on_device;               /* 1: device pointers; 0: host pointers */
+} admm_problem;
+
+typedef struct admm_params {
+    double rho[4];                   /* rho_1..rho_4 > 0 (App. A) */
+    double r_tol, s_tol;             /* stop when r < r_tol and sigma < s_tol */
+    double tau;                      /* penalty factor of the adaptation (Sec. IV-A) */
+    int32_t max_iter;                /* >= 1 */
+    int32_t check_every;             /* >= 1; residuals at t % check_every == 0 and t == max_iter */
+    int32_t precision;               /* ADMM_FP64 | ADMM_MIXED | ADMM_MIXED_FP64CUBIC */
+    int32_t xmin_mode;               /* ADMM_XMIN_EXACT | ADMM_XMIN_PAPER */
+    int32_t sweep;                   /* ADMM_GAUSS_SEIDEL | ADMM_JACOBI */
+    int32_t adapt_rho;               /* 1: rho_i <- tau rho_i or rho_i / tau by r/sigma (Sec. IV-A) */
+    int32_t reserved[4];             /* must be 0 */
+} admm_params;
+
+/* The solver state (the checkpoint).  z is not stored: after every
+ * iteration z_k^(i,j) = g_k^(i,j)(x_k^(i,j)) + zeta^(i,j) and lambda is
+ * constant over k (steps (b) and (g)), so (x, zeta, lam) determine z and
+ * lambda.  cold = 1 marks the zero start of the paper's iteration, where
+ * z = 0 instead. */
+typedef struct admm_state {
+    double *x;                       /* [m][q][n] */
+    double *s, *mu;                  /* [q][n] */
+    double *lam, *zeta, *h, *p, *nu; /* [m][q] */
+    double *x1;                      /* [m] */
+    double rho[4];                   /* penalties in force (they change with adapt_rho) */
+    int32_t cold;
+    int32_t on_device;               /* 1: the array pointers are device memory */
+} admm_state;
+
+typedef struct admm_result {
+    double *x;                       /* out [m][q][n] or NULL */
+    double *x1;                      /* out [m] or NULL */
+    int32_t on_device;               /* 1: x, x1 are device pointers */
+    int32_t iters;                   /* iterations run */
+    int32_t converged;               /* 1 if the stop test passed */
+    int32_t status;                  /* admm_status of the solve */
+    double objective;                /* (1/q) sum f(x), eq. (2) */
+    double r, sigma;                 /* residuals at the last check */
+} admm_result;
+
+typedef struct admm_handle admm_handle;
+
+/* Defaults: rho = 1, r_tol = s_tol = 1e-6, max_iter = 5000,
+ * check_every = 10 (Sec. IV-B), FP64, exact x-update, Gauss-Seidel,
+ * no adaptation, tau = 1.1 (Sec. IV-A). */
+void admm_default_params(admm_params *out);
+
+/* Validates the problem (Assumptions 1 and 3: f2, g2 >= 0; finite data;
+ * x_lo <= x_hi; c not NaN; sum_k min_{[lo,hi]} g > c is a sure
+ * infeasibility), copies it into device memory owned by the handle in the
+ * layout the kernels use, and sets the zero start.  The caller keeps its
+ * buffers.  Returns ADMM_EINVAL, ADMM_EUNSUPPORTED (m > ADMM_MAX_M or
+ * m*q > ADMM_MAX_PAIRS), ADMM_ENOMEM or ADMM_ECUDA on failure, with *out
+ * set to NULL.  Runs on the current CUDA device and synchronises it. */
+admm_status admm_create(const admm_problem *prob, const admm_params *params, admm_handle **out);
+
+/* Replaces the settings used by later solves (same validation). */
+admm_status admm_set_params(admm_handle *h, const admm_params *params);
+
+/* Solves from `warm` (NULL: continue from the handle's current state; a
+ * fresh handle holds the zero start) until the stop test or max_iter,
+ * with the whole loop on the device (one persistent launch).  Runs on
+ * `stream` (a cudaStream_t; NULL = legacy default stream) and returns after
+ * the stream has finished the solve.  Fills `out` (which may be NULL)
+ * and leaves the final state in the handle.  Returns ADMM_OK,
+ * ADMM_ENOTCONVERGED (result still filled), ADMM_ETIMEOUT, ADMM_ECUDA. */
+admm_status admm_solve(admm_handle *h, const admm_state *warm, admm_result *out, void *stream);
+
+/* Resets the handle's state to the zero start. */
+admm_status admm_reset(admm_handle *h);
+
+/* Copies the handle's current state into `out` (host or device buffers as
+ * out->on_device says; NULL array pointers are skipped).  Synchronous. */
+admm_status admm_get_state(admm_handle *h, admm_state *out, void *stream);
+
+/* Frees everything the handle owns.  NULL-safe. */
+admm_status admm_destroy(admm_handle *h);
+
+/* Diagnostics: launches a grid barrier (the one the solve kernels use)
+ * that waits for one more arrival than the grid has, with a wait bound of
+ * spin_ns (0 < spin_ns <= 5e9) over `grid` CTAs (1..64).  The wait must run
+ * out and record ADMM_ETIMEOUT, which is returned in *status_out; the
+ * device stays usable.  No counterpart in the paper: it tests the failure
+ * path of the bounded device waits without faulting the GPU. */
+admm_status admm_selftest_barrier_timeout(long long spin_ns, int grid, int *status_out);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *admm_last_error(void);
+const char *admm_status_string(admm_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ADMM_H */

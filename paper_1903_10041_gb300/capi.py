@@ -1,0 +1,288 @@
+"""Thin ctypes binding of the C ABI in ``include/admm.h`` (``libadmm.so``).
+
+Argument marshalling only: every step of the solver runs in the CUDA
+kernels of the library.  Arrays may be numpy arrays (host memory) or torch
+CUDA tensors (device memory); both must be float64 and C-contiguous.
+Importing this module raises ImportError when the library has not been
+built: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libadmm.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with paper_1903_10041_gb300.build.build() "
+                      "(or __graft_entry__.build()); there is no fallback path")
+
+_lib = C.CDLL(LIB_PATH)
+_dp = C.POINTER(C.c_double)
+
+ADMM_OK, ADMM_EINVAL, ADMM_ENOMEM, ADMM_ECUDA, ADMM_ETIMEOUT, ADMM_ENOTCONVERGED, ADMM_EUNSUPPORTED = range(7)
+STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "ENOTCONVERGED",
+                6: "EUNSUPPORTED"}
+PRECISION = {"fp64": 0, "mixed": 1, "mixed_fp64cubic": 2}
+XMIN = {"exact": 0, "paper": 1}
+SWEEP = {"gauss_seidel": 0, "jacobi": 1}
+MAX_M = 8
+MAX_PAIRS = 1024
+
+
+class admm_problem(C.Structure):
+    _fields_ = [("n", C.c_int32), ("m", C.c_int32), ("q", C.c_int32),
+                ("f2", _dp), ("f1", _dp), ("f0", _dp), ("g2", _dp), ("g1", _dp), ("g0", _dp),
+                ("x_lo", _dp), ("x_hi", _dp), ("y", _dp), ("c", _dp), ("on_device", C.c_int32)]
+
+
+class admm_params(C.Structure):
+    _fields_ = [("rho", C.c_double * 4), ("r_tol", C.c_double), ("s_tol", C.c_double), ("tau", C.c_double),
+                ("max_iter", C.c_int32), ("check_every", C.c_int32), ("precision", C.c_int32),
+                ("xmin_mode", C.c_int32), ("sweep", C.c_int32), ("adapt_rho", C.c_int32),
+                ("reserved", C.c_int32 * 4)]
+
+
+class admm_state(C.Structure):
+    _fields_ = [("x", _dp), ("s", _dp), ("mu", _dp), ("lam", _dp), ("zeta", _dp), ("h", _dp), ("p", _dp),
+                ("nu", _dp), ("x1", _dp), ("rho", C.c_double * 4), ("cold", C.c_int32),
+                ("on_device", C.c_int32)]
+
+
+class admm_result(C.Structure):
+    _fields_ = [("x", _dp), ("x1", _dp), ("on_device", C.c_int32), ("iters", C.c_int32),
+                ("converged", C.c_int32), ("status", C.c_int32), ("objective", C.c_double),
+                ("r", C.c_double), ("sigma", C.c_double)]
+
+
+_H = C.c_void_p
+_lib.admm_default_params.argtypes = [C.POINTER(admm_params)]
+_lib.admm_default_params.restype = None
+_lib.admm_create.argtypes = [C.POINTER(admm_problem), C.POINTER(admm_params), C.POINTER(_H)]
+_lib.admm_create.restype = C.c_int
+_lib.admm_set_params.argtypes = [_H, C.POINTER(admm_params)]
+_lib.admm_set_params.restype = C.c_int
+_lib.admm_solve.argtypes = [_H, C.POINTER(admm_state), C.POINTER(admm_result), C.c_void_p]
+_lib.admm_solve.restype = C.c_int
+_lib.admm_reset.argtypes = [_H]
+_lib.admm_reset.restype = C.c_int
+_lib.admm_get_state.argtypes = [_H, C.POINTER(admm_state), C.c_void_p]
+_lib.admm_get_state.restype = C.c_int
+_lib.admm_destroy.argtypes = [_H]
+_lib.admm_destroy.restype = C.c_int
+_lib.admm_last_error.argtypes = []
+_lib.admm_last_error.restype = C.c_char_p
+_lib.admm_status_string.argtypes = [C.c_int]
+_lib.admm_status_string.restype = C.c_char_p
+_lib.admm_selftest_barrier_timeout.argtypes = [C.c_longlong, C.c_int, C.POINTER(C.c_int)]
+_lib.admm_selftest_barrier_timeout.restype = C.c_int
+
+
+class AdmmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def admm_last_error() -> str:
+    return _lib.admm_last_error().decode()
+
+
+def _check(st: int, allow=(ADMM_OK,)) -> int:
+    if st not in allow:
+        raise AdmmError(st, admm_last_error())
+    return st
+
+
+# ---------------------------------------------------------------------------
+# marshalling helpers
+# ---------------------------------------------------------------------------
+def _is_torch(a) -> bool:
+    return type(a).__module__.startswith("torch")
+
+
+def _ptr(a, keep: list):
+    """Pointer to a float64 C-contiguous array; numpy (host) or torch (device)."""
+    if a is None:
+        return None, None
+    if _is_torch(a):
+        import torch
+        if a.dtype != torch.float64 or not a.is_contiguous():
+            raise TypeError("torch tensors must be float64 and contiguous")
+        keep.append(a)
+        return C.cast(C.c_void_p(a.data_ptr()), _dp), bool(a.is_cuda)
+    arr = np.ascontiguousarray(a, dtype=np.float64)
+    keep.append(arr)
+    return arr.ctypes.data_as(_dp), False
+
+
+def admm_default_params() -> admm_params:
+    p = admm_params()
+    _lib.admm_default_params(C.byref(p))
+    return p
+
+
+def make_params(par=None, **kw) -> admm_params:
+    """admm_params from a duck-typed settings object (rho, r_tol, s_tol,
+    max_iter, check_every, precision, xmin_mode, sweep, adapt_rho, tau)."""
+    p = admm_default_params()
+    src = {}
+    if par is not None:
+        for k in ("rho", "r_tol", "s_tol", "max_iter", "check_every", "precision", "xmin_mode", "sweep",
+                  "adapt_rho", "tau"):
+            if hasattr(par, k):
+                src[k] = getattr(par, k)
+    src.update(kw)
+    if "rho" in src:
+        for t in range(4):
+            p.rho[t] = float(src["rho"][t])
+    for k in ("r_tol", "s_tol", "tau"):
+        if k in src:
+            setattr(p, k, float(src[k]))
+    for k in ("max_iter", "check_every"):
+        if k in src:
+            setattr(p, k, int(src[k]))
+    if "precision" in src:
+        p.precision = PRECISION[src["precision"]] if isinstance(src["precision"], str) else int(src["precision"])
+    if "xmin_mode" in src:
+        p.xmin_mode = XMIN[src["xmin_mode"]] if isinstance(src["xmin_mode"], str) else int(src["xmin_mode"])
+    if "sweep" in src:
+        p.sweep = SWEEP[src["sweep"]] if isinstance(src["sweep"], str) else int(src["sweep"])
+    if "adapt_rho" in src:
+        p.adapt_rho = int(bool(src["adapt_rho"]))
+    return p
+
+
+def make_problem(prob, keep: list) -> admm_problem:
+    """admm_problem pointing at the arrays of a duck-typed problem object."""
+    names = ("f2", "f1", "f0", "g2", "g1", "g0", "lo", "hi", "y", "c")
+    ptrs, devs = [], set()
+    for nm in names:
+        p, d = _ptr(getattr(prob, nm), keep)
+        ptrs.append(p)
+        devs.add(d)
+    if len(devs) != 1:
+        raise TypeError("problem arrays must be all host or all device")
+    return admm_problem(int(prob.n), int(prob.m), int(prob.q), *ptrs, int(devs.pop()))
+
+
+# ---------------------------------------------------------------------------
+# the C ABI, same names
+# ---------------------------------------------------------------------------
+def admm_create(prob, par=None, **kw) -> C.c_void_p:
+    keep: list = []
+    cp = make_problem(prob, keep)
+    pp = par if isinstance(par, admm_params) else make_params(par, **kw)
+    h = _H()
+    _check(_lib.admm_create(C.byref(cp), C.byref(pp), C.byref(h)))
+    return h
+
+
+def admm_set_params(h, par=None, **kw) -> None:
+    pp = par if isinstance(par, admm_params) else make_params(par, **kw)
+    _check(_lib.admm_set_params(h, C.byref(pp)))
+
+
+def admm_reset(h) -> None:
+    _check(_lib.admm_reset(h))
+
+
+def _state_struct(st: dict, keep: list) -> admm_state:
+    names = ("x", "s", "mu", "lam", "zeta", "h", "p", "nu", "x1")
+    ptrs, devs = [], set()
+    for nm in names:
+        p, d = _ptr(st[nm], keep)
+        ptrs.append(p)
+        devs.add(d)
+    if len(devs) != 1:
+        raise TypeError("state arrays must be all host or all device")
+    rho = (C.c_double * 4)(*[float(v) for v in st["rho"]])
+    return admm_state(*ptrs, rho, int(bool(st.get("cold", False))), int(devs.pop()))
+
+
+def admm_solve(h, warm: dict | None = None, x_out=None, x1_out=None, stream=None,
+               raise_on=(ADMM_EINVAL, ADMM_ENOMEM, ADMM_ECUDA, ADMM_ETIMEOUT, ADMM_EUNSUPPORTED)) -> dict:
+    """Runs a solve.  ``x_out``/``x1_out``: optional numpy or torch buffers
+    that receive x [m, q, n] and x_1 [m].  ``stream``: a torch.cuda.Stream,
+    an integer cudaStream_t, or None (legacy default stream)."""
+    keep: list = []
+    ws = C.byref(_state_struct(warm, keep)) if warm is not None else None
+    res = admm_result()
+    if x_out is not None or x1_out is not None:
+        px, dx = _ptr(x_out, keep)
+        p1, d1 = _ptr(x1_out, keep)
+        res.x = px
+        res.x1 = p1
+        res.on_device = int(bool(dx or d1))
+    sp = None
+    if stream is not None:
+        sp = C.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
+    st = _lib.admm_solve(h, ws, C.byref(res), sp)
+    if st in raise_on:
+        raise AdmmError(st, admm_last_error())
+    return {"status": st, "iters": res.iters, "converged": bool(res.converged), "objective": res.objective,
+            "r": res.r, "sigma": res.sigma}
+
+
+def admm_get_state(h, n: int, m: int, q: int) -> dict:
+    """The handle's current state as numpy arrays (keys as in admm_state)."""
+    st = {"x": np.empty((m, q, n)), "s": np.empty((q, n)), "mu": np.empty((q, n)),
+          "lam": np.empty((m, q)), "zeta": np.empty((m, q)), "h": np.empty((m, q)), "p": np.empty((m, q)),
+          "nu": np.empty((m, q)), "x1": np.empty(m), "rho": [0.0] * 4, "cold": False}
+    keep: list = []
+    cs = _state_struct(st, keep)
+    _check(_lib.admm_get_state(h, C.byref(cs), None))
+    st["rho"] = [cs.rho[t] for t in range(4)]
+    st["cold"] = bool(cs.cold)
+    return st
+
+
+def admm_destroy(h) -> None:
+    if h:
+        _lib.admm_destroy(h)
+
+
+def admm_selftest_barrier_timeout(spin_ns: int = 20_000_000, grid: int = 4) -> int:
+    out = C.c_int(-1)
+    _check(_lib.admm_selftest_barrier_timeout(int(spin_ns), int(grid), C.byref(out)))
+    return out.value
+
+
+class Solver:
+    """Owns one handle: ``Solver(problem, params).solve()``."""
+
+    def __init__(self, prob, par=None, **kw):
+        self.n, self.m, self.q = int(prob.n), int(prob.m), int(prob.q)
+        self.h = admm_create(prob, par, **kw)
+
+    def solve(self, warm=None, **kw) -> dict:
+        return admm_solve(self.h, warm, **kw)
+
+    def set_params(self, par=None, **kw):
+        admm_set_params(self.h, par, **kw)
+
+    def reset(self):
+        admm_reset(self.h)
+
+    def state(self) -> dict:
+        return admm_get_state(self.h, self.n, self.m, self.q)
+
+    def close(self):
+        if self.h:
+            admm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,0 +1,567 @@
+// Host side of the C ABI declared in include/admm.h: validation, device
+// layout, launch configuration and state import/export for the
+// single-instance solver.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+
+using namespace admm_impl;
+
+namespace {
+
+thread_local std::string g_err;
+
+admm_status fail(admm_status s, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+#define CUDA_TRY(call)                                                                                     \
+    do {                                                                                                   \
+        cudaError_t e_ = (call);                                                                           \
+        if (e_ != cudaSuccess)                                                                             \
+            return fail(e_ == cudaErrorMemoryAllocation ? ADMM_ENOMEM : ADMM_ECUDA, "%s: %s (%s:%d)", #call, \
+                        cudaGetErrorString(e_), __FILE__, __LINE__);                                       \
+    } while (0)
+
+// Element validation flags (bits)
+enum : unsigned {
+    V_NONFINITE = 1u,   // a coefficient, bound or demand is NaN or infinite
+    V_NONCONVEX = 2u,   // f2 < 0 or g2 < 0 (Assumption 1)
+    V_BOUNDS = 4u,      // x_lo > x_hi
+    V_INFEASIBLE = 8u,  // sum_k min g > c for some (i, j)
+    V_CNAN = 16u        // c is NaN
+};
+
+__global__ void validate_elements(int n, int m, int q, int ld, const double *f2, const double *f1,
+                                  const double *f0, const double *g2, const double *g1, const double *g0,
+                                  const double *lo, const double *hi, const double *y, unsigned *flags)
+{
+    const int64_t total = (int64_t)m * q * n;
+    unsigned bits = 0;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int k = (int)(t % n);
+        const int64_t r = t / n; // i*q + j
+        const int i = (int)(r / q), j = (int)(r % q);
+        const size_t e = (size_t)r * ld + k;
+        const double v[6] = {f2[e], f1[e], f0[e], g2[e], g1[e], g0[e]};
+        for (int u = 0; u < 6; ++u)
+            if (!isfinite(v[u])) bits |= V_NONFINITE;
+        if (v[0] < 0.0 || v[3] < 0.0) bits |= V_NONCONVEX;
+        if (j == 0) {
+            const double a = lo[(size_t)i * ld + k], b = hi[(size_t)i * ld + k];
+            if (!isfinite(a) || !isfinite(b)) bits |= V_NONFINITE;
+            if (a > b) bits |= V_BOUNDS;
+        }
+        if (i == 0 && !isfinite(y[(size_t)j * ld + k])) bits |= V_NONFINITE;
+    }
+    if (bits) atomicOr(flags, bits);
+}
+
+// One CTA per pair (i, j): sum_k beta_0 (kept for the solve) and the
+// smallest achievable sum_k g (for the sure-infeasibility check).
+__global__ void pair_sums(int n, int m, int q, int ld, const double *g2, const double *g1, const double *g0,
+                          const double *lo, const double *hi, const double *c, double *sumg0, unsigned *flags)
+{
+    __shared__ double sh[2][32];
+    const int pr = blockIdx.x, i = pr / q;
+    const size_t base = (size_t)pr * ld;
+    double s0 = 0.0, smin = 0.0;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        const double a2 = g2[base + k], a1 = g1[base + k], a0 = g0[base + k];
+        const double l = lo[(size_t)i * ld + k], h = hi[(size_t)i * ld + k];
+        double xm = a2 > 0.0 ? -a1 / (2.0 * a2) : (a1 > 0.0 ? l : h);
+        xm = clampd(xm, l, h);
+        s0 += a0;
+        smin += a2 * xm * xm + a1 * xm + a0;
+    }
+    s0 = warp_sum(s0);
+    smin = warp_sum(smin);
+    if ((threadIdx.x & 31) == 0) {
+        sh[0][threadIdx.x >> 5] = s0;
+        sh[1][threadIdx.x >> 5] = smin;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            a += sh[0][w];
+            b += sh[1][w];
+        }
+        sumg0[pr] = a;
+        const double ci = c[i];
+        if (isnan(ci)) atomicOr(flags, V_CNAN);
+        else if (b > ci * (1.0 + 1e-12) + 1e-12) atomicOr(flags, V_INFEASIBLE);
+    }
+}
+
+__global__ void init_x(int n, int m, int q, int ld, const double *lo, const double *hi, double *x)
+{
+    const int64_t total = (int64_t)m * q * n;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int k = (int)(t % n);
+        const int64_t r = t / n;
+        const int i = (int)(r / q);
+        x[(size_t)r * ld + k] = clampd(0.0, lo[(size_t)i * ld + k], hi[(size_t)i * ld + k]);
+    }
+}
+
+__global__ void selftest_barrier_kernel(unsigned *bar, int *status, long long spin_ns, unsigned extra)
+{
+    // Waits for `extra` more arrivals than the grid can provide.
+    grid_barrier(bar, gridDim.x + extra, status, spin_ns, ADMM_ETIMEOUT);
+}
+
+bool params_ok(const admm_params *p)
+{
+    if (!p) return !fail(ADMM_EINVAL, "params is NULL");
+    for (int t = 0; t < 4; ++t)
+        if (!(p->rho[t] > 0.0) || !std::isfinite(p->rho[t]))
+            return !fail(ADMM_EINVAL, "rho[%d] = %g must be finite and > 0", t, p->rho[t]);
+    if (!(p->r_tol >= 0.0) || !(p->s_tol >= 0.0)) return !fail(ADMM_EINVAL, "r_tol and s_tol must be >= 0");
+    if (p->max_iter < 1) return !fail(ADMM_EINVAL, "max_iter must be >= 1");
+    if (p->check_every < 1) return !fail(ADMM_EINVAL, "check_every must be >= 1");
+    if (p->precision != ADMM_FP64)
+        return !fail(ADMM_EUNSUPPORTED, "precision %d is not available in the single-instance solver", p->precision);
+    if (p->xmin_mode != ADMM_XMIN_EXACT && p->xmin_mode != ADMM_XMIN_PAPER)
+        return !fail(ADMM_EINVAL, "bad xmin_mode %d", p->xmin_mode);
+    if (p->sweep != ADMM_GAUSS_SEIDEL && p->sweep != ADMM_JACOBI) return !fail(ADMM_EINVAL, "bad sweep %d", p->sweep);
+    if (p->adapt_rho && !(p->tau > 1.0)) return !fail(ADMM_EINVAL, "tau must be > 1 with adapt_rho");
+    for (int t = 0; t < 4; ++t)
+        if (p->reserved[t]) return !fail(ADMM_EINVAL, "reserved fields must be 0");
+    return true;
+}
+
+long long spin_limit_ns()
+{
+    const char *e = getenv("ADMM_SPIN_NS");
+    long long v = e ? atoll(e) : 0;
+    return v > 0 ? v : 2000000000LL; // 2 s per barrier wait
+}
+
+} // namespace
+
+struct admm_handle {
+    int n = 0, m = 0, q = 0, ld = 0, dev = 0, nsm = 0;
+    admm_params prm{};
+    // problem (FP64, padded rows of ld)
+    double *f2 = nullptr, *f1 = nullptr, *f0 = nullptr, *g2 = nullptr, *g1 = nullptr, *g0 = nullptr;
+    double *lo = nullptr, *hi = nullptr, *y = nullptr, *c = nullptr, *sumg0 = nullptr;
+    // state
+    double *x = nullptr, *s = nullptr, *mu = nullptr, *scal = nullptr;
+    // scratch
+    double *part = nullptr, *cpart = nullptr, *info = nullptr;
+    unsigned *bar = nullptr, *flags = nullptr;
+    int *status = nullptr;
+    double *info_host = nullptr; // pinned
+    // launch shape
+    int grid = 0, slots = 0;
+    int64_t chunk = 0;
+    size_t smem = 0;
+};
+
+namespace {
+
+void free_all(admm_handle *h)
+{
+    double **dp[] = {&h->f2, &h->f1, &h->f0, &h->g2, &h->g1, &h->g0, &h->lo, &h->hi, &h->y, &h->c,
+                     &h->sumg0, &h->x, &h->s, &h->mu, &h->scal, &h->part, &h->cpart, &h->info};
+    for (double **p : dp)
+        if (*p) {
+            cudaFree(*p);
+            *p = nullptr;
+        }
+    if (h->bar) cudaFree(h->bar);
+    if (h->flags) cudaFree(h->flags);
+    if (h->status) cudaFree(h->status);
+    if (h->info_host) cudaFreeHost(h->info_host);
+    h->bar = h->flags = nullptr;
+    h->status = nullptr;
+    h->info_host = nullptr;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        int cur;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+// rows x n doubles from a (host or device) dense source into a padded device array
+cudaError_t put_rows(double *dst, int ld, const double *src, int n, int64_t rows, bool src_dev)
+{
+    return cudaMemcpy2D(dst, (size_t)ld * 8, src, (size_t)n * 8, (size_t)n * 8, (size_t)rows,
+                        src_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice);
+}
+
+cudaError_t get_rows(double *dst, const double *src, int ld, int n, int64_t rows, bool dst_dev, cudaStream_t st)
+{
+    return cudaMemcpy2DAsync(dst, (size_t)n * 8, src, (size_t)ld * 8, (size_t)n * 8, (size_t)rows,
+                             dst_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st);
+}
+
+admm_status reset_state(admm_handle *h)
+{
+    const int m = h->m, q = h->q, mq = m * q;
+    init_x<<<std::max(1, std::min(h->nsm * 4, (int)((int64_t)m * q * h->n / 256 + 1))), 256>>>(h->n, m, q, h->ld,
+                                                                                                h->lo, h->hi, h->x);
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaMemset(h->s, 0, sizeof(double) * (size_t)q * h->ld));
+    CUDA_TRY(cudaMemset(h->mu, 0, sizeof(double) * (size_t)q * h->ld));
+    std::vector<double> sc(scal_size(m, q), 0.0);
+    for (int t = 0; t < 4; ++t) sc[5 * mq + m + t] = h->prm.rho[t];
+    sc[5 * mq + m + 4] = 1.0; // cold
+    sc[5 * mq + m + 5] = 1.0; // no pending mu rescale
+    CUDA_TRY(cudaMemcpy(h->scal, sc.data(), sizeof(double) * sc.size(), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaDeviceSynchronize());
+    return ADMM_OK;
+}
+
+} // namespace
+
+extern "C" {
+
+void admm_default_params(admm_params *p)
+{
+    if (!p) return;
+    std::memset(p, 0, sizeof *p);
+    for (int t = 0; t < 4; ++t) p->rho[t] = 1.0;
+    p->r_tol = 1e-6;
+    p->s_tol = 1e-6;
+    p->tau = 1.1;
+    p->max_iter = 5000;
+    p->check_every = 10;
+    p->precision = ADMM_FP64;
+    p->xmin_mode = ADMM_XMIN_EXACT;
+    p->sweep = ADMM_GAUSS_SEIDEL;
+    p->adapt_rho = 0;
+}
+
+const char *admm_last_error(void) { return g_err.c_str(); }
+
+const char *admm_status_string(admm_status s)
+{
+    switch (s) {
+    case ADMM_OK: return "ok";
+    case ADMM_EINVAL: return "invalid argument";
+    case ADMM_ENOMEM: return "out of memory";
+    case ADMM_ECUDA: return "CUDA error";
+    case ADMM_ETIMEOUT: return "device wait timed out";
+    case ADMM_ENOTCONVERGED: return "not converged";
+    case ADMM_EUNSUPPORTED: return "unsupported size or mode";
+    }
+    return "unknown status";
+}
+
+admm_status admm_create(const admm_problem *P, const admm_params *prm, admm_handle **out)
+{
+    g_err.clear();
+    if (!out) return fail(ADMM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!P) return fail(ADMM_EINVAL, "problem is NULL");
+    if (P->n < 1 || P->m < 1 || P->q < 1) return fail(ADMM_EINVAL, "n, m, q must be >= 1 (got %d, %d, %d)", P->n, P->m, P->q);
+    if (P->m > ADMM_MAX_M) return fail(ADMM_EUNSUPPORTED, "m = %d exceeds ADMM_MAX_M = %d", P->m, ADMM_MAX_M);
+    if ((int64_t)P->m * P->q > ADMM_MAX_PAIRS)
+        return fail(ADMM_EUNSUPPORTED, "m*q = %lld exceeds ADMM_MAX_PAIRS = %d", (long long)P->m * P->q, ADMM_MAX_PAIRS);
+    const double *arrs[] = {P->f2, P->f1, P->f0, P->g2, P->g1, P->g0, P->x_lo, P->x_hi, P->y, P->c};
+    for (const double *a : arrs)
+        if (!a) return fail(ADMM_EINVAL, "a problem array is NULL");
+    if (!params_ok(prm)) return g_err.find("precision") != std::string::npos ? ADMM_EUNSUPPORTED : ADMM_EINVAL;
+
+    admm_handle *h = new admm_handle();
+    h->n = P->n;
+    h->m = P->m;
+    h->q = P->q;
+    h->ld = (P->n + 31) / 32 * 32;
+    h->prm = *prm;
+    admm_status st = ADMM_OK;
+    auto bail = [&](admm_status s) {
+        free_all(h);
+        delete h;
+        return s;
+    };
+#define TRY(call)                                                                                          \
+    do {                                                                                                   \
+        cudaError_t e_ = (call);                                                                           \
+        if (e_ != cudaSuccess)                                                                             \
+            return bail(fail(e_ == cudaErrorMemoryAllocation ? ADMM_ENOMEM : ADMM_ECUDA, "%s: %s", #call,    \
+                             cudaGetErrorString(e_)));                                                     \
+    } while (0)
+    TRY(cudaGetDevice(&h->dev));
+    TRY(cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, h->dev));
+    const int n = h->n, m = h->m, q = h->q, ld = h->ld, mq = m * q;
+    const size_t ne = (size_t)mq * ld, nb = (size_t)m * ld, nc = (size_t)q * ld;
+    double **el[] = {&h->f2, &h->f1, &h->f0, &h->g2, &h->g1, &h->g0, &h->x};
+    for (double **p : el) {
+        TRY(cudaMalloc(p, ne * 8));
+        TRY(cudaMemset(*p, 0, ne * 8));
+    }
+    TRY(cudaMalloc(&h->lo, nb * 8));
+    TRY(cudaMalloc(&h->hi, nb * 8));
+    TRY(cudaMemset(h->lo, 0, nb * 8));
+    TRY(cudaMemset(h->hi, 0, nb * 8));
+    TRY(cudaMalloc(&h->y, nc * 8));
+    TRY(cudaMalloc(&h->s, nc * 8));
+    TRY(cudaMalloc(&h->mu, nc * 8));
+    TRY(cudaMemset(h->y, 0, nc * 8));
+    TRY(cudaMalloc(&h->c, m * 8));
+    TRY(cudaMalloc(&h->sumg0, mq * 8));
+    TRY(cudaMalloc(&h->scal, scal_size(m, q) * 8));
+    TRY(cudaMalloc(&h->info, kInfo * 8));
+    TRY(cudaMalloc(&h->bar, sizeof(unsigned)));
+    TRY(cudaMalloc(&h->flags, sizeof(unsigned)));
+    TRY(cudaMalloc(&h->status, sizeof(int)));
+    TRY(cudaMallocHost(&h->info_host, kInfo * 8));
+
+    const bool dev = P->on_device != 0;
+    TRY(put_rows(h->f2, ld, P->f2, n, mq, dev));
+    TRY(put_rows(h->f1, ld, P->f1, n, mq, dev));
+    TRY(put_rows(h->f0, ld, P->f0, n, mq, dev));
+    TRY(put_rows(h->g2, ld, P->g2, n, mq, dev));
+    TRY(put_rows(h->g1, ld, P->g1, n, mq, dev));
+    TRY(put_rows(h->g0, ld, P->g0, n, mq, dev));
+    TRY(put_rows(h->lo, ld, P->x_lo, n, m, dev));
+    TRY(put_rows(h->hi, ld, P->x_hi, n, m, dev));
+    TRY(put_rows(h->y, ld, P->y, n, q, dev));
+    TRY(cudaMemcpy(h->c, P->c, m * 8, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice));
+
+    // validation (Assumptions 1 and 3, bounds, sure infeasibility)
+    TRY(cudaMemset(h->flags, 0, sizeof(unsigned)));
+    validate_elements<<<std::max(1, std::min(h->nsm * 8, (int)(ne / 256 + 1))), 256>>>(
+        n, m, q, ld, h->f2, h->f1, h->f0, h->g2, h->g1, h->g0, h->lo, h->hi, h->y, h->flags);
+    TRY(cudaGetLastError());
+    pair_sums<<<mq, 256>>>(n, m, q, ld, h->g2, h->g1, h->g0, h->lo, h->hi, h->c, h->sumg0, h->flags);
+    TRY(cudaGetLastError());
+    unsigned flags = 0;
+    TRY(cudaMemcpy(&flags, h->flags, sizeof flags, cudaMemcpyDeviceToHost));
+    if (flags) {
+        std::string why;
+        if (flags & V_NONFINITE) why += " non-finite coefficient, bound or demand;";
+        if (flags & V_NONCONVEX) why += " f2 < 0 or g2 < 0 (Assumption 1 needs convex f, g);";
+        if (flags & V_BOUNDS) why += " x_lo > x_hi;";
+        if (flags & V_CNAN) why += " c is NaN;";
+        if (flags & V_INFEASIBLE) why += " sum_k min g > c for some (i, j): infeasible;";
+        return bail(fail(ADMM_EINVAL, "invalid problem:%s", why.c_str()));
+    }
+
+    // launch shape: contiguous equal column chunks, all SMs busy
+    h->smem = single_smem_bytes(m, q);
+    const int per_sm = single_blocks_per_sm(prm->precision, m, h->smem);
+    if (per_sm < 1) return bail(fail(ADMM_EUNSUPPORTED, "solve kernel cannot be resident (smem %zu B)", h->smem));
+    const int64_t ncols = (int64_t)q * n;
+    int64_t g = std::min<int64_t>((int64_t)h->nsm * per_sm, std::max<int64_t>(1, ncols / 32));
+    h->chunk = (ncols + g - 1) / g;
+    h->grid = (int)((ncols + h->chunk - 1) / h->chunk);
+    h->slots = 1;
+    for (int b = 0; b < h->grid; ++b) {
+        const int64_t c0 = (int64_t)b * h->chunk, c1 = std::min(c0 + h->chunk, ncols);
+        h->slots = std::max(h->slots, (int)((c1 - 1) / n - c0 / n + 1));
+    }
+    TRY(cudaMalloc(&h->part, sizeof(double) * 2 * (size_t)h->grid * h->slots * m * 4));
+    TRY(cudaMalloc(&h->cpart, sizeof(double) * 2 * (size_t)h->grid * 4));
+    st = reset_state(h);
+    if (st != ADMM_OK) return bail(st);
+#undef TRY
+    *out = h;
+    return ADMM_OK;
+}
+
+admm_status admm_set_params(admm_handle *h, const admm_params *prm)
+{
+    g_err.clear();
+    if (!h) return fail(ADMM_EINVAL, "handle is NULL");
+    if (!params_ok(prm)) return g_err.find("precision") != std::string::npos ? ADMM_EUNSUPPORTED : ADMM_EINVAL;
+    DeviceGuard dg(h->dev);
+    h->prm = *prm;
+    const int mq = h->m * h->q;
+    CUDA_TRY(cudaMemcpy(h->scal + 5 * mq + h->m, prm->rho, 4 * 8, cudaMemcpyHostToDevice));
+    return ADMM_OK;
+}
+
+admm_status admm_reset(admm_handle *h)
+{
+    g_err.clear();
+    if (!h) return fail(ADMM_EINVAL, "handle is NULL");
+    DeviceGuard dg(h->dev);
+    return reset_state(h);
+}
+
+static admm_status load_state(admm_handle *h, const admm_state *w, cudaStream_t st)
+{
+    const int n = h->n, m = h->m, q = h->q, mq = m * q, ld = h->ld;
+    const bool dev = w->on_device != 0;
+    const cudaMemcpyKind k = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (!w->x || !w->s || !w->mu || !w->lam || !w->zeta || !w->h || !w->p || !w->nu || !w->x1)
+        return fail(ADMM_EINVAL, "warm state has a NULL array");
+    for (int t = 0; t < 4; ++t)
+        if (!(w->rho[t] > 0.0)) return fail(ADMM_EINVAL, "warm state rho[%d] must be > 0", t);
+    CUDA_TRY(cudaMemcpy2DAsync(h->x, (size_t)ld * 8, w->x, (size_t)n * 8, (size_t)n * 8, (size_t)mq, k, st));
+    CUDA_TRY(cudaMemcpy2DAsync(h->s, (size_t)ld * 8, w->s, (size_t)n * 8, (size_t)n * 8, (size_t)q, k, st));
+    CUDA_TRY(cudaMemcpy2DAsync(h->mu, (size_t)ld * 8, w->mu, (size_t)n * 8, (size_t)n * 8, (size_t)q, k, st));
+    const double *pairs[5] = {w->lam, w->zeta, w->h, w->p, w->nu};
+    for (int t = 0; t < 5; ++t) CUDA_TRY(cudaMemcpyAsync(h->scal + (size_t)t * mq, pairs[t], mq * 8, k, st));
+    CUDA_TRY(cudaMemcpyAsync(h->scal + 5 * mq, w->x1, m * 8, k, st));
+    double tail[6] = {w->rho[0], w->rho[1], w->rho[2], w->rho[3], w->cold ? 1.0 : 0.0, 1.0};
+    CUDA_TRY(cudaMemcpy(h->scal + 5 * mq + m, tail, sizeof tail, cudaMemcpyHostToDevice));
+    return ADMM_OK;
+}
+
+admm_status admm_solve(admm_handle *h, const admm_state *warm, admm_result *out, void *stream)
+{
+    g_err.clear();
+    if (!h) return fail(ADMM_EINVAL, "handle is NULL");
+    DeviceGuard dg(h->dev);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (warm) {
+        admm_status s = load_state(h, warm, st);
+        if (s != ADMM_OK) return s;
+    }
+    SingleArgs a{};
+    a.n = h->n;
+    a.m = h->m;
+    a.q = h->q;
+    a.ld = h->ld;
+    a.ncols = (int64_t)h->q * h->n;
+    a.chunk = h->chunk;
+    a.slots = h->slots;
+    a.grid = h->grid;
+    a.f2 = h->f2;
+    a.f1 = h->f1;
+    a.f0 = h->f0;
+    a.g2 = h->g2;
+    a.g1 = h->g1;
+    a.g0 = h->g0;
+    a.lo = h->lo;
+    a.hi = h->hi;
+    a.y = h->y;
+    a.c = h->c;
+    a.sumg0 = h->sumg0;
+    a.x = h->x;
+    a.s = h->s;
+    a.mu = h->mu;
+    a.scal = h->scal;
+    a.part = h->part;
+    a.cpart = h->cpart;
+    a.bar = h->bar;
+    a.status = h->status;
+    a.info = h->info;
+    a.r_tol = h->prm.r_tol;
+    a.s_tol = h->prm.s_tol;
+    a.tau = h->prm.tau;
+    a.max_iter = h->prm.max_iter;
+    a.check_every = h->prm.check_every;
+    a.xmin_mode = h->prm.xmin_mode;
+    a.sweep = h->prm.sweep;
+    a.adapt = h->prm.adapt_rho;
+    a.spin_ns = spin_limit_ns();
+    CUDA_TRY(cudaMemsetAsync(h->bar, 0, sizeof(unsigned), st));
+    CUDA_TRY(cudaMemsetAsync(h->status, 0, sizeof(int), st));
+    CUDA_TRY(launch_single(h->prm.precision, a, h->smem, st));
+    CUDA_TRY(cudaMemcpyAsync(h->info_host, h->info, kInfo * 8, cudaMemcpyDeviceToHost, st));
+    if (out && out->x)
+        CUDA_TRY(get_rows(out->x, h->x, h->ld, h->n, (int64_t)h->m * h->q, out->on_device != 0, st));
+    if (out && out->x1)
+        CUDA_TRY(cudaMemcpyAsync(out->x1, h->scal + 5 * h->m * h->q, h->m * 8,
+                                 out->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    const double *inf = h->info_host;
+    admm_status s = ADMM_OK;
+    if (inf[12] != 0.0) s = (admm_status)(int)inf[12];
+    else if (inf[1] == 0.0) s = ADMM_ENOTCONVERGED;
+    if (out) {
+        out->iters = (int32_t)inf[0];
+        out->converged = inf[1] != 0.0;
+        out->r = inf[2];
+        out->sigma = inf[3];
+        out->objective = inf[11];
+        out->status = s;
+    }
+    if (s == ADMM_ETIMEOUT) return fail(s, "a grid barrier wait timed out");
+    if (s == ADMM_ENOTCONVERGED) g_err = "max_iter reached before the stop test passed";
+    return s;
+}
+
+admm_status admm_get_state(admm_handle *h, admm_state *o, void *stream)
+{
+    g_err.clear();
+    if (!h || !o) return fail(ADMM_EINVAL, "NULL argument");
+    DeviceGuard dg(h->dev);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int n = h->n, m = h->m, q = h->q, mq = m * q, ld = h->ld;
+    const bool dev = o->on_device != 0;
+    const cudaMemcpyKind k = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (o->x) CUDA_TRY(get_rows(o->x, h->x, ld, n, mq, dev, st));
+    if (o->s) CUDA_TRY(get_rows(o->s, h->s, ld, n, q, dev, st));
+    if (o->mu) CUDA_TRY(get_rows(o->mu, h->mu, ld, n, q, dev, st));
+    double *pairs[5] = {o->lam, o->zeta, o->h, o->p, o->nu};
+    for (int t = 0; t < 5; ++t)
+        if (pairs[t]) CUDA_TRY(cudaMemcpyAsync(pairs[t], h->scal + (size_t)t * mq, mq * 8, k, st));
+    if (o->x1) CUDA_TRY(cudaMemcpyAsync(o->x1, h->scal + 5 * mq, m * 8, k, st));
+    double tail[6];
+    CUDA_TRY(cudaMemcpyAsync(tail, h->scal + 5 * mq + m, sizeof tail, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    for (int t = 0; t < 4; ++t) o->rho[t] = tail[t];
+    o->cold = tail[4] != 0.0;
+    return ADMM_OK;
+}
+
+admm_status admm_destroy(admm_handle *h)
+{
+    if (!h) return ADMM_OK;
+    {
+        DeviceGuard dg(h->dev);
+        free_all(h);
+    }
+    delete h;
+    return ADMM_OK;
+}
+
+admm_status admm_selftest_barrier_timeout(long long spin_ns, int grid, int *status_out)
+{
+    g_err.clear();
+    if (!status_out || grid < 1 || grid > 64 || spin_ns <= 0 || spin_ns > 5000000000LL)
+        return fail(ADMM_EINVAL, "bad selftest arguments");
+    unsigned *bar = nullptr;
+    int *status = nullptr;
+    CUDA_TRY(cudaMalloc(&bar, sizeof(unsigned)));
+    cudaError_t e = cudaMalloc(&status, sizeof(int));
+    if (e != cudaSuccess) {
+        cudaFree(bar);
+        return fail(ADMM_ENOMEM, "cudaMalloc: %s", cudaGetErrorString(e));
+    }
+    cudaMemset(bar, 0, sizeof(unsigned));
+    cudaMemset(status, 0, sizeof(int));
+    void *args[] = {(void *)&bar, (void *)&status, (void *)&spin_ns, nullptr};
+    unsigned extra = 1;
+    args[3] = (void *)&extra;
+    e = cudaLaunchCooperativeKernel((void *)selftest_barrier_kernel, dim3(grid), dim3(32), args, 0, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    int sv = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&sv, status, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(bar);
+    cudaFree(status);
+    if (e != cudaSuccess) return fail(ADMM_ECUDA, "selftest: %s", cudaGetErrorString(e));
+    *status_out = sv;
+    return ADMM_OK;
+}
+
+} // extern "C"

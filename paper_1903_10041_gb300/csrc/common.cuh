@@ -1,0 +1,96 @@
+// Device helpers shared by the solver kernels: bounded grid barrier,
+// deterministic warp/block reductions, L2-coherent loads.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace admm_impl {
+
+__device__ __forceinline__ unsigned long long globaltimer_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ int ld_volatile_i32(const int *p)
+{
+    return *(const volatile int *)p;
+}
+
+// Loads that bypass L1: data written by other SMs since this SM last cached it.
+__device__ __forceinline__ double ldcg(const double *p) { return __ldcg(p); }
+
+// Grid-wide barrier for a cooperative launch.  `bar` counts arrivals and is
+// zeroed before the launch; barrier number b (1, 2, ...) waits for b * grid
+// arrivals.  The wait is bounded: after spin_ns nanoseconds it records
+// timeout_code in *status and returns false; it also returns false as soon
+// as another CTA has recorded an error.  Never traps.
+__device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned target, int *status,
+                                             long long spin_ns, int timeout_code)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(bar, 1u);
+        unsigned long long t0 = globaltimer_ns();
+        int ok = 1;
+        for (;;) {
+            unsigned v = ld_acquire_u32(bar);
+            if ((int)(v - target) >= 0)
+                break;
+            if (ld_volatile_i32(status) != 0) { ok = 0; break; }
+            if ((long long)(globaltimer_ns() - t0) > spin_ns) {
+                atomicCAS(status, 0, timeout_code);
+                ok = 0;
+                break;
+            }
+            __nanosleep(32);
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+template <class T> __device__ __forceinline__ T warp_sum(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+template <class T> __device__ __forceinline__ T warp_max(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+template <class T> __device__ __forceinline__ T warp_min(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+__device__ __forceinline__ double clampd(double v, double lo, double hi)
+{
+    return v < lo ? lo : (v > hi ? hi : v);
+}
+__device__ __forceinline__ float clampf(float v, float lo, float hi)
+{
+    return v < lo ? lo : (v > hi ? hi : v);
+}
+
+} // namespace admm_impl

@@ -1,0 +1,56 @@
+// Internal declarations shared by the host C ABI and the kernel translation
+// units.  Not part of the public interface.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/admm.h"
+
+namespace admm_impl {
+
+constexpr int kBlock = 256;          // threads per CTA of the solve kernels
+constexpr int kWarps = kBlock / 32;
+constexpr int kMaxM = ADMM_MAX_M;
+constexpr int kInfo = 16;            // doubles of the per-solve info record
+
+// Offsets into the scalar state vector (doubles), for mq = m*q pairs:
+//   [0, 5mq)        lam, zeta, h, p, nu   (pair arrays, mq each)
+//   [5mq, 5mq+m)    x1
+//   [5mq+m, +4)     rho_1..rho_4
+//   [5mq+m+4]       cold flag (1.0 = zero start, z = 0)
+//   [5mq+m+5]       pending mu divisor (1.0 = none)
+inline __host__ __device__ int scal_size(int m, int q) { return 5 * m * q + m + 6; }
+
+// info record written by a solve:
+//   0 iters, 1 converged, 2 r, 3 sigma, 4..7 r terms, 8..10 sigma terms,
+//   11 objective, 12 status
+struct SingleArgs {
+    int n, m, q, ld;           // ld: padded row stride of the [*][n] arrays
+    int64_t ncols;             // q * n columns (j, k)
+    int64_t chunk;             // columns per CTA (contiguous in j-major order)
+    int slots;                 // partial-record slots per CTA (rows a chunk can touch)
+    int grid;                  // CTAs
+    const void *f2, *f1, *f0, *g2, *g1, *g0, *lo, *hi, *y;   // storage type of the precision
+    const double *c, *sumg0;   // [m], [mq]
+    void *x, *s, *mu;          // state arrays (storage type)
+    double *scal;              // scalar state, in/out
+    double *part;              // [2][grid][slots][m][4] partial records (gsum, dmax, dmin, x0)
+    double *cpart;             // [2][grid][4] per-CTA column maxima and objective partials
+    unsigned *bar;             // barrier counter (zeroed before the launch)
+    int *status;               // 0 or an admm_status set by a device wait
+    double *info;              // out [kInfo]
+    double r_tol, s_tol, tau;
+    int max_iter, check_every, xmin_mode, sweep, adapt;
+    long long spin_ns;         // bound of one barrier wait
+};
+
+// Launch the persistent single-instance solve kernel (cooperative launch).
+cudaError_t launch_single(int precision, const SingleArgs &a, size_t smem, cudaStream_t st);
+// Max co-resident CTAs per SM of that kernel for the given dynamic smem.
+int single_blocks_per_sm(int precision, int m, size_t smem);
+// Dynamic shared memory the single-instance kernel needs.
+size_t single_smem_bytes(int m, int q);
+// Index of the kernel variant used for m sources (template bound).
+int single_mbound(int m);
+
+} // namespace admm_impl

@@ -1,0 +1,70 @@
+// Quartic minimiser in FP64: Algorithm 1 (Sec. III-B) and the projection of
+// step (a) of the ADMM iteration (App. A).
+//
+// minimise A x^4 + B x^3 + C x^2 + D x over [lo, hi], A >= 0 (A = 0 needs C > 0).
+// The extrema solve the monic cubic x^3 + b x^2 + c x + d with
+// b = 3B/4A, c = C/2A, d = D/4A, classified by Q = c/3 - b^2/9,
+// R = bc/6 - b^3/27 - d/2, Delta = Q^3 + R^2:
+//   Delta > 0   one real root, Cardano: S + T - b/3 (stable pair: S from
+//               R + sgn(R) sqrt(Delta), T = -Q/S, equal to the printed S, T);
+//   Q = R = 0   triple root -b/3 (Vieta);
+//   otherwise   three real roots 2 sqrt(-Q) cos((theta + 2 pi l)/3) - b/3 with
+//               theta = acos(R / sqrt(-Q^3)).  For theta in [0, pi] the l = 1
+//               root is the smallest and the l = 0 root the largest, so no
+//               sort is needed; one sincos of theta/3 gives both, since
+//               cos(t + 2pi/3) = -cos(t)/2 - (sqrt(3)/2) sin(t).
+// The middle root is a maximiser.  The minimiser is the root with the lower
+// value of F(x) = x^4/4 + (b/3) x^3 + (c/2) x^2 + d x (delta-f of Algorithm 1;
+// F is the quartic divided by 4A).  Exact mode clamps both candidate roots
+// to [lo, hi] before comparing (the constrained minimiser is always one of
+// the two clamped roots); paper mode clamps the winner (Pi(argmin)).
+// A tie keeps the smaller root, as Algorithm 1's else branch does.
+#pragma once
+#include "common.cuh"
+
+namespace admm_impl {
+
+__device__ __forceinline__ double delta_f64(double u, double v, double b, double c, double d)
+{
+    double u2 = u * u, v2 = v * v;
+    return 0.25 * (u2 * u2 - v2 * v2) + (b * (1.0 / 3.0)) * (u2 * u - v2 * v) + (0.5 * c) * (u2 - v2) + d * (u - v);
+}
+
+// Returns the minimiser; *branch (if non-null) gets 0 Cardano, 1 triple,
+// 2 trig, 3 quadratic.
+__device__ __forceinline__ double quartic_min64(double A, double B, double C, double D, double lo,
+                                                double hi, int paper_mode)
+{
+    if (A == 0.0)
+        return clampd(-D / (2.0 * C), lo, hi);
+    double inv = 1.0 / A;
+    double b = 0.75 * B * inv, c = 0.5 * C * inv, d = 0.25 * D * inv;
+    double b3 = b * (1.0 / 3.0);
+    double Q = c * (1.0 / 3.0) - b3 * b3;
+    double R = b3 * (0.5 * c) - b3 * b3 * b3 - 0.5 * d;
+    double Q3 = Q * Q * Q;
+    double Dl = Q3 + R * R;
+    if (Dl > 0.0) {
+        double sq = sqrt(Dl);
+        double S = cbrt(R >= 0.0 ? R + sq : R - sq);
+        double T = -Q / S;
+        return clampd(S + T - b3, lo, hi);
+    }
+    if (Q == 0.0 && R == 0.0)
+        return clampd(-b3, lo, hi);
+    double arg = clampd(R * rsqrt(-Q3), -1.0, 1.0);
+    double t = acos(arg) * (1.0 / 3.0);
+    double st, ct;
+    sincos(t, &st, &ct);
+    double two_sq = 2.0 * sqrt(-Q);
+    double x3 = two_sq * ct - b3;                                        // largest root
+    double x1 = two_sq * (-0.5 * ct - 0.86602540378443864676 * st) - b3; // smallest root
+    if (paper_mode) {
+        double xs = delta_f64(x1, x3, b, c, d) > 0.0 ? x3 : x1;
+        return clampd(xs, lo, hi);
+    }
+    double u = clampd(x1, lo, hi), v = clampd(x3, lo, hi);
+    return delta_f64(u, v, b, c, d) > 0.0 ? v : u;
+}
+
+} // namespace admm_impl

@@ -1,0 +1,57 @@
+"""The C-ABI library builds, loads and exports every function that
+include/*.h declares.  CPU only: no compute call is made."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for hdr in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        txt = open(hdr).read()
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(admm_\w+)\s*\(", txt, flags=re.M):
+            names.add(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1903_10041_gb300 import build
+    return ctypes.CDLL(build.build())
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for want in ("admm_create", "admm_solve", "admm_destroy", "admm_get_state", "admm_set_params",
+                 "admm_default_params", "admm_last_error"):
+        assert want in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in sorted(_declared()) if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_host_only_calls_work_without_a_gpu():
+    from paper_1903_10041_gb300 import capi
+    p = capi.admm_default_params()
+    assert p.max_iter == 5000 and p.check_every == 10 and abs(p.tau - 1.1) < 1e-15
+    assert list(p.rho) == [1.0, 1.0, 1.0, 1.0]
+    # NULL handle and NULL arguments are rejected without touching the device
+    assert capi._lib.admm_solve(None, None, None, None) == capi.ADMM_EINVAL
+    assert capi._lib.admm_destroy(None) == capi.ADMM_OK
+    assert capi._lib.admm_create(None, None, None) == capi.ADMM_EINVAL
+
+
+def test_struct_layouts_match_the_header(lib):
+    """ctypes mirrors of the C structs have the sizes the header implies."""
+    from paper_1903_10041_gb300 import capi
+    assert ctypes.sizeof(capi.admm_params) == 8 * 7 + 4 * 6 + 4 * 4
+    assert ctypes.sizeof(capi.admm_problem) == 16 + 8 * 10 + 8
+    assert ctypes.sizeof(capi.admm_state) == 8 * 9 + 8 * 4 + 8

@@ -1,0 +1,227 @@
+"""GPU (FP64 mode) vs the FP64 oracle on the same seeded inputs, through the
+C ABI.  Tolerance 1e-9 relative: max |gpu - oracle| / max(1, max |oracle|).
+
+Both sides run the same number of iterations (fixed T, stop thresholds 0)
+or to convergence with the same check interval, from the zero start."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1903_10041_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-9
+
+
+@pytest.fixture(scope="module")
+def capi():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1903_10041_gb300 import build
+    build.build()
+    from paper_1903_10041_gb300 import capi
+    return capi
+
+
+def rel(a, b):
+    a, b = np.asarray(a, float), np.asarray(b, float)
+    return float(np.abs(a - b).max() / max(1.0, np.abs(b).max()))
+
+
+def double_well(n, m, q, seed):
+    """Quartics with two local minima (trig branch of Algorithm 1):
+    large g2 and g1 of both signs so that (theta - g(x))^2 has two wells."""
+    P = W.random_problem(n, m, q, seed=seed)
+    u = W.uniform(seed, (901,), m * q * n).reshape(m, q, n)
+    v = W.uniform(seed, (902,), m * q * n).reshape(m, q, n)
+    P.g2 = 0.5 + 2.5 * u
+    P.g1 = -2.0 + 4.0 * v
+    P.g0 = np.full((m, q, n), -0.5)
+    P.c = np.full(m, np.inf)
+    return P
+
+
+def run_both(capi, oracle, P, par, threads=8):
+    st_o, rep_o = oracle.solve(P, par, threads=threads)
+    with capi.Solver(P, par) as s:
+        res = s.solve(raise_on=(1, 2, 3, 4, 6))
+        st_g = s.state()
+    return st_o, rep_o, st_g, res
+
+
+def compare_states(P, st_o, rep_o, st_g, res, tol=TOL, check_res=True):
+    errs = {
+        "x": rel(st_g["x"], st_o["x"]),
+        "s": rel(st_g["s"], st_o["s"]),
+        "mu": rel(st_g["mu"], st_o["mu"]),
+        "h": rel(st_g["h"], st_o["h"]),
+        "p": rel(st_g["p"], st_o["p"]),
+        "nu": rel(st_g["nu"], st_o["nu"]),
+        "x1": rel(st_g["x1"], st_o["x1"]),
+        "lam": rel(st_g["lam"], st_o["lam"][:, :, 0]),
+    }
+    gx = P.g2 * st_g["x"] ** 2 + P.g1 * st_g["x"] + P.g0
+    errs["z"] = rel(gx + st_g["zeta"][:, :, None], st_o["z"])
+    if check_res:
+        errs["r"] = abs(res["r"] - rep_o["r"]) / max(1.0, abs(rep_o["r"]))
+        errs["sigma"] = abs(res["sigma"] - rep_o["sigma"]) / max(1.0, abs(rep_o["sigma"]))
+    bad = {k: v for k, v in errs.items() if not v <= tol}
+    assert not bad, (bad, errs)
+    return errs
+
+
+@pytest.mark.parametrize("T", [1, 10, 100, 1000])
+def test_config0_fixed_iterations(capi, oracle_lib, T):
+    P = W.config(0)
+    par = W.Params(max_iter=T, r_tol=0.0, s_tol=0.0)
+    st_o, rep_o, st_g, res = run_both(capi, oracle_lib, P, par)
+    assert res["iters"] == T == rep_o["iters"]
+    compare_states(P, st_o, rep_o, st_g, res)
+
+
+def test_config0_to_convergence(capi, oracle_lib):
+    P = W.config(0)
+    par = W.Params()
+    st_o, rep_o, st_g, res = run_both(capi, oracle_lib, P, par)
+    assert rep_o["converged"] and res["converged"] and res["status"] == 0
+    assert res["iters"] == rep_o["iters"]
+    compare_states(P, st_o, rep_o, st_g, res)
+    assert abs(res["objective"] - oracle_lib.objective(P, st_o["x"])) <= TOL * max(1, abs(res["objective"]))
+
+
+@pytest.mark.parametrize("n,m,q,T", [
+    (37, 1, 1, 50),       # m = 1, ragged n
+    (250, 3, 7, 60),      # chunks end mid-row, q > 1
+    (1000, 4, 5, 40),     # many CTAs, m = 4
+    (97, 5, 3, 40),       # m between template bounds
+    (33, 8, 2, 40),       # m at its maximum
+    (4099, 2, 3, 30),     # long rows, ragged tail
+])
+def test_shapes_fixed_iterations(capi, oracle_lib, n, m, q, T):
+    P = W.random_problem(n, m, q, seed=100 + n + m + q)
+    par = W.Params(rho=(1.0, 1.0 / n, 1.0, 1.0), max_iter=T, r_tol=0.0, s_tol=0.0, check_every=7)
+    st_o, rep_o, st_g, res = run_both(capi, oracle_lib, P, par)
+    compare_states(P, st_o, rep_o, st_g, res)
+
+
+@pytest.mark.parametrize("mode", ["exact", "paper"])
+@pytest.mark.parametrize("sweep", ["gauss_seidel", "jacobi"])
+def test_double_well_trig_branch(capi, oracle_lib, mode, sweep):
+    P = double_well(64, 3, 4, seed=7)
+    par = W.Params(max_iter=25, r_tol=0.0, s_tol=0.0, xmin_mode=mode, sweep=sweep, check_every=5)
+    st_o, rep_o = oracle_lib.solve(P, par, threads=8)
+    assert rep_o["branch_count"][2] > 1000, rep_o["branch_count"]   # the trig branch is exercised
+    with capi.Solver(P, par) as s:
+        res = s.solve(raise_on=(1, 2, 3, 4, 6))
+        st_g = s.state()
+    compare_states(P, st_o, rep_o, st_g, res, tol=1e-8)
+
+
+def test_phev_shape_with_infinite_capacity(capi, oracle_lib):
+    P = W.phev_problem(n=300, q=8)
+    par = W.Params(rho=(1.0, 1.0 / 300, 1.0, 1.0), max_iter=200, r_tol=0.0, s_tol=0.0)
+    st_o, rep_o, st_g, res = run_both(capi, oracle_lib, P, par)
+    compare_states(P, st_o, rep_o, st_g, res)
+
+
+def test_adaptive_rho_matches(capi, oracle_lib):
+    P = W.random_problem(120, 3, 4, seed=31)
+    par = W.Params(rho=(1.0, 1.0 / 120, 1.0, 1.0), adapt_rho=True)
+    st_o, rep_o, st_g, res = run_both(capi, oracle_lib, P, par)
+    assert rep_o["converged"] and res["converged"]
+    assert res["iters"] == rep_o["iters"]
+    assert np.allclose(st_g["rho"], rep_o["rho"], rtol=1e-12, atol=0)
+    compare_states(P, st_o, rep_o, st_g, res)
+
+
+def test_config1_full_size_to_convergence(capi, oracle_lib):
+    """PHEV-shaped config at full size (n = 1000, q = 50) in the launch shape
+    the benchmark times."""
+    P = W.config(1)
+    par = W.Params(rho=(1.0, 1.0 / P.n, 1.0, 1.0))
+    st_o, rep_o, st_g, res = run_both(capi, oracle_lib, P, par, threads=16)
+    assert rep_o["converged"] and res["converged"]
+    assert res["iters"] == rep_o["iters"]
+    compare_states(P, st_o, rep_o, st_g, res)
+
+
+def test_checkpoint_resume_is_bitwise(capi):
+    """T1 iterations, export the state, resume for T2 == T1 + T2 straight."""
+    P = W.random_problem(300, 3, 4, seed=41)
+    par = W.Params(rho=(1.0, 1.0 / 300, 1.0, 1.0), r_tol=0.0, s_tol=0.0, check_every=5)
+    with capi.Solver(P, par.replace(max_iter=70)) as s:
+        s.solve(raise_on=(1, 2, 3, 4, 6))
+        straight = s.state()
+    with capi.Solver(P, par.replace(max_iter=30)) as s:
+        s.solve(raise_on=(1, 2, 3, 4, 6))
+        ck = s.state()
+    with capi.Solver(P, par.replace(max_iter=40)) as s:
+        s.solve(warm=ck, raise_on=(1, 2, 3, 4, 6))
+        resumed = s.state()
+    for k in ("x", "s", "mu", "lam", "zeta", "h", "p", "nu", "x1"):
+        assert np.array_equal(straight[k], resumed[k]), k
+
+
+def test_device_resident_inputs_and_outputs(capi, oracle_lib):
+    import torch
+    P = W.random_problem(500, 2, 3, seed=51)
+    par = W.Params(rho=(1.0, 1.0 / 500, 1.0, 1.0), max_iter=50, r_tol=0.0, s_tol=0.0)
+    D = P.copy()
+    for k, v in P.arrays().items():
+        setattr(D, k, torch.from_numpy(np.ascontiguousarray(v)).cuda())
+    x_out = torch.empty((P.m, P.q, P.n), dtype=torch.float64, device="cuda")
+    x1_out = torch.empty(P.m, dtype=torch.float64, device="cuda")
+    with capi.Solver(D, par) as s:
+        s.solve(x_out=x_out, x1_out=x1_out, stream=torch.cuda.current_stream(),
+                raise_on=(1, 2, 3, 4, 6))
+    st_o, _ = oracle_lib.solve(P, par, threads=8)
+    assert rel(x_out.cpu().numpy(), st_o["x"]) <= TOL
+    assert rel(x1_out.cpu().numpy(), st_o["x1"]) <= TOL
+
+
+@pytest.mark.parametrize("break_it,code", [
+    (lambda P: P.f2.__setitem__((0, 0, 3), -1.0), 1),
+    (lambda P: P.g2.__setitem__((1, 0, 0), -0.5), 1),
+    (lambda P: P.lo.__setitem__((0, 5), 3.0), 1),
+    (lambda P: P.y.__setitem__((0, 2), np.nan), 1),
+    (lambda P: P.c.__setitem__(0, -1e6), 1),
+    (lambda P: P.c.__setitem__(1, np.nan), 1),
+])
+def test_invalid_problems_are_rejected(capi, break_it, code):
+    P = W.random_problem(20, 2, 1, seed=61)
+    break_it(P)
+    with pytest.raises(capi.AdmmError) as e:
+        capi.admm_create(P, W.Params())
+    assert e.value.status == code
+
+
+def test_unsupported_sizes_are_rejected(capi):
+    P = W.random_problem(10, 9, 1, seed=62)
+    with pytest.raises(capi.AdmmError) as e:
+        capi.admm_create(P, W.Params())
+    assert e.value.status == capi.ADMM_EUNSUPPORTED
+    P = W.random_problem(4, 2, 600, seed=63)
+    with pytest.raises(capi.AdmmError) as e:
+        capi.admm_create(P, W.Params())
+    assert e.value.status == capi.ADMM_EUNSUPPORTED
+
+
+def test_not_converged_status_still_fills_the_result(capi):
+    P = W.config(0)
+    with capi.Solver(P, W.Params(max_iter=20)) as s:
+        res = s.solve()
+    assert res["status"] == capi.ADMM_ENOTCONVERGED and res["iters"] == 20
+    assert math.isfinite(res["objective"]) and math.isfinite(res["r"])
+
+
+def test_barrier_wait_times_out_and_device_stays_usable(capi, oracle_lib):
+    """A grid barrier that waits for an arrival that never comes gives up
+    after its bound and reports ETIMEOUT; the next solve still works."""
+    assert capi.admm_selftest_barrier_timeout(spin_ns=20_000_000, grid=4) == capi.ADMM_ETIMEOUT
+    P = W.config(0)
+    par = W.Params(max_iter=10, r_tol=0.0, s_tol=0.0)
+    st_o, rep_o, st_g, res = run_both(capi, oracle_lib, P, par)
+    compare_states(P, st_o, rep_o, st_g, res)
