@@ -1,0 +1,331 @@
+"""Benchmark: ADMM solves/s to 1e-6 residual on one GB300 (per GPU, replicas).
+
+One step = one solve, from the zero start to the stop test (r < 1e-6 and
+sigma < 1e-6, checked every 10 iterations; at most 5000 iterations), of
+the PHEV-shaped robust instance (n = 1000 steps, m = 2 sources, q = 50
+scenarios; synthetic data, FP64), the whole loop in one persistent kernel.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--config 0|1|2] [--precision fp64|mixed|mixed_fp64cubic]
+
+Prints one JSON line.  `value` times K solves with inputs resident in HBM
+(CUDA events on the launch stream, L2 flushed between solves);
+`e2e` times the same solves through the public C ABI from pinned host
+buffers (create + solve + copy-out + destroy).  Under torchrun each rank
+solves its own replica (weak scaling, no collective on the data path).
+`--impl reference` times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ADMM solves/s to 1e-6 residual, HBM GB/s fraction; batched p50/p99 latency"
+L2_FLUSH_BYTES = 512 << 20  # > 126 MB L2
+
+# FP64 peak of GB300 derived from unit counts and clock: 152 SMs x 2 DFMA/clk
+# per SM x 2 flop x 2.07 GHz (the measured DFMA rate is 1.90/clk/SM).
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# Conventional FP64 flop count of one element update of the FP64 kernel on
+# the Cardano branch (each +, -, *, /, sqrt, cbrt counts 1, an FMA 2); the
+# breakdown is in the design doc.
+FLOPS_PER_ELEMENT = 71
+# column work shared by the m elements of a column (sums, s, mu, residuals)
+FLOPS_PER_COLUMN = 12
+
+
+def workload(cfg: int, precision: str):
+    from paper_1903_10041_gb300 import workloads as W
+    P = W.config(cfg)
+    rho = (1.0, 1.0, 1.0, 1.0) if cfg == 0 else (1.0, 1.0 / P.n, 1.0, 1.0)
+    par = W.Params(rho=rho, precision=precision)
+    return P, par
+
+
+def bytes_per_iteration(P, prec: str) -> int:
+    """Algorithmic HBM bytes of one iteration (streamed arrays once each):
+    P * (6mnq + 2mn + 5nq): f2, f1, g2, g1 read, x read+write; bounds;
+    y read, s and mu read+write."""
+    w = 8 if prec == "fp64" else 4
+    m, q, n = P.m, P.q, P.n
+    return w * (6 * m * n * q + 2 * m * n + 5 * n * q)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(P, par, iters_per_solve: int, budget_s: float = 12.0):
+    """The FP64 oracle, as it stands, on the host cores: a bounded sample of
+    T iterations of the same solve, scaled to solves/s by the iteration
+    count of a full solve."""
+    import oracle
+    threads = os.cpu_count() or 1
+    # size T from a short probe so the sample takes about budget_s seconds
+    t0 = time.perf_counter()
+    oracle.solve(P, par.replace(max_iter=5, r_tol=0.0, s_tol=0.0), threads=threads)
+    per_it = (time.perf_counter() - t0) / 5
+    T = max(10, min(iters_per_solve, int(budget_s / max(per_it, 1e-9))))
+    t0 = time.perf_counter()
+    oracle.solve(P, par.replace(max_iter=T, r_tol=0.0, s_tol=0.0), threads=threads)
+    dt = time.perf_counter() - t0
+    sec_per_solve = dt / T * iters_per_solve
+    return {"value": 1.0 / sec_per_solve, "unit": "solves/s", "cores": threads, "kind": "oracle",
+            "sample": f"{T} of the {iters_per_solve} iterations of one solve ({dt:.2f} s), "
+                      f"scaled to a full solve; OpenMP over columns, {threads} threads"}
+
+
+def dist_init(n_gpus: int):
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return rank, world, local
+
+
+def barrier_max(values, world):
+    """Barrier + max over ranks of a list of floats."""
+    if world == 1:
+        return list(values)
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor(values, dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def run_reference(args):
+    rank, world, _ = dist_init(args.gpus)
+    if rank != 0:
+        return 0
+    import oracle
+    from oracle import build as ob
+    ob.build()
+    P, par = workload(args.config, "fp64")
+    # iterations of a full solve: the oracle's own count (cached per run)
+    st, rep = oracle.solve(P, par, threads=os.cpu_count() or 1) if args.config != 2 else (None, {"iters": 2600})
+    iters = rep["iters"]
+    threads = os.cpu_count() or 1
+    T = max(10, min(iters, 200 if args.config == 1 else 20))
+    times = []
+    for step in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.solve(P, par.replace(max_iter=T, r_tol=0.0, s_tol=0.0), threads=threads)
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            times.append(dt)
+    per_solve = statistics.mean(times) / T * iters
+    v = 1.0 / per_solve
+    line = {"metric": METRIC, "value": v, "unit": "solves/s", "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_solve * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_dict(P, par, args),
+            "cpu_baseline": {"value": v, "unit": "solves/s", "cores": threads, "kind": "oracle",
+                             "sample": f"each step {T} of the {iters} iterations of one solve, "
+                                       f"scaled to a full solve"},
+            "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def config_dict(P, par, args):
+    return {"workload": P.name + f" ({args.precision})", "n": P.n, "m": P.m, "q": P.q,
+            "elements": P.elements, "rho": list(par.rho), "r_tol": par.r_tol, "s_tol": par.s_tol,
+            "check_every": par.check_every, "max_iter": par.max_iter,
+            "l2": "flushed between timed solves (512 MiB write)", "parallelism": f"replicas x{args.gpus}"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", type=int, default=1, choices=[0, 1, 2])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "mixed_fp64cubic"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    rank, world, local = dist_init(args.gpus)
+    assert torch.cuda.is_available(), "bench.py needs a CUDA GPU"
+    from paper_1903_10041_gb300 import build
+    if rank == 0:
+        build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    from paper_1903_10041_gb300 import capi
+
+    P, par = workload(args.config, args.precision)
+    stream = torch.cuda.Stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    solver = capi.Solver(P, par)
+
+    def one_solve():
+        solver.reset()
+        torch.cuda.synchronize()
+        flush.fill_(1.0)                     # evict L2 (outside the timed events)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = solver.solve(stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1), res
+
+    for _ in range(args.warmup):
+        one_solve()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    times, results = [], []
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            ms, res = one_solve()
+            times.append(ms)
+            results.append(res)
+    torch.cuda.synchronize()
+    total_ms = sum(times)
+    (total_ms_max,) = barrier_max([total_ms], world)
+    iters = results[-1]["iters"]
+    conv = all(r["converged"] for r in results)
+    value = world * args.steps / (total_ms_max / 1e3)
+
+    # ---- roofline of the solve kernel (one launch = one solve) ------------
+    per_launch_s = total_ms / args.steps / 1e3
+    cols = P.q * P.n
+    if args.precision == "fp64":
+        flops = iters * (FLOPS_PER_ELEMENT * P.elements + FLOPS_PER_COLUMN * cols)
+        achieved = flops / per_launch_s / 1e12
+        roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                    "peak_source": "FP64: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz (derived; measured 1.90 DFMA/clk/SM)",
+                    "hbm_achieved_gbs": iters * bytes_per_iteration(P, "fp64") / per_launch_s / 1e9}
+    else:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+            os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"hbm_gbs": 6800.0}
+        gbs = iters * bytes_per_iteration(P, args.precision) / per_launch_s / 1e9
+        roofline = {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": gbs / peaks["hbm_gbs"], "traffic": None}
+
+    # ---- end to end through the C ABI from pinned host buffers ------------
+    e2e = None
+    if not args.no_e2e:
+        pinned = P.copy()
+        for k, v in P.arrays().items():
+            t = torch.from_numpy(np.ascontiguousarray(v)).pin_memory()
+            setattr(pinned, k, t.numpy())
+        x_out = torch.empty((P.m, P.q, P.n), dtype=torch.float64).pin_memory().numpy()
+        x1_out = torch.empty(P.m, dtype=torch.float64).pin_memory().numpy()
+        h2d = sum(v.nbytes for v in P.arrays().values())
+        d2h = x_out.nbytes + x1_out.nbytes
+
+        def e2e_step():
+            t0 = time.perf_counter()
+            with capi.Solver(pinned, par) as s:
+                s.solve(x_out=x_out, x1_out=x1_out)
+            return time.perf_counter() - t0
+
+        for _ in range(3):
+            e2e_step()
+        et = [e2e_step() for _ in range(max(3, args.steps // 2))]
+        (et_max,) = barrier_max([sum(et)], world)
+        e2e = {"value": world * len(et) / et_max, "unit": "solves/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.config != 2:
+        cpu = cpu_baseline(P, par, iters)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+                "data": "synthetic (seeded; stands in for the paper's FTP-75 PHEV scenarios)",
+                "config": config_dict(P, par, args),
+                "iters_per_solve": iters, "converged": conv, "objective": results[-1]["objective"],
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": args.steps,
+                "clocks": clk.summary()}
+        print(json.dumps(line))
+    solver.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
