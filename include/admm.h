@@ -165,6 +165,31 @@ admm_status admm_destroy(admm_handle *h);
  * path of the bounded device waits without faulting the GPU. */
 admm_status admm_selftest_barrier_timeout(long long spin_ns, int grid, int *status_out);
 
+/* Solve without any allocation, for callers that cannot allocate device
+ * memory: code in host callbacks or real-time control loops where an
+ * allocation may block or fail, controllers with a memory budget fixed at
+ * start-up, and plugins whose host application owns every allocation.  The
+ * paper has no counterpart; this is a deployment variant of admm_solve.
+ *
+ * The caller passes everything: `prob` and `state` hold device pointers in
+ * the dense layout above (on_device = 1 for both).  `state` is in/out: the
+ * solve starts from it (state->cold = 1 starts from zero: x is set to
+ * clamp(0) and every other array to 0, ignoring their contents) and leaves
+ * the final state in it, including rho and cold.  `out` may be NULL.
+ * The solver's scratch lives in a fixed 4 MiB device array inside the
+ * library, which every GPU that loads the library holds until exit.  The
+ * first call on each device looks up that array's address; make it before
+ * any stream capture.  Calls share the array and it keeps the last call's
+ * contents; each call clears what must start at zero, and calls that overlap
+ * on the GPU race on it, so the caller must serialise them.  Instances
+ * whose scratch would exceed the array are rejected with
+ * ADMM_EUNSUPPORTED (a few thousand CTA-row segments; the n = 1000, q = 50
+ * and n = 1e5, m = 4, q = 20 instances need under 100 KiB).  Only
+ * ADMM_FP64 is available.  Returns as admm_solve, after the stream has
+ * finished.  No cudaMalloc, cudaFree or other allocating call is made. */
+admm_status admm_solve_noalloc(const admm_problem *prob, const admm_params *params, admm_state *state,
+                               admm_result *out, void *stream);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char *admm_last_error(void);
 const char *admm_status_string(admm_status s);

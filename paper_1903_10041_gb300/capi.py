@@ -286,3 +286,34 @@ class Solver:
 
     def __exit__(self, *a):
         self.close()
+
+
+_lib.admm_solve_noalloc.argtypes = [C.POINTER(admm_problem), C.POINTER(admm_params), C.POINTER(admm_state),
+                                    C.POINTER(admm_result), C.c_void_p]
+_lib.admm_solve_noalloc.restype = C.c_int
+
+
+def admm_solve_noalloc(prob_dev, par, state_dev: dict, x_out=None, x1_out=None, stream=None,
+                       raise_on=(ADMM_EINVAL, ADMM_ENOMEM, ADMM_ECUDA, ADMM_ETIMEOUT, ADMM_EUNSUPPORTED)) -> dict:
+    """The allocation-free solve: ``prob_dev`` and ``state_dev`` hold torch
+    CUDA tensors (float64, contiguous); ``state_dev`` is updated in place
+    (its "rho" and "cold" entries too).  See admm_solve_noalloc in admm.h."""
+    keep: list = []
+    cp = make_problem(prob_dev, keep)
+    pp = par if isinstance(par, admm_params) else make_params(par)
+    cs = _state_struct(state_dev, keep)
+    res = admm_result()
+    if x_out is not None or x1_out is not None:
+        px, dx = _ptr(x_out, keep)
+        p1, d1 = _ptr(x1_out, keep)
+        res.x, res.x1, res.on_device = px, p1, int(bool(dx or d1))
+    sp = None
+    if stream is not None:
+        sp = C.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
+    st = _lib.admm_solve_noalloc(C.byref(cp), C.byref(pp), C.byref(cs), C.byref(res), sp)
+    if st in raise_on:
+        raise AdmmError(st, admm_last_error())
+    state_dev["rho"] = [cs.rho[t] for t in range(4)]
+    state_dev["cold"] = bool(cs.cold)
+    return {"status": st, "iters": res.iters, "converged": bool(res.converged), "objective": res.objective,
+            "r": res.r, "sigma": res.sigma}

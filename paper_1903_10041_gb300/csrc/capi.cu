@@ -154,6 +154,11 @@ long long spin_limit_ns()
 
 } // namespace
 
+namespace admm_impl {
+void set_last_error(const char *msg) { g_err = msg; }
+void clear_last_error() { g_err.clear(); }
+} // namespace admm_impl
+
 struct admm_handle {
     int n = 0, m = 0, q = 0, ld = 0, dev = 0, nsm = 0;
     admm_params prm{};

@@ -52,5 +52,8 @@ int single_blocks_per_sm(int precision, int m, size_t smem);
 size_t single_smem_bytes(int m, int q);
 // Index of the kernel variant used for m sources (template bound).
 int single_mbound(int m);
+// Thread-local message returned by admm_last_error().
+void set_last_error(const char *msg);
+void clear_last_error();
 
 } // namespace admm_impl
