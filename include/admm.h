@@ -154,6 +154,13 @@ admm_status admm_reset(admm_handle *h);
  * out->on_device says; NULL array pointers are skipped).  Synchronous. */
 admm_status admm_get_state(admm_handle *h, admm_state *out, void *stream);
 
+/* Copies the per-solve record of the last admm_solve on this handle into
+ * info_out[0 .. count-1] (count <= 16): 0 iterations, 1 converged, 2 r,
+ * 3 sigma, 4..7 the four terms of r, 8..10 the three terms of sigma,
+ * 11 objective, 12 status, 13 cubic branch decisions that FP32 could not
+ * certify and FP64 took (ADMM_MIXED).  Host-only; no device work. */
+admm_status admm_get_info(admm_handle *h, double *info_out, int count);
+
 /* Frees everything the handle owns.  NULL-safe. */
 admm_status admm_destroy(admm_handle *h);
 

@@ -77,6 +77,8 @@ _lib.admm_last_error.argtypes = []
 _lib.admm_last_error.restype = C.c_char_p
 _lib.admm_status_string.argtypes = [C.c_int]
 _lib.admm_status_string.restype = C.c_char_p
+_lib.admm_get_info.argtypes = [_H, _dp, C.c_int]
+_lib.admm_get_info.restype = C.c_int
 _lib.admm_selftest_barrier_timeout.argtypes = [C.c_longlong, C.c_int, C.POINTER(C.c_int)]
 _lib.admm_selftest_barrier_timeout.restype = C.c_int
 
@@ -240,6 +242,17 @@ def admm_get_state(h, n: int, m: int, q: int) -> dict:
     return st
 
 
+INFO_KEYS = ("iters", "converged", "r", "sigma", "r_demand", "r_z", "r_h", "r_copy", "s_z", "s_h", "s_sx",
+             "objective", "status", "fp64_escalations")
+
+
+def admm_get_info(h) -> dict:
+    """Per-solve record of the last solve on the handle (see admm.h)."""
+    buf = (C.c_double * 16)()
+    _check(_lib.admm_get_info(h, buf, 16))
+    return {k: buf[t] for t, k in enumerate(INFO_KEYS)}
+
+
 def admm_destroy(h) -> None:
     if h:
         _lib.admm_destroy(h)
@@ -269,6 +282,9 @@ class Solver:
 
     def state(self) -> dict:
         return admm_get_state(self.h, self.n, self.m, self.q)
+
+    def info(self) -> dict:
+        return admm_get_info(self.h)
 
     def close(self):
         if self.h:

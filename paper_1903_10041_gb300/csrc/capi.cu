@@ -1,6 +1,7 @@
 // Host side of the C ABI declared in include/admm.h: validation, device
 // layout, launch configuration and state import/export for the
 // single-instance solver.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -108,17 +109,6 @@ __global__ void pair_sums(int n, int m, int q, int ld, const double *g2, const d
     }
 }
 
-__global__ void init_x(int n, int m, int q, int ld, const double *lo, const double *hi, double *x)
-{
-    const int64_t total = (int64_t)m * q * n;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-        const int k = (int)(t % n);
-        const int64_t r = t / n;
-        const int i = (int)(r / q);
-        x[(size_t)r * ld + k] = clampd(0.0, lo[(size_t)i * ld + k], hi[(size_t)i * ld + k]);
-    }
-}
-
 __global__ void selftest_barrier_kernel(unsigned *bar, int *status, long long spin_ns, unsigned extra)
 {
     // Waits for `extra` more arrivals than the grid can provide.
@@ -134,8 +124,8 @@ bool params_ok(const admm_params *p)
     if (!(p->r_tol >= 0.0) || !(p->s_tol >= 0.0)) return !fail(ADMM_EINVAL, "r_tol and s_tol must be >= 0");
     if (p->max_iter < 1) return !fail(ADMM_EINVAL, "max_iter must be >= 1");
     if (p->check_every < 1) return !fail(ADMM_EINVAL, "check_every must be >= 1");
-    if (p->precision != ADMM_FP64)
-        return !fail(ADMM_EUNSUPPORTED, "precision %d is not available in the single-instance solver", p->precision);
+    if (p->precision != ADMM_FP64 && p->precision != ADMM_MIXED && p->precision != ADMM_MIXED_FP64CUBIC)
+        return !fail(ADMM_EINVAL, "bad precision %d", p->precision);
     if (p->xmin_mode != ADMM_XMIN_EXACT && p->xmin_mode != ADMM_XMIN_PAPER)
         return !fail(ADMM_EINVAL, "bad xmin_mode %d", p->xmin_mode);
     if (p->sweep != ADMM_GAUSS_SEIDEL && p->sweep != ADMM_JACOBI) return !fail(ADMM_EINVAL, "bad sweep %d", p->sweep);
@@ -162,39 +152,51 @@ void clear_last_error() { g_err.clear(); }
 struct admm_handle {
     int n = 0, m = 0, q = 0, ld = 0, dev = 0, nsm = 0;
     admm_params prm{};
-    // problem (FP64, padded rows of ld)
-    double *f2 = nullptr, *f1 = nullptr, *f0 = nullptr, *g2 = nullptr, *g1 = nullptr, *g0 = nullptr;
-    double *lo = nullptr, *hi = nullptr, *y = nullptr, *c = nullptr, *sumg0 = nullptr;
+    int esz = 8;                 // bytes per stored value: 8 (FP64) or 4 (mixed)
+    // problem, padded rows of ld, storage type by esz
+    void *f2 = nullptr, *f1 = nullptr, *f0 = nullptr, *g2 = nullptr, *g1 = nullptr, *g0 = nullptr;
+    void *lo = nullptr, *hi = nullptr, *y = nullptr;
+    double *c = nullptr, *sumg0 = nullptr;
     // state
-    double *x = nullptr, *s = nullptr, *mu = nullptr, *scal = nullptr;
+    void *x = nullptr, *s = nullptr, *mu = nullptr;
+    void *s_lo = nullptr, *mu_lo = nullptr; // mixed: low parts of float-float s, mu (inside s, mu allocations)
+    double *scal = nullptr;
     // scratch
     double *part = nullptr, *cpart = nullptr, *info = nullptr;
+    double *tmp64 = nullptr;     // FP64 staging for mixed-precision import/export (lazy)
+    size_t tmp64_n = 0;
     unsigned *bar = nullptr, *flags = nullptr;
     int *status = nullptr;
     double *info_host = nullptr; // pinned
     // launch shape
-    int grid = 0, slots = 0;
-    int64_t chunk = 0;
+    int grid = 0, slots = 0, rs = 0;
+    int64_t chunk = 0, ncols = 0;
     size_t smem = 0;
 };
 
 namespace {
 
+template <class T> void dfree(T *&p)
+{
+    if (p) cudaFree((void *)p);
+    p = nullptr;
+}
+
 void free_all(admm_handle *h)
 {
-    double **dp[] = {&h->f2, &h->f1, &h->f0, &h->g2, &h->g1, &h->g0, &h->lo, &h->hi, &h->y, &h->c,
-                     &h->sumg0, &h->x, &h->s, &h->mu, &h->scal, &h->part, &h->cpart, &h->info};
-    for (double **p : dp)
-        if (*p) {
-            cudaFree(*p);
-            *p = nullptr;
-        }
-    if (h->bar) cudaFree(h->bar);
-    if (h->flags) cudaFree(h->flags);
-    if (h->status) cudaFree(h->status);
+    void **vp[] = {&h->f2, &h->f1, &h->f0, &h->g2, &h->g1, &h->g0, &h->lo, &h->hi, &h->y, &h->x, &h->s, &h->mu};
+    for (void **p : vp) dfree(*p);
+    dfree(h->c);
+    dfree(h->sumg0);
+    dfree(h->scal);
+    dfree(h->part);
+    dfree(h->cpart);
+    dfree(h->info);
+    dfree(h->tmp64);
+    dfree(h->bar);
+    dfree(h->flags);
+    dfree(h->status);
     if (h->info_host) cudaFreeHost(h->info_host);
-    h->bar = h->flags = nullptr;
-    h->status = nullptr;
     h->info_host = nullptr;
 }
 
@@ -218,20 +220,85 @@ cudaError_t put_rows(double *dst, int ld, const double *src, int n, int64_t rows
                         src_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice);
 }
 
-cudaError_t get_rows(double *dst, const double *src, int ld, int n, int64_t rows, bool dst_dev, cudaStream_t st)
+cudaError_t ensure_tmp(admm_handle *h, size_t count)
 {
-    return cudaMemcpy2DAsync(dst, (size_t)n * 8, src, (size_t)ld * 8, (size_t)n * 8, (size_t)rows,
-                             dst_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st);
+    if (h->tmp64_n >= count) return cudaSuccess;
+    dfree(h->tmp64);
+    h->tmp64_n = 0;
+    cudaError_t e = cudaMalloc(&h->tmp64, count * 8);
+    if (e == cudaSuccess) h->tmp64_n = count;
+    return e;
+}
+
+// Handle array (padded, storage type; `lo` = low parts of a float-float
+// array or NULL) -> caller's dense FP64 rows.
+cudaError_t export_rows(admm_handle *h, double *dst, bool dst_dev, const void *src, int64_t rows, cudaStream_t st,
+                        const void *lo = nullptr)
+{
+    const int n = h->n, ld = h->ld;
+    const cudaMemcpyKind k = dst_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (h->esz == 8)
+        return cudaMemcpy2DAsync(dst, (size_t)n * 8, src, (size_t)ld * 8, (size_t)n * 8, (size_t)rows, k, st);
+    double *to = dst;
+    if (!dst_dev) {
+        cudaError_t e = ensure_tmp(h, (size_t)rows * n);
+        if (e != cudaSuccess) return e;
+        to = h->tmp64;
+    }
+    if (lo) convert_rows_ff_to_f64(to, n, (const float *)src, (const float *)lo, ld, n, rows, st);
+    else convert_rows_f32_to_f64(to, n, (const float *)src, ld, n, rows, st);
+    if (dst_dev) return cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return cudaMemcpyAsync(dst, h->tmp64, (size_t)rows * n * 8, k, st);
+}
+
+// Caller's dense FP64 rows -> handle array (padded, storage type; `lo` as in export_rows).
+cudaError_t import_rows(admm_handle *h, void *dst, const double *src, bool src_dev, int64_t rows, cudaStream_t st,
+                        void *lo = nullptr)
+{
+    const int n = h->n, ld = h->ld;
+    const cudaMemcpyKind k = src_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (h->esz == 8)
+        return cudaMemcpy2DAsync(dst, (size_t)ld * 8, src, (size_t)n * 8, (size_t)n * 8, (size_t)rows, k, st);
+    const double *from = src;
+    if (!src_dev) {
+        cudaError_t e = ensure_tmp(h, (size_t)rows * n);
+        if (e != cudaSuccess) return e;
+        e = cudaMemcpyAsync(h->tmp64, src, (size_t)rows * n * 8, k, st);
+        if (e != cudaSuccess) return e;
+        from = h->tmp64;
+    }
+    if (lo) split_rows_f64_to_ff((float *)dst, (float *)lo, ld, from, n, n, rows, st);
+    else convert_rows_f64_to_f32((float *)dst, ld, from, n, n, rows, st);
+    return cudaGetLastError();
+}
+
+template <class T>
+__global__ void init_x_t(int n, int m, int q, int ld, const T *lo, const T *hi, T *x)
+{
+    const int64_t total = (int64_t)m * q * n;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int k = (int)(t % n);
+        const int64_t r = t / n;
+        const int i = (int)(r / q);
+        const T l = lo[(size_t)i * ld + k], u = hi[(size_t)i * ld + k];
+        x[(size_t)r * ld + k] = (T)0 < l ? l : ((T)0 > u ? u : (T)0);
+    }
 }
 
 admm_status reset_state(admm_handle *h)
 {
     const int m = h->m, q = h->q, mq = m * q;
-    init_x<<<std::max(1, std::min(h->nsm * 4, (int)((int64_t)m * q * h->n / 256 + 1))), 256>>>(h->n, m, q, h->ld,
-                                                                                                h->lo, h->hi, h->x);
+    const int g = std::max(1, std::min(h->nsm * 4, (int)((int64_t)m * q * h->n / 256 + 1)));
+    if (h->esz == 8)
+        init_x_t<double><<<g, 256>>>(h->n, m, q, h->ld, (const double *)h->lo, (const double *)h->hi, (double *)h->x);
+    else
+        init_x_t<float><<<g, 256>>>(h->n, m, q, h->ld, (const float *)h->lo, (const float *)h->hi, (float *)h->x);
     CUDA_TRY(cudaGetLastError());
-    CUDA_TRY(cudaMemset(h->s, 0, sizeof(double) * (size_t)q * h->ld));
-    CUDA_TRY(cudaMemset(h->mu, 0, sizeof(double) * (size_t)q * h->ld));
+    const size_t cb = (size_t)8 * q * h->ld; // FP64, or float-float hi + lo rows
+    CUDA_TRY(cudaMemset(h->s, 0, cb));
+    CUDA_TRY(cudaMemset(h->mu, 0, cb));
     std::vector<double> sc(scal_size(m, q), 0.0);
     for (int t = 0; t < 4; ++t) sc[5 * mq + m + t] = h->prm.rho[t];
     sc[5 * mq + m + 4] = 1.0; // cold
@@ -293,13 +360,19 @@ admm_status admm_create(const admm_problem *P, const admm_params *prm, admm_hand
     if (!params_ok(prm)) return g_err.find("precision") != std::string::npos ? ADMM_EUNSUPPORTED : ADMM_EINVAL;
 
     admm_handle *h = new admm_handle();
+    const bool mixed = prm->precision != ADMM_FP64;
     h->n = P->n;
     h->m = P->m;
     h->q = P->q;
-    h->ld = (P->n + 31) / 32 * 32;
+    h->esz = mixed ? 4 : 8;
+    h->ld = mixed ? (P->n + 63) / 64 * 64 : (P->n + 31) / 32 * 32;
     h->prm = *prm;
     admm_status st = ADMM_OK;
+    // FP64 staging copies of the problem (the final arrays in FP64 mode)
+    double *s64[9] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     auto bail = [&](admm_status s) {
+        if (mixed)
+            for (double *&p : s64) dfree(p);
         free_all(h);
         delete h;
         return s;
@@ -315,19 +388,11 @@ admm_status admm_create(const admm_problem *P, const admm_params *prm, admm_hand
     TRY(cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, h->dev));
     const int n = h->n, m = h->m, q = h->q, ld = h->ld, mq = m * q;
     const size_t ne = (size_t)mq * ld, nb = (size_t)m * ld, nc = (size_t)q * ld;
-    double **el[] = {&h->f2, &h->f1, &h->f0, &h->g2, &h->g1, &h->g0, &h->x};
-    for (double **p : el) {
-        TRY(cudaMalloc(p, ne * 8));
-        TRY(cudaMemset(*p, 0, ne * 8));
+    const size_t cnt[9] = {ne, ne, ne, ne, ne, ne, nb, nb, nc};
+    for (int t = 0; t < 9; ++t) {
+        TRY(cudaMalloc(&s64[t], cnt[t] * 8));
+        TRY(cudaMemset(s64[t], 0, cnt[t] * 8));
     }
-    TRY(cudaMalloc(&h->lo, nb * 8));
-    TRY(cudaMalloc(&h->hi, nb * 8));
-    TRY(cudaMemset(h->lo, 0, nb * 8));
-    TRY(cudaMemset(h->hi, 0, nb * 8));
-    TRY(cudaMalloc(&h->y, nc * 8));
-    TRY(cudaMalloc(&h->s, nc * 8));
-    TRY(cudaMalloc(&h->mu, nc * 8));
-    TRY(cudaMemset(h->y, 0, nc * 8));
     TRY(cudaMalloc(&h->c, m * 8));
     TRY(cudaMalloc(&h->sumg0, mq * 8));
     TRY(cudaMalloc(&h->scal, scal_size(m, q) * 8));
@@ -338,23 +403,17 @@ admm_status admm_create(const admm_problem *P, const admm_params *prm, admm_hand
     TRY(cudaMallocHost(&h->info_host, kInfo * 8));
 
     const bool dev = P->on_device != 0;
-    TRY(put_rows(h->f2, ld, P->f2, n, mq, dev));
-    TRY(put_rows(h->f1, ld, P->f1, n, mq, dev));
-    TRY(put_rows(h->f0, ld, P->f0, n, mq, dev));
-    TRY(put_rows(h->g2, ld, P->g2, n, mq, dev));
-    TRY(put_rows(h->g1, ld, P->g1, n, mq, dev));
-    TRY(put_rows(h->g0, ld, P->g0, n, mq, dev));
-    TRY(put_rows(h->lo, ld, P->x_lo, n, m, dev));
-    TRY(put_rows(h->hi, ld, P->x_hi, n, m, dev));
-    TRY(put_rows(h->y, ld, P->y, n, q, dev));
+    const double *src[9] = {P->f2, P->f1, P->f0, P->g2, P->g1, P->g0, P->x_lo, P->x_hi, P->y};
+    const int64_t rows[9] = {mq, mq, mq, mq, mq, mq, m, m, q};
+    for (int t = 0; t < 9; ++t) TRY(put_rows(s64[t], ld, src[t], n, rows[t], dev));
     TRY(cudaMemcpy(h->c, P->c, m * 8, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice));
 
     // validation (Assumptions 1 and 3, bounds, sure infeasibility)
     TRY(cudaMemset(h->flags, 0, sizeof(unsigned)));
     validate_elements<<<std::max(1, std::min(h->nsm * 8, (int)(ne / 256 + 1))), 256>>>(
-        n, m, q, ld, h->f2, h->f1, h->f0, h->g2, h->g1, h->g0, h->lo, h->hi, h->y, h->flags);
+        n, m, q, ld, s64[0], s64[1], s64[2], s64[3], s64[4], s64[5], s64[6], s64[7], s64[8], h->flags);
     TRY(cudaGetLastError());
-    pair_sums<<<mq, 256>>>(n, m, q, ld, h->g2, h->g1, h->g0, h->lo, h->hi, h->c, h->sumg0, h->flags);
+    pair_sums<<<mq, 256>>>(n, m, q, ld, s64[3], s64[4], s64[5], s64[6], s64[7], h->c, h->sumg0, h->flags);
     TRY(cudaGetLastError());
     unsigned flags = 0;
     TRY(cudaMemcpy(&flags, h->flags, sizeof flags, cudaMemcpyDeviceToHost));
@@ -367,19 +426,46 @@ admm_status admm_create(const admm_problem *P, const admm_params *prm, admm_hand
         if (flags & V_INFEASIBLE) why += " sum_k min g > c for some (i, j): infeasible;";
         return bail(fail(ADMM_EINVAL, "invalid problem:%s", why.c_str()));
     }
+    void **dst[9] = {&h->f2, &h->f1, &h->f0, &h->g2, &h->g1, &h->g0, &h->lo, &h->hi, &h->y};
+    if (!mixed) {
+        for (int t = 0; t < 9; ++t) {
+            *dst[t] = s64[t];
+            s64[t] = nullptr;
+        }
+        TRY(cudaMalloc(&h->x, ne * 8));
+        TRY(cudaMalloc(&h->s, nc * 8));
+        TRY(cudaMalloc(&h->mu, nc * 8));
+    } else {
+        for (int t = 0; t < 9; ++t) {
+            TRY(cudaMalloc(dst[t], cnt[t] * 4));
+            convert_rows_f64_to_f32((float *)*dst[t], ld, s64[t], ld, ld, rows[t], 0);
+            TRY(cudaGetLastError());
+        }
+        TRY(cudaDeviceSynchronize());
+        for (double *&p : s64) dfree(p);
+        TRY(cudaMalloc(&h->x, ne * 4));
+        TRY(cudaMalloc(&h->s, nc * 8));   // float-float: hi rows then lo rows
+        TRY(cudaMalloc(&h->mu, nc * 8));
+        h->s_lo = (float *)h->s + nc;
+        h->mu_lo = (float *)h->mu + nc;
+        TRY(cudaMemset(h->x, 0, ne * 4));
+    }
 
     // launch shape: contiguous equal column chunks, all SMs busy
     h->smem = single_smem_bytes(m, q);
     const int per_sm = single_blocks_per_sm(prm->precision, m, h->smem);
     if (per_sm < 1) return bail(fail(ADMM_EUNSUPPORTED, "solve kernel cannot be resident (smem %zu B)", h->smem));
-    const int64_t ncols = (int64_t)q * n;
-    int64_t g = std::min<int64_t>((int64_t)h->nsm * per_sm, std::max<int64_t>(1, ncols / 32));
-    h->chunk = (ncols + g - 1) / g;
-    h->grid = (int)((ncols + h->chunk - 1) / h->chunk);
+    h->rs = mixed ? ld : n;
+    h->ncols = (int64_t)q * h->rs;
+    const int64_t unit = mixed ? 4 : 1;          // mixed: float4 quads of columns
+    const int64_t min_cols = mixed ? 128 : 32;   // at least a warp of work per CTA
+    int64_t g = std::min<int64_t>((int64_t)h->nsm * per_sm, std::max<int64_t>(1, h->ncols / min_cols));
+    h->chunk = ((h->ncols + g - 1) / g + unit - 1) / unit * unit;
+    h->grid = (int)((h->ncols + h->chunk - 1) / h->chunk);
     h->slots = 1;
     for (int b = 0; b < h->grid; ++b) {
-        const int64_t c0 = (int64_t)b * h->chunk, c1 = std::min(c0 + h->chunk, ncols);
-        h->slots = std::max(h->slots, (int)((c1 - 1) / n - c0 / n + 1));
+        const int64_t c0 = (int64_t)b * h->chunk, c1 = std::min(c0 + h->chunk, h->ncols);
+        h->slots = std::max(h->slots, (int)((c1 - 1) / h->rs - c0 / h->rs + 1));
     }
     TRY(cudaMalloc(&h->part, sizeof(double) * 2 * (size_t)h->grid * h->slots * m * 4));
     TRY(cudaMalloc(&h->cpart, sizeof(double) * 2 * (size_t)h->grid * 4));
@@ -395,6 +481,8 @@ admm_status admm_set_params(admm_handle *h, const admm_params *prm)
     g_err.clear();
     if (!h) return fail(ADMM_EINVAL, "handle is NULL");
     if (!params_ok(prm)) return g_err.find("precision") != std::string::npos ? ADMM_EUNSUPPORTED : ADMM_EINVAL;
+    if ((prm->precision == ADMM_FP64) != (h->prm.precision == ADMM_FP64))
+        return fail(ADMM_EINVAL, "the storage precision (FP64 or mixed) is fixed at admm_create");
     DeviceGuard dg(h->dev);
     h->prm = *prm;
     const int mq = h->m * h->q;
@@ -412,20 +500,23 @@ admm_status admm_reset(admm_handle *h)
 
 static admm_status load_state(admm_handle *h, const admm_state *w, cudaStream_t st)
 {
-    const int n = h->n, m = h->m, q = h->q, mq = m * q, ld = h->ld;
+    const int m = h->m, q = h->q, mq = m * q;
     const bool dev = w->on_device != 0;
     const cudaMemcpyKind k = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     if (!w->x || !w->s || !w->mu || !w->lam || !w->zeta || !w->h || !w->p || !w->nu || !w->x1)
         return fail(ADMM_EINVAL, "warm state has a NULL array");
     for (int t = 0; t < 4; ++t)
         if (!(w->rho[t] > 0.0)) return fail(ADMM_EINVAL, "warm state rho[%d] must be > 0", t);
-    CUDA_TRY(cudaMemcpy2DAsync(h->x, (size_t)ld * 8, w->x, (size_t)n * 8, (size_t)n * 8, (size_t)mq, k, st));
-    CUDA_TRY(cudaMemcpy2DAsync(h->s, (size_t)ld * 8, w->s, (size_t)n * 8, (size_t)n * 8, (size_t)q, k, st));
-    CUDA_TRY(cudaMemcpy2DAsync(h->mu, (size_t)ld * 8, w->mu, (size_t)n * 8, (size_t)n * 8, (size_t)q, k, st));
+    CUDA_TRY(import_rows(h, h->x, w->x, dev, mq, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    CUDA_TRY(import_rows(h, h->s, w->s, dev, q, st, h->s_lo));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    CUDA_TRY(import_rows(h, h->mu, w->mu, dev, q, st, h->mu_lo));
     const double *pairs[5] = {w->lam, w->zeta, w->h, w->p, w->nu};
     for (int t = 0; t < 5; ++t) CUDA_TRY(cudaMemcpyAsync(h->scal + (size_t)t * mq, pairs[t], mq * 8, k, st));
     CUDA_TRY(cudaMemcpyAsync(h->scal + 5 * mq, w->x1, m * 8, k, st));
     double tail[6] = {w->rho[0], w->rho[1], w->rho[2], w->rho[3], w->cold ? 1.0 : 0.0, 1.0};
+    CUDA_TRY(cudaStreamSynchronize(st));
     CUDA_TRY(cudaMemcpy(h->scal + 5 * mq + m, tail, sizeof tail, cudaMemcpyHostToDevice));
     return ADMM_OK;
 }
@@ -445,7 +536,8 @@ admm_status admm_solve(admm_handle *h, const admm_state *warm, admm_result *out,
     a.m = h->m;
     a.q = h->q;
     a.ld = h->ld;
-    a.ncols = (int64_t)h->q * h->n;
+    a.rs = h->rs;
+    a.ncols = h->ncols;
     a.chunk = h->chunk;
     a.slots = h->slots;
     a.grid = h->grid;
@@ -463,6 +555,8 @@ admm_status admm_solve(admm_handle *h, const admm_state *warm, admm_result *out,
     a.x = h->x;
     a.s = h->s;
     a.mu = h->mu;
+    a.s_lo = h->s_lo;
+    a.mu_lo = h->mu_lo;
     a.scal = h->scal;
     a.part = h->part;
     a.cpart = h->cpart;
@@ -482,8 +576,7 @@ admm_status admm_solve(admm_handle *h, const admm_state *warm, admm_result *out,
     CUDA_TRY(cudaMemsetAsync(h->status, 0, sizeof(int), st));
     CUDA_TRY(launch_single(h->prm.precision, a, h->smem, st));
     CUDA_TRY(cudaMemcpyAsync(h->info_host, h->info, kInfo * 8, cudaMemcpyDeviceToHost, st));
-    if (out && out->x)
-        CUDA_TRY(get_rows(out->x, h->x, h->ld, h->n, (int64_t)h->m * h->q, out->on_device != 0, st));
+    if (out && out->x) CUDA_TRY(export_rows(h, out->x, out->on_device != 0, h->x, (int64_t)h->m * h->q, st));
     if (out && out->x1)
         CUDA_TRY(cudaMemcpyAsync(out->x1, h->scal + 5 * h->m * h->q, h->m * 8,
                                  out->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
@@ -511,12 +604,21 @@ admm_status admm_get_state(admm_handle *h, admm_state *o, void *stream)
     if (!h || !o) return fail(ADMM_EINVAL, "NULL argument");
     DeviceGuard dg(h->dev);
     cudaStream_t st = (cudaStream_t)stream;
-    const int n = h->n, m = h->m, q = h->q, mq = m * q, ld = h->ld;
+    const int m = h->m, q = h->q, mq = m * q;
     const bool dev = o->on_device != 0;
     const cudaMemcpyKind k = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-    if (o->x) CUDA_TRY(get_rows(o->x, h->x, ld, n, mq, dev, st));
-    if (o->s) CUDA_TRY(get_rows(o->s, h->s, ld, n, q, dev, st));
-    if (o->mu) CUDA_TRY(get_rows(o->mu, h->mu, ld, n, q, dev, st));
+    if (o->x) {
+        CUDA_TRY(export_rows(h, o->x, dev, h->x, mq, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    if (o->s) {
+        CUDA_TRY(export_rows(h, o->s, dev, h->s, q, st, h->s_lo));
+        CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    if (o->mu) {
+        CUDA_TRY(export_rows(h, o->mu, dev, h->mu, q, st, h->mu_lo));
+        CUDA_TRY(cudaStreamSynchronize(st));
+    }
     double *pairs[5] = {o->lam, o->zeta, o->h, o->p, o->nu};
     for (int t = 0; t < 5; ++t)
         if (pairs[t]) CUDA_TRY(cudaMemcpyAsync(pairs[t], h->scal + (size_t)t * mq, mq * 8, k, st));
@@ -526,6 +628,14 @@ admm_status admm_get_state(admm_handle *h, admm_state *o, void *stream)
     CUDA_TRY(cudaStreamSynchronize(st));
     for (int t = 0; t < 4; ++t) o->rho[t] = tail[t];
     o->cold = tail[4] != 0.0;
+    return ADMM_OK;
+}
+
+admm_status admm_get_info(admm_handle *h, double *info_out, int count)
+{
+    g_err.clear();
+    if (!h || !info_out || count < 1) return fail(ADMM_EINVAL, "NULL argument");
+    for (int t = 0; t < count && t < kInfo; ++t) info_out[t] = h->info_host[t];
     return ADMM_OK;
 }
 

@@ -23,16 +23,18 @@ inline __host__ __device__ int scal_size(int m, int q) { return 5 * m * q + m + 
 
 // info record written by a solve:
 //   0 iters, 1 converged, 2 r, 3 sigma, 4..7 r terms, 8..10 sigma terms,
-//   11 objective, 12 status
+//   11 objective, 12 status, 13 cubic decisions escalated to FP64 (mixed)
 struct SingleArgs {
     int n, m, q, ld;           // ld: padded row stride of the [*][n] arrays
-    int64_t ncols;             // q * n columns (j, k)
+    int rs;                    // row length of the column space: n (FP64) or ld (mixed, padded)
+    int64_t ncols;             // q * rs columns (j, k)
     int64_t chunk;             // columns per CTA (contiguous in j-major order)
     int slots;                 // partial-record slots per CTA (rows a chunk can touch)
     int grid;                  // CTAs
     const void *f2, *f1, *f0, *g2, *g1, *g0, *lo, *hi, *y;   // storage type of the precision
     const double *c, *sumg0;   // [m], [mq]
     void *x, *s, *mu;          // state arrays (storage type)
+    void *s_lo, *mu_lo;        // mixed: low parts of the float-float column state s, mu
     double *scal;              // scalar state, in/out
     double *part;              // [2][grid][slots][m][4] partial records (gsum, dmax, dmin, x0)
     double *cpart;             // [2][grid][4] per-CTA column maxima and objective partials
@@ -52,6 +54,17 @@ int single_blocks_per_sm(int precision, int m, size_t smem);
 size_t single_smem_bytes(int m, int q);
 // Index of the kernel variant used for m sources (template bound).
 int single_mbound(int m);
+// Row copies with conversion (device to device): rows x n values from a
+// source with row stride sld into a destination with row stride dld.
+void convert_rows_f32_to_f64(double *dst, int64_t dld, const float *src, int64_t sld, int n, int64_t rows,
+                             cudaStream_t st);
+void convert_rows_f64_to_f32(float *dst, int64_t dld, const double *src, int64_t sld, int n, int64_t rows,
+                             cudaStream_t st);
+// Float-float column arrays (hi + lo) <-> FP64 rows.
+void convert_rows_ff_to_f64(double *dst, int64_t dld, const float *hi, const float *lo, int64_t sld, int n,
+                            int64_t rows, cudaStream_t st);
+void split_rows_f64_to_ff(float *hi, float *lo, int64_t dld, const double *src, int64_t sld, int n, int64_t rows,
+                          cudaStream_t st);
 // Thread-local message returned by admm_last_error().
 void set_last_error(const char *msg);
 void clear_last_error();

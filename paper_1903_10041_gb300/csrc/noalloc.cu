@@ -249,6 +249,7 @@ extern "C" admm_status admm_solve_noalloc(const admm_problem *P, const admm_para
     a.m = m;
     a.q = q;
     a.ld = n;
+    a.rs = n;
     a.ncols = ncols;
     a.chunk = chunk;
     a.slots = slots;

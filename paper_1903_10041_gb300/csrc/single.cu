@@ -1,19 +1,19 @@
 // Persistent single-instance solve kernel: the whole ADMM loop of App. A on
 // the device, one cooperative launch per solve.
 //
-// Work split.  The q*n columns (j, k) are taken in j-major order and cut
-// into `grid` contiguous chunks of `chunk` columns, one per CTA, so every
-// CTA does the same number of element updates.  The thread that owns a
-// column updates all m sources of it in registers (step (a) sweeps the
-// sources in order, so the Gauss-Seidel sums over l != i stay local), then
-// steps (e) and (f) for that column.  The per-(i, j) sums over k that steps
-// (b) and (d) and the residuals need are segmented reductions: each CTA
-// reduces each row segment it owns (warp shuffles, then shared memory) into
-// a partial record; after one grid barrier every CTA adds the records of
-// each row in a fixed order and runs the per-(i, j) scalar steps (b), (c),
-// (d), (g), (h), (i), the residuals and the stop test redundantly, so all
-// CTAs hold identical scalars and take the same stop decision without a
-// second barrier.  Partial records are double-buffered by iteration parity.
+// Work split.  The columns (j, k) are taken in j-major order and cut into
+// `grid` contiguous chunks of `chunk` columns, one per CTA, so every CTA
+// does the same number of element updates.  The thread that owns a column
+// updates all m sources of it in registers (step (a) sweeps the sources in
+// order, so the Gauss-Seidel sums over l != i stay local), then steps (e)
+// and (f) for that column.  The per-(i, j) sums over k that steps (b) and
+// (d) and the residuals need are segmented reductions: each CTA reduces each
+// row segment it owns (warp shuffles, then shared memory) into a partial
+// record; after one grid barrier every CTA adds the records of each row in
+// a fixed order and runs the per-(i, j) scalar steps (b), (c), (d), (g),
+// (h), (i), the residuals and the stop test redundantly, so all CTAs hold
+// identical scalars and take the same stop decision without a second
+// barrier.  Partial records are double-buffered by iteration parity.
 //
 // Identities used (derived from steps (b) and (g)): after every iteration
 // lambda^(i,j) is constant over k and z_k = g_k(x_k) + zeta with
@@ -21,8 +21,23 @@
 // g_k(x~_k) + zeta + lambda needs no per-element z or lambda.  The zero start
 // (z = 0, the paper's iteration from zeros) is flagged `cold`, where
 // theta = 0 instead.
+//
+// Precision variants (template PREC):
+//   ADMM_FP64             one column per thread, dense column space (rs = n);
+//   ADMM_MIXED            FP32 storage and element work on float4 quads of
+//                         columns over a padded column space (rs = ld); the
+//                         capacity sums over k are accumulated per thread in
+//                         float-float (about 48 bits) and reduced in FP64; the
+//                         column state s, mu is stored and updated in
+//                         float-float; the cubic's branch is decided as FP64
+//                         would decide it;
+//   ADMM_MIXED_FP64CUBIC  as ADMM_MIXED with the cubic step in FP64.
+// The per-(i, j) scalar steps, residuals and stop test are FP64 in all three.
+#include <algorithm>
+
 #include "common.cuh"
 #include "internal.h"
+#include "quartic32.cuh"
 #include "quartic64.cuh"
 
 namespace admm_impl {
@@ -36,6 +51,7 @@ struct Sm {
     double *red;  // [kWarps][kMaxM][3]
     double *mx;   // [kWarps][8]
     double *bc;   // [16] broadcast
+    float *uoff;  // [mq] zeta + lambda in FP32 (mixed variants)
 };
 
 __device__ __forceinline__ Sm carve(double *base, int m, int q)
@@ -60,10 +76,12 @@ __device__ __forceinline__ Sm carve(double *base, int m, int q)
     s.mx = t;
     t += kWarps * 8;
     s.bc = t;
+    t += 16;
+    s.uoff = (float *)t;
     return s;
 }
 
-// Block-wide max of up to 8 values; every thread gets the results in out[].
+// Block-wide max of up to 8 values; every thread gets the results in v[].
 template <int NV> __device__ __forceinline__ void block_max(double *v, const Sm &sm)
 {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -84,7 +102,9 @@ template <int NV> __device__ __forceinline__ void block_max(double *v, const Sm 
     __syncthreads();
 }
 
-// Step (a) for all sources of column (j, k), then (e), (f) for the column.
+// ---------------------------------------------------------------------------
+// FP64 phase 1: step (a) for all sources of column (j, k), then (e), (f).
+// ---------------------------------------------------------------------------
 template <int M>
 __device__ __forceinline__ void column64(const SingleArgs &a, const Sm &sm, int j, int k, bool check,
                                          bool cold, double mu_div, double *gs, double *dmx, double *dmn,
@@ -173,9 +193,200 @@ __device__ __forceinline__ void column64(const SingleArgs &a, const Sm &sm, int 
     }
 }
 
+// ---------------------------------------------------------------------------
+// Mixed phase 1: a float4 quad of columns (j, k0..k0+3), FP32 element work.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float4 ldg4(const float *p) { return __ldg((const float4 *)p); }
+__device__ __forceinline__ float4 ld4(const float *p) { return *(const float4 *)p; }
+__device__ __forceinline__ float f4(const float4 &v, int c) { return c == 0 ? v.x : (c == 1 ? v.y : (c == 2 ? v.z : v.w)); }
+
+// g = b2 x^2 + b1 x as an unevaluated sum hi + lo (error-free products and sum).
+__device__ __forceinline__ void g_ff(float b2, float b1, float x, float &hi, float &lo)
+{
+    const float x2 = x * x;
+    const float ex2 = __fmaf_rn(x, x, -x2);
+    const float p = __fmul_rn(b2, x2);
+    const float ep = __fmaf_rn(b2, x2, -p) + b2 * ex2;
+    const float r = __fmul_rn(b1, x);
+    const float er = __fmaf_rn(b1, x, -r);
+    const float s = __fadd_rn(p, r);
+    const float bb = __fsub_rn(s, p);
+    const float es = __fadd_rn(__fsub_rn(p, __fsub_rn(s, bb)), __fsub_rn(r, bb));
+    hi = s;
+    lo = es + ep + er;
+}
+
+// (hi, lo) += (a, a_lo) in float-float.
+__device__ __forceinline__ void ff_add(float &hi, float &lo, float a, float a_lo)
+{
+    const float s = __fadd_rn(hi, a);
+    const float bb = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(a, bb));
+    hi = s;
+    lo = lo + (e + a_lo);
+}
+
+// Float-float arithmetic for the column state s, mu (steps (e), (f)).
+struct FF {
+    float hi, lo;
+};
+__device__ __forceinline__ FF ff_two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ FF ff_norm(float hi, float lo)
+{
+    const float s = __fadd_rn(hi, lo);
+    return {s, __fsub_rn(lo, __fsub_rn(s, hi))};
+}
+__device__ __forceinline__ FF ff_add(FF a, FF b)
+{
+    const FF t = ff_two_sum(a.hi, b.hi);
+    return ff_norm(t.hi, __fadd_rn(t.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ FF ff_addf(FF a, float b)
+{
+    const FF t = ff_two_sum(a.hi, b);
+    return ff_norm(t.hi, __fadd_rn(t.lo, a.lo));
+}
+__device__ __forceinline__ FF ff_neg(FF a) { return {-a.hi, -a.lo}; }
+
+template <int M, bool C64>
+__device__ __forceinline__ void quad32(const SingleArgs &a, const Sm &sm, int j, int k0, bool check, bool cold,
+                                       float mu_div, float rho1, float rho3, float rho4, float iq, float *ghi,
+                                       float *glo, float *dmx, float *dmn, float &cm_r, float &cm_s, unsigned &esc,
+                                       double *rec)
+{
+    const int m = a.m, q = a.q, ld = a.ld, n = a.n;
+    const float *__restrict__ F2 = (const float *)a.f2;
+    const float *__restrict__ F1 = (const float *)a.f1;
+    const float *__restrict__ G2 = (const float *)a.g2;
+    const float *__restrict__ G1 = (const float *)a.g1;
+    const float *__restrict__ G0 = (const float *)a.g0;
+    const float *__restrict__ LO = (const float *)a.lo;
+    const float *__restrict__ HI = (const float *)a.hi;
+    const float *__restrict__ Y = (const float *)a.y;
+    float *X = (float *)a.x, *Sv = (float *)a.s, *MU = (float *)a.mu;
+    float *SL = (float *)a.s_lo, *ML = (float *)a.mu_lo;
+
+    const size_t col = (size_t)j * ld + k0;
+    const float4 y4 = ldg4(Y + col), s4 = ld4(Sv + col), m4 = ld4(MU + col);
+    const float4 sl4 = ld4(SL + col), ml4 = ld4(ML + col);
+    float yv[4] = {y4.x, y4.y, y4.z, y4.w}, st[4] = {s4.x, s4.y, s4.z, s4.w}, mu[4] = {m4.x, m4.y, m4.z, m4.w};
+    float stl[4] = {sl4.x, sl4.y, sl4.z, sl4.w}, mul[4] = {ml4.x, ml4.y, ml4.z, ml4.w};
+    if (mu_div != 1.0f) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            mu[c] = mu[c] / mu_div;
+            mul[c] = mul[c] / mu_div;
+        }
+    }
+    float xt[M][4], xs[M][4];
+#pragma unroll
+    for (int i = 0; i < M; ++i)
+        if (i < m) {
+            const float4 v = ld4(X + ((size_t)i * q + j) * ld + k0);
+            xt[i][0] = xs[i][0] = v.x;
+            xt[i][1] = xs[i][1] = v.y;
+            xt[i][2] = xs[i][2] = v.z;
+            xt[i][3] = xs[i][3] = v.w;
+        }
+    bool valid[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) valid[c] = k0 + c < n;
+
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+        if (i < m) {
+            const size_t e = ((size_t)i * q + j) * ld + k0;
+            const float4 A2 = ldg4(F2 + e), A1 = ldg4(F1 + e), B2 = ldg4(G2 + e), B1 = ldg4(G1 + e);
+            const float4 L4 = ldg4(LO + (size_t)i * ld + k0), H4 = ldg4(HI + (size_t)i * ld + k0);
+            const float4 Z4 = cold ? ldg4(G0 + e) : make_float4(0.f, 0.f, 0.f, 0.f);
+            const int pr = i * q + j;
+            const float uo = sm.uoff[pr];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const float a2 = f4(A2, c), a1 = f4(A1, c), b2 = f4(B2, c), b1 = f4(B1, c), g0 = f4(Z4, c);
+                const float x0 = xt[i][c];
+                const float gq_old = (b2 * x0 + b1) * x0;
+                const float u = cold ? -g0 : gq_old + uo;
+                float others = 0.0f;
+#pragma unroll
+                for (int l = 0; l < M; ++l)
+                    if (l < m && l != i) others += (a.sweep == ADMM_JACOBI) ? xt[l][c] : xs[l][c];
+                const float phi = ((st[c] - others) + yv[c]) + mu[c];
+                const float A = 0.5f * rho1 * b2 * b2;
+                const float B = rho1 * b2 * b1;
+                float C = a2 * iq + 0.5f * rho1 * (b1 * b1 - 2.0f * b2 * u) + 0.5f * rho3;
+                float D = a1 * iq - rho1 * b1 * u - rho3 * phi;
+                if (k0 + c == 0) {
+                    C += 0.5f * rho4;
+                    D -= rho4 * (float)(sm.x1[i] + sm.nu[pr]);
+                }
+                const float xn = C64 ? quartic_min_fp64cubic(A, B, C, D, f4(L4, c), f4(H4, c), a.xmin_mode)
+                                     : quartic_min32(A, B, C, D, f4(L4, c), f4(H4, c), a.xmin_mode, esc);
+                xs[i][c] = xn;
+                if (valid[c]) {
+                    float ghh, gll;
+                    g_ff(b2, b1, xn, ghh, gll);
+                    ff_add(ghi[i], glo[i], ghh, gll);
+                    if (check) {
+                        const float dk = cold ? ghh + g0 : ghh - gq_old;
+                        dmx[i] = fmaxf(dmx[i], dk);
+                        dmn[i] = fminf(dmn[i], dk);
+                    }
+                }
+            }
+        }
+    }
+    // (e), (f) in float-float: the column state carries about 48 bits, so
+    // mu's accumulation of ever smaller primal residuals is not lost to FP32
+    // rounding and the dual residual term of s settles below 1e-6.
+    float sn[4], snl[4], mn[4], mnl[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        FF sx = {0.0f, 0.0f}, dx = {0.0f, 0.0f};
+#pragma unroll
+        for (int i = 0; i < M; ++i)
+            if (i < m) {
+                sx = ff_addf(sx, xs[i][c]);
+                dx = ff_add(dx, ff_two_sum(xs[i][c], -xt[i][c]));
+            }
+        const FF muf = {mu[c], mul[c]}, stf = {st[c], stl[c]};
+        const FF v = ff_add(ff_addf(sx, -yv[c]), ff_neg(muf));       // sum_i x - y - mu
+        const FF s = v.hi > 0.0f ? v : FF{0.0f, 0.0f};                // (e)
+        const FF t = ff_addf(ff_add(s, ff_neg(sx)), yv[c]);           // s - sum_i x + y
+        const FF mnew = ff_add(muf, t);                                // (f)
+        sn[c] = s.hi;
+        snl[c] = s.lo;
+        mn[c] = mnew.hi;
+        mnl[c] = mnew.lo;
+        if (check && valid[c]) {
+            cm_r = fmaxf(cm_r, fabsf(t.hi + t.lo));
+            const FF d = ff_add(ff_add(s, ff_neg(stf)), ff_neg(dx));   // s - s~ - sum_i (x - x~)
+            cm_s = fmaxf(cm_s, fabsf(d.hi + d.lo));
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < M; ++i)
+        if (i < m) *(float4 *)(X + ((size_t)i * q + j) * ld + k0) = make_float4(xs[i][0], xs[i][1], xs[i][2], xs[i][3]);
+    *(float4 *)(Sv + col) = make_float4(sn[0], sn[1], sn[2], sn[3]);
+    *(float4 *)(MU + col) = make_float4(mn[0], mn[1], mn[2], mn[3]);
+    *(float4 *)(SL + col) = make_float4(snl[0], snl[1], snl[2], snl[3]);
+    *(float4 *)(ML + col) = make_float4(mnl[0], mnl[1], mnl[2], mnl[3]);
+    if (k0 == 0) {
+#pragma unroll
+        for (int i = 0; i < M; ++i)
+            if (i < m) rec[i * 4 + 3] = (double)xs[i][0];
+    }
+}
+
+// Block reduction of one row segment into its partial record.
 template <int M>
-__device__ __forceinline__ void flush_segment(double *rec, double *gs, double *dmx, double *dmn, bool check,
-                                              int m, const Sm &sm)
+__device__ __forceinline__ void flush_segment(double *rec, const double *gs, const double *dmx, const double *dmn,
+                                              bool check, int m, const Sm &sm)
 {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
@@ -206,18 +417,28 @@ __device__ __forceinline__ void flush_segment(double *rec, double *gs, double *d
     __syncthreads();
 }
 
-template <int M> __global__ void __launch_bounds__(kBlock, 1) single_fp64_kernel(SingleArgs a)
+template <int M, int PREC> struct Bounds {
+    static constexpr int minb = PREC == ADMM_FP64 ? 1 : 2;
+};
+
+template <int M, int PREC>
+__global__ void __launch_bounds__(kBlock, (Bounds<M, PREC>::minb)) single_kernel(SingleArgs a)
 {
     extern __shared__ double smem[];
-    const int m = a.m, q = a.q, n = a.n, mq = m * q;
+    constexpr bool MIXED = PREC != ADMM_FP64;
+    const int m = a.m, q = a.q, n = a.n, mq = m * q, rs = a.rs;
     const Sm sm = carve(smem, m, q);
     for (int t = threadIdx.x; t < scal_size(m, q); t += kBlock) smem[t] = a.scal[t];
+    __syncthreads();
+    if (MIXED)
+        for (int pr = threadIdx.x; pr < mq; pr += kBlock) sm.uoff[pr] = (float)(sm.zeta[pr] + sm.lam[pr]);
     __syncthreads();
 
     const int64_t c0 = (int64_t)blockIdx.x * a.chunk;
     const int64_t c1 = min(c0 + a.chunk, a.ncols);
-    const int jf = (int)(c0 / n), jl = (int)((c1 - 1) / n);
+    const int jf = (int)(c0 / rs), jl = (int)((c1 - 1) / rs);
     unsigned nbar = 0;
+    unsigned esc = 0;
     bool ok = true, conv = false;
     int it;
     double res[7] = {0, 0, 0, 0, 0, 0, 0}; // r1 r2 r3 r4 s1 s2 s3 (unscaled s)
@@ -232,18 +453,46 @@ template <int M> __global__ void __launch_bounds__(kBlock, 1) single_fp64_kernel
 
         // ---- phase 1: element updates and segment partials --------------
         for (int j = jf; j <= jl; ++j) {
-            const int64_t s0 = max(c0, (int64_t)j * n), s1 = min(c1, (int64_t)(j + 1) * n);
+            const int64_t s0 = max(c0, (int64_t)j * rs), s1 = min(c1, (int64_t)(j + 1) * rs);
             double gs[M], dmx[M], dmn[M];
-#pragma unroll
-            for (int i = 0; i < M; ++i) {
-                gs[i] = 0.0;
-                dmx[i] = -INFINITY;
-                dmn[i] = INFINITY;
-            }
             double *rec = a.part + ((size_t)(par * a.grid + blockIdx.x) * a.slots + (j - jf)) * m * 4;
-            for (int64_t cc = s0 + threadIdx.x; cc < s1; cc += kBlock)
-                column64<M>(a, sm, j, (int)(cc - (int64_t)j * n), check, cold, mu_div, gs, dmx, dmn, cm_r,
-                            cm_s, rec);
+            if constexpr (!MIXED) {
+#pragma unroll
+                for (int i = 0; i < M; ++i) {
+                    gs[i] = 0.0;
+                    dmx[i] = -INFINITY;
+                    dmn[i] = INFINITY;
+                }
+                for (int64_t cc = s0 + threadIdx.x; cc < s1; cc += kBlock)
+                    column64<M>(a, sm, j, (int)(cc - (int64_t)j * rs), check, cold, mu_div, gs, dmx, dmn, cm_r,
+                                cm_s, rec);
+            } else {
+                float ghi[M], glo[M], fmx[M], fmn[M];
+#pragma unroll
+                for (int i = 0; i < M; ++i) {
+                    ghi[i] = 0.0f;
+                    glo[i] = 0.0f;
+                    fmx[i] = -INFINITY;
+                    fmn[i] = INFINITY;
+                }
+                const float rho1 = (float)sm.rho[0], rho3 = (float)sm.rho[2], rho4 = (float)sm.rho[3];
+                const float iq = 1.0f / (float)q;
+                float fcr = 0.0f, fcs = 0.0f;
+                for (int64_t qq = s0 / 4 + threadIdx.x; qq < s1 / 4; qq += kBlock) {
+                    const int k0 = (int)(qq * 4 - (int64_t)j * rs);
+                    if (k0 >= n) continue;
+                    quad32<M, PREC == ADMM_MIXED_FP64CUBIC>(a, sm, j, k0, check, cold, (float)mu_div, rho1, rho3,
+                                                            rho4, iq, ghi, glo, fmx, fmn, fcr, fcs, esc, rec);
+                }
+#pragma unroll
+                for (int i = 0; i < M; ++i) {
+                    gs[i] = (double)ghi[i] + (double)glo[i];
+                    dmx[i] = (double)fmx[i];
+                    dmn[i] = (double)fmn[i];
+                }
+                cm_r = fmax(cm_r, (double)fcr);
+                cm_s = fmax(cm_s, (double)fcs);
+            }
             flush_segment<M>(rec, gs, dmx, dmn, check, m, sm);
         }
         if (check) {
@@ -267,11 +516,11 @@ template <int M> __global__ void __launch_bounds__(kBlock, 1) single_fp64_kernel
         double r2m = 0.0, r3m = 0.0, s1m = 0.0, s2m = 0.0;
         for (int pr = threadIdx.x; pr < mq; pr += kBlock) {
             const int i = pr / q, j = pr - i * q;
-            const int64_t rs = (int64_t)j * n;
-            const int b0 = (int)(rs / a.chunk), b1 = (int)((rs + n - 1) / a.chunk);
+            const int64_t rbeg = (int64_t)j * rs;
+            const int b0 = (int)(rbeg / a.chunk), b1 = (int)((rbeg + rs - 1) / a.chunk);
             double S = 0.0, dmx = -INFINITY, dmn = INFINITY, x0 = 0.0;
-            for (int b = b0; b <= b1; ++b) {
-                const int slot = j - (int)(((int64_t)b * a.chunk) / n);
+            for (int b = b0; b <= b1 && b < a.grid; ++b) {
+                const int slot = j - (int)(((int64_t)b * a.chunk) / rs);
                 const double *rec = a.part + ((size_t)(par * a.grid + b) * a.slots + slot) * m * 4 + i * 4;
                 S += ldcg(rec);
                 if (check) {
@@ -356,28 +605,51 @@ template <int M> __global__ void __launch_bounds__(kBlock, 1) single_fp64_kernel
                 }
             }
         }
+        if (MIXED) {
+            for (int pr = threadIdx.x; pr < mq; pr += kBlock) sm.uoff[pr] = (float)(sm.zeta[pr] + sm.lam[pr]);
+            __syncthreads();
+        }
     }
     const int iters = it > a.max_iter ? a.max_iter : it;
 
     // ---- objective (1/q) sum f(x) of eq. (2): one more barrier -----------
     if (ok) {
-        const double *F2 = (const double *)a.f2, *F1 = (const double *)a.f1, *F0 = (const double *)a.f0;
-        const double *X = (const double *)a.x;
         double acc = 0.0;
         for (int64_t cc = c0 + threadIdx.x; cc < c1; cc += kBlock) {
-            const int j = (int)(cc / n), k = (int)(cc - (int64_t)j * n);
+            const int j = (int)(cc / rs), k = (int)(cc - (int64_t)j * rs);
+            if (k >= n) continue;
             for (int i = 0; i < m; ++i) {
                 const size_t e = ((size_t)i * q + j) * a.ld + k;
-                acc += F2[e] * X[e] * X[e] + F1[e] * X[e] + F0[e];
+                double f2, f1, f0, x;
+                if constexpr (MIXED) {
+                    f2 = ((const float *)a.f2)[e];
+                    f1 = ((const float *)a.f1)[e];
+                    f0 = ((const float *)a.f0)[e];
+                    x = ((const float *)a.x)[e];
+                } else {
+                    f2 = ((const double *)a.f2)[e];
+                    f1 = ((const double *)a.f1)[e];
+                    f0 = ((const double *)a.f0)[e];
+                    x = ((const double *)a.x)[e];
+                }
+                acc += f2 * x * x + f1 * x + f0;
             }
         }
         acc = warp_sum(acc);
-        if ((threadIdx.x & 31) == 0) sm.mx[(threadIdx.x >> 5) * 8] = acc;
+        double escd = warp_sum((double)esc);
+        if ((threadIdx.x & 31) == 0) {
+            sm.mx[(threadIdx.x >> 5) * 8] = acc;
+            sm.mx[(threadIdx.x >> 5) * 8 + 1] = escd;
+        }
         __syncthreads();
         if (threadIdx.x == 0) {
-            double t = 0.0;
-            for (int w = 0; w < kWarps; ++w) t += sm.mx[w * 8];
+            double t = 0.0, te = 0.0;
+            for (int w = 0; w < kWarps; ++w) {
+                t += sm.mx[w * 8];
+                te += sm.mx[w * 8 + 1];
+            }
             a.cpart[(size_t)blockIdx.x * 4 + 2] = t;
+            a.cpart[(size_t)blockIdx.x * 4 + 3] = te;
         }
         ++nbar;
         ok = grid_barrier(a.bar, nbar * (unsigned)a.grid, a.status, a.spin_ns, ADMM_ETIMEOUT);
@@ -385,9 +657,12 @@ template <int M> __global__ void __launch_bounds__(kBlock, 1) single_fp64_kernel
     if (blockIdx.x == 0) {
         for (int t = threadIdx.x; t < scal_size(m, q); t += kBlock) a.scal[t] = smem[t];
         if (threadIdx.x == 0) {
-            double obj = 0.0;
+            double obj = 0.0, escs = 0.0;
             if (ok)
-                for (int b = 0; b < a.grid; ++b) obj += ldcg(a.cpart + (size_t)b * 4 + 2);
+                for (int b = 0; b < a.grid; ++b) {
+                    obj += ldcg(a.cpart + (size_t)b * 4 + 2);
+                    escs += ldcg(a.cpart + (size_t)b * 4 + 3);
+                }
             a.info[0] = iters;
             a.info[1] = conv ? 1.0 : 0.0;
             a.info[2] = r_last;
@@ -396,14 +671,18 @@ template <int M> __global__ void __launch_bounds__(kBlock, 1) single_fp64_kernel
             for (int t = 0; t < 3; ++t) a.info[8 + t] = res[4 + t] * sm.rho[t];
             a.info[11] = obj / (double)q;
             a.info[12] = ok ? 0.0 : (double)ld_volatile_i32(a.status);
+            a.info[13] = escs;
         }
     }
 }
 
 template <int M> void *single_fn(int precision)
 {
-    (void)precision;
-    return (void *)single_fp64_kernel<M>;
+    switch (precision) {
+    case ADMM_MIXED: return (void *)single_kernel<M, ADMM_MIXED>;
+    case ADMM_MIXED_FP64CUBIC: return (void *)single_kernel<M, ADMM_MIXED_FP64CUBIC>;
+    default: return (void *)single_kernel<M, ADMM_FP64>;
+    }
 }
 
 void *pick(int precision, int m)
@@ -422,7 +701,8 @@ int single_mbound(int m) { return m <= 2 ? 2 : (m <= 4 ? 4 : 8); }
 size_t single_smem_bytes(int m, int q)
 {
     const int mq = m * q;
-    return sizeof(double) * ((size_t)scal_size(m, q) + mq + kMaxM + kWarps * kMaxM * 3 + kWarps * 8 + 16);
+    return sizeof(double) * ((size_t)scal_size(m, q) + mq + kMaxM + kWarps * kMaxM * 3 + kWarps * 8 + 16) +
+           sizeof(float) * (size_t)mq + 16;
 }
 
 int single_blocks_per_sm(int precision, int m, size_t smem)
@@ -445,4 +725,68 @@ cudaError_t launch_single(int precision, const SingleArgs &a, size_t smem, cudaS
     return cudaLaunchCooperativeKernel(fn, dim3(a.grid), dim3(kBlock), args, smem, st);
 }
 
+} // namespace admm_impl
+
+namespace admm_impl {
+namespace {
+template <class S, class D>
+__global__ void convert_rows_kernel(D *dst, int64_t dld, const S *src, int64_t sld, int n, int64_t rows)
+{
+    const int64_t total = rows * n;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = t / n;
+        const int k = (int)(t - r * n);
+        dst[r * dld + k] = (D)src[r * sld + k];
+    }
+}
+int conv_grid(int64_t total) { return (int)std::max<int64_t>(1, std::min<int64_t>(4096, (total + 255) / 256)); }
+} // namespace
+
+void convert_rows_f32_to_f64(double *dst, int64_t dld, const float *src, int64_t sld, int n, int64_t rows,
+                             cudaStream_t st)
+{
+    convert_rows_kernel<float, double><<<conv_grid(rows * n), 256, 0, st>>>(dst, dld, src, sld, n, rows);
+}
+namespace {
+__global__ void ff_to_f64_kernel(double *dst, int64_t dld, const float *hi, const float *lo, int64_t sld, int n,
+                                 int64_t rows)
+{
+    const int64_t total = rows * n;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = t / n;
+        const int k = (int)(t - r * n);
+        dst[r * dld + k] = (double)hi[r * sld + k] + (double)lo[r * sld + k];
+    }
+}
+__global__ void f64_to_ff_kernel(float *hi, float *lo, int64_t dld, const double *src, int64_t sld, int n,
+                                 int64_t rows)
+{
+    const int64_t total = rows * n;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = t / n;
+        const int k = (int)(t - r * n);
+        const double v = src[r * sld + k];
+        const float h = (float)v;
+        hi[r * dld + k] = h;
+        lo[r * dld + k] = (float)(v - (double)h);
+    }
+}
+} // namespace
+
+void convert_rows_ff_to_f64(double *dst, int64_t dld, const float *hi, const float *lo, int64_t sld, int n,
+                            int64_t rows, cudaStream_t st)
+{
+    ff_to_f64_kernel<<<conv_grid(rows * n), 256, 0, st>>>(dst, dld, hi, lo, sld, n, rows);
+}
+void split_rows_f64_to_ff(float *hi, float *lo, int64_t dld, const double *src, int64_t sld, int n, int64_t rows,
+                          cudaStream_t st)
+{
+    f64_to_ff_kernel<<<conv_grid(rows * n), 256, 0, st>>>(hi, lo, dld, src, sld, n, rows);
+}
+
+void convert_rows_f64_to_f32(float *dst, int64_t dld, const double *src, int64_t sld, int n, int64_t rows,
+                             cudaStream_t st)
+{
+    convert_rows_kernel<double, float><<<conv_grid(rows * n), 256, 0, st>>>(dst, dld, src, sld, n, rows);
+}
 } // namespace admm_impl

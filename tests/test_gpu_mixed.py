@@ -1,0 +1,96 @@
+"""Mixed-precision solves (FP32 storage and element work, FP64 scalars and
+residuals) against the FP64 oracle: at convergence the objective matches
+to 1e-6 relative and the KKT residual of eq. (2) stays within 1e-6 of the
+oracle's own.  Both mixed policies are covered: the FP32 cubic with
+FP64-certified branch decisions and the FP64 cubic step."""
+import numpy as np
+import pytest
+
+from paper_1903_10041_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+OBJ_TOL = 1e-6
+KKT_MARGIN = 1e-6
+
+
+@pytest.fixture(scope="module")
+def capi():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1903_10041_gb300 import build
+    build.build()
+    from paper_1903_10041_gb300 import capi
+    return capi
+
+
+def _oracle_state_of(st):
+    """GPU state -> the oracle's dense state (z, lambda rebuilt from zeta, lam)."""
+    return st
+
+
+def _kkt(oracle, P, par, st, rho):
+    m, q, n = P.m, P.q, P.n
+    dense = {"x": st["x"], "z": np.zeros((m, q, n)), "lam": np.broadcast_to(st["lam"][:, :, None], (m, q, n)).copy(),
+             "s": st["s"], "mu": st["mu"], "h": st["h"], "p": st["p"], "nu": st["nu"], "x1": st["x1"]}
+    return oracle.kkt(P, par.replace(rho=tuple(rho)), dense)
+
+
+CASES = {
+    "config0": lambda: (W.config(0), W.Params()),
+    "phev_n400_q12": lambda: (W.phev_problem(400, 12), W.Params(rho=(1.0, 1.0 / 400, 1.0, 1.0))),
+    "plain_n2000_m4_q20": lambda: (W.random_problem(2000, 4, 20),
+                                   W.Params(rho=(1.0, 1.0 / 2000, 1.0, 1.0))),
+    "plain_n333_m3_q5": lambda: (W.random_problem(333, 3, 5, seed=8),
+                                 W.Params(rho=(1.0, 1.0 / 333, 1.0, 1.0))),
+}
+
+
+@pytest.mark.parametrize("precision", ["mixed", "mixed_fp64cubic"])
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_mixed_converges_to_the_oracle_solution(capi, oracle_lib, case, precision):
+    P, par = CASES[case]()
+    st_o, rep_o = oracle_lib.solve(P, par, threads=16)
+    assert rep_o["converged"]
+    k_o, _ = oracle_lib.kkt(P, par, st_o)
+    obj_o = oracle_lib.objective(P, st_o["x"])
+    with capi.Solver(P, par.replace(precision=precision)) as s:
+        res = s.solve(raise_on=(1, 2, 3, 4, 6))
+        st = s.state()
+        info = s.info()
+    assert res["converged"], (res, info)
+    rel_obj = abs(res["objective"] - obj_o) / max(1.0, abs(obj_o))
+    assert rel_obj <= OBJ_TOL, (rel_obj, res["objective"], obj_o)
+    k_g, terms = _kkt(oracle_lib, P, par, st, st["rho"])
+    assert k_g <= k_o + KKT_MARGIN, (k_g, k_o, terms)
+    assert info["fp64_escalations"] >= 0
+
+
+def test_mixed_checkpoint_resume_is_bitwise(capi):
+    P = W.random_problem(500, 3, 4, seed=42)
+    par = W.Params(rho=(1.0, 1.0 / 500, 1.0, 1.0), r_tol=0.0, s_tol=0.0, check_every=5, precision="mixed")
+    with capi.Solver(P, par.replace(max_iter=60)) as s:
+        s.solve(raise_on=(1, 2, 3, 4, 6))
+        straight = s.state()
+    with capi.Solver(P, par.replace(max_iter=25)) as s:
+        s.solve(raise_on=(1, 2, 3, 4, 6))
+        ck = s.state()
+    with capi.Solver(P, par.replace(max_iter=35)) as s:
+        s.solve(warm=ck, raise_on=(1, 2, 3, 4, 6))
+        resumed = s.state()
+    for k in ("x", "s", "mu", "lam", "zeta", "h", "p", "nu", "x1"):
+        assert np.array_equal(straight[k], resumed[k]), k
+
+
+def test_mixed_first_iterations_track_the_oracle(capi, oracle_lib):
+    """A few iterations from the zero start stay within FP32 rounding of the
+    FP64 trajectory (relative 1e-5)."""
+    P = W.random_problem(700, 2, 3, seed=43)
+    par = W.Params(rho=(1.0, 1.0 / 700, 1.0, 1.0), max_iter=5, r_tol=0.0, s_tol=0.0)
+    st_o, _ = oracle_lib.solve(P, par)
+    with capi.Solver(P, par.replace(precision="mixed")) as s:
+        s.solve(raise_on=(1, 2, 3, 4, 6))
+        st = s.state()
+    err = np.abs(st["x"] - st_o["x"]).max() / max(1.0, np.abs(st_o["x"]).max())
+    assert err < 1e-5, err
