@@ -52,12 +52,15 @@ def workload(cfg: int, precision: str):
 
 
 def bytes_per_iteration(P, prec: str) -> int:
-    """Algorithmic HBM bytes of one iteration (streamed arrays once each):
-    P * (6mnq + 2mn + 5nq): f2, f1, g2, g1 read, x read+write; bounds;
-    y read, s and mu read+write."""
-    w = 8 if prec == "fp64" else 4
+    """Algorithmic HBM bytes of one iteration (each streamed array once):
+    f2, f1, g2, g1 read and x read+write (6 per element), the bounds
+    (2 per (i, k)), y read and s, mu read+write (5 per column).  FP64: 8 bytes
+    each.  Mixed: 4 bytes each, except s and mu, which are float-float
+    (8 bytes)."""
     m, q, n = P.m, P.q, P.n
-    return w * (6 * m * n * q + 2 * m * n + 5 * n * q)
+    if prec == "fp64":
+        return 8 * (6 * m * n * q + 2 * m * n + 5 * n * q)
+    return 4 * (6 * m * n * q + 2 * m * n + n * q) + 8 * 4 * n * q
 
 
 class ClockSampler:
@@ -209,6 +212,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", type=int, default=1, choices=[0, 1, 2])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "mixed_fp64cubic"])
+    ap.add_argument("--max-iter", type=int, default=0,
+                    help="profiling only: cap the iterations of each solve (the line is then not a benchmark)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
@@ -229,6 +234,8 @@ def main():
     from paper_1903_10041_gb300 import capi
 
     P, par = workload(args.config, args.precision)
+    if args.max_iter:
+        par = par.replace(max_iter=args.max_iter)
     stream = torch.cuda.Stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     solver = capi.Solver(P, par)
@@ -319,6 +326,7 @@ def main():
                 "iters_per_solve": iters, "converged": conv, "objective": results[-1]["objective"],
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": args.steps,
+                "profiling_cap": args.max_iter or None,
                 "clocks": clk.summary()}
         print(json.dumps(line))
     solver.close()

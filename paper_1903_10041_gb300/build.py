@@ -20,10 +20,11 @@ LIB = os.path.join(HERE, "libadmm.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
+EXTRA = os.environ.get("ADMM_NVCC_FLAGS", "").split()  # extra nvcc flags (e.g. -DADMM_MIXED_VW=4)
 
 
 def _flags(verbose: bool):
-    f = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
+    f = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC] + EXTRA
     if verbose:
         f += ["-Xptxas", "-v"]
     return f

@@ -169,7 +169,7 @@ struct admm_handle {
     int *status = nullptr;
     double *info_host = nullptr; // pinned
     // launch shape
-    int grid = 0, slots = 0, rs = 0;
+    int grid = 0, nbmax = 0, rs = 0;
     int64_t chunk = 0, ncols = 0;
     size_t smem = 0;
 };
@@ -457,17 +457,17 @@ admm_status admm_create(const admm_problem *P, const admm_params *prm, admm_hand
     if (per_sm < 1) return bail(fail(ADMM_EUNSUPPORTED, "solve kernel cannot be resident (smem %zu B)", h->smem));
     h->rs = mixed ? ld : n;
     h->ncols = (int64_t)q * h->rs;
-    const int64_t unit = mixed ? 4 : 1;          // mixed: float4 quads of columns
-    const int64_t min_cols = mixed ? 128 : 32;   // at least a warp of work per CTA
+    const int64_t unit = mixed ? kMixedVW : 1;   // mixed: vectors of kMixedVW columns
+    const int64_t min_cols = mixed ? 32 * kMixedVW : 32; // at least a warp of work per CTA
     int64_t g = std::min<int64_t>((int64_t)h->nsm * per_sm, std::max<int64_t>(1, h->ncols / min_cols));
     h->chunk = ((h->ncols + g - 1) / g + unit - 1) / unit * unit;
     h->grid = (int)((h->ncols + h->chunk - 1) / h->chunk);
-    h->slots = 1;
-    for (int b = 0; b < h->grid; ++b) {
-        const int64_t c0 = (int64_t)b * h->chunk, c1 = std::min(c0 + h->chunk, h->ncols);
-        h->slots = std::max(h->slots, (int)((c1 - 1) / h->rs - c0 / h->rs + 1));
+    h->nbmax = 1;
+    for (int j = 0; j < q; ++j) {
+        const int64_t r0 = (int64_t)j * h->rs, r1 = r0 + h->rs - 1;
+        h->nbmax = std::max(h->nbmax, (int)(r1 / h->chunk - r0 / h->chunk + 1));
     }
-    TRY(cudaMalloc(&h->part, sizeof(double) * 2 * (size_t)h->grid * h->slots * m * 4));
+    TRY(cudaMalloc(&h->part, sizeof(double) * 2 * (size_t)q * h->nbmax * m * 4));
     TRY(cudaMalloc(&h->cpart, sizeof(double) * 2 * (size_t)h->grid * 4));
     st = reset_state(h);
     if (st != ADMM_OK) return bail(st);
@@ -539,7 +539,7 @@ admm_status admm_solve(admm_handle *h, const admm_state *warm, admm_result *out,
     a.rs = h->rs;
     a.ncols = h->ncols;
     a.chunk = h->chunk;
-    a.slots = h->slots;
+    a.nbmax = h->nbmax;
     a.grid = h->grid;
     a.f2 = h->f2;
     a.f1 = h->f1;

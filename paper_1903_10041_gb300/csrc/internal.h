@@ -12,6 +12,10 @@ constexpr int kBlock = 256;          // threads per CTA of the solve kernels
 constexpr int kWarps = kBlock / 32;
 constexpr int kMaxM = ADMM_MAX_M;
 constexpr int kInfo = 16;            // doubles of the per-solve info record
+#ifndef ADMM_MIXED_VW
+#define ADMM_MIXED_VW 2
+#endif
+constexpr int kMixedVW = ADMM_MIXED_VW; // columns per thread in the mixed kernels (2 or 4)
 
 // Offsets into the scalar state vector (doubles), for mq = m*q pairs:
 //   [0, 5mq)        lam, zeta, h, p, nu   (pair arrays, mq each)
@@ -29,14 +33,15 @@ struct SingleArgs {
     int rs;                    // row length of the column space: n (FP64) or ld (mixed, padded)
     int64_t ncols;             // q * rs columns (j, k)
     int64_t chunk;             // columns per CTA (contiguous in j-major order)
-    int slots;                 // partial-record slots per CTA (rows a chunk can touch)
+    int nbmax;                 // max CTAs whose chunks touch one row
     int grid;                  // CTAs
     const void *f2, *f1, *f0, *g2, *g1, *g0, *lo, *hi, *y;   // storage type of the precision
     const double *c, *sumg0;   // [m], [mq]
     void *x, *s, *mu;          // state arrays (storage type)
     void *s_lo, *mu_lo;        // mixed: low parts of the float-float column state s, mu
     double *scal;              // scalar state, in/out
-    double *part;              // [2][grid][slots][m][4] partial records (gsum, dmax, dmin, x0)
+    double *part;              // [2][q][nbmax][m][4] partial records (gsum, dmax, dmin, x0), row-major by
+                               // row j and position b - b0(j) of the CTA among those touching row j
     double *cpart;             // [2][grid][4] per-CTA column maxima and objective partials
     unsigned *bar;             // barrier counter (zeroed before the launch)
     int *status;               // 0 or an admm_status set by a device wait

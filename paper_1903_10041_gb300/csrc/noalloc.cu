@@ -201,14 +201,14 @@ extern "C" admm_status admm_solve_noalloc(const admm_problem *P, const admm_para
     const int64_t g = std::min<int64_t>((int64_t)nsm * per_sm, std::max<int64_t>(1, ncols / 32));
     const int64_t chunk = (ncols + g - 1) / g;
     const int grid = (int)((ncols + chunk - 1) / chunk);
-    int slots = 1;
-    for (int b = 0; b < grid; ++b) {
-        const int64_t c0 = (int64_t)b * chunk, c1 = std::min(c0 + chunk, ncols);
-        slots = std::max(slots, (int)((c1 - 1) / n - c0 / n + 1));
+    int nbmax = 1;
+    for (int j = 0; j < q; ++j) {
+        const int64_t r0 = (int64_t)j * n, r1 = r0 + n - 1;
+        nbmax = std::max(nbmax, (int)(r1 / chunk - r0 / chunk + 1));
     }
     // scratch layout (doubles, each region 32-double aligned)
     auto al = [](size_t v) { return (v + 31) / 32 * 32; };
-    const size_t n_part = al((size_t)2 * grid * slots * m * 4), n_cpart = al((size_t)2 * grid * 4);
+    const size_t n_part = al((size_t)2 * q * nbmax * m * 4), n_cpart = al((size_t)2 * grid * 4);
     const size_t n_scal = al((size_t)scal_size(m, q)), n_sumg0 = al((size_t)mq), n_info = al(kInfo), n_words = 32;
     const size_t need = n_part + n_cpart + n_scal + n_sumg0 + n_info + n_words;
     if (need > kScratchDoubles) {
@@ -252,7 +252,7 @@ extern "C" admm_status admm_solve_noalloc(const admm_problem *P, const admm_para
     a.rs = n;
     a.ncols = ncols;
     a.chunk = chunk;
-    a.slots = slots;
+    a.nbmax = nbmax;
     a.grid = grid;
     a.f2 = P->f2;
     a.f1 = P->f1;

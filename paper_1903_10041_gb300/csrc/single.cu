@@ -253,11 +253,28 @@ __device__ __forceinline__ FF ff_addf(FF a, float b)
 }
 __device__ __forceinline__ FF ff_neg(FF a) { return {-a.hi, -a.lo}; }
 
-template <int M, bool C64>
-__device__ __forceinline__ void quad32(const SingleArgs &a, const Sm &sm, int j, int k0, bool check, bool cold,
-                                       float mu_div, float rho1, float rho3, float rho4, float iq, float *ghi,
-                                       float *glo, float *dmx, float *dmn, float &cm_r, float &cm_s, unsigned &esc,
-                                       double *rec)
+// VW consecutive columns per thread (VW = 2 or 4), loaded as one vector.
+template <int VW> __device__ __forceinline__ void ldv(const float *p, float *v, bool ro)
+{
+    if constexpr (VW == 4) {
+        const float4 t = ro ? __ldg((const float4 *)p) : *(const float4 *)p;
+        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+    } else {
+        const float2 t = ro ? __ldg((const float2 *)p) : *(const float2 *)p;
+        v[0] = t.x; v[1] = t.y;
+    }
+}
+template <int VW> __device__ __forceinline__ void stv(float *p, const float *v)
+{
+    if constexpr (VW == 4) *(float4 *)p = make_float4(v[0], v[1], v[2], v[3]);
+    else *(float2 *)p = make_float2(v[0], v[1]);
+}
+
+template <int M, int VW, bool C64>
+__device__ __forceinline__ void vec32(const SingleArgs &a, const Sm &sm, int j, int k0, bool check, bool cold,
+                                      float mu_div, float rho1, float rho3, float rho4, float iq, float *ghi,
+                                      float *glo, float *dmx, float *dmn, float &cm_r, float &cm_s, unsigned &esc,
+                                      double *rec)
 {
     const int m = a.m, q = a.q, ld = a.ld, n = a.n;
     const float *__restrict__ F2 = (const float *)a.f2;
@@ -272,43 +289,52 @@ __device__ __forceinline__ void quad32(const SingleArgs &a, const Sm &sm, int j,
     float *SL = (float *)a.s_lo, *ML = (float *)a.mu_lo;
 
     const size_t col = (size_t)j * ld + k0;
-    const float4 y4 = ldg4(Y + col), s4 = ld4(Sv + col), m4 = ld4(MU + col);
-    const float4 sl4 = ld4(SL + col), ml4 = ld4(ML + col);
-    float yv[4] = {y4.x, y4.y, y4.z, y4.w}, st[4] = {s4.x, s4.y, s4.z, s4.w}, mu[4] = {m4.x, m4.y, m4.z, m4.w};
-    float stl[4] = {sl4.x, sl4.y, sl4.z, sl4.w}, mul[4] = {ml4.x, ml4.y, ml4.z, ml4.w};
+    float yv[VW], st[VW], mu[VW], stl[VW], mul[VW];
+    ldv<VW>(Y + col, yv, true);
+    ldv<VW>(Sv + col, st, false);
+    ldv<VW>(MU + col, mu, false);
+    ldv<VW>(SL + col, stl, false);
+    ldv<VW>(ML + col, mul, false);
     if (mu_div != 1.0f) {
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
+        for (int c = 0; c < VW; ++c) {
             mu[c] = mu[c] / mu_div;
             mul[c] = mul[c] / mu_div;
         }
     }
-    float xt[M][4], xs[M][4];
+    float xt[M][VW], xs[M][VW];
 #pragma unroll
     for (int i = 0; i < M; ++i)
         if (i < m) {
-            const float4 v = ld4(X + ((size_t)i * q + j) * ld + k0);
-            xt[i][0] = xs[i][0] = v.x;
-            xt[i][1] = xs[i][1] = v.y;
-            xt[i][2] = xs[i][2] = v.z;
-            xt[i][3] = xs[i][3] = v.w;
-        }
-    bool valid[4];
+            ldv<VW>(X + ((size_t)i * q + j) * ld + k0, xt[i], false);
 #pragma unroll
-    for (int c = 0; c < 4; ++c) valid[c] = k0 + c < n;
+            for (int c = 0; c < VW; ++c) xs[i][c] = xt[i][c];
+        }
+    bool valid[VW];
+#pragma unroll
+    for (int c = 0; c < VW; ++c) valid[c] = k0 + c < n;
 
 #pragma unroll
     for (int i = 0; i < M; ++i) {
         if (i < m) {
             const size_t e = ((size_t)i * q + j) * ld + k0;
-            const float4 A2 = ldg4(F2 + e), A1 = ldg4(F1 + e), B2 = ldg4(G2 + e), B1 = ldg4(G1 + e);
-            const float4 L4 = ldg4(LO + (size_t)i * ld + k0), H4 = ldg4(HI + (size_t)i * ld + k0);
-            const float4 Z4 = cold ? ldg4(G0 + e) : make_float4(0.f, 0.f, 0.f, 0.f);
+            float A2[VW], A1[VW], B2[VW], B1[VW], L4[VW], H4[VW], Z4[VW];
+            ldv<VW>(F2 + e, A2, true);
+            ldv<VW>(F1 + e, A1, true);
+            ldv<VW>(G2 + e, B2, true);
+            ldv<VW>(G1 + e, B1, true);
+            ldv<VW>(LO + (size_t)i * ld + k0, L4, true);
+            ldv<VW>(HI + (size_t)i * ld + k0, H4, true);
+            if (cold) ldv<VW>(G0 + e, Z4, true);
+            else {
+#pragma unroll
+                for (int c = 0; c < VW; ++c) Z4[c] = 0.0f;
+            }
             const int pr = i * q + j;
             const float uo = sm.uoff[pr];
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const float a2 = f4(A2, c), a1 = f4(A1, c), b2 = f4(B2, c), b1 = f4(B1, c), g0 = f4(Z4, c);
+            for (int c = 0; c < VW; ++c) {
+                const float a2 = A2[c], a1 = A1[c], b2 = B2[c], b1 = B1[c], g0 = Z4[c];
                 const float x0 = xt[i][c];
                 const float gq_old = (b2 * x0 + b1) * x0;
                 const float u = cold ? -g0 : gq_old + uo;
@@ -325,8 +351,8 @@ __device__ __forceinline__ void quad32(const SingleArgs &a, const Sm &sm, int j,
                     C += 0.5f * rho4;
                     D -= rho4 * (float)(sm.x1[i] + sm.nu[pr]);
                 }
-                const float xn = C64 ? quartic_min_fp64cubic(A, B, C, D, f4(L4, c), f4(H4, c), a.xmin_mode)
-                                     : quartic_min32(A, B, C, D, f4(L4, c), f4(H4, c), a.xmin_mode, esc);
+                const float xn = C64 ? quartic_min_fp64cubic(A, B, C, D, L4[c], H4[c], a.xmin_mode)
+                                     : quartic_min32(A, B, C, D, L4[c], H4[c], a.xmin_mode, esc);
                 xs[i][c] = xn;
                 if (valid[c]) {
                     float ghh, gll;
@@ -344,38 +370,39 @@ __device__ __forceinline__ void quad32(const SingleArgs &a, const Sm &sm, int j,
     // (e), (f) in float-float: the column state carries about 48 bits, so
     // mu's accumulation of ever smaller primal residuals is not lost to FP32
     // rounding and the dual residual term of s settles below 1e-6.
-    float sn[4], snl[4], mn[4], mnl[4];
+    float sn[VW], snl[VW], mn[VW], mnl[VW];
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        FF sx = {0.0f, 0.0f}, dx = {0.0f, 0.0f};
+    for (int c = 0; c < VW; ++c) {
+        FF sx = {0.0f, 0.0f};
 #pragma unroll
         for (int i = 0; i < M; ++i)
-            if (i < m) {
-                sx = ff_addf(sx, xs[i][c]);
-                dx = ff_add(dx, ff_two_sum(xs[i][c], -xt[i][c]));
-            }
+            if (i < m) sx = ff_addf(sx, xs[i][c]);
         const FF muf = {mu[c], mul[c]}, stf = {st[c], stl[c]};
         const FF v = ff_add(ff_addf(sx, -yv[c]), ff_neg(muf));       // sum_i x - y - mu
-        const FF s = v.hi > 0.0f ? v : FF{0.0f, 0.0f};                // (e)
-        const FF t = ff_addf(ff_add(s, ff_neg(sx)), yv[c]);           // s - sum_i x + y
+        const FF sv = v.hi > 0.0f ? v : FF{0.0f, 0.0f};               // (e)
+        const FF t = ff_addf(ff_add(sv, ff_neg(sx)), yv[c]);          // s - sum_i x + y
         const FF mnew = ff_add(muf, t);                                // (f)
-        sn[c] = s.hi;
-        snl[c] = s.lo;
+        sn[c] = sv.hi;
+        snl[c] = sv.lo;
         mn[c] = mnew.hi;
         mnl[c] = mnew.lo;
         if (check && valid[c]) {
             cm_r = fmaxf(cm_r, fabsf(t.hi + t.lo));
-            const FF d = ff_add(ff_add(s, ff_neg(stf)), ff_neg(dx));   // s - s~ - sum_i (x - x~)
+            FF dx = {0.0f, 0.0f};
+#pragma unroll
+            for (int i = 0; i < M; ++i)
+                if (i < m) dx = ff_add(dx, ff_two_sum(xs[i][c], -xt[i][c]));
+            const FF d = ff_add(ff_add(sv, ff_neg(stf)), ff_neg(dx));  // s - s~ - sum_i (x - x~)
             cm_s = fmaxf(cm_s, fabsf(d.hi + d.lo));
         }
     }
 #pragma unroll
     for (int i = 0; i < M; ++i)
-        if (i < m) *(float4 *)(X + ((size_t)i * q + j) * ld + k0) = make_float4(xs[i][0], xs[i][1], xs[i][2], xs[i][3]);
-    *(float4 *)(Sv + col) = make_float4(sn[0], sn[1], sn[2], sn[3]);
-    *(float4 *)(MU + col) = make_float4(mn[0], mn[1], mn[2], mn[3]);
-    *(float4 *)(SL + col) = make_float4(snl[0], snl[1], snl[2], snl[3]);
-    *(float4 *)(ML + col) = make_float4(mnl[0], mnl[1], mnl[2], mnl[3]);
+        if (i < m) stv<VW>(X + ((size_t)i * q + j) * ld + k0, xs[i]);
+    stv<VW>(Sv + col, sn);
+    stv<VW>(MU + col, mn);
+    stv<VW>(SL + col, snl);
+    stv<VW>(ML + col, mnl);
     if (k0 == 0) {
 #pragma unroll
         for (int i = 0; i < M; ++i)
@@ -417,6 +444,53 @@ __device__ __forceinline__ void flush_segment(double *rec, const double *gs, con
     __syncthreads();
 }
 
+// Mixed variant of the segment reduction, on the FP32 pipes: float-float
+// sums and FP32 max / min across the CTA in a fixed order; only the m
+// finished records are converted to FP64.
+template <int M>
+__device__ __forceinline__ void flush_segment32(double *rec, const float *ghi, const float *glo, const float *fmx,
+                                                const float *fmn, bool check, int m, const Sm &sm)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    float *red = (float *)sm.red; // [kWarps][kMaxM][4] floats fit in the double array
+#pragma unroll
+    for (int i = 0; i < M; ++i)
+        if (i < m) {
+            FF v = ff_norm(ghi[i], glo[i]);
+            float hi = fmx[i], lo = fmn[i];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const FF u = {__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+                v = ff_add(v, u);
+                if (check) {
+                    hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+                    lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+                }
+            }
+            if (lane == 0) {
+                red[(w * kMaxM + i) * 4 + 0] = v.hi;
+                red[(w * kMaxM + i) * 4 + 1] = v.lo;
+                red[(w * kMaxM + i) * 4 + 2] = hi;
+                red[(w * kMaxM + i) * 4 + 3] = lo;
+            }
+        }
+    __syncthreads();
+    if (threadIdx.x < m) {
+        const int i = threadIdx.x;
+        FF v = {0.0f, 0.0f};
+        float hi = -INFINITY, lo = INFINITY;
+        for (int ww = 0; ww < kWarps; ++ww) {
+            v = ff_add(v, FF{red[(ww * kMaxM + i) * 4 + 0], red[(ww * kMaxM + i) * 4 + 1]});
+            hi = fmaxf(hi, red[(ww * kMaxM + i) * 4 + 2]);
+            lo = fminf(lo, red[(ww * kMaxM + i) * 4 + 3]);
+        }
+        rec[i * 4 + 0] = (double)v.hi + (double)v.lo;
+        rec[i * 4 + 1] = check ? (double)hi : 0.0;
+        rec[i * 4 + 2] = check ? (double)lo : 0.0;
+    }
+    __syncthreads();
+}
+
 template <int M, int PREC> struct Bounds {
     static constexpr int minb = PREC == ADMM_FP64 ? 1 : 2;
 };
@@ -426,6 +500,7 @@ __global__ void __launch_bounds__(kBlock, (Bounds<M, PREC>::minb)) single_kernel
 {
     extern __shared__ double smem[];
     constexpr bool MIXED = PREC != ADMM_FP64;
+    constexpr int VW = kMixedVW;
     const int m = a.m, q = a.q, n = a.n, mq = m * q, rs = a.rs;
     const Sm sm = carve(smem, m, q);
     for (int t = threadIdx.x; t < scal_size(m, q); t += kBlock) smem[t] = a.scal[t];
@@ -450,12 +525,14 @@ __global__ void __launch_bounds__(kBlock, (Bounds<M, PREC>::minb)) single_kernel
         const bool cold = sm.flags[0] != 0.0;
         const double mu_div = sm.flags[1];
         double cm_r = 0.0, cm_s = 0.0;
+        float fcr_all = 0.0f, fcs_all = 0.0f;
 
         // ---- phase 1: element updates and segment partials --------------
         for (int j = jf; j <= jl; ++j) {
             const int64_t s0 = max(c0, (int64_t)j * rs), s1 = min(c1, (int64_t)(j + 1) * rs);
             double gs[M], dmx[M], dmn[M];
-            double *rec = a.part + ((size_t)(par * a.grid + blockIdx.x) * a.slots + (j - jf)) * m * 4;
+            const int pos = (int)blockIdx.x - (int)(((int64_t)j * rs) / a.chunk);
+            double *rec = a.part + ((size_t)(par * q + j) * a.nbmax + pos) * m * 4;
             if constexpr (!MIXED) {
 #pragma unroll
                 for (int i = 0; i < M; ++i) {
@@ -478,22 +555,22 @@ __global__ void __launch_bounds__(kBlock, (Bounds<M, PREC>::minb)) single_kernel
                 const float rho1 = (float)sm.rho[0], rho3 = (float)sm.rho[2], rho4 = (float)sm.rho[3];
                 const float iq = 1.0f / (float)q;
                 float fcr = 0.0f, fcs = 0.0f;
-                for (int64_t qq = s0 / 4 + threadIdx.x; qq < s1 / 4; qq += kBlock) {
-                    const int k0 = (int)(qq * 4 - (int64_t)j * rs);
+                for (int64_t qq = s0 / VW + threadIdx.x; qq < s1 / VW; qq += kBlock) {
+                    const int k0 = (int)(qq * VW - (int64_t)j * rs);
                     if (k0 >= n) continue;
-                    quad32<M, PREC == ADMM_MIXED_FP64CUBIC>(a, sm, j, k0, check, cold, (float)mu_div, rho1, rho3,
-                                                            rho4, iq, ghi, glo, fmx, fmn, fcr, fcs, esc, rec);
+                    vec32<M, VW, PREC == ADMM_MIXED_FP64CUBIC>(a, sm, j, k0, check, cold, (float)mu_div, rho1,
+                                                               rho3, rho4, iq, ghi, glo, fmx, fmn, fcr, fcs, esc,
+                                                               rec);
                 }
-#pragma unroll
-                for (int i = 0; i < M; ++i) {
-                    gs[i] = (double)ghi[i] + (double)glo[i];
-                    dmx[i] = (double)fmx[i];
-                    dmn[i] = (double)fmn[i];
-                }
-                cm_r = fmax(cm_r, (double)fcr);
-                cm_s = fmax(cm_s, (double)fcs);
+                fcr_all = fmaxf(fcr_all, fcr);
+                fcs_all = fmaxf(fcs_all, fcs);
+                flush_segment32<M>(rec, ghi, glo, fmx, fmn, check, m, sm);
             }
-            flush_segment<M>(rec, gs, dmx, dmn, check, m, sm);
+            if constexpr (!MIXED) flush_segment<M>(rec, gs, dmx, dmn, check, m, sm);
+        }
+        if (MIXED) {
+            cm_r = (double)fcr_all;
+            cm_s = (double)fcs_all;
         }
         if (check) {
             double v[2] = {cm_r, cm_s};
@@ -517,17 +594,19 @@ __global__ void __launch_bounds__(kBlock, (Bounds<M, PREC>::minb)) single_kernel
         for (int pr = threadIdx.x; pr < mq; pr += kBlock) {
             const int i = pr / q, j = pr - i * q;
             const int64_t rbeg = (int64_t)j * rs;
-            const int b0 = (int)(rbeg / a.chunk), b1 = (int)((rbeg + rs - 1) / a.chunk);
-            double S = 0.0, dmx = -INFINITY, dmn = INFINITY, x0 = 0.0;
-            for (int b = b0; b <= b1 && b < a.grid; ++b) {
-                const int slot = j - (int)(((int64_t)b * a.chunk) / rs);
-                const double *rec = a.part + ((size_t)(par * a.grid + b) * a.slots + slot) * m * 4 + i * 4;
-                S += ldcg(rec);
+            const int nb = (int)((rbeg + rs - 1) / a.chunk - rbeg / a.chunk) + 1;
+            const double *rec = a.part + ((size_t)(par * q + j) * a.nbmax) * m * 4 + i * 4;
+            const int stride = m * 4;
+            // records of row j, in CTA order; independent loads, fixed order of the sums
+            double S = 0.0, dmx = -INFINITY, dmn = INFINITY;
+            const double x0 = ldcg(rec + 3);
+#pragma unroll 8
+            for (int t = 0; t < nb; ++t) {
+                S += ldcg(rec + (size_t)t * stride);
                 if (check) {
-                    dmx = fmax(dmx, ldcg(rec + 1));
-                    dmn = fmin(dmn, ldcg(rec + 2));
+                    dmx = fmax(dmx, ldcg(rec + (size_t)t * stride + 1));
+                    dmn = fmin(dmn, ldcg(rec + (size_t)t * stride + 2));
                 }
-                if (b == b0) x0 = ldcg(rec + 3);
             }
             const double lam = sm.lam[pr], zeta = sm.zeta[pr], hh = sm.h[pr], pp = sm.p[pr];
             const double W = (S + a.sumg0[pr]) - (double)n * lam;     // 1'(g(x) - lambda)
