@@ -69,6 +69,7 @@ enum { ADMM_GAUSS_SEIDEL = 0, ADMM_JACOBI = 1 };
 
 #define ADMM_MAX_M 8          /* sources per instance */
 #define ADMM_MAX_PAIRS 1024   /* m*q per single instance */
+#define ADMM_BATCH_MAX_PAIRS 256 /* m*q per instance of a batch or server */
 
 typedef struct admm_problem {
     int32_t n, m, q;                 /* steps, sources, scenarios; all >= 1 */
@@ -196,6 +197,52 @@ admm_status admm_selftest_barrier_timeout(long long spin_ns, int grid, int *stat
  * finished.  No cudaMalloc, cudaFree or other allocating call is made. */
 admm_status admm_solve_noalloc(const admm_problem *prob, const admm_params *params, admm_state *state,
                                admm_result *out, void *stream);
+
+/* ---- Batched solves --------------------------------------------------
+ * Many independent instances of eq. (2), of uneven n, m and q, solved in one
+ * persistent launch (replayed from a CUDA graph) in ADMM_MIXED precision.
+ * The paper solves one instance at a time; batching is an addition.  Each
+ * instance runs the iteration (a)-(i) of App. A on its own team of threads
+ * (a whole CTA for instances above small_max_elements = m*q*n, one warp
+ * below it) and stops on its own stop test; its arithmetic depends only on
+ * its own shape and team kind, so it gives the same bits alone and in any
+ * mix with the same configuration. */
+typedef struct admm_batch admm_batch;
+typedef struct admm_batch_config {
+    int32_t warps_per_cta;       /* 4, 8 or 16 */
+    int32_t ctas_per_sm;         /* 0 = as many as fit */
+    int64_t small_max_elements;  /* instances with m*q*n <= this go to one-warp teams */
+} admm_batch_config;
+
+/* Validates every problem as admm_create does (m <= ADMM_MAX_M, m*q <=
+ * ADMM_BATCH_MAX_PAIRS), packs them into device memory owned by the batch
+ * (FP32 arrays; the problems may be host or device memory) and sets every
+ * instance to the zero start.  params->precision must be ADMM_MIXED;
+ * the settings apply to every instance.  Default configuration: 8 warps
+ * per CTA, small_max_elements 16384. */
+admm_status admm_batch_create(const admm_problem *probs, int32_t count, const admm_params *params,
+                              admm_batch **out);
+admm_status admm_batch_set_config(admm_batch *b, const admm_batch_config *cfg);
+admm_status admm_batch_get_config(admm_batch *b, admm_batch_config *cfg);
+/* Times each candidate configuration (warps per CTA x small threshold) on
+ * `trial_iters` iterations of this batch, keeps the fastest, and resets
+ * every instance to the zero start.  *chosen (may be NULL) receives it. */
+admm_status admm_batch_autotune(admm_batch *b, int32_t trial_iters, admm_batch_config *chosen);
+/* Enqueues the solve of every unfinished instance from its current state
+ * on `stream` (asynchronous; replays a CUDA graph captured on first use). */
+admm_status admm_batch_solve(admm_batch *b, void *stream);
+/* Waits for `stream` and fills results[0..count-1] (NULL allowed; x and x1
+ * buffers inside each result are filled when non-NULL).  Returns the first
+ * non-OK instance status, or ADMM_OK. */
+admm_status admm_batch_wait(admm_batch *b, void *stream, admm_result *results);
+/* Per-instance record as in admm_get_info (valid after admm_batch_wait). */
+admm_status admm_batch_get_info(admm_batch *b, int32_t idx, double *info, int32_t count);
+admm_status admm_batch_get_state(admm_batch *b, int32_t idx, admm_state *out);
+/* Loads a state (e.g. a warm start) into instance idx and marks it unfinished. */
+admm_status admm_batch_set_state(admm_batch *b, int32_t idx, const admm_state *in);
+/* Every instance back to the zero start; records cleared. */
+admm_status admm_batch_reset(admm_batch *b);
+admm_status admm_batch_destroy(admm_batch *b);
 
 /* Message of the last failing call on this thread ("" if none). */
 const char *admm_last_error(void);

@@ -333,3 +333,137 @@ def admm_solve_noalloc(prob_dev, par, state_dev: dict, x_out=None, x1_out=None, 
     state_dev["cold"] = bool(cs.cold)
     return {"status": st, "iters": res.iters, "converged": bool(res.converged), "objective": res.objective,
             "r": res.r, "sigma": res.sigma}
+
+
+# ---------------------------------------------------------------------------
+# batched solves
+# ---------------------------------------------------------------------------
+class admm_batch_config(C.Structure):
+    _fields_ = [("warps_per_cta", C.c_int32), ("ctas_per_sm", C.c_int32), ("small_max_elements", C.c_int64)]
+
+
+_B = C.c_void_p
+_lib.admm_batch_create.argtypes = [C.POINTER(admm_problem), C.c_int32, C.POINTER(admm_params), C.POINTER(_B)]
+_lib.admm_batch_set_config.argtypes = [_B, C.POINTER(admm_batch_config)]
+_lib.admm_batch_get_config.argtypes = [_B, C.POINTER(admm_batch_config)]
+_lib.admm_batch_autotune.argtypes = [_B, C.c_int32, C.POINTER(admm_batch_config)]
+_lib.admm_batch_solve.argtypes = [_B, C.c_void_p]
+_lib.admm_batch_wait.argtypes = [_B, C.c_void_p, C.POINTER(admm_result)]
+_lib.admm_batch_get_info.argtypes = [_B, C.c_int32, _dp, C.c_int32]
+_lib.admm_batch_get_state.argtypes = [_B, C.c_int32, C.POINTER(admm_state)]
+_lib.admm_batch_set_state.argtypes = [_B, C.c_int32, C.POINTER(admm_state)]
+_lib.admm_batch_reset.argtypes = [_B]
+_lib.admm_batch_destroy.argtypes = [_B]
+for _f in ("admm_batch_create", "admm_batch_set_config", "admm_batch_get_config", "admm_batch_autotune",
+           "admm_batch_solve", "admm_batch_wait", "admm_batch_get_info", "admm_batch_get_state",
+           "admm_batch_set_state", "admm_batch_reset", "admm_batch_destroy"):
+    getattr(_lib, _f).restype = C.c_int
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    return C.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
+
+
+def _cfg_dict(c: admm_batch_config) -> dict:
+    return {"warps_per_cta": c.warps_per_cta, "ctas_per_sm": c.ctas_per_sm,
+            "small_max_elements": c.small_max_elements}
+
+
+class Batch:
+    """Many instances solved together (admm_batch_* in admm.h); mixed precision."""
+
+    def __init__(self, problems, par=None, **kw):
+        self._keep: list = []
+        self.shapes = [(int(p.n), int(p.m), int(p.q)) for p in problems]
+        arr = (admm_problem * len(problems))(*[make_problem(p, self._keep) for p in problems])
+        pp = par if isinstance(par, admm_params) else make_params(par, **kw)
+        if pp.precision != PRECISION["mixed"]:
+            pp.precision = PRECISION["mixed"]
+        self.h = _B()
+        _check(_lib.admm_batch_create(arr, len(problems), C.byref(pp), C.byref(self.h)))
+        self._keep = []  # the batch holds its own copy of the data
+        self.count = len(problems)
+
+    def set_config(self, warps_per_cta=8, ctas_per_sm=0, small_max_elements=16384):
+        c = admm_batch_config(int(warps_per_cta), int(ctas_per_sm), int(small_max_elements))
+        _check(_lib.admm_batch_set_config(self.h, C.byref(c)))
+
+    def config(self) -> dict:
+        c = admm_batch_config()
+        _check(_lib.admm_batch_get_config(self.h, C.byref(c)))
+        return _cfg_dict(c)
+
+    def autotune(self, trial_iters: int = 30) -> dict:
+        c = admm_batch_config()
+        _check(_lib.admm_batch_autotune(self.h, int(trial_iters), C.byref(c)))
+        return _cfg_dict(c)
+
+    def solve(self, stream=None):
+        _check(_lib.admm_batch_solve(self.h, _stream_ptr(stream)))
+
+    def wait(self, stream=None, want_x: bool = False) -> list:
+        res = (admm_result * self.count)()
+        xs = []
+        if want_x:
+            for t, (n, m, q) in enumerate(self.shapes):
+                x = np.empty((m, q, n))
+                x1 = np.empty(m)
+                xs.append((x, x1))
+                res[t].x = x.ctypes.data_as(_dp)
+                res[t].x1 = x1.ctypes.data_as(_dp)
+                res[t].on_device = 0
+        st = _lib.admm_batch_wait(self.h, _stream_ptr(stream), res)
+        if st not in (ADMM_OK, ADMM_ENOTCONVERGED):
+            raise AdmmError(st, admm_last_error())
+        out = []
+        for t in range(self.count):
+            d = {"status": res[t].status, "iters": res[t].iters, "converged": bool(res[t].converged),
+                 "objective": res[t].objective, "r": res[t].r, "sigma": res[t].sigma}
+            if want_x:
+                d["x"], d["x1"] = xs[t]
+            out.append(d)
+        return out
+
+    def info(self, idx: int) -> dict:
+        buf = (C.c_double * 16)()
+        _check(_lib.admm_batch_get_info(self.h, int(idx), buf, 16))
+        return {k: buf[t] for t, k in enumerate(INFO_KEYS)}
+
+    def state(self, idx: int) -> dict:
+        n, m, q = self.shapes[idx]
+        st = {"x": np.empty((m, q, n)), "s": np.empty((q, n)), "mu": np.empty((q, n)),
+              "lam": np.empty((m, q)), "zeta": np.empty((m, q)), "h": np.empty((m, q)), "p": np.empty((m, q)),
+              "nu": np.empty((m, q)), "x1": np.empty(m), "rho": [0.0] * 4, "cold": False}
+        keep: list = []
+        cs = _state_struct(st, keep)
+        _check(_lib.admm_batch_get_state(self.h, int(idx), C.byref(cs)))
+        st["rho"] = [cs.rho[t] for t in range(4)]
+        st["cold"] = bool(cs.cold)
+        return st
+
+    def set_state(self, idx: int, st: dict):
+        keep: list = []
+        cs = _state_struct(st, keep)
+        _check(_lib.admm_batch_set_state(self.h, int(idx), C.byref(cs)))
+
+    def reset(self):
+        _check(_lib.admm_batch_reset(self.h))
+
+    def close(self):
+        if self.h:
+            _lib.admm_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

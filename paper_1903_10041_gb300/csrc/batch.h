@@ -1,0 +1,47 @@
+// Internal declarations of the batched solve kernel (batch.cu) for the host
+// code of the batch and serving APIs.  Not part of the public interface.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "internal.h"
+
+namespace admm_impl {
+
+constexpr int kWarpsMax = 16; // largest CTA of the batched kernel, in warps
+
+// One instance of a batch: sizes and offsets into the packed arrays.
+struct BatchInst {
+    int n, m, q, ld;          // ld: row stride (multiple of 4)
+    int64_t off_e;            // element arrays f2 f1 f0 g2 g1 g0 x: [m][q][ld] at off_e
+    int64_t off_b;            // bound arrays lo hi: [m][ld] at off_b
+    int64_t off_c;            // column arrays y s s_lo mu mu_lo: [q][ld] at off_c
+    int off_pair;             // sumg0: [m*q] at off_pair
+    int off_scal;             // scalar state: scal_size(m, q) doubles at off_scal
+    int off_src;              // c: [m] at off_src
+    int pad;
+};
+
+struct BatchArgs {
+    const BatchInst *inst;
+    const int *orderL;        // instances solved by whole-CTA teams, in queue order
+    const int *orderS;        // instances solved by one-warp teams, in queue order
+    int nL, nS;
+    int *qL, *qS;             // queue heads (zeroed before the launch)
+    const float *f2, *f1, *f0, *g2, *g1, *g0, *lo, *hi, *y;
+    float *x, *s, *s_lo, *mu, *mu_lo;
+    const double *c, *sumg0;
+    double *scal;             // per-instance scalar state (in/out)
+    double *out;              // per-instance record [id][kInfo]; [0] iterations so far, [14] finished
+    int slice_doubles;        // shared memory per warp-team slice
+    int iter_budget;          // > 0: stop every instance after this many more iterations
+    double r_tol, s_tol, tau;
+    int max_iter, check_every, xmin_mode, sweep, adapt;
+};
+
+size_t batch_slice_doubles(int max_m, int max_q);
+size_t batch_smem_bytes(int warps, size_t slice_doubles);
+int batch_blocks_per_sm(int warps, int mbound, size_t smem);
+cudaError_t launch_batch(int warps, int mbound, int grid, const BatchArgs &a, size_t smem, cudaStream_t st);
+
+} // namespace admm_impl

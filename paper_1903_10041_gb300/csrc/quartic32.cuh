@@ -40,7 +40,7 @@ __device__ __forceinline__ float cbrt_fast(float v)
 }
 
 // The FP64 closed form, out of line: taken only when FP32 overflows.
-__device__ __noinline__ float quartic_min_fallback64(float A, float B, float C, float D, float lo, float hi,
+static __device__ __noinline__ float quartic_min_fallback64(float A, float B, float C, float D, float lo, float hi,
                                                      int paper_mode)
 {
     return (float)quartic_min64((double)A, (double)B, (double)C, (double)D, (double)lo, (double)hi, paper_mode);
@@ -100,7 +100,7 @@ __device__ __forceinline__ float quartic_min_fp64cubic(float A, float B, float C
 }
 
 // The branch of Algorithm 1 decided in FP64 from the same A, B, C, D.
-__device__ __noinline__ int cubic_branch64(float A, float B, float C, float D)
+static __device__ __noinline__ int cubic_branch64(float A, float B, float C, float D)
 {
     const double inv64 = 1.0 / (double)A;
     const double bd = 0.75 * (double)B * inv64, cd = 0.5 * (double)C * inv64, dd = 0.25 * (double)D * inv64;

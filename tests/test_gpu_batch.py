@@ -1,0 +1,137 @@
+"""Batched solves (one persistent launch, one team per instance, mixed
+precision): every instance matches the FP64 oracle (objective to 1e-6
+relative, KKT within 1e-6 of the oracle's), gives the same bits alone and
+in the mix, and keeps doing so under every launch configuration the
+autotuner may pick."""
+import numpy as np
+import pytest
+
+from paper_1903_10041_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def capi():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1903_10041_gb300 import build
+    build.build()
+    from paper_1903_10041_gb300 import capi
+    return capi
+
+
+def small_batch(count=24, seed=1903):
+    """Instances of the batched workload recipe with n capped so the oracle
+    finishes in seconds; n spans both team kinds."""
+    probs = []
+    for t in range(count):
+        n, m, q = W.batch_shape(t, seed)
+        n = max(20, min(n, 600))
+        probs.append(W.random_problem(n, m, q, seed=seed * (1 << 32) + t))
+    return probs
+
+
+def par_for(P):
+    return W.Params(rho=(1.0, 1.0 / P.n, 1.0, 1.0), precision="mixed")
+
+
+def _kkt(oracle, P, par, st):
+    m, q, n = P.m, P.q, P.n
+    dense = {"x": st["x"], "z": np.zeros((m, q, n)), "lam": np.broadcast_to(st["lam"][:, :, None], (m, q, n)).copy(),
+             "s": st["s"], "mu": st["mu"], "h": st["h"], "p": st["p"], "nu": st["nu"], "x1": st["x1"]}
+    return oracle.kkt(P, par.replace(rho=tuple(st["rho"])), dense)[0]
+
+
+def test_batch_matches_the_oracle_per_instance(capi, oracle_lib):
+    probs = small_batch()
+    # one common rho_2 needs one common n scale: use each instance's own n by
+    # solving groups with equal settings; here rho_2 = 1/600 for all
+    par = W.Params(rho=(1.0, 1.0 / 600, 1.0, 1.0), precision="mixed")
+    with capi.Batch(probs, par) as B:
+        B.set_config(8, 0, 4096)
+        B.solve()
+        res = B.wait()
+        states = [B.state(t) for t in range(len(probs))]
+    kinds = {"small": 0, "large": 0}
+    for t, P in enumerate(probs):
+        kinds["small" if P.elements <= 4096 else "large"] += 1
+        st_o, rep_o = oracle_lib.solve(P, par.replace(precision="fp64"), threads=16)
+        assert rep_o["converged"] and res[t]["converged"], (t, res[t], rep_o["iters"])
+        obj_o = oracle_lib.objective(P, st_o["x"])
+        assert abs(res[t]["objective"] - obj_o) <= 1e-6 * max(1.0, abs(obj_o)), (t, res[t]["objective"], obj_o)
+        k_o = oracle_lib.kkt(P, par, st_o)[0]
+        assert _kkt(oracle_lib, P, par, states[t]) <= k_o + 1e-6, t
+    assert kinds["small"] > 0 and kinds["large"] > 0
+
+
+@pytest.mark.parametrize("cfg", [(8, 0, 4096), (4, 1, 0), (16, 0, 10**9)])
+def test_batch_result_is_the_same_alone_and_in_the_mix(capi, cfg):
+    probs = small_batch(16, seed=7)
+    par = W.Params(rho=(1.0, 1.0 / 600, 1.0, 1.0), precision="mixed")
+    with capi.Batch(probs, par) as B:
+        B.set_config(*cfg)
+        B.solve()
+        mix = B.wait(want_x=True)
+    for t in (0, 5, 11):
+        with capi.Batch([probs[t]], par) as B1:
+            B1.set_config(*cfg)
+            B1.solve()
+            alone = B1.wait(want_x=True)[0]
+        assert alone["iters"] == mix[t]["iters"]
+        assert np.array_equal(alone["x"], mix[t]["x"]), t
+        assert alone["objective"] == mix[t]["objective"]
+
+
+def test_batch_autotune_picks_a_valid_config_and_still_solves(capi, oracle_lib):
+    probs = small_batch(12, seed=11)
+    par = W.Params(rho=(1.0, 1.0 / 600, 1.0, 1.0), precision="mixed")
+    with capi.Batch(probs, par) as B:
+        cfg = B.autotune(trial_iters=20)
+        assert cfg["warps_per_cta"] in (4, 8, 16) and cfg["ctas_per_sm"] >= 1
+        B.solve()
+        res = B.wait()
+    for t in (0, 3):
+        st_o, _ = oracle_lib.solve(probs[t], par.replace(precision="fp64"), threads=16)
+        obj_o = oracle_lib.objective(probs[t], st_o["x"])
+        assert res[t]["converged"]
+        assert abs(res[t]["objective"] - obj_o) <= 1e-6 * max(1.0, abs(obj_o))
+
+
+def test_batch_equals_its_graph_replay_and_reset(capi):
+    probs = small_batch(10, seed=13)
+    par = W.Params(rho=(1.0, 1.0 / 600, 1.0, 1.0), precision="mixed")
+    with capi.Batch(probs, par) as B:
+        B.solve()
+        a = B.wait(want_x=True)
+        B.reset()
+        B.solve()
+        b = B.wait(want_x=True)
+    for u, v in zip(a, b):
+        assert u["iters"] == v["iters"] and np.array_equal(u["x"], v["x"])
+
+
+def test_batch_warm_start_from_a_state(capi):
+    probs = small_batch(6, seed=17)
+    par = W.Params(rho=(1.0, 1.0 / 600, 1.0, 1.0), precision="mixed")
+    with capi.Batch(probs, par) as B:
+        B.solve()
+        first = B.wait()
+        st = B.state(2)
+        B.set_state(2, st)           # restart instance 2 from its own solution
+        B.solve()
+        again = B.wait()
+    # from its own solution it converges within a few check intervals (a cold
+    # start takes thousands of iterations)
+    assert again[2]["converged"] and again[2]["iters"] <= 5 * par.check_every
+    assert first[2]["iters"] > 20 * par.check_every
+    assert again[0]["iters"] == first[0]["iters"]      # finished instances are left alone
+
+
+def test_batch_rejects_invalid_instances(capi):
+    probs = small_batch(3, seed=19)
+    probs[1].g2[0, 0, 0] = -1.0
+    with pytest.raises(capi.AdmmError) as e:
+        capi.Batch(probs, W.Params(precision="mixed"))
+    assert e.value.status == capi.ADMM_EINVAL
