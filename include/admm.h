@@ -47,7 +47,8 @@ typedef enum admm_status {
     ADMM_ECUDA = 3,          /* a CUDA runtime call failed */
     ADMM_ETIMEOUT = 4,       /* a bounded device-side wait gave up */
     ADMM_ENOTCONVERGED = 5,  /* max_iter reached; the result is still filled */
-    ADMM_EUNSUPPORTED = 6    /* sizes beyond this build's limits */
+    ADMM_EUNSUPPORTED = 6,   /* sizes beyond this build's limits */
+    ADMM_EPENDING = 7        /* a served request has not finished yet */
 } admm_status;
 
 /* Arithmetic of the per-element work (the stored state follows it). */
@@ -243,6 +244,47 @@ admm_status admm_batch_set_state(admm_batch *b, int32_t idx, const admm_state *i
 /* Every instance back to the zero start; records cleared. */
 admm_status admm_batch_reset(admm_batch *b);
 admm_status admm_batch_destroy(admm_batch *b);
+
+/* ---- Serving: continuous batching of re-solves --------------------------
+ * A request loop for model-predictive control: each request is an instance
+ * of eq. (2) (host arrays, copied at submit), optionally tied to a session
+ * (one controller).  A worker thread runs ticks of `tick_iters` iterations
+ * of the batched kernel over every instance on the GPU; between ticks it
+ * retires finished instances and admits queued requests in arrival order
+ * while the device store has room (memory-based admission; idle sessions
+ * are evicted least-recently-used first) and a slot is free.  A session
+ * keeps its instance resident after a solve, and its next request is
+ * warm-started from that state moved one step forward on the device (the
+ * receding horizon of Sec. II and Alg. 2); requests of a session run one at
+ * a time in order.  The paper runs one solve per sampling instant; the
+ * server is an addition.  ADMM_MIXED precision only. */
+typedef struct admm_server admm_server;
+typedef struct admm_server_config {
+    int64_t store_elements;      /* device store capacity, in elements m*q*ld (ld = n rounded up to 4) */
+    int32_t max_active;          /* instances on the GPU at once */
+    int32_t tick_iters;          /* iterations per tick */
+    int32_t max_m, max_q;        /* largest m and q a request may have (m*q <= ADMM_BATCH_MAX_PAIRS) */
+    admm_batch_config batch;     /* launch configuration of a tick */
+} admm_server_config;
+
+/* store 2^27 elements, 4096 active, 50 iterations per tick, max_m 4,
+ * max_q 20, 8 warps per CTA, small_max_elements 16384. */
+void admm_server_default_config(admm_server_config *cfg);
+admm_status admm_server_create(const admm_params *params, const admm_server_config *cfg, admm_server **out);
+/* Validates and queues a request; session >= 0 ties it to that session
+ * (warm start from the session's resident state when the shapes match),
+ * -1 for a one-off solve.  *ticket identifies it for admm_server_poll. */
+admm_status admm_server_submit(admm_server *s, const admm_problem *prob, int64_t session, int64_t *ticket);
+/* Waits up to wait_ms for a request.  ADMM_EPENDING if not finished; else
+ * fills `out` (status inside; x and x1 host buffers filled when non-NULL)
+ * and times[0..2] = seconds from submit to admission, seconds from submit
+ * to completion, 1 if warm-started; the ticket is then forgotten. */
+admm_status admm_server_poll(admm_server *s, int64_t ticket, int32_t wait_ms, admm_result *out, double *times);
+/* stats[0..6]: ticks, admitted, finished, active, queued, free fraction of
+ * the store, sessions. */
+admm_status admm_server_stats(admm_server *s, double *stats, int32_t count);
+/* Stops the worker (in-flight requests are dropped) and frees everything. */
+admm_status admm_server_destroy(admm_server *s);
 
 /* Message of the last failing call on this thread ("" if none). */
 const char *admm_last_error(void);

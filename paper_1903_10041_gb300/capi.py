@@ -467,3 +467,96 @@ class Batch:
 
     def __exit__(self, *a):
         self.close()
+
+
+# ---------------------------------------------------------------------------
+# serving
+# ---------------------------------------------------------------------------
+ADMM_EPENDING = 7
+STATUS_NAMES[7] = "EPENDING"
+
+
+class admm_server_config(C.Structure):
+    _fields_ = [("store_elements", C.c_int64), ("max_active", C.c_int32), ("tick_iters", C.c_int32),
+                ("max_m", C.c_int32), ("max_q", C.c_int32), ("batch", admm_batch_config)]
+
+
+_S = C.c_void_p
+_lib.admm_server_default_config.argtypes = [C.POINTER(admm_server_config)]
+_lib.admm_server_default_config.restype = None
+_lib.admm_server_create.argtypes = [C.POINTER(admm_params), C.POINTER(admm_server_config), C.POINTER(_S)]
+_lib.admm_server_submit.argtypes = [_S, C.POINTER(admm_problem), C.c_int64, C.POINTER(C.c_int64)]
+_lib.admm_server_poll.argtypes = [_S, C.c_int64, C.c_int32, C.POINTER(admm_result), _dp]
+_lib.admm_server_stats.argtypes = [_S, _dp, C.c_int32]
+_lib.admm_server_destroy.argtypes = [_S]
+for _f in ("admm_server_create", "admm_server_submit", "admm_server_poll", "admm_server_stats",
+           "admm_server_destroy"):
+    getattr(_lib, _f).restype = C.c_int
+
+
+class Server:
+    """Continuous-batching request loop (admm_server_* in admm.h)."""
+
+    def __init__(self, par=None, store_elements=1 << 27, max_active=4096, tick_iters=50, max_m=4, max_q=20,
+                 warps_per_cta=8, ctas_per_sm=0, small_max_elements=16384, **kw):
+        pp = par if isinstance(par, admm_params) else make_params(par, **kw)
+        pp.precision = PRECISION["mixed"]
+        cfg = admm_server_config()
+        _lib.admm_server_default_config(C.byref(cfg))
+        cfg.store_elements, cfg.max_active, cfg.tick_iters = int(store_elements), int(max_active), int(tick_iters)
+        cfg.max_m, cfg.max_q = int(max_m), int(max_q)
+        cfg.batch = admm_batch_config(int(warps_per_cta), int(ctas_per_sm), int(small_max_elements))
+        self.h = _S()
+        _check(_lib.admm_server_create(C.byref(pp), C.byref(cfg), C.byref(self.h)))
+        self._shapes = {}
+
+    def submit(self, prob, session: int = -1) -> int:
+        keep: list = []
+        cp = make_problem(prob, keep)
+        t = C.c_int64()
+        _check(_lib.admm_server_submit(self.h, C.byref(cp), int(session), C.byref(t)))
+        self._shapes[t.value] = (int(prob.n), int(prob.m), int(prob.q))
+        return t.value
+
+    def poll(self, ticket: int, wait_ms: int = 0, want_x: bool = False):
+        """None while pending; else a result dict (with x, x1 if want_x)."""
+        n, m, q = self._shapes[ticket]
+        res = admm_result()
+        x = x1 = None
+        if want_x:
+            x, x1 = np.empty((m, q, n)), np.empty(m)
+            res.x, res.x1 = x.ctypes.data_as(_dp), x1.ctypes.data_as(_dp)
+        times = (C.c_double * 3)()
+        st = _lib.admm_server_poll(self.h, int(ticket), int(wait_ms), C.byref(res), times)
+        if st == ADMM_EPENDING:
+            return None
+        del self._shapes[ticket]
+        d = {"status": res.status if st == ADMM_OK else st, "iters": res.iters, "converged": bool(res.converged),
+             "objective": res.objective, "r": res.r, "sigma": res.sigma, "admit_s": times[0],
+             "latency_s": times[1], "warm": bool(times[2])}
+        if want_x:
+            d["x"], d["x1"] = x, x1
+        return d
+
+    def stats(self) -> dict:
+        buf = (C.c_double * 7)()
+        _check(_lib.admm_server_stats(self.h, buf, 7))
+        keys = ("ticks", "admitted", "finished", "active", "queued", "store_free_frac", "sessions")
+        return {k: buf[t] for t, k in enumerate(keys)}
+
+    def close(self):
+        if self.h:
+            _lib.admm_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

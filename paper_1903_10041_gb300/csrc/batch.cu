@@ -310,13 +310,14 @@ template <int NW, int M> __global__ void __launch_bounds__(NW * 32, 16 / NW) bat
 {
     extern __shared__ double smem[];
     __shared__ int s_item;
+    const int nL = a.nLS ? a.nLS[0] : a.nL, nS = a.nLS ? a.nLS[1] : a.nS;
     // Large instances: the whole CTA is one team.
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(a.qL, 1);
         __syncthreads();
         const int item = s_item;
         __syncthreads();
-        if (item >= a.nL) break;
+        if (item >= nL) break;
         solve_instance<NW * 32, M>(a, a.orderL[item], smem, threadIdx.x);
     }
     // Small instances: each warp is a team with its own slice.
@@ -326,7 +327,7 @@ template <int NW, int M> __global__ void __launch_bounds__(NW * 32, 16 / NW) bat
         int item = 0;
         if (lane == 0) item = atomicAdd(a.qS, 1);
         item = __shfl_sync(0xffffffffu, item, 0);
-        if (item >= a.nS) break;
+        if (item >= nS) break;
         solve_instance<32, M>(a, a.orderS[item], slice, lane);
     }
 }
@@ -349,7 +350,53 @@ void *batch_pick(int warps, int mb)
     }
 }
 
+// Receding-horizon warm start (Sec. II, Alg. 2): the previous solution of a
+// controller moved one step forward in place (x_k <- x_{k+1}, last step
+// kept; the same for s and mu), x_1^(i) reset to the mean of the new first
+// moves, cold flag cleared.  One CTA per instance.
+__global__ void shift_state_kernel(const BatchInst *inst, const int *ids, int count, float *x, float *s, float *s_lo,
+                                   float *mu, float *mu_lo, double *scal)
+{
+    for (int t = blockIdx.x; t < count; t += gridDim.x) {
+        const BatchInst I = inst[ids[t]];
+        const int n = I.n, rows_e = I.m * I.q;
+        // rows of x, then rows of s, s_lo, mu, mu_lo; each shifted left by one
+        for (int r = 0; r < rows_e + 4 * I.q; ++r) {
+            float *row;
+            if (r < rows_e) row = x + I.off_e + (int64_t)r * I.ld;
+            else {
+                const int c = (r - rows_e) / I.q, j = (r - rows_e) % I.q;
+                float *base = c == 0 ? s : (c == 1 ? s_lo : (c == 2 ? mu : mu_lo));
+                row = base + I.off_c + (int64_t)j * I.ld;
+            }
+            for (int k0 = 0; k0 < n - 1; k0 += blockDim.x) {
+                const int k = k0 + threadIdx.x;
+                const float v = k < n - 1 ? row[k + 1] : 0.0f;
+                __syncthreads();
+                if (k < n - 1) row[k] = v;
+                __syncthreads();
+            }
+        }
+        double *sc = scal + I.off_scal;
+        const int mq = I.m * I.q;
+        if (threadIdx.x < I.m) {
+            const int i = threadIdx.x;
+            double sum = 0.0;
+            for (int j = 0; j < I.q; ++j) sum += (double)x[I.off_e + ((int64_t)i * I.q + j) * I.ld];
+            sc[5 * mq + i] = sum / (double)I.q;
+        }
+        if (threadIdx.x == 0) sc[5 * mq + I.m + 4] = 0.0;
+        __syncthreads();
+    }
+}
+
 } // namespace
+
+void launch_shift_state(const BatchInst *inst, const int *ids, int count, float *x, float *s, float *s_lo, float *mu,
+                        float *mu_lo, double *scal, cudaStream_t st)
+{
+    if (count > 0) shift_state_kernel<<<std::min(count, 1024), 256, 0, st>>>(inst, ids, count, x, s, s_lo, mu, mu_lo, scal);
+}
 
 size_t batch_slice_doubles(int max_m, int max_q)
 {

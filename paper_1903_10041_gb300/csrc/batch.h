@@ -27,6 +27,7 @@ struct BatchArgs {
     const int *orderL;        // instances solved by whole-CTA teams, in queue order
     const int *orderS;        // instances solved by one-warp teams, in queue order
     int nL, nS;
+    const int *nLS;           // if non-null, {nL, nS} are read from device memory (graph replays)
     int *qL, *qS;             // queue heads (zeroed before the launch)
     const float *f2, *f1, *f0, *g2, *g1, *g0, *lo, *hi, *y;
     float *x, *s, *s_lo, *mu, *mu_lo;
@@ -39,9 +40,17 @@ struct BatchArgs {
     int max_iter, check_every, xmin_mode, sweep, adapt;
 };
 
+// Kernel variant (register arrays for M sources) of a batch or server: 4 for
+// every m <= 4, else 8.  It must not depend on which instances share a
+// launch, so that an instance gives the same bits alone and in any mix.
+inline int batch_mbound(int max_m) { return max_m <= 4 ? 4 : 8; }
+
 size_t batch_slice_doubles(int max_m, int max_q);
 size_t batch_smem_bytes(int warps, size_t slice_doubles);
 int batch_blocks_per_sm(int warps, int mbound, size_t smem);
 cudaError_t launch_batch(int warps, int mbound, int grid, const BatchArgs &a, size_t smem, cudaStream_t st);
+// Moves the state of instances ids[0..count-1] one step forward (receding horizon).
+void launch_shift_state(const BatchInst *inst, const int *ids, int count, float *x, float *s, float *s_lo, float *mu,
+                        float *mu_lo, double *scal, cudaStream_t st);
 
 } // namespace admm_impl

@@ -135,7 +135,7 @@ admm_status build_queues(admm_batch *b)
     all.insert(all.end(), S.begin(), S.end());
     BTRY(cudaMemcpy(b->d_order, all.data(), sizeof(int) * std::max<size_t>(all.size(), 1), cudaMemcpyHostToDevice));
     // launch shape
-    const int mb = single_mbound(b->max_m);
+    const int mb = batch_mbound(b->max_m);
     b->smem = batch_smem_bytes(b->cfg.warps_per_cta, b->slice);
     const int per_sm = batch_blocks_per_sm(b->cfg.warps_per_cta, mb, b->smem);
     if (per_sm < 1) return bfail(ADMM_EUNSUPPORTED, "batched kernel cannot be resident with this configuration");
@@ -183,7 +183,7 @@ admm_status ensure_graph(admm_batch *b)
     cudaGraph_t g = nullptr;
     BTRY(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaMemsetAsync(b->d_q, 0, 2 * sizeof(int), b->cap);
-    if (e == cudaSuccess) e = launch_batch(b->cfg.warps_per_cta, single_mbound(b->max_m), b->grid, a, b->smem, b->cap);
+    if (e == cudaSuccess) e = launch_batch(b->cfg.warps_per_cta, batch_mbound(b->max_m), b->grid, a, b->smem, b->cap);
     cudaError_t e2 = cudaStreamEndCapture(b->cap, &g);
     if (e != cudaSuccess || e2 != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
@@ -433,7 +433,7 @@ admm_status admm_batch_autotune(admm_batch *b, int32_t trial_iters, admm_batch_c
             const BatchArgs a = make_args(b);
             cudaMemset(b->d_q, 0, 2 * sizeof(int));
             cudaEventRecord(e0, b->cap);
-            cudaError_t e = launch_batch(w, single_mbound(b->max_m), b->grid, a, b->smem, b->cap);
+            cudaError_t e = launch_batch(w, batch_mbound(b->max_m), b->grid, a, b->smem, b->cap);
             cudaEventRecord(e1, b->cap);
             if (e != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) continue;
             float ms = 0.0f;

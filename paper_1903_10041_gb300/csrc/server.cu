@@ -1,0 +1,560 @@
+// Serving: continuous batching of MPC re-solves (admm_server_* in admm.h).
+//
+// Requests (a problem, optionally tied to a session = one controller) are
+// validated and packed to FP32 on the submitting thread, then queued.  A
+// worker thread runs ticks: it admits queued requests in arrival order
+// while the device store has room and a slot is free (memory-based
+// admission; idle sessions are evicted least-recently-used first when the
+// store is full), replays a CUDA graph that runs `tick_iters` iterations of
+// the batched kernel on every active instance, and retires the instances
+// that finished (converged or out of iterations), copying their results to
+// the host.  Requests that arrive while others are on the GPU join at the
+// next tick.  A session keeps its instance's state resident on the device
+// after a solve; the next request of that session is warm-started from it,
+// moved one step forward on the device (the receding horizon of Sec. II and
+// Alg. 2).  An instance's arithmetic depends only on its own shape and team
+// kind, so its result is the same alone and in any mix.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "store.h"
+
+using namespace admm_impl;
+
+namespace {
+
+double now_s()
+{
+    using namespace std::chrono;
+    return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+struct Request {
+    int64_t ticket = 0, session = -1;
+    Staged staged;
+    double t_submit = 0, t_admit = 0, t_finish = 0;
+    int slot = -1;
+    bool warm = false, done = false;
+    admm_status status = ADMM_OK;
+    double info[kInfo] = {};
+    std::vector<double> x, x1;
+};
+
+struct Session {
+    BatchInst inst{};
+    bool resident = false;
+    bool busy = false;
+    double last_used = 0;
+};
+
+} // namespace
+
+struct admm_server {
+    admm_params prm{};
+    admm_server_config cfg{};
+    int dev = 0, nsm = 0, grid = 0, mbound = 8;
+    size_t slice = 0, smem = 0;
+    Store store;
+    cudaStream_t st = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    BatchInst *d_inst = nullptr, *h_inst = nullptr;
+    int *d_order = nullptr, *h_order = nullptr; // [0, max) CTA-team queue, [max, 2 max) warp-team queue
+    int *d_counts = nullptr, *h_counts = nullptr, *d_q = nullptr;
+    int *d_shift = nullptr, *h_shift = nullptr;
+    double *d_out = nullptr, *h_out = nullptr, *d_tmp = nullptr;
+    size_t tmp_n = 0;
+    float *pinned = nullptr;
+    size_t pinned_n = 0;
+
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<std::shared_ptr<Request>> pending;
+    std::map<int64_t, std::shared_ptr<Request>> reqs;
+    std::vector<std::shared_ptr<Request>> active; // by slot
+    std::vector<int> free_slots;
+    std::map<int64_t, Session> sessions;
+    int64_t next_ticket = 1;
+    bool stop = false;
+    double stats[8] = {};
+    std::string worker_error;
+    std::thread worker;
+};
+
+namespace {
+
+admm_status sfail(admm_status s, const std::string &msg)
+{
+    set_last_error(msg.c_str());
+    return s;
+}
+
+cudaError_t ensure_tmp(admm_server *S, size_t n)
+{
+    if (S->tmp_n >= n) return cudaSuccess;
+    if (S->d_tmp) cudaFree(S->d_tmp);
+    S->d_tmp = nullptr;
+    S->tmp_n = 0;
+    cudaError_t e = cudaMalloc(&S->d_tmp, n * sizeof(double));
+    if (e == cudaSuccess) S->tmp_n = n;
+    return e;
+}
+
+cudaError_t ensure_pinned(admm_server *S, size_t n)
+{
+    if (S->pinned_n >= n) return cudaSuccess;
+    if (S->pinned) cudaFreeHost(S->pinned);
+    S->pinned = nullptr;
+    S->pinned_n = 0;
+    cudaError_t e = cudaMallocHost(&S->pinned, n * sizeof(float));
+    if (e == cudaSuccess) S->pinned_n = n;
+    return e;
+}
+
+// Reserves store room for a request, evicting idle resident sessions
+// (least recently used first) when needed.  Caller holds no lock; only the
+// worker thread touches the store and sessions' allocations.
+bool place_with_eviction(admm_server *S, const Staged &st, BatchInst &I, int64_t keep_session)
+{
+    for (;;) {
+        if (S->store.place(st.n, st.m, st.q, I)) return true;
+        int64_t victim = -1;
+        double oldest = 1e300;
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            for (auto &kv : S->sessions)
+                if (kv.first != keep_session && kv.second.resident && !kv.second.busy && kv.second.last_used < oldest) {
+                    oldest = kv.second.last_used;
+                    victim = kv.first;
+                }
+            if (victim < 0) return false;
+            S->store.release(S->sessions[victim].inst);
+            S->sessions[victim].resident = false;
+        }
+    }
+}
+
+void worker_loop(admm_server *S)
+{
+    cudaSetDevice(S->dev);
+    const int maxa = S->cfg.max_active;
+    std::vector<int> shift_ids;
+    for (;;) {
+        std::vector<std::shared_ptr<Request>> admit;
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            S->cv_work.wait(lk, [&] {
+                const bool any_active = std::any_of(S->active.begin(), S->active.end(), [](auto &p) { return (bool)p; });
+                return S->stop || any_active || !S->pending.empty();
+            });
+            if (S->stop) return;
+            // FIFO admission: take the head while a slot is free; a session
+            // with a solve in flight keeps its later requests queued.
+            while (!S->pending.empty() && !S->free_slots.empty() && (int)admit.size() < maxa) {
+                auto r = S->pending.front();
+                if (r->session >= 0 && S->sessions[r->session].busy) break;
+                S->pending.pop_front();
+                if (r->session >= 0) S->sessions[r->session].busy = true;
+                admit.push_back(r);
+                r->slot = S->free_slots.back();
+                S->free_slots.pop_back();
+            }
+        }
+        // place and upload the admitted requests (worker-only state)
+        shift_ids.clear();
+        std::vector<std::shared_ptr<Request>> back_to_queue;
+        for (auto &r : admit) {
+            const Staged &sg = r->staged;
+            BatchInst I{};
+            bool reuse = false;
+            if (r->session >= 0) {
+                std::lock_guard<std::mutex> lk(S->mu);
+                Session &ss = S->sessions[r->session];
+                if (ss.resident && ss.inst.n == sg.n && ss.inst.m == sg.m && ss.inst.q == sg.q) {
+                    I = ss.inst;
+                    reuse = true;
+                }
+            }
+            if (!reuse && !place_with_eviction(S, sg, I, r->session)) {
+                back_to_queue.push_back(r); // store full: wait for a later tick
+                continue;
+            }
+            const InstSizes z = inst_sizes(sg.n, sg.m, sg.q);
+            cudaError_t e = ensure_pinned(S, 7 * (size_t)z.e + 2 * (size_t)z.b + (size_t)z.c);
+            if (e == cudaSuccess) {
+                if (reuse) {
+                    // new problem data, but keep x, s, mu and the scalar state
+                    const Staged &keep = sg; // f, g, bounds, y and c are replaced; x, s, mu, scalars kept
+                    float *dst_e[6] = {S->store.f2, S->store.f1, S->store.f0, S->store.g2, S->store.g1, S->store.g0};
+                    e = cudaStreamSynchronize(S->st);
+                    size_t at = 0;
+                    for (int t = 0; t < 6 && e == cudaSuccess; ++t) {
+                        std::memcpy(S->pinned + at, keep.e[t].data(), sizeof(float) * z.e);
+                        e = cudaMemcpyAsync(dst_e[t] + I.off_e, S->pinned + at, sizeof(float) * z.e,
+                                            cudaMemcpyHostToDevice, S->st);
+                        at += z.e;
+                    }
+                    float *dst_b[2] = {S->store.lo, S->store.hi};
+                    for (int t = 0; t < 2 && e == cudaSuccess; ++t) {
+                        std::memcpy(S->pinned + at, keep.b[t].data(), sizeof(float) * z.b);
+                        e = cudaMemcpyAsync(dst_b[t] + I.off_b, S->pinned + at, sizeof(float) * z.b,
+                                            cudaMemcpyHostToDevice, S->st);
+                        at += z.b;
+                    }
+                    if (e == cudaSuccess) {
+                        std::memcpy(S->pinned + at, keep.y.data(), sizeof(float) * z.c);
+                        e = cudaMemcpyAsync(S->store.y + I.off_c, S->pinned + at, sizeof(float) * z.c,
+                                            cudaMemcpyHostToDevice, S->st);
+                    }
+                    if (e == cudaSuccess)
+                        e = cudaMemcpyAsync(S->store.sumg0 + I.off_pair, keep.sumg0.data(), sizeof(double) * z.p,
+                                            cudaMemcpyHostToDevice, S->st);
+                    if (e == cudaSuccess)
+                        e = cudaMemcpyAsync(S->store.c + I.off_src, keep.c.data(), sizeof(double) * z.m,
+                                            cudaMemcpyHostToDevice, S->st);
+                    if (e == cudaSuccess) e = cudaStreamSynchronize(S->st);
+                    r->warm = true;
+                    shift_ids.push_back(r->slot);
+                } else {
+                    e = S->store.upload(I, sg, S->prm, S->pinned, S->pinned_n, S->st);
+                }
+            }
+            if (e != cudaSuccess) {
+                if (!reuse) S->store.release(I);
+                std::lock_guard<std::mutex> lk(S->mu);
+                S->free_slots.push_back(r->slot);
+                r->slot = -1;
+                if (r->session >= 0) S->sessions[r->session].busy = false;
+                S->worker_error = cudaGetErrorString(e);
+                r->status = ADMM_ECUDA;
+                r->done = true;
+                r->t_finish = now_s();
+                S->cv_done.notify_all();
+                continue;
+            }
+            S->h_inst[r->slot] = I;
+            cudaMemcpyAsync(S->d_inst + r->slot, &S->h_inst[r->slot], sizeof(BatchInst), cudaMemcpyHostToDevice, S->st);
+            cudaMemsetAsync(S->d_out + (size_t)r->slot * kInfo, 0, sizeof(double) * kInfo, S->st);
+            if (r->session >= 0) {
+                std::lock_guard<std::mutex> lk(S->mu);
+                Session &ss = S->sessions[r->session];
+                ss.inst = I;
+                ss.resident = true;
+            }
+            r->t_admit = now_s();
+            std::lock_guard<std::mutex> lk(S->mu);
+            S->active[r->slot] = r;
+            S->stats[1] += 1;
+        }
+        if (!back_to_queue.empty()) {
+            std::lock_guard<std::mutex> lk(S->mu);
+            const bool any_active = std::any_of(S->active.begin(), S->active.end(), [](auto &p) { return (bool)p; });
+            for (auto it = back_to_queue.rbegin(); it != back_to_queue.rend(); ++it) {
+                S->free_slots.push_back((*it)->slot);
+                (*it)->slot = -1;
+                if ((*it)->session >= 0) S->sessions[(*it)->session].busy = false;
+                if (any_active) {
+                    S->pending.push_front(*it); // retried when running instances free the store
+                } else {
+                    // nothing runs and every idle session is evicted: it can never fit
+                    (*it)->status = ADMM_ENOMEM;
+                    (*it)->done = true;
+                    (*it)->t_finish = now_s();
+                }
+            }
+            S->cv_done.notify_all();
+        }
+        if (!shift_ids.empty()) {
+            std::copy(shift_ids.begin(), shift_ids.end(), S->h_shift);
+            cudaMemcpyAsync(S->d_shift, S->h_shift, sizeof(int) * shift_ids.size(), cudaMemcpyHostToDevice, S->st);
+            launch_shift_state(S->d_inst, S->d_shift, (int)shift_ids.size(), S->store.x, S->store.s, S->store.s_lo,
+                               S->store.mu, S->store.mu_lo, S->store.scal, S->st);
+        }
+        // queues of the active instances for this tick
+        int nL = 0, nS = 0;
+        std::vector<int> ids;
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            for (int s = 0; s < maxa; ++s)
+                if (S->active[s]) ids.push_back(s);
+        }
+        auto work = [&](int s) { return (int64_t)S->h_inst[s].m * S->h_inst[s].q * S->h_inst[s].ld; };
+        std::sort(ids.begin(), ids.end(), [&](int u, int v) { return work(u) != work(v) ? work(u) > work(v) : u < v; });
+        for (int s : ids) {
+            const int64_t el = (int64_t)S->h_inst[s].m * S->h_inst[s].q * S->h_inst[s].n;
+            if (el > S->cfg.batch.small_max_elements) S->h_order[nL++] = s;
+        }
+        for (int s : ids) {
+            const int64_t el = (int64_t)S->h_inst[s].m * S->h_inst[s].q * S->h_inst[s].n;
+            if (el <= S->cfg.batch.small_max_elements) S->h_order[maxa + nS++] = s;
+        }
+        if (ids.empty()) continue;
+        S->h_counts[0] = nL;
+        S->h_counts[1] = nS;
+        cudaMemcpyAsync(S->d_order, S->h_order, sizeof(int) * nL, cudaMemcpyHostToDevice, S->st);
+        cudaMemcpyAsync(S->d_order + maxa, S->h_order + maxa, sizeof(int) * nS, cudaMemcpyHostToDevice, S->st);
+        cudaMemcpyAsync(S->d_counts, S->h_counts, 2 * sizeof(int), cudaMemcpyHostToDevice, S->st);
+        cudaError_t e = cudaGraphLaunch(S->exec, S->st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(S->h_out, S->d_out, sizeof(double) * kInfo * maxa, cudaMemcpyDeviceToHost, S->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(S->st);
+        S->stats[0] += 1;
+        // retire finished instances
+        for (int s : ids) {
+            const double *o = S->h_out + (size_t)s * kInfo;
+            if (e == cudaSuccess && o[14] == 0.0) continue;
+            std::shared_ptr<Request> r;
+            {
+                std::lock_guard<std::mutex> lk(S->mu);
+                r = S->active[s];
+            }
+            const BatchInst I = S->h_inst[s];
+            if (e == cudaSuccess) {
+                std::memcpy(r->info, o, sizeof(double) * kInfo);
+                r->x.resize((size_t)I.m * I.q * I.n);
+                r->x1.resize(I.m);
+                admm_state so{};
+                so.x = r->x.data();
+                so.x1 = r->x1.data();
+                cudaError_t e2 = ensure_tmp(S, r->x.size());
+                if (e2 == cudaSuccess) e2 = store_get_state(S->store, I, &so, S->d_tmp, S->st);
+                r->status = e2 != cudaSuccess ? ADMM_ECUDA
+                                              : (o[12] != 0.0 ? (admm_status)(int)o[12]
+                                                              : (o[1] != 0.0 ? ADMM_OK : ADMM_ENOTCONVERGED));
+            } else {
+                r->status = ADMM_ECUDA;
+                S->worker_error = cudaGetErrorString(e);
+            }
+            std::lock_guard<std::mutex> lk(S->mu);
+            if (r->session >= 0) {
+                Session &ss = S->sessions[r->session];
+                ss.busy = false;
+                ss.last_used = now_s();
+            } else {
+                S->store.release(I);
+            }
+            S->active[s] = nullptr;
+            S->free_slots.push_back(s);
+            r->t_finish = now_s();
+            r->done = true;
+            S->stats[2] += 1;
+        }
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            S->cv_done.notify_all();
+        }
+    }
+}
+
+} // namespace
+
+extern "C" {
+
+void admm_server_default_config(admm_server_config *c)
+{
+    if (!c) return;
+    std::memset(c, 0, sizeof *c);
+    c->store_elements = 1LL << 27;
+    c->max_active = 4096;
+    c->tick_iters = 50;
+    c->max_m = 4;
+    c->max_q = 20;
+    c->batch.warps_per_cta = 8;
+    c->batch.ctas_per_sm = 0;
+    c->batch.small_max_elements = 16384;
+}
+
+admm_status admm_server_create(const admm_params *prm, const admm_server_config *cfg, admm_server **out)
+{
+    clear_last_error();
+    if (!out || !prm || !cfg) return sfail(ADMM_EINVAL, "NULL argument");
+    *out = nullptr;
+    if (prm->precision != ADMM_MIXED) return sfail(ADMM_EUNSUPPORTED, "the server runs ADMM_MIXED only");
+    if (cfg->max_active < 1 || cfg->tick_iters < 1 || cfg->store_elements < 1024 || cfg->max_m < 1 ||
+        cfg->max_m > ADMM_MAX_M || cfg->max_q < 1 || (int64_t)cfg->max_m * cfg->max_q > ADMM_BATCH_MAX_PAIRS)
+        return sfail(ADMM_EINVAL, "bad server configuration");
+    if (cfg->batch.warps_per_cta != 4 && cfg->batch.warps_per_cta != 8 && cfg->batch.warps_per_cta != 16)
+        return sfail(ADMM_EINVAL, "warps_per_cta must be 4, 8 or 16");
+    for (int t = 0; t < 4; ++t)
+        if (!(prm->rho[t] > 0.0)) return sfail(ADMM_EINVAL, "rho must be > 0");
+    admm_server *S = new admm_server();
+    S->prm = *prm;
+    S->cfg = *cfg;
+    const int maxa = cfg->max_active;
+    auto bail = [&](admm_status s, const std::string &m) {
+        S->store.free_all();
+        void *d[] = {S->d_inst, S->d_order, S->d_counts, S->d_q, S->d_shift, S->d_out, S->d_tmp};
+        for (void *p : d)
+            if (p) cudaFree(p);
+        void *h[] = {S->h_inst, S->h_order, S->h_counts, S->h_shift, S->h_out, S->pinned};
+        for (void *p : h)
+            if (p) cudaFreeHost(p);
+        if (S->st) cudaStreamDestroy(S->st);
+        delete S;
+        return sfail(s, m);
+    };
+    cudaError_t e = cudaGetDevice(&S->dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&S->nsm, cudaDevAttrMultiProcessorCount, S->dev);
+    const int64_t E = cfg->store_elements;
+    if (e == cudaSuccess)
+        e = S->store.allocate(E, E, E, (int64_t)maxa * cfg->max_m * cfg->max_q,
+                              (int64_t)maxa * scal_size(cfg->max_m, cfg->max_q), (int64_t)maxa * cfg->max_m);
+    if (e == cudaSuccess) e = cudaMalloc(&S->d_inst, sizeof(BatchInst) * maxa);
+    if (e == cudaSuccess) e = cudaMalloc(&S->d_order, sizeof(int) * 2 * maxa);
+    if (e == cudaSuccess) e = cudaMalloc(&S->d_counts, sizeof(int) * 2);
+    if (e == cudaSuccess) e = cudaMalloc(&S->d_q, sizeof(int) * 2);
+    if (e == cudaSuccess) e = cudaMalloc(&S->d_shift, sizeof(int) * maxa);
+    if (e == cudaSuccess) e = cudaMalloc(&S->d_out, sizeof(double) * kInfo * maxa);
+    if (e == cudaSuccess) e = cudaMallocHost(&S->h_inst, sizeof(BatchInst) * maxa);
+    if (e == cudaSuccess) e = cudaMallocHost(&S->h_order, sizeof(int) * 2 * maxa);
+    if (e == cudaSuccess) e = cudaMallocHost(&S->h_counts, sizeof(int) * 2);
+    if (e == cudaSuccess) e = cudaMallocHost(&S->h_shift, sizeof(int) * maxa);
+    if (e == cudaSuccess) e = cudaMallocHost(&S->h_out, sizeof(double) * kInfo * maxa);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMemset(S->d_out, 0, sizeof(double) * kInfo * maxa);
+    if (e != cudaSuccess)
+        return bail(e == cudaErrorMemoryAllocation ? ADMM_ENOMEM : ADMM_ECUDA, cudaGetErrorString(e));
+    std::memset(S->h_inst, 0, sizeof(BatchInst) * maxa);
+    // launch shape of a tick: kernel and slices for the configured max m, q
+    S->mbound = batch_mbound(cfg->max_m);
+    S->slice = batch_slice_doubles(cfg->max_m, cfg->max_q);
+    S->smem = batch_smem_bytes(cfg->batch.warps_per_cta, S->slice);
+    const int per_sm = batch_blocks_per_sm(cfg->batch.warps_per_cta, S->mbound, S->smem);
+    if (per_sm < 1) return bail(ADMM_EUNSUPPORTED, "tick kernel cannot be resident");
+    S->grid = S->nsm * (cfg->batch.ctas_per_sm > 0 ? std::min(cfg->batch.ctas_per_sm, per_sm) : per_sm);
+    // capture the tick: reset queue heads, run tick_iters iterations of every active instance
+    BatchArgs a{};
+    a.inst = S->d_inst;
+    a.orderL = S->d_order;
+    a.orderS = S->d_order + maxa;
+    a.nLS = S->d_counts;
+    a.qL = S->d_q;
+    a.qS = S->d_q + 1;
+    S->store.fill_args(a);
+    a.f0 = S->store.f0;
+    a.out = S->d_out;
+    a.slice_doubles = (int)S->slice;
+    a.iter_budget = cfg->tick_iters;
+    a.r_tol = prm->r_tol;
+    a.s_tol = prm->s_tol;
+    a.tau = prm->tau;
+    a.max_iter = prm->max_iter;
+    a.check_every = prm->check_every;
+    a.xmin_mode = prm->xmin_mode;
+    a.sweep = prm->sweep;
+    a.adapt = prm->adapt_rho;
+    cudaGraph_t g = nullptr;
+    e = cudaStreamBeginCapture(S->st, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) e = cudaMemsetAsync(S->d_q, 0, 2 * sizeof(int), S->st);
+    if (e == cudaSuccess) e = launch_batch(cfg->batch.warps_per_cta, S->mbound, S->grid, a, S->smem, S->st);
+    cudaError_t e2 = cudaStreamEndCapture(S->st, &g);
+    if (e == cudaSuccess && e2 == cudaSuccess) e = cudaGraphInstantiate(&S->exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess || e2 != cudaSuccess)
+        return bail(ADMM_ECUDA, std::string("tick graph: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+    S->active.assign(maxa, nullptr);
+    for (int s = maxa - 1; s >= 0; --s) S->free_slots.push_back(s);
+    S->worker = std::thread(worker_loop, S);
+    *out = S;
+    return ADMM_OK;
+}
+
+admm_status admm_server_submit(admm_server *S, const admm_problem *P, int64_t session, int64_t *ticket)
+{
+    clear_last_error();
+    if (!S || !P || !ticket) return sfail(ADMM_EINVAL, "NULL argument");
+    if (P->on_device) return sfail(ADMM_EINVAL, "server requests take host arrays (on_device = 0)");
+    if (P->m > S->cfg.max_m || P->q > S->cfg.max_q)
+        return sfail(ADMM_EUNSUPPORTED, "instance exceeds the server's max_m or max_q");
+    auto r = std::make_shared<Request>();
+    r->t_submit = now_s();
+    std::string why;
+    if (!stage_instance(*P, r->staged, why)) return sfail(ADMM_EINVAL, "invalid problem: " + why);
+    const InstSizes z = inst_sizes(P->n, P->m, P->q);
+    if (z.e > S->cfg.store_elements) return sfail(ADMM_EUNSUPPORTED, "instance larger than the device store");
+    std::lock_guard<std::mutex> lk(S->mu);
+    r->ticket = S->next_ticket++;
+    r->session = session;
+    if (session >= 0) S->sessions[session]; // creates the session record
+    S->reqs[r->ticket] = r;
+    S->pending.push_back(r);
+    *ticket = r->ticket;
+    S->cv_work.notify_one();
+    return ADMM_OK;
+}
+
+admm_status admm_server_poll(admm_server *S, int64_t ticket, int32_t wait_ms, admm_result *out, double *times)
+{
+    clear_last_error();
+    if (!S) return sfail(ADMM_EINVAL, "server is NULL");
+    std::unique_lock<std::mutex> lk(S->mu);
+    auto it = S->reqs.find(ticket);
+    if (it == S->reqs.end()) return sfail(ADMM_EINVAL, "unknown ticket");
+    std::shared_ptr<Request> r = it->second;
+    if (!r->done && wait_ms > 0)
+        S->cv_done.wait_for(lk, std::chrono::milliseconds(wait_ms), [&] { return r->done; });
+    if (!r->done) return ADMM_EPENDING;
+    S->reqs.erase(it);
+    lk.unlock();
+    if (times) {
+        times[0] = r->t_admit > 0 ? r->t_admit - r->t_submit : -1.0;
+        times[1] = r->t_finish - r->t_submit;
+        times[2] = r->warm ? 1.0 : 0.0;
+    }
+    if (out) {
+        out->iters = (int32_t)r->info[0];
+        out->converged = r->info[1] != 0.0;
+        out->r = r->info[2];
+        out->sigma = r->info[3];
+        out->objective = r->info[11];
+        out->status = r->status;
+        if (out->x && !r->x.empty()) std::memcpy(out->x, r->x.data(), sizeof(double) * r->x.size());
+        if (out->x1 && !r->x1.empty()) std::memcpy(out->x1, r->x1.data(), sizeof(double) * r->x1.size());
+    }
+    return r->status == ADMM_ENOTCONVERGED ? ADMM_OK : r->status;
+}
+
+admm_status admm_server_stats(admm_server *S, double *stats, int32_t count)
+{
+    if (!S || !stats || count < 1) return sfail(ADMM_EINVAL, "bad argument");
+    std::lock_guard<std::mutex> lk(S->mu);
+    double v[8] = {S->stats[0], S->stats[1], S->stats[2], 0.0, (double)S->pending.size(), 0.0, 0.0, 0.0};
+    for (auto &p : S->active)
+        if (p) v[3] += 1;
+    v[5] = (double)S->store.ae.free_total() / (double)std::max<int64_t>(1, S->store.ae.capacity());
+    v[6] = (double)S->sessions.size();
+    for (int t = 0; t < count && t < 8; ++t) stats[t] = v[t];
+    return ADMM_OK;
+}
+
+admm_status admm_server_destroy(admm_server *S)
+{
+    if (!S) return ADMM_OK;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stop = true;
+        S->cv_work.notify_all();
+    }
+    if (S->worker.joinable()) S->worker.join();
+    if (S->exec) cudaGraphExecDestroy(S->exec);
+    S->store.free_all();
+    void *d[] = {S->d_inst, S->d_order, S->d_counts, S->d_q, S->d_shift, S->d_out, S->d_tmp};
+    for (void *p : d)
+        if (p) cudaFree(p);
+    void *h[] = {S->h_inst, S->h_order, S->h_counts, S->h_shift, S->h_out, S->pinned};
+    for (void *p : h)
+        if (p) cudaFreeHost(p);
+    if (S->st) cudaStreamDestroy(S->st);
+    delete S;
+    return ADMM_OK;
+}
+
+} // extern "C"

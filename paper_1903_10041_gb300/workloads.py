@@ -194,12 +194,25 @@ def batch_instance(instance: int, seed: int = SEED) -> Problem:
     return p
 
 
-def shifted_demand(p: Problem, step: int, seed: int = SEED) -> Problem:
-    """Receding-horizon re-solve (Sec. II; Alg. 2): the demand of every scenario
-    moves one step forward and a fresh last sample is drawn, U[0.5, 2]."""
+def receding_step(p: Problem, step: int, seed: int = SEED) -> Problem:
+    """Receding-horizon re-solve (Sec. II; Alg. 2) of a plain-recipe problem:
+    the horizon moves one sampling instant forward, so every per-step array
+    (f, g, bounds, demand) moves one step and a fresh last step is drawn from
+    the same recipe as :func:`random_problem`; the capacities are kept."""
     out = p.copy()
-    fresh = 0.5 + 1.5 * uniform(seed, (T_Y, 7, step), p.q)
-    out.y = np.concatenate([p.y[:, 1:], fresh[:, None]], axis=1)
+    m, q = p.m, p.q
+
+    def fresh(tag, shape, a, b):
+        return (a + (b - a) * uniform(seed, (tag, 7, step), int(np.prod(shape)))).reshape(shape)
+
+    last = {"f2": fresh(T_F2, (m, q), 0.1, 1.0), "f1": fresh(T_F1, (m, q), -1.0, 1.0),
+            "f0": np.zeros((m, q)), "g2": fresh(T_G2, (m, q), 0.01, 0.1), "g1": np.ones((m, q)),
+            "g0": np.zeros((m, q))}
+    for k, v in last.items():
+        setattr(out, k, np.concatenate([getattr(p, k)[:, :, 1:], v[:, :, None]], axis=2))
+    out.lo = np.concatenate([p.lo[:, 1:], np.full((m, 1), -1.0)], axis=1)
+    out.hi = np.concatenate([p.hi[:, 1:], np.full((m, 1), 2.0)], axis=1)
+    out.y = np.concatenate([p.y[:, 1:], fresh(T_Y, (q, 1), 0.5, 2.0)], axis=1)
     return out
 
 

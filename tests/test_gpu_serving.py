@@ -1,0 +1,102 @@
+"""Serving (continuous batching of re-solves): results equal the same
+request solved alone, warm starts from a session's resident state converge
+faster, and admission waits for device memory instead of failing."""
+import time
+
+import numpy as np
+import pytest
+
+from paper_1903_10041_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def capi():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1903_10041_gb300 import build
+    build.build()
+    from paper_1903_10041_gb300 import capi
+    return capi
+
+
+PAR = W.Params(rho=(1.0, 1.0 / 600, 1.0, 1.0), precision="mixed")
+
+
+def requests(count, seed):
+    out = []
+    for t in range(count):
+        n, m, q = W.batch_shape(t, seed)
+        out.append(W.random_problem(max(20, min(n, 600)), m, q, seed=seed * 1000 + t))
+    return out
+
+
+def wait_all(S, tickets, timeout_s=120.0):
+    res, t0 = {}, time.time()
+    while len(res) < len(tickets):
+        for t in tickets:
+            if t not in res:
+                r = S.poll(t, wait_ms=5, want_x=True)
+                if r is not None:
+                    res[t] = r
+        assert time.time() - t0 < timeout_s, "served requests did not finish"
+    return [res[t] for t in tickets]
+
+
+def test_served_result_is_the_same_alone_and_in_the_mix(capi, oracle_lib):
+    probs = requests(20, seed=5)
+    with capi.Server(PAR, tick_iters=40, small_max_elements=4096) as S:
+        alone = [wait_all(S, [S.submit(P)])[0] for P in probs[:4]]
+        # the same problems again, now submitted together with 16 others at staggered times
+        tickets = []
+        for t, P in enumerate(probs):
+            tickets.append(S.submit(P))
+            if t % 5 == 4:
+                time.sleep(0.002)
+        mix = wait_all(S, tickets)
+    for t in range(4):
+        assert alone[t]["converged"] and mix[t]["converged"]
+        assert alone[t]["iters"] == mix[t]["iters"]
+        assert np.array_equal(alone[t]["x"], mix[t]["x"]), t
+    for t in (0, 7, 13):
+        st_o, _ = oracle_lib.solve(probs[t], PAR.replace(precision="fp64"), threads=16)
+        obj_o = oracle_lib.objective(probs[t], st_o["x"])
+        assert abs(mix[t]["objective"] - obj_o) <= 1e-6 * max(1.0, abs(obj_o)), t
+
+
+def test_session_warm_start_after_a_one_step_shift(capi, oracle_lib):
+    P0 = W.random_problem(400, 3, 6, seed=77)
+    P1 = W.receding_step(P0, step=1)
+    with capi.Server(PAR, tick_iters=40) as S:
+        r0 = wait_all(S, [S.submit(P0, session=7)])[0]
+        r1 = wait_all(S, [S.submit(P1, session=7)])[0]
+        cold = wait_all(S, [S.submit(P1)])[0]
+    assert r0["converged"] and r1["converged"] and cold["converged"]
+    assert r1["warm"] and not cold["warm"]
+    assert r1["iters"] < cold["iters"], (r1["iters"], cold["iters"])
+    st_o, _ = oracle_lib.solve(P1, PAR.replace(precision="fp64"), threads=16)
+    obj_o = oracle_lib.objective(P1, st_o["x"])
+    assert abs(r1["objective"] - obj_o) <= 1e-6 * max(1.0, abs(obj_o))
+
+
+def test_admission_waits_for_device_memory(capi):
+    probs = requests(12, seed=9)
+    biggest = max(P.m * P.q * ((P.n + 3) // 4 * 4) for P in probs)
+    with capi.Server(PAR, tick_iters=20, store_elements=2 * biggest, max_active=64) as S:
+        tickets = [S.submit(P) for P in probs]
+        seen_queue = S.stats()["queued"] > 0
+        res = wait_all(S, tickets)
+        st = S.stats()
+    assert all(r["converged"] for r in res)
+    assert st["finished"] == len(probs)
+    assert seen_queue or st["ticks"] > 1
+
+
+def test_oversized_request_is_rejected(capi):
+    P = W.random_problem(100, 5, 2, seed=3)
+    with capi.Server(PAR, max_m=4) as S:
+        with pytest.raises(capi.AdmmError) as e:
+            S.submit(P)
+    assert e.value.status == capi.ADMM_EUNSUPPORTED
