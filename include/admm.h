@@ -92,7 +92,9 @@ typedef struct admm_params {
     int32_t xmin_mode;               /* ADMM_XMIN_EXACT | ADMM_XMIN_PAPER */
     int32_t sweep;                   /* ADMM_GAUSS_SEIDEL | ADMM_JACOBI */
     int32_t adapt_rho;               /* 1: rho_i <- tau rho_i or rho_i / tau by r/sigma (Sec. IV-A) */
-    int32_t reserved[4];             /* must be 0 */
+    int32_t rho2_over_n;             /* 1: each instance uses rho_2 = rho[1] / n (the capacity
+                                        penalty acts on a sum of n terms) */
+    int32_t reserved[3];             /* must be 0 */
 } admm_params;
 
 /* The solver state (the checkpoint).  z is not stored: after every
@@ -275,6 +277,23 @@ admm_status admm_server_create(const admm_params *params, const admm_server_conf
  * (warm start from the session's resident state when the shapes match),
  * -1 for a one-off solve.  *ticket identifies it for admm_server_poll. */
 admm_status admm_server_submit(admm_server *s, const admm_problem *prob, int64_t session, int64_t *ticket);
+/* The newest sampling step of a receding horizon: its data at the new
+ * last step k = n-1 (f, g [m][q], bounds [m], demand [q]; host memory). */
+typedef struct admm_step {
+    int32_t m, q;
+    const double *f2, *f1, *f0, *g2, *g1, *g0; /* [m][q] */
+    const double *x_lo, *x_hi;                 /* [m] */
+    const double *y;                           /* [q] */
+} admm_step;
+/* Re-solve of a session after one sampling instant: on the device, the
+ * session's resident instance (data and state) moves one step forward,
+ * `step` becomes its last step, and the solve warm-starts from the moved
+ * state.  Only the new step crosses the bus.  The request fails with
+ * ADMM_EINVAL (reported by admm_server_poll) if the session holds no
+ * resident instance of that m, q (submit a full problem first).  The step
+ * is checked elementwise (finite, f2, g2 >= 0, lo <= hi), not for sure
+ * infeasibility. */
+admm_status admm_server_submit_step(admm_server *s, int64_t session, const admm_step *step, int64_t *ticket);
 /* Waits up to wait_ms for a request.  ADMM_EPENDING if not finished; else
  * fills `out` (status inside; x and x1 host buffers filled when non-NULL)
  * and times[0..2] = seconds from submit to admission, seconds from submit

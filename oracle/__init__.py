@@ -119,8 +119,10 @@ class _Holder:
                           ("f2", "f1", "f0", "g2", "g1", "g0", "lo", "hi", "y", "c")])
 
 
-def _params(par, threads: int = 1, count_differs: bool = False) -> _Params:
+def _params(par, threads: int = 1, count_differs: bool = False, n: int | None = None) -> _Params:
     rho = tuple(float(r) for r in par.rho)
+    if getattr(par, "rho2_over_n", False):
+        rho = (rho[0], rho[1] / n, rho[2], rho[3])
     return _Params(rho[0], rho[1], rho[2], rho[3], float(par.r_tol), float(par.s_tol), int(par.max_iter),
                    int(par.check_every), _MODES[par.xmin_mode], _SWEEPS[par.sweep], int(threads),
                    int(count_differs), int(getattr(par, "adapt_rho", False)), float(getattr(par, "tau", 1.1)))
@@ -151,7 +153,7 @@ def solve(prob, par, state: dict | None = None, threads: int = 1, count_differs:
     H = _Holder(prob)
     st = init_state(prob) if state is None else {k: _f64(state[k]).copy() for k in STATE_KEYS}
     rep = _Report()
-    rc = lib().orc_solve(C.byref(H.c), C.byref(_params(par, threads, count_differs)),
+    rc = lib().orc_solve(C.byref(H.c), C.byref(_params(par, threads, count_differs, H.n)),
                          C.byref(_state_struct(st)), C.byref(rep))
     if rc != 0:
         raise MemoryError("oracle: allocation failed")
@@ -173,5 +175,5 @@ def kkt(prob, par, state: dict):
     H = _Holder(prob)
     st = {k: _f64(state[k]) for k in STATE_KEYS}
     t = np.zeros(8)
-    v = lib().orc_kkt(C.byref(H.c), C.byref(_params(par)), C.byref(_state_struct(st)), _ptr(t))
+    v = lib().orc_kkt(C.byref(H.c), C.byref(_params(par, n=H.n)), C.byref(_state_struct(st)), _ptr(t))
     return v, t

@@ -43,7 +43,7 @@ class admm_params(C.Structure):
     _fields_ = [("rho", C.c_double * 4), ("r_tol", C.c_double), ("s_tol", C.c_double), ("tau", C.c_double),
                 ("max_iter", C.c_int32), ("check_every", C.c_int32), ("precision", C.c_int32),
                 ("xmin_mode", C.c_int32), ("sweep", C.c_int32), ("adapt_rho", C.c_int32),
-                ("reserved", C.c_int32 * 4)]
+                ("rho2_over_n", C.c_int32), ("reserved", C.c_int32 * 3)]
 
 
 class admm_state(C.Structure):
@@ -134,7 +134,7 @@ def make_params(par=None, **kw) -> admm_params:
     src = {}
     if par is not None:
         for k in ("rho", "r_tol", "s_tol", "max_iter", "check_every", "precision", "xmin_mode", "sweep",
-                  "adapt_rho", "tau"):
+                  "adapt_rho", "tau", "rho2_over_n"):
             if hasattr(par, k):
                 src[k] = getattr(par, k)
     src.update(kw)
@@ -155,6 +155,8 @@ def make_params(par=None, **kw) -> admm_params:
         p.sweep = SWEEP[src["sweep"]] if isinstance(src["sweep"], str) else int(src["sweep"])
     if "adapt_rho" in src:
         p.adapt_rho = int(bool(src["adapt_rho"]))
+    if "rho2_over_n" in src:
+        p.rho2_over_n = int(bool(src["rho2_over_n"]))
     return p
 
 
@@ -494,6 +496,15 @@ for _f in ("admm_server_create", "admm_server_submit", "admm_server_poll", "admm
     getattr(_lib, _f).restype = C.c_int
 
 
+class admm_step(C.Structure):
+    _fields_ = [("m", C.c_int32), ("q", C.c_int32), ("f2", _dp), ("f1", _dp), ("f0", _dp), ("g2", _dp),
+                ("g1", _dp), ("g0", _dp), ("x_lo", _dp), ("x_hi", _dp), ("y", _dp)]
+
+
+_lib.admm_server_submit_step.argtypes = [_S, C.c_int64, C.POINTER(admm_step), C.POINTER(C.c_int64)]
+_lib.admm_server_submit_step.restype = C.c_int
+
+
 class Server:
     """Continuous-batching request loop (admm_server_* in admm.h)."""
 
@@ -509,6 +520,20 @@ class Server:
         self.h = _S()
         _check(_lib.admm_server_create(C.byref(pp), C.byref(cfg), C.byref(self.h)))
         self._shapes = {}
+        self._session_n = {}
+
+    def submit_step(self, session: int, step: dict) -> int:
+        """Receding-horizon step request (admm_server_submit_step): ``step``
+        holds f2, f1, f0, g2, g1, g0 [m, q], lo, hi [m] and y [q]."""
+        keep: list = []
+        m, q = step["f2"].shape
+        ptrs = [_ptr(step[k], keep)[0] for k in ("f2", "f1", "f0", "g2", "g1", "g0", "lo", "hi", "y")]
+        cs = admm_step(int(m), int(q), *ptrs)
+        t = C.c_int64()
+        _check(_lib.admm_server_submit_step(self.h, int(session), C.byref(cs), C.byref(t)))
+        n = self._session_n.get(int(session))
+        self._shapes[t.value] = (n if n is not None else 0, int(m), int(q))
+        return t.value
 
     def submit(self, prob, session: int = -1) -> int:
         keep: list = []
@@ -516,6 +541,8 @@ class Server:
         t = C.c_int64()
         _check(_lib.admm_server_submit(self.h, C.byref(cp), int(session), C.byref(t)))
         self._shapes[t.value] = (int(prob.n), int(prob.m), int(prob.q))
+        if session >= 0:
+            self._session_n[int(session)] = int(prob.n)
         return t.value
 
     def poll(self, ticket: int, wait_ms: int = 0, want_x: bool = False):

@@ -390,7 +390,99 @@ __global__ void shift_state_kernel(const BatchInst *inst, const int *ids, int co
     }
 }
 
+// Receding-horizon step request: the whole instance (coefficients, bounds,
+// demand, x, s, mu) moves one step forward in place; the new last step's
+// data comes from `payload` (per instance, FP32: f2 f1 f0 g2 g1 g0 [m][q],
+// lo hi [m], y [q]); x at the new last step is clamped to its new bounds;
+// sum_k beta_0 is recomputed; x_1^(i) = mean of the new first moves; cold
+// flag cleared.  One CTA per instance.
+__global__ void shift_step_kernel(const BatchInst *inst, const int *ids, int count, const float *payload,
+                                  int payload_stride, float *f2, float *f1, float *f0, float *g2, float *g1, float *g0,
+                                  float *lo, float *hi, float *y, float *x, float *s, float *s_lo, float *mu,
+                                  float *mu_lo, double *sumg0, double *scal)
+{
+    for (int t = blockIdx.x; t < count; t += gridDim.x) {
+        const int id = ids[t];
+        const BatchInst I = inst[id];
+        const int n = I.n, m = I.m, q = I.q, mq = m * q;
+        const float *pl = payload + (size_t)id * payload_stride;
+        float *erows[7] = {f2, f1, f0, g2, g1, g0, x};
+        float *crows[5] = {y, s, s_lo, mu, mu_lo};
+        const int nrows = 7 * mq + 2 * m + 5 * q;
+        for (int r = 0; r < nrows; ++r) {
+            float *row;
+            if (r < 7 * mq) row = erows[r / mq] + I.off_e + (int64_t)(r % mq) * I.ld;
+            else if (r < 7 * mq + 2 * m) {
+                const int rr = r - 7 * mq;
+                row = (rr < m ? lo : hi) + I.off_b + (int64_t)(rr % m) * I.ld;
+            } else {
+                const int rr = r - 7 * mq - 2 * m;
+                row = crows[rr / q] + I.off_c + (int64_t)(rr % q) * I.ld;
+            }
+            for (int k0 = 0; k0 < n - 1; k0 += blockDim.x) {
+                const int k = k0 + threadIdx.x;
+                const float v = k < n - 1 ? row[k + 1] : 0.0f;
+                __syncthreads();
+                if (k < n - 1) row[k] = v;
+                __syncthreads();
+            }
+        }
+        // the new last step
+        const int last = n - 1;
+        for (int u = threadIdx.x; u < mq; u += blockDim.x) {
+            const int64_t e = I.off_e + (int64_t)u * I.ld + last;
+            f2[e] = pl[0 * mq + u];
+            f1[e] = pl[1 * mq + u];
+            f0[e] = pl[2 * mq + u];
+            g2[e] = pl[3 * mq + u];
+            g1[e] = pl[4 * mq + u];
+            g0[e] = pl[5 * mq + u];
+        }
+        for (int i = threadIdx.x; i < m; i += blockDim.x) {
+            lo[I.off_b + (int64_t)i * I.ld + last] = pl[6 * mq + i];
+            hi[I.off_b + (int64_t)i * I.ld + last] = pl[6 * mq + m + i];
+        }
+        for (int j = threadIdx.x; j < q; j += blockDim.x) y[I.off_c + (int64_t)j * I.ld + last] = pl[6 * mq + 2 * m + j];
+        __syncthreads();
+        for (int u = threadIdx.x; u < mq; u += blockDim.x) {
+            const int i = u / q;
+            const int64_t e = I.off_e + (int64_t)u * I.ld + last;
+            const float l = lo[I.off_b + (int64_t)i * I.ld + last], h = hi[I.off_b + (int64_t)i * I.ld + last];
+            x[e] = x[e] < l ? l : (x[e] > h ? h : x[e]);
+        }
+        // sum_k beta_0 per pair (one warp per pair, fixed order)
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+        for (int u = w; u < mq; u += nw) {
+            double acc = 0.0;
+            for (int k = lane; k < n; k += 32) acc += (double)g0[I.off_e + (int64_t)u * I.ld + k];
+            acc = warp_sum(acc);
+            if (lane == 0) sumg0[I.off_pair + u] = acc;
+        }
+        __syncthreads();
+        double *sc = scal + I.off_scal;
+        if (threadIdx.x < m) {
+            const int i = threadIdx.x;
+            double sum = 0.0;
+            for (int j = 0; j < q; ++j) sum += (double)x[I.off_e + ((int64_t)i * q + j) * I.ld];
+            sc[5 * mq + i] = sum / (double)q;
+        }
+        if (threadIdx.x == 0) sc[5 * mq + m + 4] = 0.0;
+        __syncthreads();
+    }
+}
+
 } // namespace
+
+void launch_shift_step(const BatchInst *inst, const int *ids, int count, const float *payload, int payload_stride,
+                       float *f2, float *f1, float *f0, float *g2, float *g1, float *g0, float *lo, float *hi,
+                       float *y, float *x, float *s, float *s_lo, float *mu, float *mu_lo, double *sumg0,
+                       double *scal, cudaStream_t st)
+{
+    if (count > 0)
+        shift_step_kernel<<<std::min(count, 1024), 256, 0, st>>>(inst, ids, count, payload, payload_stride, f2, f1, f0,
+                                                                 g2, g1, g0, lo, hi, y, x, s, s_lo, mu, mu_lo, sumg0,
+                                                                 scal);
+}
 
 void launch_shift_state(const BatchInst *inst, const int *ids, int count, float *x, float *s, float *s_lo, float *mu,
                         float *mu_lo, double *scal, cudaStream_t st)

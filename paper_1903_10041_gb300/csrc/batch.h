@@ -49,6 +49,12 @@ size_t batch_slice_doubles(int max_m, int max_q);
 size_t batch_smem_bytes(int warps, size_t slice_doubles);
 int batch_blocks_per_sm(int warps, int mbound, size_t smem);
 cudaError_t launch_batch(int warps, int mbound, int grid, const BatchArgs &a, size_t smem, cudaStream_t st);
+// Moves data and state of instances ids[0..count-1] one step forward and
+// writes the new last step from payload + id * payload_stride.
+void launch_shift_step(const BatchInst *inst, const int *ids, int count, const float *payload, int payload_stride,
+                       float *f2, float *f1, float *f0, float *g2, float *g1, float *g0, float *lo, float *hi,
+                       float *y, float *x, float *s, float *s_lo, float *mu, float *mu_lo, double *sumg0,
+                       double *scal, cudaStream_t st);
 // Moves the state of instances ids[0..count-1] one step forward (receding horizon).
 void launch_shift_state(const BatchInst *inst, const int *ids, int count, float *x, float *s, float *s_lo, float *mu,
                         float *mu_lo, double *scal, cudaStream_t st);

@@ -205,6 +205,7 @@ admm_status reset_all(admm_batch *b)
         const int mq = I.m * I.q;
         double *p = sc.data() + I.off_scal;
         for (int u = 0; u < 4; ++u) p[5 * mq + I.m + u] = b->prm.rho[u];
+        if (b->prm.rho2_over_n) p[5 * mq + I.m + 1] = b->prm.rho[1] / (double)I.n;
         p[5 * mq + I.m + 4] = 1.0;
         p[5 * mq + I.m + 5] = 1.0;
     }

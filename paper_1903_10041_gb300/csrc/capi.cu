@@ -130,7 +130,7 @@ bool params_ok(const admm_params *p)
         return !fail(ADMM_EINVAL, "bad xmin_mode %d", p->xmin_mode);
     if (p->sweep != ADMM_GAUSS_SEIDEL && p->sweep != ADMM_JACOBI) return !fail(ADMM_EINVAL, "bad sweep %d", p->sweep);
     if (p->adapt_rho && !(p->tau > 1.0)) return !fail(ADMM_EINVAL, "tau must be > 1 with adapt_rho");
-    for (int t = 0; t < 4; ++t)
+    for (int t = 0; t < 3; ++t)
         if (p->reserved[t]) return !fail(ADMM_EINVAL, "reserved fields must be 0");
     return true;
 }
@@ -301,6 +301,7 @@ admm_status reset_state(admm_handle *h)
     CUDA_TRY(cudaMemset(h->mu, 0, cb));
     std::vector<double> sc(scal_size(m, q), 0.0);
     for (int t = 0; t < 4; ++t) sc[5 * mq + m + t] = h->prm.rho[t];
+    if (h->prm.rho2_over_n) sc[5 * mq + m + 1] = h->prm.rho[1] / (double)h->n;
     sc[5 * mq + m + 4] = 1.0; // cold
     sc[5 * mq + m + 5] = 1.0; // no pending mu rescale
     CUDA_TRY(cudaMemcpy(h->scal, sc.data(), sizeof(double) * sc.size(), cudaMemcpyHostToDevice));
@@ -486,7 +487,9 @@ admm_status admm_set_params(admm_handle *h, const admm_params *prm)
     DeviceGuard dg(h->dev);
     h->prm = *prm;
     const int mq = h->m * h->q;
-    CUDA_TRY(cudaMemcpy(h->scal + 5 * mq + h->m, prm->rho, 4 * 8, cudaMemcpyHostToDevice));
+    double rho[4] = {prm->rho[0], prm->rho[1], prm->rho[2], prm->rho[3]};
+    if (prm->rho2_over_n) rho[1] /= (double)h->n;
+    CUDA_TRY(cudaMemcpy(h->scal + 5 * mq + h->m, rho, 4 * 8, cudaMemcpyHostToDevice));
     return ADMM_OK;
 }
 

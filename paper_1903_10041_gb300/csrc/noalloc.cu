@@ -226,7 +226,8 @@ extern "C" admm_status admm_solve_noalloc(const admm_problem *P, const admm_para
     noalloc_zero_flags<<<1, 1, 0, cs>>>(flags);
     noalloc_prepare<<<mq, 256, 0, cs>>>(n, m, q, P->f2, P->f1, P->f0, P->g2, P->g1, P->g0, P->x_lo, P->x_hi, P->y,
                                        P->c, st->x, st->s, st->mu, st->lam, st->zeta, st->h, st->p, st->nu, st->x1,
-                                       st->cold ? prm->rho[0] : st->rho[0], st->cold ? prm->rho[1] : st->rho[1],
+                                       st->cold ? prm->rho[0] : st->rho[0],
+                                       st->cold ? (prm->rho2_over_n ? prm->rho[1] / (double)n : prm->rho[1]) : st->rho[1],
                                        st->cold ? prm->rho[2] : st->rho[2], st->cold ? prm->rho[3] : st->rho[3],
                                        st->cold ? 1 : 0, scal, sumg0, bar, status, flags);
     cudaError_t e = cudaGetLastError();

@@ -16,6 +16,7 @@
 // kind, so its result is the same alone and in any mix.
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -40,7 +41,10 @@ double now_s()
 
 struct Request {
     int64_t ticket = 0, session = -1;
-    Staged staged;
+    Staged staged;               // full problem (is_step == false)
+    bool is_step = false;        // receding-horizon step of a resident session
+    int step_m = 0, step_q = 0;
+    std::vector<float> payload;  // step data: f2 f1 f0 g2 g1 g0 [m][q], lo hi [m], y [q]
     double t_submit = 0, t_admit = 0, t_finish = 0;
     int slot = -1;
     bool warm = false, done = false;
@@ -70,6 +74,9 @@ struct admm_server {
     int *d_order = nullptr, *h_order = nullptr; // [0, max) CTA-team queue, [max, 2 max) warp-team queue
     int *d_counts = nullptr, *h_counts = nullptr, *d_q = nullptr;
     int *d_shift = nullptr, *h_shift = nullptr;
+    int *d_stepids = nullptr, *h_stepids = nullptr;
+    float *d_payload = nullptr, *h_payload = nullptr;
+    int payload_stride = 0;
     double *d_out = nullptr, *h_out = nullptr, *d_tmp = nullptr;
     size_t tmp_n = 0;
     float *pinned = nullptr;
@@ -171,7 +178,47 @@ void worker_loop(admm_server *S)
         // place and upload the admitted requests (worker-only state)
         shift_ids.clear();
         std::vector<std::shared_ptr<Request>> back_to_queue;
+        std::vector<int> step_ids;
         for (auto &r : admit) {
+            if (r->is_step) {
+                BatchInst I{};
+                bool ok = false;
+                {
+                    std::lock_guard<std::mutex> lk(S->mu);
+                    Session &ss = S->sessions[r->session];
+                    if (ss.resident && ss.inst.m == r->step_m && ss.inst.q == r->step_q) {
+                        I = ss.inst;
+                        ok = true;
+                    }
+                }
+                if (!ok) { // the session has no resident instance of that shape
+                    std::lock_guard<std::mutex> lk(S->mu);
+                    S->free_slots.push_back(r->slot);
+                    r->slot = -1;
+                    S->sessions[r->session].busy = false;
+                    r->status = ADMM_EINVAL;
+                    r->done = true;
+                    r->t_finish = now_s();
+                    S->cv_done.notify_all();
+                    continue;
+                }
+                std::memcpy(S->h_payload + (size_t)r->slot * S->payload_stride, r->payload.data(),
+                            sizeof(float) * r->payload.size());
+                cudaMemcpyAsync(S->d_payload + (size_t)r->slot * S->payload_stride,
+                                S->h_payload + (size_t)r->slot * S->payload_stride, sizeof(float) * r->payload.size(),
+                                cudaMemcpyHostToDevice, S->st);
+                S->h_inst[r->slot] = I;
+                cudaMemcpyAsync(S->d_inst + r->slot, &S->h_inst[r->slot], sizeof(BatchInst), cudaMemcpyHostToDevice,
+                                S->st);
+                cudaMemsetAsync(S->d_out + (size_t)r->slot * kInfo, 0, sizeof(double) * kInfo, S->st);
+                step_ids.push_back(r->slot);
+                r->warm = true;
+                r->t_admit = now_s();
+                std::lock_guard<std::mutex> lk(S->mu);
+                S->active[r->slot] = r;
+                S->stats[1] += 1;
+                continue;
+            }
             const Staged &sg = r->staged;
             BatchInst I{};
             bool reuse = false;
@@ -271,6 +318,14 @@ void worker_loop(admm_server *S)
                 }
             }
             S->cv_done.notify_all();
+        }
+        if (!step_ids.empty()) {
+            std::copy(step_ids.begin(), step_ids.end(), S->h_stepids);
+            cudaMemcpyAsync(S->d_stepids, S->h_stepids, sizeof(int) * step_ids.size(), cudaMemcpyHostToDevice, S->st);
+            Store &T = S->store;
+            launch_shift_step(S->d_inst, S->d_stepids, (int)step_ids.size(), S->d_payload, S->payload_stride, T.f2,
+                              T.f1, T.f0, T.g2, T.g1, T.g0, T.lo, T.hi, T.y, T.x, T.s, T.s_lo, T.mu, T.mu_lo, T.sumg0,
+                              T.scal, S->st);
         }
         if (!shift_ids.empty()) {
             std::copy(shift_ids.begin(), shift_ids.end(), S->h_shift);
@@ -391,10 +446,10 @@ admm_status admm_server_create(const admm_params *prm, const admm_server_config 
     const int maxa = cfg->max_active;
     auto bail = [&](admm_status s, const std::string &m) {
         S->store.free_all();
-        void *d[] = {S->d_inst, S->d_order, S->d_counts, S->d_q, S->d_shift, S->d_out, S->d_tmp};
+        void *d[] = {S->d_inst, S->d_order, S->d_counts, S->d_q, S->d_shift, S->d_out, S->d_tmp, S->d_stepids, S->d_payload};
         for (void *p : d)
             if (p) cudaFree(p);
-        void *h[] = {S->h_inst, S->h_order, S->h_counts, S->h_shift, S->h_out, S->pinned};
+        void *h[] = {S->h_inst, S->h_order, S->h_counts, S->h_shift, S->h_out, S->pinned, S->h_stepids, S->h_payload};
         for (void *p : h)
             if (p) cudaFreeHost(p);
         if (S->st) cudaStreamDestroy(S->st);
@@ -418,6 +473,11 @@ admm_status admm_server_create(const admm_params *prm, const admm_server_config 
     if (e == cudaSuccess) e = cudaMallocHost(&S->h_counts, sizeof(int) * 2);
     if (e == cudaSuccess) e = cudaMallocHost(&S->h_shift, sizeof(int) * maxa);
     if (e == cudaSuccess) e = cudaMallocHost(&S->h_out, sizeof(double) * kInfo * maxa);
+    S->payload_stride = (6 * cfg->max_m * cfg->max_q + 2 * cfg->max_m + cfg->max_q + 3) / 4 * 4;
+    if (e == cudaSuccess) e = cudaMalloc(&S->d_stepids, sizeof(int) * maxa);
+    if (e == cudaSuccess) e = cudaMallocHost(&S->h_stepids, sizeof(int) * maxa);
+    if (e == cudaSuccess) e = cudaMalloc(&S->d_payload, sizeof(float) * (size_t)maxa * S->payload_stride);
+    if (e == cudaSuccess) e = cudaMallocHost(&S->h_payload, sizeof(float) * (size_t)maxa * S->payload_stride);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->st, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMemset(S->d_out, 0, sizeof(double) * kInfo * maxa);
     if (e != cudaSuccess)
@@ -491,6 +551,49 @@ admm_status admm_server_submit(admm_server *S, const admm_problem *P, int64_t se
     return ADMM_OK;
 }
 
+admm_status admm_server_submit_step(admm_server *S, int64_t session, const admm_step *st, int64_t *ticket)
+{
+    clear_last_error();
+    if (!S || !st || !ticket || session < 0) return sfail(ADMM_EINVAL, "bad argument");
+    const int m = st->m, q = st->q, mq = m * q;
+    if (m < 1 || q < 1 || m > S->cfg.max_m || q > S->cfg.max_q) return sfail(ADMM_EINVAL, "bad step shape");
+    const double *arrs[9] = {st->f2, st->f1, st->f0, st->g2, st->g1, st->g0, st->x_lo, st->x_hi, st->y};
+    for (const double *a : arrs)
+        if (!a) return sfail(ADMM_EINVAL, "a step array is NULL");
+    auto r = std::make_shared<Request>();
+    r->t_submit = now_s();
+    r->is_step = true;
+    r->step_m = m;
+    r->step_q = q;
+    r->payload.resize((size_t)6 * mq + 2 * m + q);
+    for (int t = 0; t < 6; ++t)
+        for (int u = 0; u < mq; ++u) {
+            const double v = arrs[t][u];
+            if (!std::isfinite(v)) return sfail(ADMM_EINVAL, "non-finite step coefficient");
+            if ((t == 0 || t == 3) && v < 0.0) return sfail(ADMM_EINVAL, "f2 < 0 or g2 < 0 in the step");
+            r->payload[(size_t)t * mq + u] = (float)v;
+        }
+    for (int i = 0; i < m; ++i) {
+        if (!std::isfinite(st->x_lo[i]) || !std::isfinite(st->x_hi[i]) || st->x_lo[i] > st->x_hi[i])
+            return sfail(ADMM_EINVAL, "bad step bounds");
+        r->payload[(size_t)6 * mq + i] = (float)st->x_lo[i];
+        r->payload[(size_t)6 * mq + m + i] = (float)st->x_hi[i];
+    }
+    for (int j = 0; j < q; ++j) {
+        if (!std::isfinite(st->y[j])) return sfail(ADMM_EINVAL, "non-finite step demand");
+        r->payload[(size_t)6 * mq + 2 * m + j] = (float)st->y[j];
+    }
+    std::lock_guard<std::mutex> lk(S->mu);
+    r->ticket = S->next_ticket++;
+    r->session = session;
+    S->sessions[session];
+    S->reqs[r->ticket] = r;
+    S->pending.push_back(r);
+    *ticket = r->ticket;
+    S->cv_work.notify_one();
+    return ADMM_OK;
+}
+
 admm_status admm_server_poll(admm_server *S, int64_t ticket, int32_t wait_ms, admm_result *out, double *times)
 {
     clear_last_error();
@@ -546,10 +649,10 @@ admm_status admm_server_destroy(admm_server *S)
     if (S->worker.joinable()) S->worker.join();
     if (S->exec) cudaGraphExecDestroy(S->exec);
     S->store.free_all();
-    void *d[] = {S->d_inst, S->d_order, S->d_counts, S->d_q, S->d_shift, S->d_out, S->d_tmp};
+    void *d[] = {S->d_inst, S->d_order, S->d_counts, S->d_q, S->d_shift, S->d_out, S->d_tmp, S->d_stepids, S->d_payload};
     for (void *p : d)
         if (p) cudaFree(p);
-    void *h[] = {S->h_inst, S->h_order, S->h_counts, S->h_shift, S->h_out, S->pinned};
+    void *h[] = {S->h_inst, S->h_order, S->h_counts, S->h_shift, S->h_out, S->pinned, S->h_stepids, S->h_payload};
     for (void *p : h)
         if (p) cudaFreeHost(p);
     if (S->st) cudaStreamDestroy(S->st);

@@ -275,6 +275,7 @@ cudaError_t Store::upload(const BatchInst &I, const Staged &S, const admm_params
     std::vector<double> sc(z.s, 0.0);
     const int mq = I.m * I.q;
     for (int t = 0; t < 4; ++t) sc[5 * mq + I.m + t] = prm.rho[t];
+    if (prm.rho2_over_n) sc[5 * mq + I.m + 1] = prm.rho[1] / (double)I.n;
     sc[5 * mq + I.m + 4] = 1.0;
     sc[5 * mq + I.m + 5] = 1.0;
     if (r == cudaSuccess)

@@ -114,6 +114,7 @@ class Params:
     sweep: str = "gauss_seidel"   # "gauss_seidel" | "jacobi"
     adapt_rho: bool = False       # Sec. IV-A penalty adaptation
     tau: float = 1.1
+    rho2_over_n: bool = False     # each instance uses rho_2 = rho[1] / n
 
     def replace(self, **kw) -> "Params":
         return dataclasses.replace(self, **kw)
@@ -194,25 +195,29 @@ def batch_instance(instance: int, seed: int = SEED) -> Problem:
     return p
 
 
-def receding_step(p: Problem, step: int, seed: int = SEED) -> Problem:
-    """Receding-horizon re-solve (Sec. II; Alg. 2) of a plain-recipe problem:
-    the horizon moves one sampling instant forward, so every per-step array
-    (f, g, bounds, demand) moves one step and a fresh last step is drawn from
-    the same recipe as :func:`random_problem`; the capacities are kept."""
-    out = p.copy()
-    m, q = p.m, p.q
-
+def step_data(m: int, q: int, step: int, seed: int = SEED) -> dict:
+    """The data of a new last step for a plain-recipe controller at sampling
+    instant ``step``: f2, f1, f0, g2, g1, g0 [m, q], lo, hi [m], y [q]."""
     def fresh(tag, shape, a, b):
         return (a + (b - a) * uniform(seed, (tag, 7, step), int(np.prod(shape)))).reshape(shape)
 
-    last = {"f2": fresh(T_F2, (m, q), 0.1, 1.0), "f1": fresh(T_F1, (m, q), -1.0, 1.0),
-            "f0": np.zeros((m, q)), "g2": fresh(T_G2, (m, q), 0.01, 0.1), "g1": np.ones((m, q)),
-            "g0": np.zeros((m, q))}
-    for k, v in last.items():
-        setattr(out, k, np.concatenate([getattr(p, k)[:, :, 1:], v[:, :, None]], axis=2))
-    out.lo = np.concatenate([p.lo[:, 1:], np.full((m, 1), -1.0)], axis=1)
-    out.hi = np.concatenate([p.hi[:, 1:], np.full((m, 1), 2.0)], axis=1)
-    out.y = np.concatenate([p.y[:, 1:], fresh(T_Y, (q, 1), 0.5, 2.0)], axis=1)
+    return {"f2": fresh(T_F2, (m, q), 0.1, 1.0), "f1": fresh(T_F1, (m, q), -1.0, 1.0), "f0": np.zeros((m, q)),
+            "g2": fresh(T_G2, (m, q), 0.01, 0.1), "g1": np.ones((m, q)), "g0": np.zeros((m, q)),
+            "lo": np.full(m, -1.0), "hi": np.full(m, 2.0), "y": fresh(T_Y, (q,), 0.5, 2.0)}
+
+
+def receding_step(p: Problem, step: int, seed: int = SEED) -> Problem:
+    """Receding-horizon re-solve (Sec. II; Alg. 2) of a plain-recipe problem:
+    the horizon moves one sampling instant forward, so every per-step array
+    (f, g, bounds, demand) moves one step and the new last step is
+    :func:`step_data`; the capacities are kept."""
+    out = p.copy()
+    d = step_data(p.m, p.q, step, seed)
+    for k in ("f2", "f1", "f0", "g2", "g1", "g0"):
+        setattr(out, k, np.concatenate([getattr(p, k)[:, :, 1:], d[k][:, :, None]], axis=2))
+    out.lo = np.concatenate([p.lo[:, 1:], d["lo"][:, None]], axis=1)
+    out.hi = np.concatenate([p.hi[:, 1:], d["hi"][:, None]], axis=1)
+    out.y = np.concatenate([p.y[:, 1:], d["y"][:, None]], axis=1)
     return out
 
 

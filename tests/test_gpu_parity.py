@@ -225,3 +225,18 @@ def test_barrier_wait_times_out_and_device_stays_usable(capi, oracle_lib):
     par = W.Params(max_iter=10, r_tol=0.0, s_tol=0.0)
     st_o, rep_o, st_g, res = run_both(capi, oracle_lib, P, par)
     compare_states(P, st_o, rep_o, st_g, res)
+
+
+def test_rho2_over_n_equals_explicit_rho2(capi, oracle_lib):
+    P = W.random_problem(250, 2, 3, seed=91)
+    a = W.Params(rho=(1.0, 1.0, 1.0, 1.0), rho2_over_n=True, max_iter=80, r_tol=0.0, s_tol=0.0)
+    b = W.Params(rho=(1.0, 1.0 / 250, 1.0, 1.0), max_iter=80, r_tol=0.0, s_tol=0.0)
+    with capi.Solver(P, a) as s:
+        s.solve(raise_on=(1, 2, 3, 4, 6))
+        sa = s.state()
+    with capi.Solver(P, b) as s:
+        s.solve(raise_on=(1, 2, 3, 4, 6))
+        sb = s.state()
+    assert np.array_equal(sa["x"], sb["x"]) and sa["rho"] == sb["rho"]
+    st_o, _ = oracle_lib.solve(P, a, threads=8)
+    assert rel(sa["x"], st_o["x"]) <= TOL

@@ -100,3 +100,31 @@ def test_oversized_request_is_rejected(capi):
         with pytest.raises(capi.AdmmError) as e:
             S.submit(P)
     assert e.value.status == capi.ADMM_EUNSUPPORTED
+
+
+def test_step_request_slides_the_horizon_on_the_device(capi, oracle_lib):
+    """A step request moves the session's resident instance one step on the
+    device; the result is the receding-horizon problem's solution."""
+    P0 = W.random_problem(400, 3, 6, seed=78)
+    P1 = W.receding_step(P0, step=1)
+    with capi.Server(PAR, tick_iters=40) as S:
+        r0 = wait_all(S, [S.submit(P0, session=9)])[0]
+        r1 = wait_all(S, [S.submit_step(9, W.step_data(3, 6, step=1))])[0]
+        cold = wait_all(S, [S.submit(P1)])[0]
+    assert r0["converged"] and r1["converged"] and cold["converged"]
+    assert r1["warm"] and r1["iters"] < cold["iters"], (r1["iters"], cold["iters"])
+    st_o, _ = oracle_lib.solve(P1, PAR.replace(precision="fp64"), threads=16)
+    obj_o = oracle_lib.objective(P1, st_o["x"])
+    assert abs(r1["objective"] - obj_o) <= 1e-6 * max(1.0, abs(obj_o))
+    assert abs(cold["objective"] - obj_o) <= 1e-6 * max(1.0, abs(obj_o))
+
+
+def test_step_request_without_a_resident_session_fails_cleanly(capi):
+    with capi.Server(PAR) as S:
+        t = S.submit_step(123, W.step_data(2, 3, step=1))
+        res = None
+        for _ in range(200):
+            res = S.poll(t, wait_ms=10)
+            if res is not None:
+                break
+    assert res is not None and res["status"] == capi.ADMM_EINVAL
