@@ -197,6 +197,221 @@ def run_reference(args):
     return 0
 
 
+def oracle_sample_errors(probs, par, results, states, idx, oracle):
+    """Objective error and KKT excess against the FP64 oracle on a sample."""
+    errs, kkts = [], []
+    for t in idx:
+        P = probs[t]
+        st_o, rep_o = oracle.solve(P, par.replace(precision="fp64"), threads=os.cpu_count() or 1)
+        obj_o = oracle.objective(P, st_o["x"])
+        errs.append(abs(results[t]["objective"] - obj_o) / max(1.0, abs(obj_o)))
+        st = states[t]
+        import numpy as np
+        m, q, n = P.m, P.q, P.n
+        dense = {"x": st["x"], "z": np.zeros((m, q, n)),
+                 "lam": np.broadcast_to(st["lam"][:, :, None], (m, q, n)).copy(), "s": st["s"], "mu": st["mu"],
+                 "h": st["h"], "p": st["p"], "nu": st["nu"], "x1": st["x1"]}
+        k_g = oracle.kkt(P, par.replace(rho=tuple(st["rho"]), rho2_over_n=False), dense)[0]
+        k_o = oracle.kkt(P, par.replace(precision="fp64"), st_o)[0]
+        kkts.append(k_g - k_o)
+    return {"instances": list(map(int, idx)), "max_rel_objective_err": max(errs), "max_kkt_excess": max(kkts),
+            "per_instance_rel_objective_err": [float(e) for e in errs]}
+
+
+def run_batched(args):
+    """configs[3]: `count` instances of uneven n, m, q in one launch (mixed)."""
+    import numpy as np
+    import torch
+    rank, world, local = dist_init(args.gpus)
+    from paper_1903_10041_gb300 import build
+    if rank == 0:
+        build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    from paper_1903_10041_gb300 import capi
+    from paper_1903_10041_gb300 import workloads as W
+    base = rank * args.count
+    probs = [W.batch_instance(base + t) for t in range(args.count)]
+    par = W.Params(rho=(1.0, 1.0, 1.0, 1.0), rho2_over_n=True, precision="mixed", adapt_rho=args.adapt)
+    if args.max_iter:
+        par = par.replace(max_iter=args.max_iter)
+    B = capi.Batch(probs, par)
+    cfg = B.autotune(trial_iters=30)
+    stream = torch.cuda.Stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def one():
+        B.reset()
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        B.solve(stream=stream)
+        e1.record(stream)
+        res = B.wait(stream=stream)
+        return e0.elapsed_time(e1), res
+
+    for _ in range(args.warmup):
+        one()
+    times, res = [], None
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            ms, res = one()
+            times.append(ms)
+    (tot_ms,) = barrier_max([sum(times)], world)
+    value = world * args.count * args.steps / (tot_ms / 1e3)
+    per_batch_s = sum(times) / args.steps / 1e3
+    iters = np.array([r["iters"] for r in res])
+    conv = np.array([r["converged"] for r in res])
+    byts = sum(int(r["iters"]) * bytes_per_iteration(P, "mixed") for r, P in zip(res, probs))
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"hbm_gbs": 6800.0}
+    gbs = byts / per_batch_s / 1e9
+    roofline = {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": gbs / peaks["hbm_gbs"], "traffic": None}
+    # oracle error on a sample: the 6 smallest instances and 6 spread over the batch (m*q*n <= 40000)
+    import oracle
+    order = np.argsort([P.elements for P in probs])
+    small = [int(t) for t in order[:6]]
+    spread = [int(t) for t in order[len(order) // 8: len(order) // 2: max(1, len(order) // 48)]
+              if probs[int(t)].elements <= 40000][:6]
+    idx = small + spread
+    states = {t: B.state(t) for t in idx}
+    errors = oracle_sample_errors(probs, par, res, states, idx, oracle) if rank == 0 else None
+    # end to end: create from pinned host arrays, solve, read every result (objective, x)
+    e2e = None
+    if not args.no_e2e:
+        t0 = time.perf_counter()
+        B2 = capi.Batch(probs, par)
+        B2.set_config(cfg["warps_per_cta"], cfg["ctas_per_sm"], cfg["small_max_elements"])
+        B2.solve()
+        out = B2.wait(want_x=True)
+        e2e_s = time.perf_counter() - t0
+        B2.close()
+        h2d = sum(sum(v.nbytes for v in P.arrays().values()) for P in probs)
+        d2h = sum(o["x"].nbytes + o["x1"].nbytes for o in out)
+        (e2e_max,) = barrier_max([e2e_s], world)
+        e2e = {"value": world * args.count / e2e_max, "unit": "solves/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # oracle seconds per element-iteration on two sample instances, scaled to the batch
+        t_el = []
+        for t in small[:1] + spread[:1]:
+            P = probs[t]
+            T = 200
+            t0 = time.perf_counter()
+            oracle.solve(P, par.replace(precision="fp64", max_iter=T, r_tol=0.0, s_tol=0.0),
+                         threads=os.cpu_count() or 1)
+            t_el.append((time.perf_counter() - t0) / (T * P.elements))
+        el_it = float(sum(int(r["iters"]) * P.elements for r, P in zip(res, probs)))
+        sec = el_it * float(np.mean(t_el))
+        cpu = {"value": args.count / sec, "unit": "solves/s", "cores": os.cpu_count() or 1, "kind": "oracle",
+               "sample": f"200 iterations of instances {small[:1] + spread[:1]}, scaled by element-iterations to "
+                         f"the whole batch ({el_it:.3g} element-iterations)"}
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+                "data": "synthetic (seeded per instance)",
+                "config": {"workload": f"batched: {args.count} instances, n log-uniform [50,5000], m in {{2,3,4}}, "
+                                       f"q in [1,20], mixed precision", "count": args.count,
+                           "elements": int(sum(P.elements for P in probs)), "autotuned": cfg,
+                           "rho": "(1, 1/n, 1, 1) per instance" + (", adapted (Sec. IV-A)" if args.adapt else ""),
+                           "l2": "inputs larger than L2 (and flushed)",
+                           "parallelism": f"replicas x{world}"},
+                "iters": {"mean": float(iters.mean()), "max": int(iters.max()), "min": int(iters.min())},
+                "converged_frac": float(conv.mean()), "oracle_error_sample": errors,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
+                "clocks": clk.summary()}
+        print(json.dumps(line))
+    B.close()
+    return 0
+
+
+def run_serving(args):
+    """configs[4]: Poisson arrivals of receding-horizon re-solves of `count`
+    controllers sized as the batched workload; continuous batching."""
+    import numpy as np
+    import torch
+    rank, world, local = dist_init(args.gpus)
+    from paper_1903_10041_gb300 import build
+    if rank == 0:
+        build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    from paper_1903_10041_gb300 import capi
+    from paper_1903_10041_gb300 import workloads as W
+    par = W.Params(rho=(1.0, 1.0, 1.0, 1.0), rho2_over_n=True, precision="mixed")
+    base = rank * args.count
+    shapes = [W.batch_shape(base + c) for c in range(args.count)]
+    total_el = sum(((n + 3) // 4 * 4) * m * q for n, m, q in shapes)
+    S = capi.Server(par, store_elements=int(total_el * 1.25) + (1 << 20), max_active=args.count,
+                    tick_iters=args.tick_iters, max_m=4, max_q=20)
+    # every controller's first solve (cold), then the timed window of step re-solves
+    for c in range(args.count):
+        S.submit(W.batch_instance(base + c), session=c)
+    done = 0
+    while done < args.count:
+        t, lat, it, st = S.drain()
+        done += len(t)
+        time.sleep(0.001)
+    rng = np.random.default_rng(1903 + rank)
+    steps = np.zeros(args.count, dtype=np.int64)
+    lat_all, it_all, st_all = [], [], []
+    submitted = 0
+    t_start = time.perf_counter()
+    next_t = t_start + rng.exponential(1.0 / args.rate)
+    with ClockSampler(local) as clk:
+        while True:
+            now = time.perf_counter()
+            if now - t_start >= args.duration:
+                break
+            while next_t <= now:
+                c = int(rng.integers(args.count))
+                steps[c] += 1
+                n, m, q = shapes[c]
+                S.submit_step(c, W.step_data(m, q, int(steps[c]), seed=W.SEED * (1 << 32) + base + c))
+                submitted += 1
+                next_t += rng.exponential(1.0 / args.rate)
+            t, lat, it, st = S.drain()
+            lat_all.extend(lat.tolist())
+            it_all.extend(it.tolist())
+            st_all.extend(st.tolist())
+            time.sleep(0.0005)
+        window = time.perf_counter() - t_start
+        finished_in_window = len(lat_all)
+        t_end = time.perf_counter()
+        while len(lat_all) < submitted and time.perf_counter() - t_end < 120:
+            t, lat, it, st = S.drain()
+            lat_all.extend(lat.tolist())
+            it_all.extend(it.tolist())
+            st_all.extend(st.tolist())
+            time.sleep(0.001)
+    stats = S.stats()
+    S.close()
+    lat = np.array(lat_all) * 1e3
+    value = finished_in_window / window
+    (vmin,) = barrier_max([-value], world)
+    if rank == 0:
+        line = {"metric": METRIC, "value": value * world, "unit": "solves/s", "n_gpus": world,
+                "steps": submitted, "warmup": args.count, "ms_per_step": float(np.mean(lat)) if len(lat) else None,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+                "data": "synthetic (seeded receding-horizon steps per controller)",
+                "config": {"workload": f"serving: Poisson {args.rate:g}/s re-solves of {args.count} controllers "
+                                       f"sized as the batched workload, {args.duration:g} s window",
+                           "tick_iters": args.tick_iters, "rho": "(1, 1/n, 1, 1) per instance",
+                           "parallelism": f"replicas x{world}"},
+                "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                               "mean": float(np.mean(lat)), "max": float(np.max(lat))} if len(lat) else None,
+                "submitted": submitted, "finished": len(lat_all),
+                "iters": {"mean": float(np.mean(it_all)), "max": int(np.max(it_all))} if it_all else None,
+                "ok_frac": float(np.mean(np.array(st_all) == 0)) if st_all else None,
+                "server_stats": stats, "gpu_launches": int(stats["ticks"]), "clocks": clk.summary()}
+        print(json.dumps(line))
+    return 0
+
+
 def config_dict(P, par, args):
     return {"workload": P.name + f" ({args.precision})", "n": P.n, "m": P.m, "q": P.q,
             "elements": P.elements, "rho": list(par.rho), "r_tol": par.r_tol, "s_tol": par.s_tol,
@@ -210,7 +425,12 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", type=int, default=1, choices=[0, 1, 2])
+    ap.add_argument("--config", type=int, default=1, choices=[0, 1, 2, 3, 4])
+    ap.add_argument("--count", type=int, default=4096, help="instances (3) or controllers (4)")
+    ap.add_argument("--duration", type=float, default=60.0, help="serving window in seconds (4)")
+    ap.add_argument("--rate", type=float, default=2000.0, help="Poisson arrival rate per second (4)")
+    ap.add_argument("--tick-iters", type=int, default=20, help="iterations per serving tick (4)")
+    ap.add_argument("--adapt", action="store_true", help="penalty adaptation of Sec. IV-A (3)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "mixed_fp64cubic"])
     ap.add_argument("--max-iter", type=int, default=0,
                     help="profiling only: cap the iterations of each solve (the line is then not a benchmark)")
@@ -221,6 +441,8 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.config in (3, 4):
+        return run_batched(args) if args.config == 3 else run_serving(args)
 
     import numpy as np
     import torch

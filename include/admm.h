@@ -299,6 +299,11 @@ admm_status admm_server_submit_step(admm_server *s, int64_t session, const admm_
  * and times[0..2] = seconds from submit to admission, seconds from submit
  * to completion, 1 if warm-started; the ticket is then forgotten. */
 admm_status admm_server_poll(admm_server *s, int64_t ticket, int32_t wait_ms, admm_result *out, double *times);
+/* Takes up to `max` finished requests in ticket order: their tickets,
+ * seconds from submit to completion, iterations and status; *count gets
+ * how many.  Drained tickets are forgotten (their x is not kept). */
+admm_status admm_server_drain(admm_server *s, int32_t max, int64_t *tickets, double *latency_s, int32_t *iters,
+                              int32_t *status, int32_t *count);
 /* stats[0..6]: ticks, admitted, finished, active, queued, free fraction of
  * the store, sessions. */
 admm_status admm_server_stats(admm_server *s, double *stats, int32_t count);

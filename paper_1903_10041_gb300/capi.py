@@ -502,6 +502,9 @@ class admm_step(C.Structure):
 
 
 _lib.admm_server_submit_step.argtypes = [_S, C.c_int64, C.POINTER(admm_step), C.POINTER(C.c_int64)]
+_lib.admm_server_drain.argtypes = [_S, C.c_int32, C.POINTER(C.c_int64), _dp, C.POINTER(C.c_int32),
+                                   C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
+_lib.admm_server_drain.restype = C.c_int
 _lib.admm_server_submit_step.restype = C.c_int
 
 
@@ -564,6 +567,21 @@ class Server:
         if want_x:
             d["x"], d["x1"] = x, x1
         return d
+
+    def drain(self, max_count: int = 65536):
+        """Finished requests as (tickets, latency_s, iters, status) numpy arrays."""
+        t = np.empty(max_count, dtype=np.int64)
+        lat = np.empty(max_count)
+        it = np.empty(max_count, dtype=np.int32)
+        st = np.empty(max_count, dtype=np.int32)
+        cnt = C.c_int32()
+        _check(_lib.admm_server_drain(self.h, int(max_count), t.ctypes.data_as(C.POINTER(C.c_int64)),
+                                      lat.ctypes.data_as(_dp), it.ctypes.data_as(C.POINTER(C.c_int32)),
+                                      st.ctypes.data_as(C.POINTER(C.c_int32)), C.byref(cnt)))
+        k = cnt.value
+        for tk in t[:k]:
+            self._shapes.pop(int(tk), None)
+        return t[:k], lat[:k], it[:k], st[:k]
 
     def stats(self) -> dict:
         buf = (C.c_double * 7)()

@@ -163,12 +163,17 @@ void worker_loop(admm_server *S)
                 return S->stop || any_active || !S->pending.empty();
             });
             if (S->stop) return;
-            // FIFO admission: take the head while a slot is free; a session
-            // with a solve in flight keeps its later requests queued.
-            while (!S->pending.empty() && !S->free_slots.empty() && (int)admit.size() < maxa) {
-                auto r = S->pending.front();
-                if (r->session >= 0 && S->sessions[r->session].busy) break;
-                S->pending.pop_front();
+            // Admission in arrival order while slots are free.  A request of
+            // a session with a solve in flight (or admitted earlier in this
+            // pass) stays queued, keeping its session's order, without
+            // blocking the requests of other sessions behind it.
+            for (auto it = S->pending.begin(); it != S->pending.end() && !S->free_slots.empty();) {
+                auto r = *it;
+                if (r->session >= 0 && S->sessions[r->session].busy) {
+                    ++it;
+                    continue;
+                }
+                it = S->pending.erase(it);
                 if (r->session >= 0) S->sessions[r->session].busy = true;
                 admit.push_back(r);
                 r->slot = S->free_slots.back();
@@ -623,6 +628,30 @@ admm_status admm_server_poll(admm_server *S, int64_t ticket, int32_t wait_ms, ad
         if (out->x1 && !r->x1.empty()) std::memcpy(out->x1, r->x1.data(), sizeof(double) * r->x1.size());
     }
     return r->status == ADMM_ENOTCONVERGED ? ADMM_OK : r->status;
+}
+
+admm_status admm_server_drain(admm_server *S, int32_t max, int64_t *tickets, double *latency_s, int32_t *iters,
+                              int32_t *status, int32_t *count)
+{
+    if (!S || !count || max < 0 || (max > 0 && (!tickets || !latency_s || !iters || !status)))
+        return sfail(ADMM_EINVAL, "bad argument");
+    std::lock_guard<std::mutex> lk(S->mu);
+    int k = 0;
+    for (auto it = S->reqs.begin(); it != S->reqs.end() && k < max;) {
+        const std::shared_ptr<Request> &r = it->second;
+        if (!r->done) {
+            ++it;
+            continue;
+        }
+        tickets[k] = r->ticket;
+        latency_s[k] = r->t_finish - r->t_submit;
+        iters[k] = (int32_t)r->info[0];
+        status[k] = (int32_t)r->status;
+        ++k;
+        it = S->reqs.erase(it);
+    }
+    *count = k;
+    return ADMM_OK;
 }
 
 admm_status admm_server_stats(admm_server *S, double *stats, int32_t count)
