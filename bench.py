@@ -212,7 +212,7 @@ def oracle_sample_errors(probs, par, results, states, idx, oracle):
                  "lam": np.broadcast_to(st["lam"][:, :, None], (m, q, n)).copy(), "s": st["s"], "mu": st["mu"],
                  "h": st["h"], "p": st["p"], "nu": st["nu"], "x1": st["x1"]}
         k_g = oracle.kkt(P, par.replace(rho=tuple(st["rho"]), rho2_over_n=False), dense)[0]
-        k_o = oracle.kkt(P, par.replace(precision="fp64"), st_o)[0]
+        k_o = oracle.kkt(P, par.replace(precision="fp64", rho=tuple(rep_o["rho"]), rho2_over_n=False), st_o)[0]
         kkts.append(k_g - k_o)
     return {"instances": list(map(int, idx)), "max_rel_objective_err": max(errs), "max_kkt_excess": max(kkts),
             "per_instance_rel_objective_err": [float(e) for e in errs]}
