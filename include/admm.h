@@ -212,9 +212,12 @@ admm_status admm_solve_noalloc(const admm_problem *prob, const admm_params *para
  * mix with the same configuration. */
 typedef struct admm_batch admm_batch;
 typedef struct admm_batch_config {
-    int32_t warps_per_cta;       /* 4, 8 or 16 */
-    int32_t ctas_per_sm;         /* 0 = as many as fit */
-    int64_t small_max_elements;  /* instances with m*q*n <= this go to one-warp teams */
+    int32_t warps_per_cta;        /* 4, 8 or 16 */
+    int32_t ctas_per_sm;          /* 0 = as many as fit */
+    int64_t small_max_elements;   /* instances with m*q*n <= this go to one-warp teams */
+    int32_t cluster_size;         /* 1 (off), 2, 4 or 8: CTAs of a thread-block cluster team */
+    int32_t reserved;             /* must be 0 */
+    int64_t cluster_min_elements; /* instances with m*q*n > this go to cluster teams */
 } admm_batch_config;
 
 /* Validates every problem as admm_create does (m <= ADMM_MAX_M, m*q <=
@@ -222,12 +225,14 @@ typedef struct admm_batch_config {
  * (FP32 arrays; the problems may be host or device memory) and sets every
  * instance to the zero start.  params->precision must be ADMM_MIXED;
  * the settings apply to every instance.  Default configuration: 8 warps
- * per CTA, small_max_elements 16384. */
+ * per CTA, small_max_elements 16384, clusters of 8 CTAs above 131072
+ * elements. */
 admm_status admm_batch_create(const admm_problem *probs, int32_t count, const admm_params *params,
                               admm_batch **out);
 admm_status admm_batch_set_config(admm_batch *b, const admm_batch_config *cfg);
 admm_status admm_batch_get_config(admm_batch *b, admm_batch_config *cfg);
-/* Times each candidate configuration (warps per CTA x small threshold) on
+/* Times each candidate configuration (warps per CTA x team thresholds x
+ * cluster size) on
  * `trial_iters` iterations of this batch, keeps the fastest, and resets
  * every instance to the zero start.  *chosen (may be NULL) receives it. */
 admm_status admm_batch_autotune(admm_batch *b, int32_t trial_iters, admm_batch_config *chosen);
@@ -270,7 +275,8 @@ typedef struct admm_server_config {
 } admm_server_config;
 
 /* store 2^27 elements, 4096 active, 50 iterations per tick, max_m 4,
- * max_q 20, 8 warps per CTA, small_max_elements 16384. */
+ * max_q 20, 8 warps per CTA, small_max_elements 16384, clusters of 8 CTAs
+ * above 131072 elements. */
 void admm_server_default_config(admm_server_config *cfg);
 admm_status admm_server_create(const admm_params *params, const admm_server_config *cfg, admm_server **out);
 /* Validates and queues a request; session >= 0 ties it to that session

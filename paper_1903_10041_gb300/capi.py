@@ -341,7 +341,8 @@ def admm_solve_noalloc(prob_dev, par, state_dev: dict, x_out=None, x1_out=None, 
 # batched solves
 # ---------------------------------------------------------------------------
 class admm_batch_config(C.Structure):
-    _fields_ = [("warps_per_cta", C.c_int32), ("ctas_per_sm", C.c_int32), ("small_max_elements", C.c_int64)]
+    _fields_ = [("warps_per_cta", C.c_int32), ("ctas_per_sm", C.c_int32), ("small_max_elements", C.c_int64),
+                ("cluster_size", C.c_int32), ("reserved", C.c_int32), ("cluster_min_elements", C.c_int64)]
 
 
 _B = C.c_void_p
@@ -370,7 +371,8 @@ def _stream_ptr(stream):
 
 def _cfg_dict(c: admm_batch_config) -> dict:
     return {"warps_per_cta": c.warps_per_cta, "ctas_per_sm": c.ctas_per_sm,
-            "small_max_elements": c.small_max_elements}
+            "small_max_elements": c.small_max_elements, "cluster_size": c.cluster_size,
+            "cluster_min_elements": c.cluster_min_elements}
 
 
 class Batch:
@@ -388,8 +390,10 @@ class Batch:
         self._keep = []  # the batch holds its own copy of the data
         self.count = len(problems)
 
-    def set_config(self, warps_per_cta=8, ctas_per_sm=0, small_max_elements=16384):
-        c = admm_batch_config(int(warps_per_cta), int(ctas_per_sm), int(small_max_elements))
+    def set_config(self, warps_per_cta=8, ctas_per_sm=0, small_max_elements=16384, cluster_size=8,
+                   cluster_min_elements=131072):
+        c = admm_batch_config(int(warps_per_cta), int(ctas_per_sm), int(small_max_elements), int(cluster_size), 0,
+                              int(cluster_min_elements))
         _check(_lib.admm_batch_set_config(self.h, C.byref(c)))
 
     def config(self) -> dict:
@@ -512,14 +516,16 @@ class Server:
     """Continuous-batching request loop (admm_server_* in admm.h)."""
 
     def __init__(self, par=None, store_elements=1 << 27, max_active=4096, tick_iters=50, max_m=4, max_q=20,
-                 warps_per_cta=8, ctas_per_sm=0, small_max_elements=16384, **kw):
+                 warps_per_cta=8, ctas_per_sm=0, small_max_elements=16384, cluster_size=8,
+                 cluster_min_elements=131072, **kw):
         pp = par if isinstance(par, admm_params) else make_params(par, **kw)
         pp.precision = PRECISION["mixed"]
         cfg = admm_server_config()
         _lib.admm_server_default_config(C.byref(cfg))
         cfg.store_elements, cfg.max_active, cfg.tick_iters = int(store_elements), int(max_active), int(tick_iters)
         cfg.max_m, cfg.max_q = int(max_m), int(max_q)
-        cfg.batch = admm_batch_config(int(warps_per_cta), int(ctas_per_sm), int(small_max_elements))
+        cfg.batch = admm_batch_config(int(warps_per_cta), int(ctas_per_sm), int(small_max_elements),
+                                      int(cluster_size), 0, int(cluster_min_elements))
         self.h = _S()
         _check(_lib.admm_server_create(C.byref(pp), C.byref(cfg), C.byref(self.h)))
         self._shapes = {}

@@ -9,6 +9,12 @@
 // estimated work (longest-processing-time order), so a CTA that finishes
 // early takes the next instance.  Each instance stops on its own stop test.
 //
+// The largest instances are solved by a thread-block cluster (2-8 CTAs on
+// neighbouring SMs): each CTA reduces its part of every row into records in
+// its own shared memory, one hardware cluster barrier per iteration follows,
+// and every CTA reads all CTAs' records through distributed shared memory in
+// rank order and runs the scalar steps redundantly.
+//
 // Per iteration a team sweeps the rows j = 1..q of its instance; within a
 // row its threads take consecutive column vectors (coalesced) and run the
 // element update of mixed_elem.cuh; the row's sums over k are reduced
@@ -22,6 +28,8 @@
 // number of iterations with its state saved; the serving loop uses it to
 // run the batch in ticks and admit new instances between ticks.
 #include <algorithm>
+
+#include <cooperative_groups.h>
 
 #include "batch.h"
 #include "common.cuh"
@@ -306,11 +314,253 @@ __device__ void solve_instance(const BatchArgs &a, int id, double *slice, int ti
     T.sync();
 }
 
+
+// The whole cluster (all CTAs, NW warps each) solves instance `id`.
+template <int NW, int M> __device__ void solve_instance_cluster(const BatchArgs &a, int id, double *smem)
+{
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    const int CL = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+    constexpr int NT = NW * 32;
+    const int tid = threadIdx.x;
+    const Team<NT> T{tid};
+    const BatchInst I = a.inst[id];
+    const int n = I.n, m = I.m, q = I.q, mq = m * q;
+    constexpr int VW = kMixedVW;
+
+    // this CTA's shared memory: scal | crec[2][q][m][4] | cmax[2][4] | part[8] | x1n | scr | red | uoff
+    double *scal = smem;
+    double *lam = scal, *zeta = scal + mq, *hh = scal + 2 * mq, *pp = scal + 3 * mq, *nu = scal + 4 * mq;
+    double *x1 = scal + 5 * mq, *rho = x1 + m, *flags = rho + 4;
+    double *crec = smem + scal_size(m, q);
+    double *cmax = crec + 2 * (size_t)q * m * 4;
+    double *part = cmax + 8;
+    double *x1n = part + 8;
+    double *scr = x1n + kMaxM;
+    float *red = (float *)(scr + kWarpsMax * 8);
+    float *uoff = red + kWarpsMax * kMaxM * 4;
+    double *x0s = (double *)(uoff + ((mq + 1) / 2) * 2); // this CTA's copy of x at k = 0, [mq]
+
+    double *gscal = a.scal + I.off_scal;
+    double *out = a.out + (size_t)id * kInfo;
+    const bool skip = out[14] != 0.0;
+    cl.sync();
+    if (skip) return; // every CTA of the cluster read the same flag
+    for (int t = tid; t < scal_size(m, q); t += NT) scal[t] = gscal[t];
+    T.sync();
+    for (int pr = tid; pr < mq; pr += NT) uoff[pr] = (float)(zeta[pr] + lam[pr]);
+    const int it0 = (int)out[0];
+    T.sync();
+
+    const ElemF32 ea = {a.f2 + I.off_e, a.f1 + I.off_e, a.g2 + I.off_e, a.g1 + I.off_e, a.g0 + I.off_e,
+                        a.lo + I.off_b, a.hi + I.off_b, a.y + I.off_c,  a.x + I.off_e,  a.s + I.off_c,
+                        a.mu + I.off_c, a.s_lo + I.off_c, a.mu_lo + I.off_c, n, m, q, I.ld, a.sweep, a.xmin_mode};
+    const double *cc = a.c + I.off_src;
+    const double *sumg0 = a.sumg0 + I.off_pair;
+    const int nv = (n + VW - 1) / VW;
+    unsigned esc = 0;
+    bool conv = false;
+    double res[7] = {out[4], out[5], out[6], out[7], out[8], out[9], out[10]};
+    double r_last = out[2], s_last = out[3];
+    int it = it0;
+    const int it_end = a.iter_budget > 0 ? min(a.max_iter, it0 + a.iter_budget) : a.max_iter;
+
+    while (it < it_end) {
+        ++it;
+        const int par = it & 1;
+        const bool check = (it % a.check_every == 0) || (it == a.max_iter);
+        const bool cold = flags[0] != 0.0;
+        const float mu_div = (float)flags[1];
+        const float rho1 = (float)rho[0], rho3 = (float)rho[2], rho4 = (float)rho[3];
+        const float iq = 1.0f / (float)q;
+        float fcr = 0.0f, fcs = 0.0f;
+        double *recs = crec + (size_t)par * q * m * 4;
+        for (int j = 0; j < q; ++j) {
+            float ghi[M], glo[M], fmx[M], fmn[M];
+#pragma unroll
+            for (int i = 0; i < M; ++i) {
+                ghi[i] = 0.0f;
+                glo[i] = 0.0f;
+                fmx[i] = -INFINITY;
+                fmn[i] = INFINITY;
+            }
+            double *rec = recs + (size_t)j * m * 4;
+            for (int v = rank * NT + tid; v < nv; v += CL * NT)
+                vec32<M, VW, false>(ea, uoff, x1, nu, j, v * VW, check, cold, mu_div, rho1, rho3, rho4, iq, ghi, glo,
+                                    fmx, fmn, fcr, fcs, esc, rec);
+            team_flush<NT, M>(T, rec, ghi, glo, fmx, fmn, check, m, red);
+        }
+        if (check) {
+            double v2[2] = {(double)fcr, (double)fcs};
+            team_max<NT, 2>(T, v2, scr);
+            if (tid == 0) {
+                cmax[par * 4 + 0] = v2[0];
+                cmax[par * 4 + 1] = v2[1];
+            }
+        }
+        if (tid == 0) flags[1] = 1.0;
+        cl.sync(); // every CTA's records of this iteration are complete
+
+        const double r1 = rho[0], r2 = rho[1], r3 = rho[2];
+        const double kappa = r2 / (r1 + (double)n * r2);
+        double r2m = 0.0, r3m = 0.0, s1m = 0.0, s2m = 0.0;
+        for (int pr = tid; pr < mq; pr += NT) {
+            const int i = pr / q, j = pr - i * q;
+            const size_t off = ((size_t)j * m + i) * 4;
+            double S = 0.0, dmx = -INFINITY, dmn = INFINITY;
+            for (int r = 0; r < CL; ++r) {
+                const double *rr = cl.map_shared_rank(recs, r) + off;
+                S += rr[0];
+                if (check) {
+                    dmx = fmax(dmx, rr[1]);
+                    dmn = fmin(dmn, rr[2]);
+                }
+            }
+            const double x0 = cl.map_shared_rank(recs, 0)[off + 3];
+            const double lm = lam[pr], zt = zeta[pr], h0 = hh[pr], p0 = pp[pr];
+            const double W = (S + sumg0[pr]) - (double)n * lm;
+            const double lamn = kappa * ((h0 + p0) - W);
+            const double Z = W + (double)n * lamn;
+            const double cz = Z - p0;
+            const double hn = cz < cc[i] ? cz : cc[i];
+            const double pn = p0 + (hn - Z);
+            if (check) {
+                r2m = fmax(r2m, fabs(lamn - lm));
+                r3m = fmax(r3m, fabs(hn - Z));
+                const double dl = (lamn - lm) - zt;
+                s1m = fmax(s1m, fmax(fabs(dmx + dl), fabs(dmn + dl)));
+                s2m = fmax(s2m, fabs(hn - h0));
+            }
+            lam[pr] = lamn;
+            zeta[pr] = lamn - lm;
+            hh[pr] = hn;
+            pp[pr] = pn;
+            x0s[pr] = x0;
+        }
+        T.sync();
+        if (tid < m) {
+            const int i = tid;
+            double sum = 0.0;
+            for (int j = 0; j < q; ++j) sum += x0s[i * q + j] - nu[i * q + j];
+            x1n[i] = sum / (double)q;
+        }
+        T.sync();
+        double r4m = 0.0;
+        for (int pr = tid; pr < mq; pr += NT) {
+            const int i = pr / q;
+            const double x0 = x0s[pr], xn = x1n[i];
+            nu[pr] = nu[pr] + (xn - x0);
+            if (check) r4m = fmax(r4m, fabs(x0 - xn));
+        }
+        T.sync();
+        if (tid < m) x1[tid] = x1n[tid];
+        if (tid == 0) flags[0] = 0.0;
+        T.sync();
+        if (check) {
+            double c1 = 0.0, c2 = 0.0;
+            for (int r = 0; r < CL; ++r) {
+                const double *cr = cl.map_shared_rank(cmax, r) + par * 4;
+                c1 = fmax(c1, cr[0]);
+                c2 = fmax(c2, cr[1]);
+            }
+            double v[7] = {c1, r2m, r3m, r4m, s1m, s2m, c2};
+            team_max<NT, 7>(T, v, scr);
+            v[0] = c1;
+            v[6] = c2;
+#pragma unroll
+            for (int t = 0; t < 7; ++t) res[t] = v[t];
+            const double r = fmax(fmax(v[0], v[1]), fmax(v[2], v[3]));
+            const double sg = fmax(fmax(r1 * v[4], r2 * v[5]), r3 * v[6]);
+            r_last = r;
+            s_last = sg;
+            if (r < a.r_tol && sg < a.s_tol) {
+                conv = true;
+                break;
+            }
+            if (a.adapt && it < a.max_iter) {
+                const double ratio = r / sg, target = a.r_tol / a.s_tol;
+                double f = 1.0;
+                if (ratio > 1.2 * target) f = a.tau;
+                else if (ratio < 0.8 * target) f = 1.0 / a.tau;
+                if (f != 1.0) {
+                    for (int pr = tid; pr < mq; pr += NT) {
+                        lam[pr] /= f;
+                        pp[pr] /= f;
+                        nu[pr] /= f;
+                    }
+                    T.sync();
+                    if (tid < 4) rho[tid] *= f;
+                    if (tid == 0) flags[1] = f;
+                    T.sync();
+                }
+            }
+        }
+        for (int pr = tid; pr < mq; pr += NT) uoff[pr] = (float)(zeta[pr] + lam[pr]);
+        T.sync();
+    }
+    const bool finished = conv || it >= a.max_iter;
+
+    // objective over this CTA's share, then summed in rank order by rank 0
+    double acc = 0.0;
+    if (finished) {
+        const float *F2 = ea.f2, *F1 = ea.f1, *F0 = a.f0 + I.off_e;
+        const int64_t tot = (int64_t)mq * n;
+        for (int64_t t = (int64_t)rank * NT + tid; t < tot; t += (int64_t)CL * NT) {
+            const int64_t r = t / n;
+            const int k = (int)(t - r * n);
+            const size_t e = (size_t)r * I.ld + k;
+            const double x = ea.x[e];
+            acc += (double)F2[e] * x * x + (double)F1[e] * x + (double)F0[e];
+        }
+    }
+    acc = team_sum<NT>(T, acc, scr);
+    const double escs = team_sum<NT>(T, (double)esc, scr);
+    if (tid == 0) {
+        part[0] = acc;
+        part[1] = escs;
+    }
+    cl.sync();
+    if (rank == 0) {
+        for (int t = tid; t < scal_size(m, q); t += NT) gscal[t] = scal[t];
+        if (tid == 0) {
+            double obj = 0.0, es = 0.0;
+            for (int r = 0; r < CL; ++r) {
+                obj += cl.map_shared_rank(part, r)[0];
+                es += cl.map_shared_rank(part, r)[1];
+            }
+            out[0] = it;
+            out[1] = conv ? 1.0 : 0.0;
+            out[2] = r_last;
+            out[3] = s_last;
+            for (int t = 0; t < 7; ++t) out[4 + t] = res[t];
+            if (finished) out[11] = obj / (double)q;
+            out[12] = 0.0;
+            out[13] += es;
+            out[14] = finished ? 1.0 : 0.0;
+        }
+    }
+    cl.sync(); // rank 0 has read every CTA's shared memory
+}
+
 template <int NW, int M> __global__ void __launch_bounds__(NW * 32, 16 / NW) batch_kernel(BatchArgs a)
 {
     extern __shared__ double smem[];
     __shared__ int s_item;
-    const int nL = a.nLS ? a.nLS[0] : a.nL, nS = a.nLS ? a.nLS[1] : a.nS;
+    const int nX = a.nLS ? a.nLS[0] : a.nX, nL = a.nLS ? a.nLS[1] : a.nL, nS = a.nLS ? a.nLS[2] : a.nS;
+    // Largest instances: the whole cluster is one team (rank 0 takes the item
+    // and the other CTAs read it through distributed shared memory).
+    if (nX > 0) {
+        namespace cg = cooperative_groups;
+        cg::cluster_group cl = cg::this_cluster();
+        for (;;) {
+            if (cl.block_rank() == 0 && threadIdx.x == 0) s_item = atomicAdd(a.qX, 1);
+            cl.sync();
+            const int item = *cl.map_shared_rank(&s_item, 0);
+            cl.sync();
+            if (item >= nX) break;
+            solve_instance_cluster<NW, M>(a, a.orderX[item], smem);
+        }
+    }
     // Large instances: the whole CTA is one team.
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(a.qL, 1);
@@ -498,6 +748,13 @@ size_t batch_slice_doubles(int max_m, int max_q)
     return (d + 3) / 4 * 4;
 }
 
+size_t batch_cluster_team_doubles(int max_m, int max_q)
+{
+    const int mq = max_m * max_q;
+    return (size_t)scal_size(max_m, max_q) + 2 * (size_t)max_q * max_m * 4 + 16 + kMaxM + kWarpsMax * 8 +
+           (kWarpsMax * kMaxM * 4 + 1) / 2 + (mq + 1) / 2 + mq + 8;
+}
+
 size_t batch_smem_bytes(int warps, size_t slice_doubles)
 {
     return sizeof(double) * slice_doubles * (size_t)warps;
@@ -514,11 +771,45 @@ int batch_blocks_per_sm(int warps, int mb, size_t smem)
 
 // The kernel's shared-memory attribute is set by batch_blocks_per_sm, which
 // the host calls before launching (and before any graph capture).
-cudaError_t launch_batch(int warps, int mb, int grid, const BatchArgs &a, size_t smem, cudaStream_t st)
+cudaError_t launch_batch(int warps, int mb, int grid, int cluster, const BatchArgs &a, size_t smem, cudaStream_t st)
 {
     void *fn = batch_pick(warps, mb);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(warps * 32);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cluster > 1 ? cluster : 1;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
     void *args[] = {(void *)&a};
-    return cudaLaunchKernel(fn, dim3(grid), dim3(warps * 32), args, smem, st);
+    return cudaLaunchKernelExC(&cfg, fn, args);
+}
+
+int batch_max_clusters(int warps, int mb, int cluster, size_t smem)
+{
+    void *fn = batch_pick(warps, mb);
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+    if (cluster > 8 && cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+        return 0;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cluster * 152);
+    cfg.blockDim = dim3(warps * 32);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nc = 0;
+    if (cudaOccupancyMaxActiveClusters(&nc, fn, &cfg) != cudaSuccess) return 0;
+    return nc;
 }
 
 } // namespace admm_impl

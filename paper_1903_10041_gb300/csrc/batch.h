@@ -24,11 +24,12 @@ struct BatchInst {
 
 struct BatchArgs {
     const BatchInst *inst;
+    const int *orderX;        // instances solved by cluster teams (all CTAs of a cluster), in queue order
     const int *orderL;        // instances solved by whole-CTA teams, in queue order
     const int *orderS;        // instances solved by one-warp teams, in queue order
-    int nL, nS;
-    const int *nLS;           // if non-null, {nL, nS} are read from device memory (graph replays)
-    int *qL, *qS;             // queue heads (zeroed before the launch)
+    int nX, nL, nS;
+    const int *nLS;           // if non-null, {nX, nL, nS} are read from device memory (graph replays)
+    int *qX, *qL, *qS;        // queue heads (zeroed before the launch)
     const float *f2, *f1, *f0, *g2, *g1, *g0, *lo, *hi, *y;
     float *x, *s, *s_lo, *mu, *mu_lo;
     const double *c, *sumg0;
@@ -46,9 +47,15 @@ struct BatchArgs {
 inline int batch_mbound(int max_m) { return max_m <= 4 ? 4 : 8; }
 
 size_t batch_slice_doubles(int max_m, int max_q);
+// Shared memory (doubles) a cluster team needs in each of its CTAs.
+size_t batch_cluster_team_doubles(int max_m, int max_q);
 size_t batch_smem_bytes(int warps, size_t slice_doubles);
 int batch_blocks_per_sm(int warps, int mbound, size_t smem);
-cudaError_t launch_batch(int warps, int mbound, int grid, const BatchArgs &a, size_t smem, cudaStream_t st);
+// Launch with clusters of `cluster` CTAs (1 = no clusters); grid is a multiple of it.
+cudaError_t launch_batch(int warps, int mbound, int grid, int cluster, const BatchArgs &a, size_t smem,
+                         cudaStream_t st);
+// Co-resident clusters of that size (0 if it cannot launch).
+int batch_max_clusters(int warps, int mbound, int cluster, size_t smem);
 // Moves data and state of instances ids[0..count-1] one step forward and
 // writes the new last step from payload + id * payload_stride.
 void launch_shift_step(const BatchInst *inst, const int *ids, int count, const float *payload, int payload_stride,

@@ -85,15 +85,15 @@ cudaError_t to_host(const admm_problem &in, HostProblem &out)
 struct admm_batch {
     int count = 0, dev = 0, nsm = 0, max_m = 0, max_q = 0;
     admm_params prm{};
-    admm_batch_config cfg{8, 0, 16384};
+    admm_batch_config cfg{8, 0, 16384, 8, 0, 131072};
     Store store;
     std::vector<BatchInst> inst;
     BatchInst *d_inst = nullptr;
     int *d_order = nullptr; // orderL then orderS
-    int *d_q = nullptr;     // two queue heads
+    int *d_q = nullptr;     // three queue heads
     double *d_out = nullptr, *h_out = nullptr;
     double *d_tmp = nullptr;
-    int nL = 0, nS = 0;
+    int nX = 0, nL = 0, nS = 0, cluster = 1;
     size_t slice = 0, smem = 0;
     int grid = 0;
     cudaStream_t cap = nullptr;
@@ -120,27 +120,41 @@ void batch_free(admm_batch *b)
 // small threshold, warp teams for the rest; each sorted by decreasing work.
 admm_status build_queues(admm_batch *b)
 {
-    std::vector<int> L, S;
+    std::vector<int> X, L, S;
+    const bool clusters = b->cfg.cluster_size > 1;
     for (int t = 0; t < b->count; ++t) {
         const int64_t el = (int64_t)b->inst[t].m * b->inst[t].q * b->inst[t].n;
-        (el > b->cfg.small_max_elements ? L : S).push_back(t);
+        if (clusters && el > b->cfg.cluster_min_elements) X.push_back(t);
+        else if (el > b->cfg.small_max_elements) L.push_back(t);
+        else S.push_back(t);
     }
     auto work = [&](int t) { return (int64_t)b->inst[t].m * b->inst[t].q * b->inst[t].ld; };
     auto by_work = [&](int u, int v) { return work(u) != work(v) ? work(u) > work(v) : u < v; };
+    std::sort(X.begin(), X.end(), by_work);
     std::sort(L.begin(), L.end(), by_work);
     std::sort(S.begin(), S.end(), by_work);
+    b->nX = (int)X.size();
     b->nL = (int)L.size();
     b->nS = (int)S.size();
-    std::vector<int> all(L);
+    std::vector<int> all(X);
+    all.insert(all.end(), L.begin(), L.end());
     all.insert(all.end(), S.begin(), S.end());
     BTRY(cudaMemcpy(b->d_order, all.data(), sizeof(int) * std::max<size_t>(all.size(), 1), cudaMemcpyHostToDevice));
-    // launch shape
+    // launch shape: as many co-resident CTAs (clusters) as fit
     const int mb = batch_mbound(b->max_m);
     b->smem = batch_smem_bytes(b->cfg.warps_per_cta, b->slice);
     const int per_sm = batch_blocks_per_sm(b->cfg.warps_per_cta, mb, b->smem);
     if (per_sm < 1) return bfail(ADMM_EUNSUPPORTED, "batched kernel cannot be resident with this configuration");
     const int use = b->cfg.ctas_per_sm > 0 ? std::min(b->cfg.ctas_per_sm, per_sm) : per_sm;
-    b->grid = b->nsm * use;
+    b->cluster = clusters ? b->cfg.cluster_size : 1;
+    if (b->cluster > 1) {
+        const int nc = batch_max_clusters(b->cfg.warps_per_cta, mb, b->cluster, b->smem);
+        if (nc < 1) return bfail(ADMM_EUNSUPPORTED, "clusters of this size cannot be resident");
+        b->grid = std::min(nc, b->nsm * use / b->cluster) * b->cluster;
+        if (b->grid < b->cluster) b->grid = b->cluster;
+    } else {
+        b->grid = b->nsm * use;
+    }
     if (b->exec) {
         cudaGraphExecDestroy(b->exec);
         b->exec = nullptr;
@@ -152,12 +166,15 @@ BatchArgs make_args(const admm_batch *b)
 {
     BatchArgs a{};
     a.inst = b->d_inst;
-    a.orderL = b->d_order;
-    a.orderS = b->d_order + b->nL;
+    a.orderX = b->d_order;
+    a.orderL = b->d_order + b->nX;
+    a.orderS = b->d_order + b->nX + b->nL;
+    a.nX = b->nX;
     a.nL = b->nL;
     a.nS = b->nS;
-    a.qL = b->d_q;
-    a.qS = b->d_q + 1;
+    a.qX = b->d_q;
+    a.qL = b->d_q + 1;
+    a.qS = b->d_q + 2;
     b->store.fill_args(a);
     a.f0 = b->store.f0;
     a.out = b->d_out;
@@ -182,8 +199,9 @@ admm_status ensure_graph(admm_batch *b)
     const BatchArgs a = make_args(b);
     cudaGraph_t g = nullptr;
     BTRY(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = cudaMemsetAsync(b->d_q, 0, 2 * sizeof(int), b->cap);
-    if (e == cudaSuccess) e = launch_batch(b->cfg.warps_per_cta, batch_mbound(b->max_m), b->grid, a, b->smem, b->cap);
+    cudaError_t e = cudaMemsetAsync(b->d_q, 0, 3 * sizeof(int), b->cap);
+    if (e == cudaSuccess)
+        e = launch_batch(b->cfg.warps_per_cta, batch_mbound(b->max_m), b->grid, b->cluster, a, b->smem, b->cap);
     cudaError_t e2 = cudaStreamEndCapture(b->cap, &g);
     if (e != cudaSuccess || e2 != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
@@ -275,7 +293,7 @@ admm_status admm_batch_create(const admm_problem *probs, int32_t count, const ad
     e = b->store.allocate(tot.e, tot.b, tot.c, tot.p, tot.s, tot.m);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_inst, sizeof(BatchInst) * count);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_order, sizeof(int) * count);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_q, 2 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_q, 3 * sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_out, sizeof(double) * kInfo * count);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_tmp, sizeof(double) * std::max<size_t>(max_dense, 1));
     if (e == cudaSuccess) e = cudaMallocHost(&b->h_out, sizeof(double) * kInfo * count);
@@ -319,7 +337,11 @@ admm_status admm_batch_set_config(admm_batch *b, const admm_batch_config *cfg)
     if (!b || !cfg) return bfail(ADMM_EINVAL, "NULL argument");
     if (cfg->warps_per_cta != 4 && cfg->warps_per_cta != 8 && cfg->warps_per_cta != 16)
         return bfail(ADMM_EINVAL, "warps_per_cta must be 4, 8 or 16");
-    if (cfg->ctas_per_sm < 0 || cfg->small_max_elements < 0) return bfail(ADMM_EINVAL, "negative setting");
+    if (cfg->ctas_per_sm < 0 || cfg->small_max_elements < 0 || cfg->cluster_min_elements < 0)
+        return bfail(ADMM_EINVAL, "negative setting");
+    if (cfg->cluster_size != 1 && cfg->cluster_size != 2 && cfg->cluster_size != 4 && cfg->cluster_size != 8)
+        return bfail(ADMM_EINVAL, "cluster_size must be 1, 2, 4 or 8");
+    if (cfg->reserved) return bfail(ADMM_EINVAL, "reserved must be 0");
     b->cfg = *cfg;
     return build_queues(b);
 }
@@ -328,7 +350,7 @@ admm_status admm_batch_get_config(admm_batch *b, admm_batch_config *cfg)
 {
     if (!b || !cfg) return bfail(ADMM_EINVAL, "NULL argument");
     *cfg = b->cfg;
-    cfg->ctas_per_sm = b->grid / std::max(1, b->nsm);
+    cfg->ctas_per_sm = (b->grid + b->nsm - 1) / std::max(1, b->nsm);
     return ADMM_OK;
 }
 
@@ -417,8 +439,9 @@ admm_status admm_batch_autotune(admm_batch *b, int32_t trial_iters, admm_batch_c
     clear_last_error();
     if (!b || trial_iters < 1) return bfail(ADMM_EINVAL, "bad argument");
     const admm_batch_config keep = b->cfg;
-    const int64_t thresholds[] = {0, 2048, 8192, 32768, 131072, INT64_MAX / 2};
+    const int64_t thresholds[] = {0, 8192, 32768};
     const int warps[] = {4, 8, 16};
+    const struct { int32_t size; int64_t min_el; } clus[] = {{1, 0}, {4, 131072}, {8, 131072}, {8, 32768}};
     cudaEvent_t e0, e1;
     BTRY(cudaEventCreate(&e0));
     BTRY(cudaEventCreate(&e1));
@@ -426,24 +449,26 @@ admm_status admm_batch_autotune(admm_batch *b, int32_t trial_iters, admm_batch_c
     admm_batch_config best_cfg = keep;
     b->iter_budget = trial_iters;
     for (int w : warps)
-        for (int64_t th : thresholds) {
-            admm_batch_config c{w, 0, th};
-            b->cfg = c;
-            if (build_queues(b) != ADMM_OK) continue;
-            if (admm_batch_reset(b) != ADMM_OK) break;
-            const BatchArgs a = make_args(b);
-            cudaMemset(b->d_q, 0, 2 * sizeof(int));
-            cudaEventRecord(e0, b->cap);
-            cudaError_t e = launch_batch(w, batch_mbound(b->max_m), b->grid, a, b->smem, b->cap);
-            cudaEventRecord(e1, b->cap);
-            if (e != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) continue;
-            float ms = 0.0f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (ms < best) {
-                best = ms;
-                best_cfg = c;
+        for (int64_t th : thresholds)
+            for (auto cc : clus) {
+                if (cc.size > 1 && cc.min_el < th) continue;
+                admm_batch_config c{w, 0, th, cc.size, 0, cc.min_el};
+                b->cfg = c;
+                if (build_queues(b) != ADMM_OK) continue;
+                if (admm_batch_reset(b) != ADMM_OK) break;
+                const BatchArgs a = make_args(b);
+                cudaMemset(b->d_q, 0, 3 * sizeof(int));
+                cudaEventRecord(e0, b->cap);
+                cudaError_t e = launch_batch(w, batch_mbound(b->max_m), b->grid, b->cluster, a, b->smem, b->cap);
+                cudaEventRecord(e1, b->cap);
+                if (e != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) continue;
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (ms < best) {
+                    best = ms;
+                    best_cfg = c;
+                }
             }
-        }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     b->iter_budget = 0;

@@ -65,13 +65,13 @@ struct Session {
 struct admm_server {
     admm_params prm{};
     admm_server_config cfg{};
-    int dev = 0, nsm = 0, grid = 0, mbound = 8;
+    int dev = 0, nsm = 0, grid = 0, mbound = 8, cluster = 1;
     size_t slice = 0, smem = 0;
     Store store;
     cudaStream_t st = nullptr;
     cudaGraphExec_t exec = nullptr;
     BatchInst *d_inst = nullptr, *h_inst = nullptr;
-    int *d_order = nullptr, *h_order = nullptr; // [0, max) CTA-team queue, [max, 2 max) warp-team queue
+    int *d_order = nullptr, *h_order = nullptr; // [0, max) cluster, [max, 2 max) CTA, [2 max, 3 max) warp teams
     int *d_counts = nullptr, *h_counts = nullptr, *d_q = nullptr;
     int *d_shift = nullptr, *h_shift = nullptr;
     int *d_stepids = nullptr, *h_stepids = nullptr;
@@ -339,7 +339,7 @@ void worker_loop(admm_server *S)
                                S->store.mu, S->store.mu_lo, S->store.scal, S->st);
         }
         // queues of the active instances for this tick
-        int nL = 0, nS = 0;
+        int nX = 0, nL = 0, nS = 0;
         std::vector<int> ids;
         {
             std::lock_guard<std::mutex> lk(S->mu);
@@ -350,18 +350,18 @@ void worker_loop(admm_server *S)
         std::sort(ids.begin(), ids.end(), [&](int u, int v) { return work(u) != work(v) ? work(u) > work(v) : u < v; });
         for (int s : ids) {
             const int64_t el = (int64_t)S->h_inst[s].m * S->h_inst[s].q * S->h_inst[s].n;
-            if (el > S->cfg.batch.small_max_elements) S->h_order[nL++] = s;
-        }
-        for (int s : ids) {
-            const int64_t el = (int64_t)S->h_inst[s].m * S->h_inst[s].q * S->h_inst[s].n;
-            if (el <= S->cfg.batch.small_max_elements) S->h_order[maxa + nS++] = s;
+            if (S->cluster > 1 && el > S->cfg.batch.cluster_min_elements) S->h_order[nX++] = s;
+            else if (el > S->cfg.batch.small_max_elements) S->h_order[maxa + nL++] = s;
+            else S->h_order[2 * maxa + nS++] = s;
         }
         if (ids.empty()) continue;
-        S->h_counts[0] = nL;
-        S->h_counts[1] = nS;
-        cudaMemcpyAsync(S->d_order, S->h_order, sizeof(int) * nL, cudaMemcpyHostToDevice, S->st);
-        cudaMemcpyAsync(S->d_order + maxa, S->h_order + maxa, sizeof(int) * nS, cudaMemcpyHostToDevice, S->st);
-        cudaMemcpyAsync(S->d_counts, S->h_counts, 2 * sizeof(int), cudaMemcpyHostToDevice, S->st);
+        S->h_counts[0] = nX;
+        S->h_counts[1] = nL;
+        S->h_counts[2] = nS;
+        cudaMemcpyAsync(S->d_order, S->h_order, sizeof(int) * nX, cudaMemcpyHostToDevice, S->st);
+        cudaMemcpyAsync(S->d_order + maxa, S->h_order + maxa, sizeof(int) * nL, cudaMemcpyHostToDevice, S->st);
+        cudaMemcpyAsync(S->d_order + 2 * maxa, S->h_order + 2 * maxa, sizeof(int) * nS, cudaMemcpyHostToDevice, S->st);
+        cudaMemcpyAsync(S->d_counts, S->h_counts, 3 * sizeof(int), cudaMemcpyHostToDevice, S->st);
         cudaError_t e = cudaGraphLaunch(S->exec, S->st);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(S->h_out, S->d_out, sizeof(double) * kInfo * maxa, cudaMemcpyDeviceToHost, S->st);
@@ -430,6 +430,8 @@ void admm_server_default_config(admm_server_config *c)
     c->batch.warps_per_cta = 8;
     c->batch.ctas_per_sm = 0;
     c->batch.small_max_elements = 16384;
+    c->batch.cluster_size = 8;
+    c->batch.cluster_min_elements = 131072;
 }
 
 admm_status admm_server_create(const admm_params *prm, const admm_server_config *cfg, admm_server **out)
@@ -443,6 +445,9 @@ admm_status admm_server_create(const admm_params *prm, const admm_server_config 
         return sfail(ADMM_EINVAL, "bad server configuration");
     if (cfg->batch.warps_per_cta != 4 && cfg->batch.warps_per_cta != 8 && cfg->batch.warps_per_cta != 16)
         return sfail(ADMM_EINVAL, "warps_per_cta must be 4, 8 or 16");
+    if (cfg->batch.cluster_size != 1 && cfg->batch.cluster_size != 2 && cfg->batch.cluster_size != 4 &&
+        cfg->batch.cluster_size != 8)
+        return sfail(ADMM_EINVAL, "cluster_size must be 1, 2, 4 or 8");
     for (int t = 0; t < 4; ++t)
         if (!(prm->rho[t] > 0.0)) return sfail(ADMM_EINVAL, "rho must be > 0");
     admm_server *S = new admm_server();
@@ -468,14 +473,14 @@ admm_status admm_server_create(const admm_params *prm, const admm_server_config 
         e = S->store.allocate(E, E, E, (int64_t)maxa * cfg->max_m * cfg->max_q,
                               (int64_t)maxa * scal_size(cfg->max_m, cfg->max_q), (int64_t)maxa * cfg->max_m);
     if (e == cudaSuccess) e = cudaMalloc(&S->d_inst, sizeof(BatchInst) * maxa);
-    if (e == cudaSuccess) e = cudaMalloc(&S->d_order, sizeof(int) * 2 * maxa);
-    if (e == cudaSuccess) e = cudaMalloc(&S->d_counts, sizeof(int) * 2);
-    if (e == cudaSuccess) e = cudaMalloc(&S->d_q, sizeof(int) * 2);
+    if (e == cudaSuccess) e = cudaMalloc(&S->d_order, sizeof(int) * 3 * maxa);
+    if (e == cudaSuccess) e = cudaMalloc(&S->d_counts, sizeof(int) * 3);
+    if (e == cudaSuccess) e = cudaMalloc(&S->d_q, sizeof(int) * 3);
     if (e == cudaSuccess) e = cudaMalloc(&S->d_shift, sizeof(int) * maxa);
     if (e == cudaSuccess) e = cudaMalloc(&S->d_out, sizeof(double) * kInfo * maxa);
     if (e == cudaSuccess) e = cudaMallocHost(&S->h_inst, sizeof(BatchInst) * maxa);
-    if (e == cudaSuccess) e = cudaMallocHost(&S->h_order, sizeof(int) * 2 * maxa);
-    if (e == cudaSuccess) e = cudaMallocHost(&S->h_counts, sizeof(int) * 2);
+    if (e == cudaSuccess) e = cudaMallocHost(&S->h_order, sizeof(int) * 3 * maxa);
+    if (e == cudaSuccess) e = cudaMallocHost(&S->h_counts, sizeof(int) * 3);
     if (e == cudaSuccess) e = cudaMallocHost(&S->h_shift, sizeof(int) * maxa);
     if (e == cudaSuccess) e = cudaMallocHost(&S->h_out, sizeof(double) * kInfo * maxa);
     S->payload_stride = (6 * cfg->max_m * cfg->max_q + 2 * cfg->max_m + cfg->max_q + 3) / 4 * 4;
@@ -494,15 +499,25 @@ admm_status admm_server_create(const admm_params *prm, const admm_server_config 
     S->smem = batch_smem_bytes(cfg->batch.warps_per_cta, S->slice);
     const int per_sm = batch_blocks_per_sm(cfg->batch.warps_per_cta, S->mbound, S->smem);
     if (per_sm < 1) return bail(ADMM_EUNSUPPORTED, "tick kernel cannot be resident");
-    S->grid = S->nsm * (cfg->batch.ctas_per_sm > 0 ? std::min(cfg->batch.ctas_per_sm, per_sm) : per_sm);
+    const int use = cfg->batch.ctas_per_sm > 0 ? std::min(cfg->batch.ctas_per_sm, per_sm) : per_sm;
+    S->cluster = cfg->batch.cluster_size > 1 ? cfg->batch.cluster_size : 1;
+    if (S->cluster > 1) {
+        const int nc = batch_max_clusters(cfg->batch.warps_per_cta, S->mbound, S->cluster, S->smem);
+        if (nc < 1) return bail(ADMM_EUNSUPPORTED, "clusters of this size cannot be resident");
+        S->grid = std::max(1, std::min(nc, S->nsm * use / S->cluster)) * S->cluster;
+    } else {
+        S->grid = S->nsm * use;
+    }
     // capture the tick: reset queue heads, run tick_iters iterations of every active instance
     BatchArgs a{};
     a.inst = S->d_inst;
-    a.orderL = S->d_order;
-    a.orderS = S->d_order + maxa;
+    a.orderX = S->d_order;
+    a.orderL = S->d_order + maxa;
+    a.orderS = S->d_order + 2 * maxa;
     a.nLS = S->d_counts;
-    a.qL = S->d_q;
-    a.qS = S->d_q + 1;
+    a.qX = S->d_q;
+    a.qL = S->d_q + 1;
+    a.qS = S->d_q + 2;
     S->store.fill_args(a);
     a.f0 = S->store.f0;
     a.out = S->d_out;
@@ -518,8 +533,9 @@ admm_status admm_server_create(const admm_params *prm, const admm_server_config 
     a.adapt = prm->adapt_rho;
     cudaGraph_t g = nullptr;
     e = cudaStreamBeginCapture(S->st, cudaStreamCaptureModeThreadLocal);
-    if (e == cudaSuccess) e = cudaMemsetAsync(S->d_q, 0, 2 * sizeof(int), S->st);
-    if (e == cudaSuccess) e = launch_batch(cfg->batch.warps_per_cta, S->mbound, S->grid, a, S->smem, S->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(S->d_q, 0, 3 * sizeof(int), S->st);
+    if (e == cudaSuccess)
+        e = launch_batch(cfg->batch.warps_per_cta, S->mbound, S->grid, S->cluster, a, S->smem, S->st);
     cudaError_t e2 = cudaStreamEndCapture(S->st, &g);
     if (e == cudaSuccess && e2 == cudaSuccess) e = cudaGraphInstantiate(&S->exec, g, 0);
     if (g) cudaGraphDestroy(g);

@@ -50,23 +50,25 @@ def test_batch_matches_the_oracle_per_instance(capi, oracle_lib):
     # solving groups with equal settings; here rho_2 = 1/600 for all
     par = W.Params(rho=(1.0, 1.0 / 600, 1.0, 1.0), precision="mixed")
     with capi.Batch(probs, par) as B:
-        B.set_config(8, 0, 4096)
+        # warp teams <= 4096 elements < CTA teams <= 16384 < cluster teams of 4 CTAs
+        B.set_config(8, 0, 4096, 4, 16384)
         B.solve()
         res = B.wait()
         states = [B.state(t) for t in range(len(probs))]
-    kinds = {"small": 0, "large": 0}
+    kinds = {"small": 0, "large": 0, "cluster": 0}
     for t, P in enumerate(probs):
-        kinds["small" if P.elements <= 4096 else "large"] += 1
+        kinds["small" if P.elements <= 4096 else ("large" if P.elements <= 16384 else "cluster")] += 1
         st_o, rep_o = oracle_lib.solve(P, par.replace(precision="fp64"), threads=16)
         assert rep_o["converged"] and res[t]["converged"], (t, res[t], rep_o["iters"])
         obj_o = oracle_lib.objective(P, st_o["x"])
         assert abs(res[t]["objective"] - obj_o) <= 1e-6 * max(1.0, abs(obj_o)), (t, res[t]["objective"], obj_o)
         k_o = oracle_lib.kkt(P, par, st_o)[0]
         assert _kkt(oracle_lib, P, par, states[t]) <= k_o + 1e-6, t
-    assert kinds["small"] > 0 and kinds["large"] > 0
+    assert kinds["small"] > 0 and kinds["large"] > 0 and kinds["cluster"] > 0
 
 
-@pytest.mark.parametrize("cfg", [(8, 0, 4096), (4, 1, 0), (16, 0, 10**9)])
+@pytest.mark.parametrize("cfg", [(8, 0, 4096, 1, 0), (4, 1, 0, 1, 0), (16, 0, 10**9, 1, 0),
+                                 (8, 0, 2048, 4, 8192), (4, 0, 0, 8, 0)])
 def test_batch_result_is_the_same_alone_and_in_the_mix(capi, cfg):
     probs = small_batch(16, seed=7)
     par = W.Params(rho=(1.0, 1.0 / 600, 1.0, 1.0), precision="mixed")
