@@ -236,7 +236,12 @@ def run_batched(args):
     if args.max_iter:
         par = par.replace(max_iter=args.max_iter)
     B = capi.Batch(probs, par)
-    cfg = B.autotune(trial_iters=30)
+    if args.batch_config:
+        w, c, sm, cl, cm = (int(v) for v in args.batch_config.split(","))
+        B.set_config(w, c, sm, cl, cm)
+        cfg = B.config()
+    else:
+        cfg = B.autotune(trial_iters=30)
     stream = torch.cuda.Stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
@@ -346,8 +351,12 @@ def run_serving(args):
     base = rank * args.count
     shapes = [W.batch_shape(base + c) for c in range(args.count)]
     total_el = sum(((n + 3) // 4 * 4) * m * q for n, m, q in shapes)
+    bc = {}
+    if args.batch_config:
+        w, c, sm, cl, cm = (int(v) for v in args.batch_config.split(","))
+        bc = dict(warps_per_cta=w, ctas_per_sm=c, small_max_elements=sm, cluster_size=cl, cluster_min_elements=cm)
     S = capi.Server(par, store_elements=int(total_el * 1.25) + (1 << 20), max_active=args.count,
-                    tick_iters=args.tick_iters, max_m=4, max_q=20)
+                    tick_iters=args.tick_iters, max_m=4, max_q=20, **bc)
     # every controller's first solve (cold), then the timed window of step re-solves
     for c in range(args.count):
         S.submit(W.batch_instance(base + c), session=c)
@@ -431,6 +440,8 @@ def main():
     ap.add_argument("--rate", type=float, default=2000.0, help="Poisson arrival rate per second (4)")
     ap.add_argument("--tick-iters", type=int, default=20, help="iterations per serving tick (4)")
     ap.add_argument("--adapt", action="store_true", help="penalty adaptation of Sec. IV-A (3)")
+    ap.add_argument("--batch-config", default="",
+                    help="warps,ctas_per_sm,small_max,cluster,cluster_min instead of the autotuner (3, 4)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "mixed_fp64cubic"])
     ap.add_argument("--max-iter", type=int, default=0,
                     help="profiling only: cap the iterations of each solve (the line is then not a benchmark)")

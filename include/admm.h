@@ -225,8 +225,7 @@ typedef struct admm_batch_config {
  * (FP32 arrays; the problems may be host or device memory) and sets every
  * instance to the zero start.  params->precision must be ADMM_MIXED;
  * the settings apply to every instance.  Default configuration: 8 warps
- * per CTA, small_max_elements 16384, clusters of 8 CTAs above 131072
- * elements. */
+ * per CTA, small_max_elements 16384, no clusters (cluster_size 1). */
 admm_status admm_batch_create(const admm_problem *probs, int32_t count, const admm_params *params,
                               admm_batch **out);
 admm_status admm_batch_set_config(admm_batch *b, const admm_batch_config *cfg);
@@ -275,8 +274,7 @@ typedef struct admm_server_config {
 } admm_server_config;
 
 /* store 2^27 elements, 4096 active, 50 iterations per tick, max_m 4,
- * max_q 20, 8 warps per CTA, small_max_elements 16384, clusters of 8 CTAs
- * above 131072 elements. */
+ * max_q 20, 8 warps per CTA, small_max_elements 16384, no clusters. */
 void admm_server_default_config(admm_server_config *cfg);
 admm_status admm_server_create(const admm_params *params, const admm_server_config *cfg, admm_server **out);
 /* Validates and queues a request; session >= 0 ties it to that session

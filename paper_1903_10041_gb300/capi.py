@@ -390,7 +390,7 @@ class Batch:
         self._keep = []  # the batch holds its own copy of the data
         self.count = len(problems)
 
-    def set_config(self, warps_per_cta=8, ctas_per_sm=0, small_max_elements=16384, cluster_size=8,
+    def set_config(self, warps_per_cta=8, ctas_per_sm=0, small_max_elements=16384, cluster_size=1,
                    cluster_min_elements=131072):
         c = admm_batch_config(int(warps_per_cta), int(ctas_per_sm), int(small_max_elements), int(cluster_size), 0,
                               int(cluster_min_elements))
@@ -516,7 +516,7 @@ class Server:
     """Continuous-batching request loop (admm_server_* in admm.h)."""
 
     def __init__(self, par=None, store_elements=1 << 27, max_active=4096, tick_iters=50, max_m=4, max_q=20,
-                 warps_per_cta=8, ctas_per_sm=0, small_max_elements=16384, cluster_size=8,
+                 warps_per_cta=8, ctas_per_sm=0, small_max_elements=16384, cluster_size=1,
                  cluster_min_elements=131072, **kw):
         pp = par if isinstance(par, admm_params) else make_params(par, **kw)
         pp.precision = PRECISION["mixed"]

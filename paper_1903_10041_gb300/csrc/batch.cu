@@ -49,59 +49,7 @@ template <int NT> struct Team {
     }
 };
 
-// Team-wide float-float sum and FP32 max/min for m row records.
-template <int NT, int M>
-__device__ __forceinline__ void team_flush(const Team<NT> &T, double *rec, const float *ghi, const float *glo,
-                                           const float *fmx, const float *fmn, bool check, int m, float *red)
-{
-    const int lane = T.tid & 31, w = T.tid >> 5;
-#pragma unroll
-    for (int i = 0; i < M; ++i)
-        if (i < m) {
-            FF v = ff_norm(ghi[i], glo[i]);
-            float hi = fmx[i], lo = fmn[i];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const FF u = {__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
-                v = ff_add(v, u);
-                if (check) {
-                    hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
-                    lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
-                }
-            }
-            if (NT == 32) {
-                if (lane == 0) {
-                    rec[i * 4 + 0] = (double)v.hi + (double)v.lo;
-                    rec[i * 4 + 1] = check ? (double)hi : 0.0;
-                    rec[i * 4 + 2] = check ? (double)lo : 0.0;
-                }
-            } else if (lane == 0) {
-                red[(w * kMaxM + i) * 4 + 0] = v.hi;
-                red[(w * kMaxM + i) * 4 + 1] = v.lo;
-                red[(w * kMaxM + i) * 4 + 2] = hi;
-                red[(w * kMaxM + i) * 4 + 3] = lo;
-            }
-        }
-    if constexpr (NT > 32) {
-        __syncthreads();
-        if (T.tid < m) {
-            const int i = T.tid;
-            FF v = {0.0f, 0.0f};
-            float hi = -INFINITY, lo = INFINITY;
-            for (int ww = 0; ww < NT / 32; ++ww) {
-                v = ff_add(v, FF{red[(ww * kMaxM + i) * 4 + 0], red[(ww * kMaxM + i) * 4 + 1]});
-                hi = fmaxf(hi, red[(ww * kMaxM + i) * 4 + 2]);
-                lo = fminf(lo, red[(ww * kMaxM + i) * 4 + 3]);
-            }
-            rec[i * 4 + 0] = (double)v.hi + (double)v.lo;
-            rec[i * 4 + 1] = check ? (double)hi : 0.0;
-            rec[i * 4 + 2] = check ? (double)lo : 0.0;
-        }
-    }
-    T.sync();
-}
-
-// Team-wide max of NV doubles (every thread gets the result).
+// Team-wide max of NV doubles over NT threads of one CTA (every thread gets the result).
 template <int NT, int NV> __device__ __forceinline__ void team_max(const Team<NT> &T, double *v, double *scr)
 {
 #pragma unroll
@@ -120,7 +68,7 @@ template <int NT, int NV> __device__ __forceinline__ void team_max(const Team<NT
     }
 }
 
-// Team-wide FP64 sum (fixed order), every thread gets the result.
+// Team-wide FP64 sum over NT threads of one CTA (fixed order), every thread gets the result.
 template <int NT> __device__ __forceinline__ double team_sum(const Team<NT> &T, double v, double *scr)
 {
     v = warp_sum(v);
@@ -136,228 +84,86 @@ template <int NT> __device__ __forceinline__ double team_sum(const Team<NT> &T, 
     return v;
 }
 
-template <int NT, int M>
-__device__ void solve_instance(const BatchArgs &a, int id, double *slice, int tid)
+enum { TEAM_WARP = 0, TEAM_CTA = 1, TEAM_CLUSTER = 2 };
+
+// Segments per row for a team of W warps: rows are cut so that about one
+// (row, segment) work item falls to each warp, but no segment is shorter
+// than two vectors per lane.
+__host__ __device__ inline int team_segments(int W, int q, int nv)
 {
-    const Team<NT> T{tid};
-    const BatchInst I = a.inst[id];
-    const int n = I.n, m = I.m, q = I.q, mq = m * q;
-    constexpr int VW = kMixedVW;
-
-    // team slice: scalar state | row records [q][m][4] | x1n | scratch | red (floats) | uoff (floats)
-    double *scal = slice;
-    double *lam = scal, *zeta = scal + mq, *hh = scal + 2 * mq, *pp = scal + 3 * mq, *nu = scal + 4 * mq;
-    double *x1 = scal + 5 * mq, *rho = x1 + m, *flags = rho + 4;
-    double *recs = slice + scal_size(m, q);
-    double *x1n = recs + (size_t)q * m * 4;
-    double *scr = x1n + kMaxM;
-    float *red = (float *)(scr + kWarpsMax * 8);
-    float *uoff = red + kWarpsMax * kMaxM * 4;
-
-    double *gscal = a.scal + I.off_scal;
-    double *out = a.out + (size_t)id * kInfo;
-    if (out[14] != 0.0) return; // already finished (converged or out of iterations)
-    for (int t = tid; t < scal_size(m, q); t += NT) scal[t] = gscal[t];
-    T.sync();
-    for (int pr = tid; pr < mq; pr += NT) uoff[pr] = (float)(zeta[pr] + lam[pr]);
-    const int it0 = (int)out[0];
-    T.sync();
-
-    const ElemF32 ea = {a.f2 + I.off_e, a.f1 + I.off_e, a.g2 + I.off_e, a.g1 + I.off_e, a.g0 + I.off_e,
-                        a.lo + I.off_b, a.hi + I.off_b, a.y + I.off_c,  a.x + I.off_e,  a.s + I.off_c,
-                        a.mu + I.off_c, a.s_lo + I.off_c, a.mu_lo + I.off_c, n, m, q, I.ld, a.sweep, a.xmin_mode};
-    const double *cc = a.c + I.off_src;
-    const double *sumg0 = a.sumg0 + I.off_pair;
-    const int nv = (n + VW - 1) / VW;
-    unsigned esc = 0;
-    bool conv = false;
-    double res[7] = {out[4], out[5], out[6], out[7], out[8], out[9], out[10]};
-    double r_last = out[2], s_last = out[3];
-    int it = it0;
-    const int it_end = a.iter_budget > 0 ? min(a.max_iter, it0 + a.iter_budget) : a.max_iter;
-
-    while (it < it_end) {
-        ++it;
-        const bool check = (it % a.check_every == 0) || (it == a.max_iter);
-        const bool cold = flags[0] != 0.0;
-        const float mu_div = (float)flags[1];
-        const float rho1 = (float)rho[0], rho3 = (float)rho[2], rho4 = (float)rho[3];
-        const float iq = 1.0f / (float)q;
-        float fcr = 0.0f, fcs = 0.0f;
-        for (int j = 0; j < q; ++j) {
-            float ghi[M], glo[M], fmx[M], fmn[M];
-#pragma unroll
-            for (int i = 0; i < M; ++i) {
-                ghi[i] = 0.0f;
-                glo[i] = 0.0f;
-                fmx[i] = -INFINITY;
-                fmn[i] = INFINITY;
-            }
-            double *rec = recs + (size_t)j * m * 4;
-            for (int v = tid; v < nv; v += NT)
-                vec32<M, VW, false>(ea, uoff, x1, nu, j, v * VW, check, cold, mu_div, rho1, rho3, rho4, iq, ghi, glo,
-                                    fmx, fmn, fcr, fcs, esc, rec);
-            team_flush<NT, M>(T, rec, ghi, glo, fmx, fmn, check, m, red);
-        }
-        if (tid == 0) flags[1] = 1.0;
-
-        // per-(i, j) scalar steps, as in the single-instance kernel
-        const double r1 = rho[0], r2 = rho[1], r3 = rho[2];
-        const double kappa = r2 / (r1 + (double)n * r2);
-        double r2m = 0.0, r3m = 0.0, s1m = 0.0, s2m = 0.0;
-        for (int pr = tid; pr < mq; pr += NT) {
-            const int i = pr / q, j = pr - i * q;
-            const double *rec = recs + ((size_t)j * m + i) * 4;
-            const double S = rec[0], dmx = rec[1], dmn = rec[2], x0 = rec[3];
-            const double lm = lam[pr], zt = zeta[pr], h0 = hh[pr], p0 = pp[pr];
-            const double W = (S + sumg0[pr]) - (double)n * lm;
-            const double lamn = kappa * ((h0 + p0) - W);
-            const double Z = W + (double)n * lamn;
-            const double cz = Z - p0;
-            const double hn = cz < cc[i] ? cz : cc[i];
-            const double pn = p0 + (hn - Z);
-            if (check) {
-                r2m = fmax(r2m, fabs(lamn - lm));
-                r3m = fmax(r3m, fabs(hn - Z));
-                const double dl = (lamn - lm) - zt;
-                s1m = fmax(s1m, fmax(fabs(dmx + dl), fabs(dmn + dl)));
-                s2m = fmax(s2m, fabs(hn - h0));
-            }
-            lam[pr] = lamn;
-            zeta[pr] = lamn - lm;
-            hh[pr] = hn;
-            pp[pr] = pn;
-        }
-        T.sync();
-        if (tid < m) {
-            const int i = tid;
-            double sum = 0.0;
-            for (int j = 0; j < q; ++j) sum += recs[((size_t)j * m + i) * 4 + 3] - nu[i * q + j];
-            x1n[i] = sum / (double)q;
-        }
-        T.sync();
-        double r4m = 0.0;
-        for (int pr = tid; pr < mq; pr += NT) {
-            const int i = pr / q, j = pr - i * q;
-            const double x0 = recs[((size_t)j * m + i) * 4 + 3], xn = x1n[i];
-            nu[pr] = nu[pr] + (xn - x0);
-            if (check) r4m = fmax(r4m, fabs(x0 - xn));
-        }
-        T.sync();
-        if (tid < m) x1[tid] = x1n[tid];
-        if (tid == 0) flags[0] = 0.0;
-        T.sync();
-        if (check) {
-            double v[7] = {(double)fcr, r2m, r3m, r4m, s1m, s2m, (double)fcs};
-            team_max<NT, 7>(T, v, scr);
-#pragma unroll
-            for (int t = 0; t < 7; ++t) res[t] = v[t];
-            const double r = fmax(fmax(v[0], v[1]), fmax(v[2], v[3]));
-            const double sg = fmax(fmax(r1 * v[4], r2 * v[5]), r3 * v[6]);
-            r_last = r;
-            s_last = sg;
-            if (r < a.r_tol && sg < a.s_tol) {
-                conv = true;
-                break;
-            }
-            if (a.adapt && it < a.max_iter) {
-                const double ratio = r / sg, target = a.r_tol / a.s_tol;
-                double f = 1.0;
-                if (ratio > 1.2 * target) f = a.tau;
-                else if (ratio < 0.8 * target) f = 1.0 / a.tau;
-                if (f != 1.0) {
-                    for (int pr = tid; pr < mq; pr += NT) {
-                        lam[pr] /= f;
-                        pp[pr] /= f;
-                        nu[pr] /= f;
-                    }
-                    T.sync();
-                    if (tid < 4) rho[tid] *= f;
-                    if (tid == 0) flags[1] = f;
-                    T.sync();
-                }
-            }
-        }
-        for (int pr = tid; pr < mq; pr += NT) uoff[pr] = (float)(zeta[pr] + lam[pr]);
-        T.sync();
-    }
-    const bool finished = conv || it >= a.max_iter;
-
-    // objective (1/q) sum f(x) of eq. (2) once the instance is finished
-    double obj = 0.0;
-    if (finished) {
-        double acc = 0.0;
-        const float *F2 = ea.f2, *F1 = ea.f1, *F0 = a.f0 + I.off_e;
-        const int64_t tot = (int64_t)mq * n;
-        for (int64_t t = tid; t < tot; t += NT) {
-            const int64_t r = t / n;
-            const int k = (int)(t - r * n);
-            const size_t e = (size_t)r * I.ld + k;
-            const double x = ea.x[e];
-            acc += (double)F2[e] * x * x + (double)F1[e] * x + (double)F0[e];
-        }
-        obj = team_sum<NT>(T, acc, scr) / (double)q;
-    }
-    const double escs = team_sum<NT>(T, (double)esc, scr);
-    for (int t = tid; t < scal_size(m, q); t += NT) gscal[t] = scal[t];
-    if (tid == 0) {
-        out[0] = it;
-        out[1] = conv ? 1.0 : 0.0;
-        out[2] = r_last;
-        out[3] = s_last;
-        for (int t = 0; t < 7; ++t) out[4 + t] = res[t];
-        if (finished) out[11] = obj;
-        out[12] = 0.0;
-        out[13] += escs;
-        out[14] = finished ? 1.0 : 0.0;
-    }
-    T.sync();
+    const int want = (W + q - 1) / q;
+    const int cap = nv / 64 > 1 ? nv / 64 : 1;
+    return want < 1 ? 1 : (want < cap ? want : cap);
 }
 
-
-// The whole cluster (all CTAs, NW warps each) solves instance `id`.
-template <int NW, int M> __device__ void solve_instance_cluster(const BatchArgs &a, int id, double *smem)
+// One team solves instance `id` from its saved state until it stops or the
+// iteration budget runs out.  KIND: one warp (slice = that warp's shared
+// memory), one CTA, or a thread-block cluster (every CTA runs this
+// function; each holds a copy of the scalar state and records of the work
+// items its warps processed).  Work per iteration: items (row j, segment)
+// in a fixed order, one per warp in turn; each warp reduces its items with
+// shuffles only; one team barrier; then the per-(i, j) scalar steps read the
+// records of each row in segment order.
+template <int KIND, int NW, int M> __device__ void solve_team(const BatchArgs &a, int id, double *smem)
 {
     namespace cg = cooperative_groups;
-    cg::cluster_group cl = cg::this_cluster();
-    const int CL = (int)cl.num_blocks(), rank = (int)cl.block_rank();
-    constexpr int NT = NW * 32;
-    const int tid = threadIdx.x;
-    const Team<NT> T{tid};
+    constexpr int NTL = KIND == TEAM_WARP ? 32 : NW * 32; // threads of this CTA in the team
+    constexpr int NWT = NTL / 32;
+    constexpr int VW = kMixedVW;
+    const int lane = threadIdx.x & 31;
+    const int tid = KIND == TEAM_WARP ? lane : (int)threadIdx.x;
+    const int wl = KIND == TEAM_WARP ? 0 : (int)(threadIdx.x >> 5);
+    int CL = 1, rank = 0;
+    if constexpr (KIND == TEAM_CLUSTER) {
+        CL = (int)cg::this_cluster().num_blocks();
+        rank = (int)cg::this_cluster().block_rank();
+    }
+    const Team<NTL> T{tid};
+    auto sync_local = [&]() {
+        if constexpr (KIND == TEAM_WARP) __syncwarp();
+        else __syncthreads();
+    };
+    auto sync_team = [&]() {
+        if constexpr (KIND == TEAM_CLUSTER) cg::this_cluster().sync();
+        else sync_local();
+    };
+
     const BatchInst I = a.inst[id];
     const int n = I.n, m = I.m, q = I.q, mq = m * q;
-    constexpr int VW = kMixedVW;
+    const int nv = (n + VW - 1) / VW;
+    const int W = NWT * CL, gw = rank * NWT + wl;
+    const int S = team_segments(W, q, nv);
+    const int seg = (nv + S - 1) / S;
+    const int items = q * S;
 
-    // this CTA's shared memory: scal | crec[2][q][m][4] | cmax[2][4] | part[8] | x1n | scr | red | uoff
+    // shared memory: scal | rec[2][items][m][4] | cmax[2][NWT][2] | part[8] | x0s[mq] | x1n | scr | uoff
     double *scal = smem;
     double *lam = scal, *zeta = scal + mq, *hh = scal + 2 * mq, *pp = scal + 3 * mq, *nu = scal + 4 * mq;
     double *x1 = scal + 5 * mq, *rho = x1 + m, *flags = rho + 4;
-    double *crec = smem + scal_size(m, q);
-    double *cmax = crec + 2 * (size_t)q * m * 4;
-    double *part = cmax + 8;
-    double *x1n = part + 8;
+    double *rec0 = smem + scal_size(m, q);
+    double *cmax = rec0 + 2 * (size_t)items * m * 4;
+    double *part = cmax + 4 * NWT;
+    double *x0s = part + 8;
+    double *x1n = x0s + mq;
     double *scr = x1n + kMaxM;
-    float *red = (float *)(scr + kWarpsMax * 8);
-    float *uoff = red + kWarpsMax * kMaxM * 4;
-    double *x0s = (double *)(uoff + ((mq + 1) / 2) * 2); // this CTA's copy of x at k = 0, [mq]
+    float *uoff = (float *)(scr + kWarpsMax * 8);
 
     double *gscal = a.scal + I.off_scal;
     double *out = a.out + (size_t)id * kInfo;
     const bool skip = out[14] != 0.0;
-    cl.sync();
-    if (skip) return; // every CTA of the cluster read the same flag
-    for (int t = tid; t < scal_size(m, q); t += NT) scal[t] = gscal[t];
-    T.sync();
-    for (int pr = tid; pr < mq; pr += NT) uoff[pr] = (float)(zeta[pr] + lam[pr]);
+    sync_team();
+    if (skip) return; // every member read the same flag
+    for (int t = tid; t < scal_size(m, q); t += NTL) scal[t] = gscal[t];
+    sync_local();
+    for (int pr = tid; pr < mq; pr += NTL) uoff[pr] = (float)(zeta[pr] + lam[pr]);
     const int it0 = (int)out[0];
-    T.sync();
+    sync_local();
 
     const ElemF32 ea = {a.f2 + I.off_e, a.f1 + I.off_e, a.g2 + I.off_e, a.g1 + I.off_e, a.g0 + I.off_e,
                         a.lo + I.off_b, a.hi + I.off_b, a.y + I.off_c,  a.x + I.off_e,  a.s + I.off_c,
                         a.mu + I.off_c, a.s_lo + I.off_c, a.mu_lo + I.off_c, n, m, q, I.ld, a.sweep, a.xmin_mode};
     const double *cc = a.c + I.off_src;
     const double *sumg0 = a.sumg0 + I.off_pair;
-    const int nv = (n + VW - 1) / VW;
     unsigned esc = 0;
     bool conv = false;
     double res[7] = {out[4], out[5], out[6], out[7], out[8], out[9], out[10]};
@@ -374,8 +180,10 @@ template <int NW, int M> __device__ void solve_instance_cluster(const BatchArgs 
         const float rho1 = (float)rho[0], rho3 = (float)rho[2], rho4 = (float)rho[3];
         const float iq = 1.0f / (float)q;
         float fcr = 0.0f, fcs = 0.0f;
-        double *recs = crec + (size_t)par * q * m * 4;
-        for (int j = 0; j < q; ++j) {
+        double *recs = rec0 + (size_t)par * items * m * 4;
+        for (int item = gw; item < items; item += W) {
+            const int j = item / S, sg = item - j * S;
+            const int v0 = sg * seg, v1 = min(nv, v0 + seg);
             float ghi[M], glo[M], fmx[M], fmn[M];
 #pragma unroll
             for (int i = 0; i < M; ++i) {
@@ -384,43 +192,63 @@ template <int NW, int M> __device__ void solve_instance_cluster(const BatchArgs 
                 fmx[i] = -INFINITY;
                 fmn[i] = INFINITY;
             }
-            double *rec = recs + (size_t)j * m * 4;
-            for (int v = rank * NT + tid; v < nv; v += CL * NT)
+            double *rec = recs + (size_t)item * m * 4;
+            for (int v = v0 + lane; v < v1; v += 32)
                 vec32<M, VW, false>(ea, uoff, x1, nu, j, v * VW, check, cold, mu_div, rho1, rho3, rho4, iq, ghi, glo,
                                     fmx, fmn, fcr, fcs, esc, rec);
-            team_flush<NT, M>(T, rec, ghi, glo, fmx, fmn, check, m, red);
+#pragma unroll
+            for (int i = 0; i < M; ++i)
+                if (i < m) {
+                    FF v = ff_norm(ghi[i], glo[i]);
+                    float hi = fmx[i], lo = fmn[i];
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        const FF u = {__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+                        v = ff_add(v, u);
+                        if (check) {
+                            hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+                            lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+                        }
+                    }
+                    if (lane == 0) {
+                        rec[i * 4 + 0] = (double)v.hi + (double)v.lo;
+                        rec[i * 4 + 1] = check ? (double)hi : 0.0;
+                        rec[i * 4 + 2] = check ? (double)lo : 0.0;
+                    }
+                }
         }
         if (check) {
-            double v2[2] = {(double)fcr, (double)fcs};
-            team_max<NT, 2>(T, v2, scr);
-            if (tid == 0) {
-                cmax[par * 4 + 0] = v2[0];
-                cmax[par * 4 + 1] = v2[1];
+            const float wr = warp_max(fcr), ws = warp_max(fcs);
+            if (lane == 0) {
+                cmax[(par * NWT + wl) * 2 + 0] = (double)wr;
+                cmax[(par * NWT + wl) * 2 + 1] = (double)ws;
             }
         }
         if (tid == 0) flags[1] = 1.0;
-        cl.sync(); // every CTA's records of this iteration are complete
+        sync_team(); // every record of this iteration is complete and visible
 
         const double r1 = rho[0], r2 = rho[1], r3 = rho[2];
         const double kappa = r2 / (r1 + (double)n * r2);
         double r2m = 0.0, r3m = 0.0, s1m = 0.0, s2m = 0.0;
-        for (int pr = tid; pr < mq; pr += NT) {
+        for (int pr = tid; pr < mq; pr += NTL) {
             const int i = pr / q, j = pr - i * q;
-            const size_t off = ((size_t)j * m + i) * 4;
-            double S = 0.0, dmx = -INFINITY, dmn = INFINITY;
-            for (int r = 0; r < CL; ++r) {
-                const double *rr = cl.map_shared_rank(recs, r) + off;
-                S += rr[0];
+            double Ssum = 0.0, dmx = -INFINITY, dmn = INFINITY, x0 = 0.0;
+            for (int sg = 0; sg < S; ++sg) {
+                const int item = j * S + sg;
+                const double *rb = recs;
+                if constexpr (KIND == TEAM_CLUSTER) rb = cg::this_cluster().map_shared_rank(recs, (item % W) / NWT);
+                const double *rr = rb + ((size_t)item * m + i) * 4;
+                Ssum += rr[0];
                 if (check) {
                     dmx = fmax(dmx, rr[1]);
                     dmn = fmin(dmn, rr[2]);
                 }
+                if (sg == 0) x0 = rr[3];
             }
-            const double x0 = cl.map_shared_rank(recs, 0)[off + 3];
             const double lm = lam[pr], zt = zeta[pr], h0 = hh[pr], p0 = pp[pr];
-            const double W = (S + sumg0[pr]) - (double)n * lm;
-            const double lamn = kappa * ((h0 + p0) - W);
-            const double Z = W + (double)n * lamn;
+            const double Wv = (Ssum + sumg0[pr]) - (double)n * lm;
+            const double lamn = kappa * ((h0 + p0) - Wv);
+            const double Z = Wv + (double)n * lamn;
             const double cz = Z - p0;
             const double hn = cz < cc[i] ? cz : cc[i];
             const double pn = p0 + (hn - Z);
@@ -437,75 +265,76 @@ template <int NW, int M> __device__ void solve_instance_cluster(const BatchArgs 
             pp[pr] = pn;
             x0s[pr] = x0;
         }
-        T.sync();
+        sync_local();
         if (tid < m) {
             const int i = tid;
             double sum = 0.0;
             for (int j = 0; j < q; ++j) sum += x0s[i * q + j] - nu[i * q + j];
             x1n[i] = sum / (double)q;
         }
-        T.sync();
+        sync_local();
         double r4m = 0.0;
-        for (int pr = tid; pr < mq; pr += NT) {
+        for (int pr = tid; pr < mq; pr += NTL) {
             const int i = pr / q;
             const double x0 = x0s[pr], xn = x1n[i];
             nu[pr] = nu[pr] + (xn - x0);
             if (check) r4m = fmax(r4m, fabs(x0 - xn));
         }
-        T.sync();
+        sync_local();
         if (tid < m) x1[tid] = x1n[tid];
         if (tid == 0) flags[0] = 0.0;
-        T.sync();
+        sync_local();
         if (check) {
             double c1 = 0.0, c2 = 0.0;
             for (int r = 0; r < CL; ++r) {
-                const double *cr = cl.map_shared_rank(cmax, r) + par * 4;
-                c1 = fmax(c1, cr[0]);
-                c2 = fmax(c2, cr[1]);
+                const double *cb = cmax;
+                if constexpr (KIND == TEAM_CLUSTER) cb = cg::this_cluster().map_shared_rank(cmax, r);
+                for (int w = 0; w < NWT; ++w) {
+                    c1 = fmax(c1, cb[(par * NWT + w) * 2 + 0]);
+                    c2 = fmax(c2, cb[(par * NWT + w) * 2 + 1]);
+                }
             }
             double v[7] = {c1, r2m, r3m, r4m, s1m, s2m, c2};
-            team_max<NT, 7>(T, v, scr);
-            v[0] = c1;
-            v[6] = c2;
+            team_max<NTL, 7>(T, v, scr);
 #pragma unroll
             for (int t = 0; t < 7; ++t) res[t] = v[t];
             const double r = fmax(fmax(v[0], v[1]), fmax(v[2], v[3]));
-            const double sg = fmax(fmax(r1 * v[4], r2 * v[5]), r3 * v[6]);
+            const double sgm = fmax(fmax(r1 * v[4], r2 * v[5]), r3 * v[6]);
             r_last = r;
-            s_last = sg;
-            if (r < a.r_tol && sg < a.s_tol) {
+            s_last = sgm;
+            if (r < a.r_tol && sgm < a.s_tol) {
                 conv = true;
                 break;
             }
-            if (a.adapt && it < a.max_iter) {
-                const double ratio = r / sg, target = a.r_tol / a.s_tol;
+            if (a.adapt && it < a.max_iter) { // Sec. IV-A, duals rescaled by rho_old / rho_new
+                const double ratio = r / sgm, target = a.r_tol / a.s_tol;
                 double f = 1.0;
                 if (ratio > 1.2 * target) f = a.tau;
                 else if (ratio < 0.8 * target) f = 1.0 / a.tau;
                 if (f != 1.0) {
-                    for (int pr = tid; pr < mq; pr += NT) {
+                    for (int pr = tid; pr < mq; pr += NTL) {
                         lam[pr] /= f;
                         pp[pr] /= f;
                         nu[pr] /= f;
                     }
-                    T.sync();
+                    sync_local();
                     if (tid < 4) rho[tid] *= f;
                     if (tid == 0) flags[1] = f;
-                    T.sync();
+                    sync_local();
                 }
             }
         }
-        for (int pr = tid; pr < mq; pr += NT) uoff[pr] = (float)(zeta[pr] + lam[pr]);
-        T.sync();
+        for (int pr = tid; pr < mq; pr += NTL) uoff[pr] = (float)(zeta[pr] + lam[pr]);
+        sync_local();
     }
     const bool finished = conv || it >= a.max_iter;
 
-    // objective over this CTA's share, then summed in rank order by rank 0
+    // objective (1/q) sum f(x) of eq. (2): each CTA sums its share, rank 0 adds in rank order
     double acc = 0.0;
     if (finished) {
         const float *F2 = ea.f2, *F1 = ea.f1, *F0 = a.f0 + I.off_e;
         const int64_t tot = (int64_t)mq * n;
-        for (int64_t t = (int64_t)rank * NT + tid; t < tot; t += (int64_t)CL * NT) {
+        for (int64_t t = (int64_t)rank * NTL + tid; t < tot; t += (int64_t)CL * NTL) {
             const int64_t r = t / n;
             const int k = (int)(t - r * n);
             const size_t e = (size_t)r * I.ld + k;
@@ -513,20 +342,22 @@ template <int NW, int M> __device__ void solve_instance_cluster(const BatchArgs 
             acc += (double)F2[e] * x * x + (double)F1[e] * x + (double)F0[e];
         }
     }
-    acc = team_sum<NT>(T, acc, scr);
-    const double escs = team_sum<NT>(T, (double)esc, scr);
+    acc = team_sum<NTL>(T, acc, scr);
+    const double escs = team_sum<NTL>(T, (double)esc, scr);
     if (tid == 0) {
         part[0] = acc;
         part[1] = escs;
     }
-    cl.sync();
+    sync_team();
     if (rank == 0) {
-        for (int t = tid; t < scal_size(m, q); t += NT) gscal[t] = scal[t];
+        for (int t = tid; t < scal_size(m, q); t += NTL) gscal[t] = scal[t];
         if (tid == 0) {
             double obj = 0.0, es = 0.0;
             for (int r = 0; r < CL; ++r) {
-                obj += cl.map_shared_rank(part, r)[0];
-                es += cl.map_shared_rank(part, r)[1];
+                const double *pb = part;
+                if constexpr (KIND == TEAM_CLUSTER) pb = cg::this_cluster().map_shared_rank(part, r);
+                obj += pb[0];
+                es += pb[1];
             }
             out[0] = it;
             out[1] = conv ? 1.0 : 0.0;
@@ -539,7 +370,7 @@ template <int NW, int M> __device__ void solve_instance_cluster(const BatchArgs 
             out[14] = finished ? 1.0 : 0.0;
         }
     }
-    cl.sync(); // rank 0 has read every CTA's shared memory
+    sync_team(); // rank 0 has read every member's shared memory
 }
 
 template <int NW, int M> __global__ void __launch_bounds__(NW * 32, 16 / NW) batch_kernel(BatchArgs a)
@@ -558,7 +389,7 @@ template <int NW, int M> __global__ void __launch_bounds__(NW * 32, 16 / NW) bat
             const int item = *cl.map_shared_rank(&s_item, 0);
             cl.sync();
             if (item >= nX) break;
-            solve_instance_cluster<NW, M>(a, a.orderX[item], smem);
+            solve_team<TEAM_CLUSTER, NW, M>(a, a.orderX[item], smem);
         }
     }
     // Large instances: the whole CTA is one team.
@@ -568,7 +399,7 @@ template <int NW, int M> __global__ void __launch_bounds__(NW * 32, 16 / NW) bat
         const int item = s_item;
         __syncthreads();
         if (item >= nL) break;
-        solve_instance<NW * 32, M>(a, a.orderL[item], smem, threadIdx.x);
+        solve_team<TEAM_CTA, NW, M>(a, a.orderL[item], smem);
     }
     // Small instances: each warp is a team with its own slice.
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -578,7 +409,7 @@ template <int NW, int M> __global__ void __launch_bounds__(NW * 32, 16 / NW) bat
         if (lane == 0) item = atomicAdd(a.qS, 1);
         item = __shfl_sync(0xffffffffu, item, 0);
         if (item >= nS) break;
-        solve_instance<32, M>(a, a.orderS[item], slice, lane);
+        solve_team<TEAM_WARP, NW, M>(a, a.orderS[item], slice);
     }
 }
 
@@ -740,19 +571,26 @@ void launch_shift_state(const BatchInst *inst, const int *ids, int count, float 
     if (count > 0) shift_state_kernel<<<std::min(count, 1024), 256, 0, st>>>(inst, ids, count, x, s, s_lo, mu, mu_lo, scal);
 }
 
-size_t batch_slice_doubles(int max_m, int max_q)
+// Shared memory (doubles) of one team: scalar state, double-buffered records
+// of `items` work items, per-warp column maxima, x at k = 0, scratch, and
+// the FP32 zeta + lambda vector.
+static size_t team_doubles(int m, int q, int items, int nwt)
 {
-    const int mq = max_m * max_q;
-    size_t d = (size_t)scal_size(max_m, max_q) + (size_t)max_q * max_m * 4 + kMaxM + kWarpsMax * 8 +
-               (kWarpsMax * kMaxM * 4 + 1) / 2 + (mq + 1) / 2 + 8;
-    return (d + 3) / 4 * 4;
+    const int mq = m * q;
+    return (size_t)scal_size(m, q) + 2 * (size_t)items * m * 4 + 4 * (size_t)nwt + 8 + mq + kMaxM + kWarpsMax * 8 +
+           (mq + 1) / 2 + 8;
 }
 
-size_t batch_cluster_team_doubles(int max_m, int max_q)
+size_t batch_slice_doubles(int max_m, int max_q)
 {
-    const int mq = max_m * max_q;
-    return (size_t)scal_size(max_m, max_q) + 2 * (size_t)max_q * max_m * 4 + 16 + kMaxM + kWarpsMax * 8 +
-           (kWarpsMax * kMaxM * 4 + 1) / 2 + (mq + 1) / 2 + mq + 8;
+    // a one-warp team has one segment per row
+    return (team_doubles(max_m, max_q, max_q, 1) + 3) / 4 * 4;
+}
+
+size_t batch_cluster_team_doubles(int max_m, int max_q, int warps, int cluster)
+{
+    // at most q + W items (W = warps x cluster)
+    return team_doubles(max_m, max_q, max_q + warps * cluster, warps);
 }
 
 size_t batch_smem_bytes(int warps, size_t slice_doubles)

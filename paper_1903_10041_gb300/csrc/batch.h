@@ -47,8 +47,8 @@ struct BatchArgs {
 inline int batch_mbound(int max_m) { return max_m <= 4 ? 4 : 8; }
 
 size_t batch_slice_doubles(int max_m, int max_q);
-// Shared memory (doubles) a cluster team needs in each of its CTAs.
-size_t batch_cluster_team_doubles(int max_m, int max_q);
+// Shared memory (doubles) a CTA or cluster team needs in each of its CTAs.
+size_t batch_cluster_team_doubles(int max_m, int max_q, int warps, int cluster);
 size_t batch_smem_bytes(int warps, size_t slice_doubles);
 int batch_blocks_per_sm(int warps, int mbound, size_t smem);
 // Launch with clusters of `cluster` CTAs (1 = no clusters); grid is a multiple of it.

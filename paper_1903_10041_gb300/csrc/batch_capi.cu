@@ -85,7 +85,7 @@ cudaError_t to_host(const admm_problem &in, HostProblem &out)
 struct admm_batch {
     int count = 0, dev = 0, nsm = 0, max_m = 0, max_q = 0;
     admm_params prm{};
-    admm_batch_config cfg{8, 0, 16384, 8, 0, 131072};
+    admm_batch_config cfg{8, 0, 16384, 1, 0, 131072};
     Store store;
     std::vector<BatchInst> inst;
     BatchInst *d_inst = nullptr;
@@ -142,7 +142,9 @@ admm_status build_queues(admm_batch *b)
     BTRY(cudaMemcpy(b->d_order, all.data(), sizeof(int) * std::max<size_t>(all.size(), 1), cudaMemcpyHostToDevice));
     // launch shape: as many co-resident CTAs (clusters) as fit
     const int mb = batch_mbound(b->max_m);
-    b->smem = batch_smem_bytes(b->cfg.warps_per_cta, b->slice);
+    b->smem = std::max(batch_smem_bytes(b->cfg.warps_per_cta, b->slice),
+                       sizeof(double) * batch_cluster_team_doubles(b->max_m, b->max_q, b->cfg.warps_per_cta,
+                                                                   clusters ? b->cfg.cluster_size : 1));
     const int per_sm = batch_blocks_per_sm(b->cfg.warps_per_cta, mb, b->smem);
     if (per_sm < 1) return bfail(ADMM_EUNSUPPORTED, "batched kernel cannot be resident with this configuration");
     const int use = b->cfg.ctas_per_sm > 0 ? std::min(b->cfg.ctas_per_sm, per_sm) : per_sm;

@@ -430,7 +430,7 @@ void admm_server_default_config(admm_server_config *c)
     c->batch.warps_per_cta = 8;
     c->batch.ctas_per_sm = 0;
     c->batch.small_max_elements = 16384;
-    c->batch.cluster_size = 8;
+    c->batch.cluster_size = 1;
     c->batch.cluster_min_elements = 131072;
 }
 
@@ -496,7 +496,9 @@ admm_status admm_server_create(const admm_params *prm, const admm_server_config 
     // launch shape of a tick: kernel and slices for the configured max m, q
     S->mbound = batch_mbound(cfg->max_m);
     S->slice = batch_slice_doubles(cfg->max_m, cfg->max_q);
-    S->smem = batch_smem_bytes(cfg->batch.warps_per_cta, S->slice);
+    S->smem = std::max(batch_smem_bytes(cfg->batch.warps_per_cta, S->slice),
+                       sizeof(double) * batch_cluster_team_doubles(cfg->max_m, cfg->max_q, cfg->batch.warps_per_cta,
+                                                                   std::max(1, cfg->batch.cluster_size)));
     const int per_sm = batch_blocks_per_sm(cfg->batch.warps_per_cta, S->mbound, S->smem);
     if (per_sm < 1) return bail(ADMM_EUNSUPPORTED, "tick kernel cannot be resident");
     const int use = cfg->batch.ctas_per_sm > 0 ? std::min(cfg->batch.ctas_per_sm, per_sm) : per_sm;
