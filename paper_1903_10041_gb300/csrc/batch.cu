@@ -1,435 +1,23 @@
-// Batched solve: thousands of independent instances of uneven n, m, q in one
-// persistent launch (mixed precision).
-//
-// Each instance is solved by one team of threads that runs the whole ADMM
-// loop of App. A for it with team-local synchronisation only: a whole CTA
-// for large instances, or a single warp for small ones (so a CTA of W warps
-// holds W small instances at once).  Teams take work from two global
-// queues of instance ids, large ones first, each sorted by decreasing
-// estimated work (longest-processing-time order), so a CTA that finishes
-// early takes the next instance.  Each instance stops on its own stop test.
-//
-// The largest instances are solved by a thread-block cluster (2-8 CTAs on
-// neighbouring SMs): each CTA reduces its part of every row into records in
-// its own shared memory, one hardware cluster barrier per iteration follows,
-// and every CTA reads all CTAs' records through distributed shared memory in
-// rank order and runs the scalar steps redundantly.
-//
-// Per iteration a team sweeps the rows j = 1..q of its instance; within a
-// row its threads take consecutive column vectors (coalesced) and run the
-// element update of mixed_elem.cuh; the row's sums over k are reduced
-// across the team in a fixed order into a record in shared memory, and the
-// per-(i, j) scalar steps, residuals and stop test follow on the team.  The
-// arithmetic and its order depend only on the instance's own shape and its
-// team kind (fixed by the instance's size), so an instance gives the same
-// bits alone and in any mix.
-//
-// An iteration budget lets a launch stop every instance after a given
-// number of iterations with its state saved; the serving loop uses it to
-// run the batch in ticks and admit new instances between ticks.
+// Batched solve: host-side launch helpers, kernel selection and the
+// receding-horizon shift kernels.  The persistent kernel itself is in
+// batch_kernel.cuh, instantiated per CTA shape in batch_w4/8/16.cu.
 #include <algorithm>
-
-#include <cooperative_groups.h>
 
 #include "batch.h"
 #include "common.cuh"
-#include "mixed_elem.cuh"
 
 namespace admm_impl {
-
-namespace {
-
-// Team of NT threads (32 = one warp; or the whole CTA).
-template <int NT> struct Team {
-    int tid;
-    __device__ __forceinline__ void sync() const
-    {
-        if constexpr (NT == 32) __syncwarp();
-        else __syncthreads();
-    }
-};
-
-// Team-wide max of NV doubles over NT threads of one CTA (every thread gets the result).
-template <int NT, int NV> __device__ __forceinline__ void team_max(const Team<NT> &T, double *v, double *scr)
-{
-#pragma unroll
-    for (int t = 0; t < NV; ++t) v[t] = warp_max(v[t]);
-    if constexpr (NT > 32) {
-        const int lane = T.tid & 31, w = T.tid >> 5;
-        if (lane == 0)
-            for (int t = 0; t < NV; ++t) scr[w * 8 + t] = v[t];
-        __syncthreads();
-        for (int t = 0; t < NV; ++t) {
-            double r = 0.0;
-            for (int ww = 0; ww < NT / 32; ++ww) r = fmax(r, scr[ww * 8 + t]);
-            v[t] = r;
-        }
-        __syncthreads();
-    }
-}
-
-// Team-wide FP64 sum over NT threads of one CTA (fixed order), every thread gets the result.
-template <int NT> __device__ __forceinline__ double team_sum(const Team<NT> &T, double v, double *scr)
-{
-    v = warp_sum(v);
-    if constexpr (NT > 32) {
-        const int lane = T.tid & 31, w = T.tid >> 5;
-        if (lane == 0) scr[w * 8] = v;
-        __syncthreads();
-        double r = 0.0;
-        for (int ww = 0; ww < NT / 32; ++ww) r += scr[ww * 8];
-        __syncthreads();
-        return r;
-    }
-    return v;
-}
-
-enum { TEAM_WARP = 0, TEAM_CTA = 1, TEAM_CLUSTER = 2 };
-
-// Segments per row for a team of W warps: rows are cut so that about one
-// (row, segment) work item falls to each warp, but no segment is shorter
-// than two vectors per lane.
-__host__ __device__ inline int team_segments(int W, int q, int nv)
-{
-    const int want = (W + q - 1) / q;
-    const int cap = nv / 64 > 1 ? nv / 64 : 1;
-    return want < 1 ? 1 : (want < cap ? want : cap);
-}
-
-// One team solves instance `id` from its saved state until it stops or the
-// iteration budget runs out.  KIND: one warp (slice = that warp's shared
-// memory), one CTA, or a thread-block cluster (every CTA runs this
-// function; each holds a copy of the scalar state and records of the work
-// items its warps processed).  Work per iteration: items (row j, segment)
-// in a fixed order, one per warp in turn; each warp reduces its items with
-// shuffles only; one team barrier; then the per-(i, j) scalar steps read the
-// records of each row in segment order.
-template <int KIND, int NW, int M> __device__ void solve_team(const BatchArgs &a, int id, double *smem)
-{
-    namespace cg = cooperative_groups;
-    constexpr int NTL = KIND == TEAM_WARP ? 32 : NW * 32; // threads of this CTA in the team
-    constexpr int NWT = NTL / 32;
-    constexpr int VW = kMixedVW;
-    const int lane = threadIdx.x & 31;
-    const int tid = KIND == TEAM_WARP ? lane : (int)threadIdx.x;
-    const int wl = KIND == TEAM_WARP ? 0 : (int)(threadIdx.x >> 5);
-    int CL = 1, rank = 0;
-    if constexpr (KIND == TEAM_CLUSTER) {
-        CL = (int)cg::this_cluster().num_blocks();
-        rank = (int)cg::this_cluster().block_rank();
-    }
-    const Team<NTL> T{tid};
-    auto sync_local = [&]() {
-        if constexpr (KIND == TEAM_WARP) __syncwarp();
-        else __syncthreads();
-    };
-    auto sync_team = [&]() {
-        if constexpr (KIND == TEAM_CLUSTER) cg::this_cluster().sync();
-        else sync_local();
-    };
-
-    const BatchInst I = a.inst[id];
-    const int n = I.n, m = I.m, q = I.q, mq = m * q;
-    const int nv = (n + VW - 1) / VW;
-    const int W = NWT * CL, gw = rank * NWT + wl;
-    const int S = team_segments(W, q, nv);
-    const int seg = (nv + S - 1) / S;
-    const int items = q * S;
-
-    // shared memory: scal | rec[2][items][m][4] | cmax[2][NWT][2] | part[8] | x0s[mq] | x1n | scr | uoff
-    double *scal = smem;
-    double *lam = scal, *zeta = scal + mq, *hh = scal + 2 * mq, *pp = scal + 3 * mq, *nu = scal + 4 * mq;
-    double *x1 = scal + 5 * mq, *rho = x1 + m, *flags = rho + 4;
-    double *rec0 = smem + scal_size(m, q);
-    double *cmax = rec0 + 2 * (size_t)items * m * 4;
-    double *part = cmax + 4 * NWT;
-    double *x0s = part + 8;
-    double *x1n = x0s + mq;
-    double *scr = x1n + kMaxM;
-    float *uoff = (float *)(scr + kWarpsMax * 8);
-
-    double *gscal = a.scal + I.off_scal;
-    double *out = a.out + (size_t)id * kInfo;
-    const bool skip = out[14] != 0.0;
-    sync_team();
-    if (skip) return; // every member read the same flag
-    for (int t = tid; t < scal_size(m, q); t += NTL) scal[t] = gscal[t];
-    sync_local();
-    for (int pr = tid; pr < mq; pr += NTL) uoff[pr] = (float)(zeta[pr] + lam[pr]);
-    const int it0 = (int)out[0];
-    sync_local();
-
-    const ElemF32 ea = {a.f2 + I.off_e, a.f1 + I.off_e, a.g2 + I.off_e, a.g1 + I.off_e, a.g0 + I.off_e,
-                        a.lo + I.off_b, a.hi + I.off_b, a.y + I.off_c,  a.x + I.off_e,  a.s + I.off_c,
-                        a.mu + I.off_c, a.s_lo + I.off_c, a.mu_lo + I.off_c, n, m, q, I.ld, a.sweep, a.xmin_mode};
-    const double *cc = a.c + I.off_src;
-    const double *sumg0 = a.sumg0 + I.off_pair;
-    unsigned esc = 0;
-    bool conv = false;
-    double res[7] = {out[4], out[5], out[6], out[7], out[8], out[9], out[10]};
-    double r_last = out[2], s_last = out[3];
-    int it = it0;
-    const int it_end = a.iter_budget > 0 ? min(a.max_iter, it0 + a.iter_budget) : a.max_iter;
-
-    while (it < it_end) {
-        ++it;
-        const int par = it & 1;
-        const bool check = (it % a.check_every == 0) || (it == a.max_iter);
-        const bool cold = flags[0] != 0.0;
-        const float mu_div = (float)flags[1];
-        const float rho1 = (float)rho[0], rho3 = (float)rho[2], rho4 = (float)rho[3];
-        const float iq = 1.0f / (float)q;
-        float fcr = 0.0f, fcs = 0.0f;
-        double *recs = rec0 + (size_t)par * items * m * 4;
-        for (int item = gw; item < items; item += W) {
-            const int j = item / S, sg = item - j * S;
-            const int v0 = sg * seg, v1 = min(nv, v0 + seg);
-            float ghi[M], glo[M], fmx[M], fmn[M];
-#pragma unroll
-            for (int i = 0; i < M; ++i) {
-                ghi[i] = 0.0f;
-                glo[i] = 0.0f;
-                fmx[i] = -INFINITY;
-                fmn[i] = INFINITY;
-            }
-            double *rec = recs + (size_t)item * m * 4;
-            for (int v = v0 + lane; v < v1; v += 32)
-                vec32<M, VW, false>(ea, uoff, x1, nu, j, v * VW, check, cold, mu_div, rho1, rho3, rho4, iq, ghi, glo,
-                                    fmx, fmn, fcr, fcs, esc, rec);
-#pragma unroll
-            for (int i = 0; i < M; ++i)
-                if (i < m) {
-                    FF v = ff_norm(ghi[i], glo[i]);
-                    float hi = fmx[i], lo = fmn[i];
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) {
-                        const FF u = {__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
-                        v = ff_add(v, u);
-                        if (check) {
-                            hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
-                            lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
-                        }
-                    }
-                    if (lane == 0) {
-                        rec[i * 4 + 0] = (double)v.hi + (double)v.lo;
-                        rec[i * 4 + 1] = check ? (double)hi : 0.0;
-                        rec[i * 4 + 2] = check ? (double)lo : 0.0;
-                    }
-                }
-        }
-        if (check) {
-            const float wr = warp_max(fcr), ws = warp_max(fcs);
-            if (lane == 0) {
-                cmax[(par * NWT + wl) * 2 + 0] = (double)wr;
-                cmax[(par * NWT + wl) * 2 + 1] = (double)ws;
-            }
-        }
-        if (tid == 0) flags[1] = 1.0;
-        sync_team(); // every record of this iteration is complete and visible
-
-        const double r1 = rho[0], r2 = rho[1], r3 = rho[2];
-        const double kappa = r2 / (r1 + (double)n * r2);
-        double r2m = 0.0, r3m = 0.0, s1m = 0.0, s2m = 0.0;
-        for (int pr = tid; pr < mq; pr += NTL) {
-            const int i = pr / q, j = pr - i * q;
-            double Ssum = 0.0, dmx = -INFINITY, dmn = INFINITY, x0 = 0.0;
-            for (int sg = 0; sg < S; ++sg) {
-                const int item = j * S + sg;
-                const double *rb = recs;
-                if constexpr (KIND == TEAM_CLUSTER) rb = cg::this_cluster().map_shared_rank(recs, (item % W) / NWT);
-                const double *rr = rb + ((size_t)item * m + i) * 4;
-                Ssum += rr[0];
-                if (check) {
-                    dmx = fmax(dmx, rr[1]);
-                    dmn = fmin(dmn, rr[2]);
-                }
-                if (sg == 0) x0 = rr[3];
-            }
-            const double lm = lam[pr], zt = zeta[pr], h0 = hh[pr], p0 = pp[pr];
-            const double Wv = (Ssum + sumg0[pr]) - (double)n * lm;
-            const double lamn = kappa * ((h0 + p0) - Wv);
-            const double Z = Wv + (double)n * lamn;
-            const double cz = Z - p0;
-            const double hn = cz < cc[i] ? cz : cc[i];
-            const double pn = p0 + (hn - Z);
-            if (check) {
-                r2m = fmax(r2m, fabs(lamn - lm));
-                r3m = fmax(r3m, fabs(hn - Z));
-                const double dl = (lamn - lm) - zt;
-                s1m = fmax(s1m, fmax(fabs(dmx + dl), fabs(dmn + dl)));
-                s2m = fmax(s2m, fabs(hn - h0));
-            }
-            lam[pr] = lamn;
-            zeta[pr] = lamn - lm;
-            hh[pr] = hn;
-            pp[pr] = pn;
-            x0s[pr] = x0;
-        }
-        sync_local();
-        if (tid < m) {
-            const int i = tid;
-            double sum = 0.0;
-            for (int j = 0; j < q; ++j) sum += x0s[i * q + j] - nu[i * q + j];
-            x1n[i] = sum / (double)q;
-        }
-        sync_local();
-        double r4m = 0.0;
-        for (int pr = tid; pr < mq; pr += NTL) {
-            const int i = pr / q;
-            const double x0 = x0s[pr], xn = x1n[i];
-            nu[pr] = nu[pr] + (xn - x0);
-            if (check) r4m = fmax(r4m, fabs(x0 - xn));
-        }
-        sync_local();
-        if (tid < m) x1[tid] = x1n[tid];
-        if (tid == 0) flags[0] = 0.0;
-        sync_local();
-        if (check) {
-            double c1 = 0.0, c2 = 0.0;
-            for (int r = 0; r < CL; ++r) {
-                const double *cb = cmax;
-                if constexpr (KIND == TEAM_CLUSTER) cb = cg::this_cluster().map_shared_rank(cmax, r);
-                for (int w = 0; w < NWT; ++w) {
-                    c1 = fmax(c1, cb[(par * NWT + w) * 2 + 0]);
-                    c2 = fmax(c2, cb[(par * NWT + w) * 2 + 1]);
-                }
-            }
-            double v[7] = {c1, r2m, r3m, r4m, s1m, s2m, c2};
-            team_max<NTL, 7>(T, v, scr);
-#pragma unroll
-            for (int t = 0; t < 7; ++t) res[t] = v[t];
-            const double r = fmax(fmax(v[0], v[1]), fmax(v[2], v[3]));
-            const double sgm = fmax(fmax(r1 * v[4], r2 * v[5]), r3 * v[6]);
-            r_last = r;
-            s_last = sgm;
-            if (r < a.r_tol && sgm < a.s_tol) {
-                conv = true;
-                break;
-            }
-            if (a.adapt && it < a.max_iter) { // Sec. IV-A, duals rescaled by rho_old / rho_new
-                const double ratio = r / sgm, target = a.r_tol / a.s_tol;
-                double f = 1.0;
-                if (ratio > 1.2 * target) f = a.tau;
-                else if (ratio < 0.8 * target) f = 1.0 / a.tau;
-                if (f != 1.0) {
-                    for (int pr = tid; pr < mq; pr += NTL) {
-                        lam[pr] /= f;
-                        pp[pr] /= f;
-                        nu[pr] /= f;
-                    }
-                    sync_local();
-                    if (tid < 4) rho[tid] *= f;
-                    if (tid == 0) flags[1] = f;
-                    sync_local();
-                }
-            }
-        }
-        for (int pr = tid; pr < mq; pr += NTL) uoff[pr] = (float)(zeta[pr] + lam[pr]);
-        sync_local();
-    }
-    const bool finished = conv || it >= a.max_iter;
-
-    // objective (1/q) sum f(x) of eq. (2): each CTA sums its share, rank 0 adds in rank order
-    double acc = 0.0;
-    if (finished) {
-        const float *F2 = ea.f2, *F1 = ea.f1, *F0 = a.f0 + I.off_e;
-        const int64_t tot = (int64_t)mq * n;
-        for (int64_t t = (int64_t)rank * NTL + tid; t < tot; t += (int64_t)CL * NTL) {
-            const int64_t r = t / n;
-            const int k = (int)(t - r * n);
-            const size_t e = (size_t)r * I.ld + k;
-            const double x = ea.x[e];
-            acc += (double)F2[e] * x * x + (double)F1[e] * x + (double)F0[e];
-        }
-    }
-    acc = team_sum<NTL>(T, acc, scr);
-    const double escs = team_sum<NTL>(T, (double)esc, scr);
-    if (tid == 0) {
-        part[0] = acc;
-        part[1] = escs;
-    }
-    sync_team();
-    if (rank == 0) {
-        for (int t = tid; t < scal_size(m, q); t += NTL) gscal[t] = scal[t];
-        if (tid == 0) {
-            double obj = 0.0, es = 0.0;
-            for (int r = 0; r < CL; ++r) {
-                const double *pb = part;
-                if constexpr (KIND == TEAM_CLUSTER) pb = cg::this_cluster().map_shared_rank(part, r);
-                obj += pb[0];
-                es += pb[1];
-            }
-            out[0] = it;
-            out[1] = conv ? 1.0 : 0.0;
-            out[2] = r_last;
-            out[3] = s_last;
-            for (int t = 0; t < 7; ++t) out[4 + t] = res[t];
-            if (finished) out[11] = obj / (double)q;
-            out[12] = 0.0;
-            out[13] += es;
-            out[14] = finished ? 1.0 : 0.0;
-        }
-    }
-    sync_team(); // rank 0 has read every member's shared memory
-}
-
-template <int NW, int M> __global__ void __launch_bounds__(NW * 32, 16 / NW) batch_kernel(BatchArgs a)
-{
-    extern __shared__ double smem[];
-    __shared__ int s_item;
-    const int nX = a.nLS ? a.nLS[0] : a.nX, nL = a.nLS ? a.nLS[1] : a.nL, nS = a.nLS ? a.nLS[2] : a.nS;
-    // Largest instances: the whole cluster is one team (rank 0 takes the item
-    // and the other CTAs read it through distributed shared memory).
-    if (nX > 0) {
-        namespace cg = cooperative_groups;
-        cg::cluster_group cl = cg::this_cluster();
-        for (;;) {
-            if (cl.block_rank() == 0 && threadIdx.x == 0) s_item = atomicAdd(a.qX, 1);
-            cl.sync();
-            const int item = *cl.map_shared_rank(&s_item, 0);
-            cl.sync();
-            if (item >= nX) break;
-            solve_team<TEAM_CLUSTER, NW, M>(a, a.orderX[item], smem);
-        }
-    }
-    // Large instances: the whole CTA is one team.
-    for (;;) {
-        if (threadIdx.x == 0) s_item = atomicAdd(a.qL, 1);
-        __syncthreads();
-        const int item = s_item;
-        __syncthreads();
-        if (item >= nL) break;
-        solve_team<TEAM_CTA, NW, M>(a, a.orderL[item], smem);
-    }
-    // Small instances: each warp is a team with its own slice.
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    double *slice = smem + (size_t)w * a.slice_doubles;
-    for (;;) {
-        int item = 0;
-        if (lane == 0) item = atomicAdd(a.qS, 1);
-        item = __shfl_sync(0xffffffffu, item, 0);
-        if (item >= nS) break;
-        solve_team<TEAM_WARP, NW, M>(a, a.orderS[item], slice);
-    }
-}
-
-template <int NW> void *batch_fn(int mb)
-{
-    switch (mb) {
-    case 2: return (void *)batch_kernel<NW, 2>;
-    case 4: return (void *)batch_kernel<NW, 4>;
-    default: return (void *)batch_kernel<NW, 8>;
-    }
-}
 
 void *batch_pick(int warps, int mb)
 {
     switch (warps) {
-    case 4: return batch_fn<4>(mb);
-    case 16: return batch_fn<16>(mb);
-    default: return batch_fn<8>(mb);
+    case 4: return batch_fn_w4(mb);
+    case 16: return batch_fn_w16(mb);
+    default: return batch_fn_w8(mb);
     }
 }
+
+namespace {
 
 // Receding-horizon warm start (Sec. II, Alg. 2): the previous solution of a
 // controller moved one step forward in place (x_k <- x_{k+1}, last step

@@ -47,6 +47,10 @@ struct BatchArgs {
 inline int batch_mbound(int max_m) { return max_m <= 4 ? 4 : 8; }
 
 size_t batch_slice_doubles(int max_m, int max_q);
+// The persistent kernel for CTAs of 4, 8 or 16 warps and source bound mbound.
+void *batch_fn_w4(int mbound);
+void *batch_fn_w8(int mbound);
+void *batch_fn_w16(int mbound);
 // Shared memory (doubles) a CTA or cluster team needs in each of its CTAs.
 size_t batch_cluster_team_doubles(int max_m, int max_q, int warps, int cluster);
 size_t batch_smem_bytes(int warps, size_t slice_doubles);

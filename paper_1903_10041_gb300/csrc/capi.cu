@@ -169,8 +169,9 @@ struct admm_handle {
     int *status = nullptr;
     double *info_host = nullptr; // pinned
     // launch shape
-    int grid = 0, nbmax = 0, rs = 0;
+    int grid = 0, nbmax = 0, rs = 0, minb = 1;
     int64_t chunk = 0, ncols = 0;
+    int pieces = 0;
     size_t smem = 0;
 };
 
@@ -454,20 +455,15 @@ admm_status admm_create(const admm_problem *P, const admm_params *prm, admm_hand
 
     // launch shape: contiguous equal column chunks, all SMs busy
     h->smem = single_smem_bytes(m, q);
-    const int per_sm = single_blocks_per_sm(prm->precision, m, h->smem);
-    if (per_sm < 1) return bail(fail(ADMM_EUNSUPPORTED, "solve kernel cannot be resident (smem %zu B)", h->smem));
     h->rs = mixed ? ld : n;
     h->ncols = (int64_t)q * h->rs;
-    const int64_t unit = mixed ? kMixedVW : 1;   // mixed: vectors of kMixedVW columns
-    const int64_t min_cols = mixed ? 32 * kMixedVW : 32; // at least a warp of work per CTA
-    int64_t g = std::min<int64_t>((int64_t)h->nsm * per_sm, std::max<int64_t>(1, h->ncols / min_cols));
-    h->chunk = ((h->ncols + g - 1) / g + unit - 1) / unit * unit;
-    h->grid = (int)((h->ncols + h->chunk - 1) / h->chunk);
-    h->nbmax = 1;
-    for (int j = 0; j < q; ++j) {
-        const int64_t r0 = (int64_t)j * h->rs, r1 = r0 + h->rs - 1;
-        h->nbmax = std::max(h->nbmax, (int)(r1 / h->chunk - r0 / h->chunk + 1));
-    }
+    const SingleShape sh = single_shape(prm->precision, m, q, h->rs, h->nsm, h->smem);
+    if (sh.grid < 1) return bail(fail(ADMM_EUNSUPPORTED, "solve kernel cannot be resident (smem %zu B)", h->smem));
+    h->chunk = sh.chunk;
+    h->pieces = sh.pieces;
+    h->grid = sh.grid;
+    h->nbmax = sh.nbmax;
+    h->minb = sh.minb;
     TRY(cudaMalloc(&h->part, sizeof(double) * 2 * (size_t)q * h->nbmax * m * 4));
     TRY(cudaMalloc(&h->cpart, sizeof(double) * 2 * (size_t)h->grid * 4));
     st = reset_state(h);
@@ -542,6 +538,7 @@ admm_status admm_solve(admm_handle *h, const admm_state *warm, admm_result *out,
     a.rs = h->rs;
     a.ncols = h->ncols;
     a.chunk = h->chunk;
+    a.pieces = h->pieces;
     a.nbmax = h->nbmax;
     a.grid = h->grid;
     a.f2 = h->f2;
@@ -577,7 +574,7 @@ admm_status admm_solve(admm_handle *h, const admm_state *warm, admm_result *out,
     a.spin_ns = spin_limit_ns();
     CUDA_TRY(cudaMemsetAsync(h->bar, 0, sizeof(unsigned), st));
     CUDA_TRY(cudaMemsetAsync(h->status, 0, sizeof(int), st));
-    CUDA_TRY(launch_single(h->prm.precision, a, h->smem, st));
+    CUDA_TRY(launch_single(h->prm.precision, h->minb, a, h->smem, st));
     CUDA_TRY(cudaMemcpyAsync(h->info_host, h->info, kInfo * 8, cudaMemcpyDeviceToHost, st));
     if (out && out->x) CUDA_TRY(export_rows(h, out->x, out->on_device != 0, h->x, (int64_t)h->m * h->q, st));
     if (out && out->x1)

@@ -43,17 +43,19 @@ __device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned target, int
         atomicAdd(bar, 1u);
         unsigned long long t0 = globaltimer_ns();
         int ok = 1;
-        for (;;) {
+        for (unsigned spins = 1;; ++spins) {
             unsigned v = ld_acquire_u32(bar);
             if ((int)(v - target) >= 0)
                 break;
-            if (ld_volatile_i32(status) != 0) { ok = 0; break; }
-            if ((long long)(globaltimer_ns() - t0) > spin_ns) {
-                atomicCAS(status, 0, timeout_code);
-                ok = 0;
-                break;
+            if ((spins & 15) == 0) { // error flag and time limit every 16 polls
+                if (ld_volatile_i32(status) != 0) { ok = 0; break; }
+                if ((long long)(globaltimer_ns() - t0) > spin_ns) {
+                    atomicCAS(status, 0, timeout_code);
+                    ok = 0;
+                    break;
+                }
             }
-            __nanosleep(32);
+            __nanosleep(32); // leave issue slots to co-resident CTAs still computing
         }
         __threadfence();
         s_ok = ok;

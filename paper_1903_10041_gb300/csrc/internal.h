@@ -32,8 +32,9 @@ struct SingleArgs {
     int n, m, q, ld;           // ld: padded row stride of the [*][n] arrays
     int rs;                    // row length of the column space: n (FP64) or ld (mixed, padded)
     int64_t ncols;             // q * rs columns (j, k)
-    int64_t chunk;             // columns per CTA (contiguous in j-major order)
-    int nbmax;                 // max CTAs whose chunks touch one row
+    int64_t chunk;             // flat split: columns per CTA (contiguous in j-major order)
+    int pieces;                // > 0: row-aligned split, CTA b takes piece b % pieces of row b / pieces
+    int nbmax;                 // max CTAs whose columns touch one row
     int grid;                  // CTAs
     const void *f2, *f1, *f0, *g2, *g1, *g0, *lo, *hi, *y;   // storage type of the precision
     const double *c, *sumg0;   // [m], [mq]
@@ -51,10 +52,29 @@ struct SingleArgs {
     long long spin_ns;         // bound of one barrier wait
 };
 
-// Launch the persistent single-instance solve kernel (cooperative launch).
-cudaError_t launch_single(int precision, const SingleArgs &a, size_t smem, cudaStream_t st);
+// Launch the persistent single-instance solve kernel (cooperative launch);
+// minb selects the register-budget variant (1 or 2 CTAs per SM).
+cudaError_t launch_single(int precision, int minb, const SingleArgs &a, size_t smem, cudaStream_t st);
 // Max co-resident CTAs per SM of that kernel for the given dynamic smem.
-int single_blocks_per_sm(int precision, int m, size_t smem);
+int single_blocks_per_sm(int precision, int m, int minb, size_t smem);
+// Launch shape of a solve: CTAs, columns per CTA (a multiple of the vector
+// width in mixed precision), kernel variant, and the most CTAs touching one
+// row j (records per row).  grid = 0: the kernel cannot be resident.
+struct SingleShape {
+    int grid;
+    int64_t chunk;
+    int pieces;
+    int minb;
+    int nbmax;
+};
+
+// Column bound t (0..p) of the row-aligned split of a row of rs columns
+// into p pieces, on multiples of `unit`.
+inline __host__ __device__ int64_t piece_bound(int t, int64_t rs, int p, int unit)
+{
+    return (int64_t)t * rs / p / unit * unit;
+}
+SingleShape single_shape(int precision, int m, int q, int64_t rs, int nsm, size_t smem);
 // Dynamic shared memory the single-instance kernel needs.
 size_t single_smem_bytes(int m, int q);
 // Index of the kernel variant used for m sources (template bound).

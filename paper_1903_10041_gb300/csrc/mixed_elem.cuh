@@ -141,6 +141,18 @@ __device__ __forceinline__ void vec32(const ElemF32 &a, const float *uoff, const
     bool valid[VW];
 #pragma unroll
     for (int c = 0; c < VW; ++c) valid[c] = k0 + c < n;
+    const bool jac = a.sweep == ADMM_JACOBI;
+    // sum of x over the sources: Gauss-Seidel keeps it current as the sweep
+    // replaces x_i, Jacobi keeps the previous iterate's
+    float xsum[VW];
+#pragma unroll
+    for (int c = 0; c < VW; ++c) {
+        float t = 0.0f;
+#pragma unroll
+        for (int i = 0; i < M; ++i)
+            if (i < m) t += xt[i][c];
+        xsum[c] = t;
+    }
 
 #pragma unroll
     for (int i = 0; i < M; ++i) {
@@ -166,10 +178,7 @@ __device__ __forceinline__ void vec32(const ElemF32 &a, const float *uoff, const
                 const float x0 = xt[i][c];
                 const float gq_old = (b2 * x0 + b1) * x0;
                 const float u = cold ? -g0 : gq_old + uo;
-                float others = 0.0f;
-#pragma unroll
-                for (int l = 0; l < M; ++l)
-                    if (l < m && l != i) others += (a.sweep == ADMM_JACOBI) ? xt[l][c] : xs[l][c];
+                const float others = xsum[c] - x0; // sum over l != i (x_i is still x0 here)
                 const float phi = ((st[c] - others) + yv[c]) + mu[c];
                 const float A = 0.5f * rho1 * b2 * b2;
                 const float B = rho1 * b2 * b1;
@@ -181,6 +190,7 @@ __device__ __forceinline__ void vec32(const ElemF32 &a, const float *uoff, const
                 }
                 const float xn = C64 ? quartic_min_fp64cubic(A, B, C, D, L4[c], H4[c], a.xmin_mode)
                                      : quartic_min32(A, B, C, D, L4[c], H4[c], a.xmin_mode, esc);
+                if (!jac) xsum[c] += xn - x0;
                 xs[i][c] = xn;
                 if (valid[c]) {
                     float ghh, gll;

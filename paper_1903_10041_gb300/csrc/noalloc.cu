@@ -194,18 +194,11 @@ extern "C" admm_status admm_solve_noalloc(const admm_problem *P, const admm_para
     if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return nfail(ADMM_ECUDA, "cudaDeviceGetAttribute failed");
     const size_t smem = single_smem_bytes(m, q);
-    const int per_sm = single_blocks_per_sm(prm->precision, m, smem);
-    if (per_sm < 1) return nfail(ADMM_EUNSUPPORTED, "solve kernel cannot be resident");
     // the same launch shape as admm_create
-    const int64_t ncols = (int64_t)q * n;
-    const int64_t g = std::min<int64_t>((int64_t)nsm * per_sm, std::max<int64_t>(1, ncols / 32));
-    const int64_t chunk = (ncols + g - 1) / g;
-    const int grid = (int)((ncols + chunk - 1) / chunk);
-    int nbmax = 1;
-    for (int j = 0; j < q; ++j) {
-        const int64_t r0 = (int64_t)j * n, r1 = r0 + n - 1;
-        nbmax = std::max(nbmax, (int)(r1 / chunk - r0 / chunk + 1));
-    }
+    const SingleShape sh = single_shape(prm->precision, m, q, n, nsm, smem);
+    if (sh.grid < 1) return nfail(ADMM_EUNSUPPORTED, "solve kernel cannot be resident");
+    const int64_t ncols = (int64_t)q * n, chunk = sh.chunk;
+    const int grid = sh.grid, nbmax = sh.nbmax;
     // scratch layout (doubles, each region 32-double aligned)
     auto al = [](size_t v) { return (v + 31) / 32 * 32; };
     const size_t n_part = al((size_t)2 * q * nbmax * m * 4), n_cpart = al((size_t)2 * grid * 4);
@@ -253,6 +246,7 @@ extern "C" admm_status admm_solve_noalloc(const admm_problem *P, const admm_para
     a.rs = n;
     a.ncols = ncols;
     a.chunk = chunk;
+    a.pieces = sh.pieces;
     a.nbmax = nbmax;
     a.grid = grid;
     a.f2 = P->f2;
@@ -284,7 +278,7 @@ extern "C" admm_status admm_solve_noalloc(const admm_problem *P, const admm_para
     a.sweep = prm->sweep;
     a.adapt = prm->adapt_rho;
     a.spin_ns = 2000000000LL;
-    e = launch_single(prm->precision, a, smem, cs);
+    e = launch_single(prm->precision, sh.minb, a, smem, cs);
     if (e != cudaSuccess) return nfail(ADMM_ECUDA, "solve launch: ", cudaGetErrorString(e));
     noalloc_finish<<<(mq + 255) / 256, 256, 0, cs>>>(m, q, scal, st->lam, st->zeta, st->h, st->p, st->nu, st->x1);
     double hinfo[kInfo], tail[6];

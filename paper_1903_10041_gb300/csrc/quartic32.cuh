@@ -148,11 +148,12 @@ __device__ __forceinline__ float quartic_min32(float A, float B, float C, float 
         if (!isfinite(x)) return quartic_min_fallback64(A, B, C, D, lo, hi, paper_mode);
         return clampf(x, lo, hi);
     }
+    // three real roots: t = theta/3 lies in [0, pi/3], where the fast sine and
+    // cosine are accurate to a few ulp; the Newton step below removes their error
     const float nQ = fmaxf(-Q, 0.0f);
     const float arg = nQ > 0.0f ? fminf(fmaxf(R * rsqrtf(nQ * nQ * nQ), -1.0f), 1.0f) : (R >= 0.0f ? 1.0f : -1.0f);
     const float t = acosf(arg) * (1.0f / 3.0f);
-    float st, ct;
-    sincosf(t, &st, &ct);
+    const float st = __sinf(t), ct = __cosf(t);
     const float two_sq = 2.0f * sqrt_fast(nQ);
     float x3 = two_sq * ct - b3;
     float x1 = two_sq * (-0.5f * ct - 0.86602540378f * st) - b3;

@@ -19,10 +19,61 @@
 // to [lo, hi] before comparing (the constrained minimiser is always one of
 // the two clamped roots); paper mode clamps the winner (Pi(argmin)).
 // A tie keeps the smaller root, as Algorithm 1's else branch does.
+//
+// FP64 arithmetic is the scarce resource on this GPU (1/64 of the FP32 rate),
+// so the two divisions and the cube root of the Cardano branch use FP32
+// seeds from the special-function unit followed by FP64 Newton steps
+// instead of the library routines: about a third of the FP64 instructions
+// of the element update.  Each result is within a few ulp of the correctly
+// rounded one.
 #pragma once
 #include "common.cuh"
 
 namespace admm_impl {
+
+__device__ __forceinline__ float rcp_approx_f32(float v)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+}
+
+// 1/a: FP32 seed (relative error below 2^-22), then two Newton steps
+// r <- r + r (1 - a r), each squaring the relative error.  Operands outside
+// the FP32 normal range take the FP64 division.
+__device__ __forceinline__ double rcp64(double a)
+{
+    const double aa = fabs(a);
+    if (!(aa > 1e-30 && aa < 1e30)) return 1.0 / a;
+    double r = (double)rcp_approx_f32((float)a);
+    double e = fma(-a, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-a, r, 1.0);
+    return fma(r, e, r);
+}
+
+// S = cbrt(v) and 1/S for v != 0.  Seed w ~ |v|^(-1/3) from the FP32
+// log2/exp2 units (relative error below 2e-5 over the accepted range), then
+// two Newton steps on f(w) = w^-3 - |v|, w <- w (4 - |v| w^3) / 3; with
+// w = w*(1 + e) the new error is about -2 e^2.  Operands outside the FP32
+// normal range take the library cube root.
+__device__ __forceinline__ void cbrt_rcbrt64(double v, double &S, double &invS)
+{
+    const double av = fabs(v);
+    if (!(av > 1e-30 && av < 1e30)) {
+        S = cbrt(v);
+        invS = 1.0 / S;
+        return;
+    }
+    float l, wf;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l) : "f"((float)av));
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(wf) : "f"(l * (-1.0f / 3.0f)));
+    double w = (double)wf;
+    w = w * fma(-av, w * w * w, 4.0) * (1.0 / 3.0);
+    w = w * fma(-av, w * w * w, 4.0) * (1.0 / 3.0);
+    S = copysign(av * w * w, v);
+    invS = copysign(w, v);
+}
 
 __device__ __forceinline__ double delta_f64(double u, double v, double b, double c, double d)
 {
@@ -36,8 +87,8 @@ __device__ __forceinline__ double quartic_min64(double A, double B, double C, do
                                                 double hi, int paper_mode)
 {
     if (A == 0.0)
-        return clampd(-D / (2.0 * C), lo, hi);
-    double inv = 1.0 / A;
+        return clampd(-D * rcp64(2.0 * C), lo, hi);
+    double inv = rcp64(A);
     double b = 0.75 * B * inv, c = 0.5 * C * inv, d = 0.25 * D * inv;
     double b3 = b * (1.0 / 3.0);
     double Q = c * (1.0 / 3.0) - b3 * b3;
@@ -46,8 +97,9 @@ __device__ __forceinline__ double quartic_min64(double A, double B, double C, do
     double Dl = Q3 + R * R;
     if (Dl > 0.0) {
         double sq = sqrt(Dl);
-        double S = cbrt(R >= 0.0 ? R + sq : R - sq);
-        double T = -Q / S;
+        double S, invS;
+        cbrt_rcbrt64(R >= 0.0 ? R + sq : R - sq, S, invS);
+        double T = -Q * invS;
         return clampd(S + T - b3, lo, hi);
     }
     if (Q == 0.0 && R == 0.0)

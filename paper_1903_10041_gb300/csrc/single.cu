@@ -2,8 +2,11 @@
 // the device, one cooperative launch per solve.
 //
 // Work split.  The columns (j, k) are taken in j-major order and cut into
-// `grid` contiguous chunks of `chunk` columns, one per CTA, so every CTA
-// does the same number of element updates.  The thread that owns a column
+// one contiguous range per CTA of (nearly) equal length: either every row j
+// cut into the same number of pieces (no CTA straddles two rows), or, for
+// short rows, flat chunks of `chunk` columns, where the row segments of one
+// CTA are worked on side by side by disjoint warps (or, when the segments are
+// long, one after another by all warps).  The thread that owns a column
 // updates all m sources of it in registers (step (a) sweeps the sources in
 // order, so the Gauss-Seidel sums over l != i stay local), then steps (e)
 // and (f) for that column.  The per-(i, j) sums over k that steps (b) and
@@ -24,8 +27,8 @@
 //
 // Precision variants (template PREC):
 //   ADMM_FP64             one column per thread, dense column space (rs = n);
-//   ADMM_MIXED            FP32 storage and element work on float4 quads of
-//                         columns over a padded column space (rs = ld); the
+//   ADMM_MIXED            FP32 storage and element work on vectors of
+//                         kMixedVW columns over a padded column space (rs = ld); the
 //                         capacity sums over k are accumulated per thread in
 //                         float-float (about 48 bits) and reduced in FP64; the
 //                         column state s, mu is stored and updated in
@@ -51,6 +54,7 @@ struct Sm {
     double *red;  // [kWarps][kMaxM][3]
     double *mx;   // [kWarps][8]
     double *bc;   // [16] broadcast
+    int *segof;   // [kWarps] segment (within the pass) of each warp
     float *uoff;  // [mq] zeta + lambda in FP32 (mixed variants)
 };
 
@@ -77,6 +81,8 @@ __device__ __forceinline__ Sm carve(double *base, int m, int q)
     t += kWarps * 8;
     s.bc = t;
     t += 16;
+    s.segof = (int *)t;
+    t += kWarps;
     s.uoff = (float *)t;
     return s;
 }
@@ -193,10 +199,107 @@ __device__ __forceinline__ void column64(const SingleArgs &a, const Sm &sm, int 
     }
 }
 
-// Block reduction of one row segment into its partial record.
+// Warp plan of one pass over the row segments jb..je (at most kWarps rows)
+// of the chunk [c0, c1): segment s gets warps [W_s, W_s+1) with
+// W_s = s + floor((kWarps - ns) * (columns before s) / (columns in the pass)),
+// at least one warp each and the rest in proportion to length, so the
+// segments of a CTA run side by side.  The plan depends only on the launch
+// shape, so it is the same in every iteration.
+struct SegPlan {
+    int j;          // row of this warp's segment
+    int seg;        // its index within the pass (j - jb)
+    int lw, nw;     // this warp's index among the segment's warps, their count
+    int64_t s0, s1; // the segment's columns [s0, s1)
+};
+
+__device__ __forceinline__ SegPlan seg_plan(int64_t c0, int64_t c1, int64_t rs, int jb, int je, int w)
+{
+    SegPlan p{};
+    const int ns = je - jb + 1;
+    if (ns == 1) {
+        p.j = jb;
+        p.lw = w;
+        p.nw = kWarps;
+    } else {
+        const int64_t b0 = max(c0, (int64_t)jb * rs), b1 = min(c1, (int64_t)(je + 1) * rs);
+        const float scale = (float)(kWarps - ns) / (float)(b1 - b0);
+        int wlo = 0, whi = kWarps;
+        for (int t = 0; t < ns; ++t) {
+            const int64_t before = max(c0, (int64_t)(jb + t) * rs) - b0;
+            const int ws = t + (int)floorf(scale * (float)before);
+            if (ws <= w) {
+                p.seg = t;
+                wlo = ws;
+            } else {
+                whi = min(whi, ws);
+            }
+        }
+        p.lw = w - wlo;
+        p.nw = whi - wlo;
+        p.j = jb + p.seg;
+    }
+    p.s0 = max(c0, (int64_t)p.j * rs);
+    p.s1 = min(c1, (int64_t)(p.j + 1) * rs);
+    return p;
+}
+
+// Rows per pass for the chunk [c0, c1) spanning rows jf..jl: all of them
+// side by side (kWarps per pass), or one at a time on all warps when that
+// takes fewer rounds of column work (long segments, where splitting the
+// warps unevenly costs more than the extra reduction barrier, counted as a
+// quarter round).  unit: columns per thread and round.
+__device__ __noinline__ int pass_rows(int64_t c0, int64_t c1, int64_t rs, int jf, int jl, int unit)
+{
+    const int ns = jl - jf + 1;
+    if (ns == 1 || ns > kWarps) return kWarps;
+    int64_t conc = 0, seq4 = (int64_t)(ns - 1); // seq in quarter rounds
+    for (int w = 0; w < kWarps; ++w) {
+        const SegPlan sp = seg_plan(c0, c1, rs, jf, jl, w);
+        if (sp.lw != 0) continue;
+        const int64_t v = (sp.s1 - sp.s0 + unit - 1) / unit;
+        conc = max(conc, (v + 32 * sp.nw - 1) / (32 * sp.nw));
+        seq4 += 4 * ((v + 32 * kWarps - 1) / (32 * kWarps));
+    }
+    return 4 * conc <= seq4 ? kWarps : 1;
+}
+
+// Columns [c0, c1) of this CTA.
+__device__ __forceinline__ void cta_columns(const SingleArgs &a, int unit, int64_t &c0, int64_t &c1)
+{
+    if (a.pieces > 0) {
+        const int j = (int)blockIdx.x / a.pieces, t = (int)blockIdx.x - j * a.pieces;
+        c0 = (int64_t)j * a.rs + piece_bound(t, a.rs, a.pieces, unit);
+        c1 = (int64_t)j * a.rs + piece_bound(t + 1, a.rs, a.pieces, unit);
+    } else {
+        c0 = (int64_t)blockIdx.x * a.chunk;
+        c1 = min(c0 + a.chunk, a.ncols);
+    }
+}
+
+// CTAs whose columns touch row j.
+__device__ __forceinline__ int row_ctas(const SingleArgs &a, int j)
+{
+    if (a.pieces > 0) return a.pieces;
+    const int64_t rbeg = (int64_t)j * a.rs;
+    return (int)((rbeg + a.rs - 1) / a.chunk - rbeg / a.chunk) + 1;
+}
+
+// Partial record of row j written by this CTA (position among the CTAs
+// touching row j, in column order).
+__device__ __forceinline__ double *seg_record(const SingleArgs &a, int par, int j)
+{
+    const int pos = a.pieces > 0 ? (int)blockIdx.x % a.pieces
+                                 : (int)blockIdx.x - (int)(((int64_t)j * a.rs) / a.chunk);
+    return a.part + ((size_t)(par * a.q + j) * a.nbmax + pos) * a.m * 4;
+}
+
+// Reduction of one pass of row segments into their partial records: warp
+// sums by shuffles, then per (segment, source) the sum over that segment's
+// warps in warp order.
 template <int M>
-__device__ __forceinline__ void flush_segment(double *rec, const double *gs, const double *dmx, const double *dmn,
-                                              bool check, int m, const Sm &sm)
+__device__ __forceinline__ void flush_segments(const SingleArgs &a, int par, int jb, const double *gs,
+                                               const double *dmx, const double *dmn, bool check, int m,
+                                               const SegPlan &sp, const Sm &sm)
 {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
@@ -211,30 +314,37 @@ __device__ __forceinline__ void flush_segment(double *rec, const double *gs, con
                 sm.red[(w * kMaxM + i) * 3 + 2] = lo;
             }
         }
+    if (lane == 0) sm.segof[w] = sp.seg;
     __syncthreads();
-    if (threadIdx.x < m) {
-        const int i = threadIdx.x;
+    if (threadIdx.x < kWarps * m) {
+        const int sg = threadIdx.x / m, i = threadIdx.x - sg * m;
         double v = 0.0, hi = -INFINITY, lo = INFINITY;
-        for (int ww = 0; ww < kWarps; ++ww) {
-            v += sm.red[(ww * kMaxM + i) * 3 + 0];
-            hi = fmax(hi, sm.red[(ww * kMaxM + i) * 3 + 1]);
-            lo = fmin(lo, sm.red[(ww * kMaxM + i) * 3 + 2]);
+        bool any = false;
+        for (int ww = 0; ww < kWarps; ++ww)
+            if (sm.segof[ww] == sg) {
+                any = true;
+                v += sm.red[(ww * kMaxM + i) * 3 + 0];
+                hi = fmax(hi, sm.red[(ww * kMaxM + i) * 3 + 1]);
+                lo = fmin(lo, sm.red[(ww * kMaxM + i) * 3 + 2]);
+            }
+        if (any) {
+            double *rec = seg_record(a, par, jb + sg);
+            rec[i * 4 + 0] = v;
+            rec[i * 4 + 1] = hi;
+            rec[i * 4 + 2] = lo;
         }
-        rec[i * 4 + 0] = v;
-        rec[i * 4 + 1] = hi;
-        rec[i * 4 + 2] = lo;
     }
     __syncthreads();
 }
 
-// Mixed variant of the segment reduction, on the FP32 pipes: float-float
-// sums and FP32 max / min across the CTA in a fixed order; only the m
-// finished records are converted to FP64.
+// Mixed variant, on the FP32 pipes: float-float sums and FP32 max / min in
+// a fixed order; only the finished records are converted to FP64.
 template <int M>
-__device__ __forceinline__ void flush_segment32(double *rec, const float *ghi, const float *glo, const float *fmx,
-                                                const float *fmn, bool check, int m, float *red)
+__device__ __forceinline__ void flush_segments32(const SingleArgs &a, int par, int jb, const float *ghi,
+                                                 const float *glo, const float *fmx, const float *fmn, bool check,
+                                                 int m, const SegPlan &sp, const Sm &sm)
 {
-    // red: [kWarps][kMaxM][4] floats of shared memory
+    float *red = (float *)sm.red; // [kWarps][kMaxM][4] floats
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
     for (int i = 0; i < M; ++i)
@@ -257,29 +367,35 @@ __device__ __forceinline__ void flush_segment32(double *rec, const float *ghi, c
                 red[(w * kMaxM + i) * 4 + 3] = lo;
             }
         }
+    if (lane == 0) sm.segof[w] = sp.seg;
     __syncthreads();
-    if (threadIdx.x < m) {
-        const int i = threadIdx.x;
+    if (threadIdx.x < kWarps * m) {
+        const int sg = threadIdx.x / m, i = threadIdx.x - sg * m;
         FF v = {0.0f, 0.0f};
         float hi = -INFINITY, lo = INFINITY;
-        for (int ww = 0; ww < kWarps; ++ww) {
-            v = ff_add(v, FF{red[(ww * kMaxM + i) * 4 + 0], red[(ww * kMaxM + i) * 4 + 1]});
-            hi = fmaxf(hi, red[(ww * kMaxM + i) * 4 + 2]);
-            lo = fminf(lo, red[(ww * kMaxM + i) * 4 + 3]);
+        bool any = false;
+        for (int ww = 0; ww < kWarps; ++ww)
+            if (sm.segof[ww] == sg) {
+                any = true;
+                v = ff_add(v, FF{red[(ww * kMaxM + i) * 4 + 0], red[(ww * kMaxM + i) * 4 + 1]});
+                hi = fmaxf(hi, red[(ww * kMaxM + i) * 4 + 2]);
+                lo = fminf(lo, red[(ww * kMaxM + i) * 4 + 3]);
+            }
+        if (any) {
+            double *rec = seg_record(a, par, jb + sg);
+            rec[i * 4 + 0] = (double)v.hi + (double)v.lo;
+            rec[i * 4 + 1] = check ? (double)hi : 0.0;
+            rec[i * 4 + 2] = check ? (double)lo : 0.0;
         }
-        rec[i * 4 + 0] = (double)v.hi + (double)v.lo;
-        rec[i * 4 + 1] = check ? (double)hi : 0.0;
-        rec[i * 4 + 2] = check ? (double)lo : 0.0;
     }
     __syncthreads();
 }
 
-template <int M, int PREC> struct Bounds {
-    static constexpr int minb = PREC == ADMM_FP64 ? 1 : 2;
-};
-
-template <int M, int PREC>
-__global__ void __launch_bounds__(kBlock, (Bounds<M, PREC>::minb)) single_kernel(SingleArgs a)
+// MINB: CTAs per SM the register budget is sized for.  FP64 takes 1 (its
+// element update needs about 250 registers); the mixed kernel comes in both:
+// 1 for problems that fill at most one CTA per SM (no spills), 2 otherwise.
+template <int M, int PREC, int MINB>
+__global__ void __launch_bounds__(kBlock, MINB) single_kernel(SingleArgs a)
 {
     extern __shared__ double smem[];
     constexpr bool MIXED = PREC != ADMM_FP64;
@@ -292,9 +408,10 @@ __global__ void __launch_bounds__(kBlock, (Bounds<M, PREC>::minb)) single_kernel
         for (int pr = threadIdx.x; pr < mq; pr += kBlock) sm.uoff[pr] = (float)(sm.zeta[pr] + sm.lam[pr]);
     __syncthreads();
 
-    const int64_t c0 = (int64_t)blockIdx.x * a.chunk;
-    const int64_t c1 = min(c0 + a.chunk, a.ncols);
+    int64_t c0, c1;
+    cta_columns(a, MIXED ? VW : 1, c0, c1);
     const int jf = (int)(c0 / rs), jl = (int)((c1 - 1) / rs);
+    const int prows = pass_rows(c0, c1, rs, jf, jl, MIXED ? VW : 1);
     unsigned nbar = 0;
     unsigned esc = 0;
     bool ok = true, conv = false;
@@ -311,21 +428,27 @@ __global__ void __launch_bounds__(kBlock, (Bounds<M, PREC>::minb)) single_kernel
         float fcr_all = 0.0f, fcs_all = 0.0f;
 
         // ---- phase 1: element updates and segment partials --------------
-        for (int j = jf; j <= jl; ++j) {
-            const int64_t s0 = max(c0, (int64_t)j * rs), s1 = min(c1, (int64_t)(j + 1) * rs);
-            double gs[M], dmx[M], dmn[M];
-            const int pos = (int)blockIdx.x - (int)(((int64_t)j * rs) / a.chunk);
-            double *rec = a.part + ((size_t)(par * q + j) * a.nbmax + pos) * m * 4;
+        // The rows j the chunk touches are taken prows at a time; within a
+        // pass every row segment gets its own warps, so its segments run
+        // concurrently and one reduction barrier closes them all.
+        for (int jb = jf; jb <= jl; jb += prows) {
+            const SegPlan sp = seg_plan(c0, c1, rs, jb, min(jl, jb + prows - 1), threadIdx.x >> 5);
+            const int j = sp.j;
+            double *rec = seg_record(a, par, j);
+            // row-local column range of the segment (k), and this thread's start and step
+            const int kb = (int)(sp.s0 - (int64_t)j * rs), ke = (int)(sp.s1 - (int64_t)j * rs);
+            const int first = sp.lw * 32 + (threadIdx.x & 31), stride = sp.nw * 32;
             if constexpr (!MIXED) {
+                double gs[M], dmx[M], dmn[M];
 #pragma unroll
                 for (int i = 0; i < M; ++i) {
                     gs[i] = 0.0;
                     dmx[i] = -INFINITY;
                     dmn[i] = INFINITY;
                 }
-                for (int64_t cc = s0 + threadIdx.x; cc < s1; cc += kBlock)
-                    column64<M>(a, sm, j, (int)(cc - (int64_t)j * rs), check, cold, mu_div, gs, dmx, dmn, cm_r,
-                                cm_s, rec);
+                for (int k = kb + first; k < ke; k += stride)
+                    column64<M>(a, sm, j, k, check, cold, mu_div, gs, dmx, dmn, cm_r, cm_s, rec);
+                flush_segments<M>(a, par, jb, gs, dmx, dmn, check, m, sp, sm);
             } else {
                 float ghi[M], glo[M], fmx[M], fmn[M];
 #pragma unroll
@@ -345,18 +468,16 @@ __global__ void __launch_bounds__(kBlock, (Bounds<M, PREC>::minb)) single_kernel
                                     (float *)a.mu_lo,    a.n,                 a.m,
                                     a.q,                 a.ld,                a.sweep,
                                     a.xmin_mode};
-                for (int64_t qq = s0 / VW + threadIdx.x; qq < s1 / VW; qq += kBlock) {
-                    const int k0 = (int)(qq * VW - (int64_t)j * rs);
-                    if (k0 >= n) continue;
+                const int kn = min(ke, n); // padding columns k >= n are skipped
+                for (int k0 = kb + first * VW; k0 < kn; k0 += stride * VW) {
                     vec32<M, VW, PREC == ADMM_MIXED_FP64CUBIC>(ea, sm.uoff, sm.x1, sm.nu, j, k0, check, cold,
                                                                (float)mu_div, rho1, rho3, rho4, iq, ghi, glo, fmx,
                                                                fmn, fcr, fcs, esc, rec);
                 }
                 fcr_all = fmaxf(fcr_all, fcr);
                 fcs_all = fmaxf(fcs_all, fcs);
-                flush_segment32<M>(rec, ghi, glo, fmx, fmn, check, m, (float *)sm.red);
+                flush_segments32<M>(a, par, jb, ghi, glo, fmx, fmn, check, m, sp, sm);
             }
-            if constexpr (!MIXED) flush_segment<M>(rec, gs, dmx, dmn, check, m, sm);
         }
         if (MIXED) {
             cm_r = (double)fcr_all;
@@ -383,8 +504,7 @@ __global__ void __launch_bounds__(kBlock, (Bounds<M, PREC>::minb)) single_kernel
         double r2m = 0.0, r3m = 0.0, s1m = 0.0, s2m = 0.0;
         for (int pr = threadIdx.x; pr < mq; pr += kBlock) {
             const int i = pr / q, j = pr - i * q;
-            const int64_t rbeg = (int64_t)j * rs;
-            const int nb = (int)((rbeg + rs - 1) / a.chunk - rbeg / a.chunk) + 1;
+            const int nb = row_ctas(a, j);
             const double *rec = a.part + ((size_t)(par * q + j) * a.nbmax) * m * 4 + i * 4;
             const int stride = m * 4;
             // records of row j, in CTA order; independent loads, fixed order of the sums
@@ -419,11 +539,12 @@ __global__ void __launch_bounds__(kBlock, (Bounds<M, PREC>::minb)) single_kernel
             sm.x0[pr] = x0;
         }
         __syncthreads();
-        if (threadIdx.x < m) {                                       // (c), mean over j
-            const int i = threadIdx.x;
+        for (int i = threadIdx.x >> 5; i < m; i += kWarps) {        // (c), mean over j: warp i, source i
+            const int lane = threadIdx.x & 31;
             double sum = 0.0;
-            for (int j = 0; j < q; ++j) sum += sm.x0[i * q + j] - sm.nu[i * q + j];
-            sm.x1n[i] = sum / (double)q;
+            for (int j = lane; j < q; j += 32) sum += sm.x0[i * q + j] - sm.nu[i * q + j];
+            sum = warp_sum(sum);
+            if (lane == 0) sm.x1n[i] = sum / (double)q;
         }
         __syncthreads();
         double r4m = 0.0;
@@ -545,21 +666,24 @@ __global__ void __launch_bounds__(kBlock, (Bounds<M, PREC>::minb)) single_kernel
     }
 }
 
-template <int M> void *single_fn(int precision)
+template <int M> void *single_fn(int precision, int minb)
 {
     switch (precision) {
-    case ADMM_MIXED: return (void *)single_kernel<M, ADMM_MIXED>;
-    case ADMM_MIXED_FP64CUBIC: return (void *)single_kernel<M, ADMM_MIXED_FP64CUBIC>;
-    default: return (void *)single_kernel<M, ADMM_FP64>;
+    case ADMM_MIXED:
+        return minb == 1 ? (void *)single_kernel<M, ADMM_MIXED, 1> : (void *)single_kernel<M, ADMM_MIXED, 2>;
+    case ADMM_MIXED_FP64CUBIC:
+        return minb == 1 ? (void *)single_kernel<M, ADMM_MIXED_FP64CUBIC, 1>
+                         : (void *)single_kernel<M, ADMM_MIXED_FP64CUBIC, 2>;
+    default: return (void *)single_kernel<M, ADMM_FP64, 1>;
     }
 }
 
-void *pick(int precision, int m)
+void *pick(int precision, int m, int minb)
 {
     switch (single_mbound(m)) {
-    case 2: return single_fn<2>(precision);
-    case 4: return single_fn<4>(precision);
-    default: return single_fn<8>(precision);
+    case 2: return single_fn<2>(precision, minb);
+    case 4: return single_fn<4>(precision, minb);
+    default: return single_fn<8>(precision, minb);
     }
 }
 
@@ -570,13 +694,13 @@ int single_mbound(int m) { return m <= 2 ? 2 : (m <= 4 ? 4 : 8); }
 size_t single_smem_bytes(int m, int q)
 {
     const int mq = m * q;
-    return sizeof(double) * ((size_t)scal_size(m, q) + mq + kMaxM + kWarps * kMaxM * 3 + kWarps * 8 + 16) +
+    return sizeof(double) * ((size_t)scal_size(m, q) + mq + kMaxM + kWarps * kMaxM * 3 + kWarps * 8 + 16 + kWarps) +
            sizeof(float) * (size_t)mq + 16;
 }
 
-int single_blocks_per_sm(int precision, int m, size_t smem)
+int single_blocks_per_sm(int precision, int m, int minb, size_t smem)
 {
-    void *fn = pick(precision, m);
+    void *fn = pick(precision, m, minb);
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return 0;
     int nb = 0;
@@ -584,9 +708,52 @@ int single_blocks_per_sm(int precision, int m, size_t smem)
     return nb;
 }
 
-cudaError_t launch_single(int precision, const SingleArgs &a, size_t smem, cudaStream_t st)
+SingleShape single_shape(int precision, int m, int q, int64_t rs, int nsm, size_t smem)
 {
-    void *fn = pick(precision, a.m);
+    SingleShape sh{};
+    const bool mixed = precision != ADMM_FP64;
+    const int64_t unit = mixed ? kMixedVW : 1;   // mixed: vectors of kMixedVW columns
+    const int64_t ncols = (int64_t)q * rs;
+    // Contiguous equal column chunks over as many SMs as there are warps of
+    // work (FP64 throughput per SM is the scarce resource), one CTA per SM
+    // while that covers every column vector in a single pass, two otherwise.
+    sh.minb = (mixed && ncols > (int64_t)nsm * kBlock * unit) ? 2 : 1;
+    int per_sm = single_blocks_per_sm(precision, m, sh.minb, smem);
+    if (per_sm < 1 && sh.minb == 2) {
+        sh.minb = 1;
+        per_sm = single_blocks_per_sm(precision, m, 1, smem);
+    }
+    if (per_sm < 1) return sh;
+    const int64_t g = std::min<int64_t>((int64_t)nsm * per_sm, std::max<int64_t>(1, ncols / (32 * unit)));
+    sh.chunk = ((ncols + g - 1) / g + unit - 1) / unit * unit;
+    // Row-aligned split when every row gets whole pieces and the largest
+    // piece is within 5 % of the flat chunk: no CTA then straddles two rows
+    // (a straddling CTA reduces two segments and finishes last).
+    const int p = (int)(g / q);
+    if (p >= 1) {
+        int64_t big = 0;
+        for (int t = 0; t < p; ++t)
+            big = std::max(big, piece_bound(t + 1, rs, p, (int)unit) - piece_bound(t, rs, p, (int)unit));
+        if (piece_bound(1, rs, p, (int)unit) > 0 && 20 * big <= 21 * sh.chunk) {
+            sh.pieces = p;
+            sh.grid = q * p;
+            sh.nbmax = p;
+            return sh;
+        }
+    }
+    sh.pieces = 0;
+    sh.grid = (int)((ncols + sh.chunk - 1) / sh.chunk);
+    sh.nbmax = 1;
+    for (int j = 0; j < q; ++j) {
+        const int64_t r0 = (int64_t)j * rs, r1 = r0 + rs - 1;
+        sh.nbmax = std::max(sh.nbmax, (int)(r1 / sh.chunk - r0 / sh.chunk + 1));
+    }
+    return sh;
+}
+
+cudaError_t launch_single(int precision, int minb, const SingleArgs &a, size_t smem, cudaStream_t st)
+{
+    void *fn = pick(precision, a.m, minb);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     SingleArgs copy = a;
