@@ -192,9 +192,11 @@ template <int KIND, int NW, int M> __device__ void solve_team(const BatchArgs &a
                 fmn[i] = INFINITY;
             }
             double *rec = recs + (size_t)item * m * 4;
-            for (int v = v0 + lane; v < v1; v += 32)
+            for (int v = v0 + lane; v < v1; v += 32) {
+                if (v + 32 < v1) prefetch_vec32<M>(ea, j, (v + 32) * VW, cold);
                 vec32<M, VW, false>(ea, uoff, x1, nu, j, v * VW, check, cold, mu_div, rho1, rho3, rho4, iq, ghi, glo,
                                     fmx, fmn, fcr, fcs, esc, rec);
+            }
 #pragma unroll
             for (int i = 0; i < M; ++i)
                 if (i < m) {

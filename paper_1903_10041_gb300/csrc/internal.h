@@ -8,8 +8,9 @@
 
 namespace admm_impl {
 
-constexpr int kBlock = 256;          // threads per CTA of the solve kernels
-constexpr int kWarps = kBlock / 32;
+constexpr int kBlock = 256;          // threads per CTA of the mixed-precision solve kernel
+constexpr int kBlockF64 = 384;       // threads per CTA of the FP64 solve kernel
+constexpr int kSingleWarpsMax = 12;  // most warps per CTA of the single-instance kernels
 constexpr int kMaxM = ADMM_MAX_M;
 constexpr int kInfo = 16;            // doubles of the per-solve info record
 #ifndef ADMM_MIXED_VW
@@ -79,6 +80,8 @@ SingleShape single_shape(int precision, int m, int q, int64_t rs, int nsm, size_
 size_t single_smem_bytes(int m, int q);
 // Index of the kernel variant used for m sources (template bound).
 int single_mbound(int m);
+// Threads per CTA of the single-instance kernel of a precision.
+int single_threads(int precision);
 // Row copies with conversion (device to device): rows x n values from a
 // source with row stride sld into a destination with row stride dld.
 void convert_rows_f32_to_f64(double *dst, int64_t dld, const float *src, int64_t sld, int n, int64_t rows,

@@ -95,6 +95,35 @@ struct ElemF32 {
     int n, m, q, ld, sweep, xmin_mode;
 };
 
+// L2 prefetch of everything vec32 reads for the columns (j, k0..): issued
+// one vector ahead, so the loads of the next vector hit L2 instead of
+// waiting on HBM.  Prefetches are hints and touch only rows the update reads.
+__device__ __forceinline__ void prefetch_l2(const void *p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
+template <int M>
+__device__ __forceinline__ void prefetch_vec32(const ElemF32 &a, int j, int k0, bool cold)
+{
+    const size_t col = (size_t)j * a.ld + k0;
+    prefetch_l2(a.y + col);
+    prefetch_l2(a.s + col);
+    prefetch_l2(a.mu + col);
+    prefetch_l2(a.s_lo + col);
+    prefetch_l2(a.mu_lo + col);
+#pragma unroll
+    for (int i = 0; i < M; ++i)
+        if (i < a.m) {
+            const size_t e = ((size_t)i * a.q + j) * a.ld + k0;
+            prefetch_l2(a.x + e);
+            prefetch_l2(a.f2 + e);
+            prefetch_l2(a.f1 + e);
+            prefetch_l2(a.g2 + e);
+            prefetch_l2(a.g1 + e);
+            if (cold) prefetch_l2(a.g0 + e);
+            prefetch_l2(a.lo + (size_t)i * a.ld + k0);
+            prefetch_l2(a.hi + (size_t)i * a.ld + k0);
+        }
+}
+
 // Step (a) for all sources of VW columns (j, k0..k0+VW-1), then (e), (f).
 // uoff[pr] = zeta + lambda of pair pr in FP32; x1 and nu are the FP64 pair
 // scalars (read at k = 0 only).  rec (if k0 == 0) receives x at k = 0.

@@ -51,10 +51,10 @@ struct Sm {
     double *lam, *zeta, *h, *p, *nu, *x1, *rho, *flags; // mirror of the scalar state
     double *x0;   // [mq]
     double *x1n;  // [kMaxM]
-    double *red;  // [kWarps][kMaxM][3]
-    double *mx;   // [kWarps][8]
+    double *red;  // [kSingleWarpsMax][kMaxM][3]
+    double *mx;   // [kSingleWarpsMax][8]
     double *bc;   // [16] broadcast
-    int *segof;   // [kWarps] segment (within the pass) of each warp
+    int *segof;   // [kSingleWarpsMax] segment (within the pass) of each warp
     float *uoff;  // [mq] zeta + lambda in FP32 (mixed variants)
 };
 
@@ -76,19 +76,19 @@ __device__ __forceinline__ Sm carve(double *base, int m, int q)
     s.x1n = t;
     t += kMaxM;
     s.red = t;
-    t += kWarps * kMaxM * 3;
+    t += kSingleWarpsMax * kMaxM * 3;
     s.mx = t;
-    t += kWarps * 8;
+    t += kSingleWarpsMax * 8;
     s.bc = t;
     t += 16;
     s.segof = (int *)t;
-    t += kWarps;
+    t += kSingleWarpsMax;
     s.uoff = (float *)t;
     return s;
 }
 
 // Block-wide max of up to 8 values; every thread gets the results in v[].
-template <int NV> __device__ __forceinline__ void block_max(double *v, const Sm &sm)
+template <int NV, int NWP> __device__ __forceinline__ void block_max(double *v, const Sm &sm)
 {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
@@ -99,7 +99,7 @@ template <int NV> __device__ __forceinline__ void block_max(double *v, const Sm 
     __syncthreads();
     if (threadIdx.x < NV) {
         double r = 0.0;
-        for (int ww = 0; ww < kWarps; ++ww) r = fmax(r, sm.mx[ww * 8 + threadIdx.x]);
+        for (int ww = 0; ww < NWP; ++ww) r = fmax(r, sm.mx[ww * 8 + threadIdx.x]);
         sm.bc[threadIdx.x] = r;
     }
     __syncthreads();
@@ -199,9 +199,10 @@ __device__ __forceinline__ void column64(const SingleArgs &a, const Sm &sm, int 
     }
 }
 
-// Warp plan of one pass over the row segments jb..je (at most kWarps rows)
-// of the chunk [c0, c1): segment s gets warps [W_s, W_s+1) with
-// W_s = s + floor((kWarps - ns) * (columns before s) / (columns in the pass)),
+// Warp plan of one pass over the row segments jb..je (at most NWP rows, the
+// CTA's warp count) of the chunk [c0, c1): segment s gets warps
+// [W_s, W_s+1) with W_s = s + floor((NWP - ns) * (columns before s) /
+// (columns in the pass)),
 // at least one warp each and the rest in proportion to length, so the
 // segments of a CTA run side by side.  The plan depends only on the launch
 // shape, so it is the same in every iteration.
@@ -212,6 +213,7 @@ struct SegPlan {
     int64_t s0, s1; // the segment's columns [s0, s1)
 };
 
+template <int NWP>
 __device__ __forceinline__ SegPlan seg_plan(int64_t c0, int64_t c1, int64_t rs, int jb, int je, int w)
 {
     SegPlan p{};
@@ -219,11 +221,11 @@ __device__ __forceinline__ SegPlan seg_plan(int64_t c0, int64_t c1, int64_t rs, 
     if (ns == 1) {
         p.j = jb;
         p.lw = w;
-        p.nw = kWarps;
+        p.nw = NWP;
     } else {
         const int64_t b0 = max(c0, (int64_t)jb * rs), b1 = min(c1, (int64_t)(je + 1) * rs);
-        const float scale = (float)(kWarps - ns) / (float)(b1 - b0);
-        int wlo = 0, whi = kWarps;
+        const float scale = (float)(NWP - ns) / (float)(b1 - b0);
+        int wlo = 0, whi = NWP;
         for (int t = 0; t < ns; ++t) {
             const int64_t before = max(c0, (int64_t)(jb + t) * rs) - b0;
             const int ws = t + (int)floorf(scale * (float)before);
@@ -244,23 +246,24 @@ __device__ __forceinline__ SegPlan seg_plan(int64_t c0, int64_t c1, int64_t rs, 
 }
 
 // Rows per pass for the chunk [c0, c1) spanning rows jf..jl: all of them
-// side by side (kWarps per pass), or one at a time on all warps when that
+// side by side (NWP per pass), or one at a time on all warps when that
 // takes fewer rounds of column work (long segments, where splitting the
 // warps unevenly costs more than the extra reduction barrier, counted as a
 // quarter round).  unit: columns per thread and round.
+template <int NWP>
 __device__ __noinline__ int pass_rows(int64_t c0, int64_t c1, int64_t rs, int jf, int jl, int unit)
 {
     const int ns = jl - jf + 1;
-    if (ns == 1 || ns > kWarps) return kWarps;
+    if (ns == 1 || ns > NWP) return NWP;
     int64_t conc = 0, seq4 = (int64_t)(ns - 1); // seq in quarter rounds
-    for (int w = 0; w < kWarps; ++w) {
-        const SegPlan sp = seg_plan(c0, c1, rs, jf, jl, w);
+    for (int w = 0; w < NWP; ++w) {
+        const SegPlan sp = seg_plan<NWP>(c0, c1, rs, jf, jl, w);
         if (sp.lw != 0) continue;
         const int64_t v = (sp.s1 - sp.s0 + unit - 1) / unit;
         conc = max(conc, (v + 32 * sp.nw - 1) / (32 * sp.nw));
-        seq4 += 4 * ((v + 32 * kWarps - 1) / (32 * kWarps));
+        seq4 += 4 * ((v + 32 * NWP - 1) / (32 * NWP));
     }
-    return 4 * conc <= seq4 ? kWarps : 1;
+    return 4 * conc <= seq4 ? NWP : 1;
 }
 
 // Columns [c0, c1) of this CTA.
@@ -296,7 +299,7 @@ __device__ __forceinline__ double *seg_record(const SingleArgs &a, int par, int 
 // Reduction of one pass of row segments into their partial records: warp
 // sums by shuffles, then per (segment, source) the sum over that segment's
 // warps in warp order.
-template <int M>
+template <int M, int NWP>
 __device__ __forceinline__ void flush_segments(const SingleArgs &a, int par, int jb, const double *gs,
                                                const double *dmx, const double *dmn, bool check, int m,
                                                const SegPlan &sp, const Sm &sm)
@@ -316,11 +319,11 @@ __device__ __forceinline__ void flush_segments(const SingleArgs &a, int par, int
         }
     if (lane == 0) sm.segof[w] = sp.seg;
     __syncthreads();
-    if (threadIdx.x < kWarps * m) {
+    if (threadIdx.x < NWP * m) {
         const int sg = threadIdx.x / m, i = threadIdx.x - sg * m;
         double v = 0.0, hi = -INFINITY, lo = INFINITY;
         bool any = false;
-        for (int ww = 0; ww < kWarps; ++ww)
+        for (int ww = 0; ww < NWP; ++ww)
             if (sm.segof[ww] == sg) {
                 any = true;
                 v += sm.red[(ww * kMaxM + i) * 3 + 0];
@@ -339,12 +342,12 @@ __device__ __forceinline__ void flush_segments(const SingleArgs &a, int par, int
 
 // Mixed variant, on the FP32 pipes: float-float sums and FP32 max / min in
 // a fixed order; only the finished records are converted to FP64.
-template <int M>
+template <int M, int NWP>
 __device__ __forceinline__ void flush_segments32(const SingleArgs &a, int par, int jb, const float *ghi,
                                                  const float *glo, const float *fmx, const float *fmn, bool check,
                                                  int m, const SegPlan &sp, const Sm &sm)
 {
-    float *red = (float *)sm.red; // [kWarps][kMaxM][4] floats
+    float *red = (float *)sm.red; // [NWP][kMaxM][4] floats
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
     for (int i = 0; i < M; ++i)
@@ -369,12 +372,12 @@ __device__ __forceinline__ void flush_segments32(const SingleArgs &a, int par, i
         }
     if (lane == 0) sm.segof[w] = sp.seg;
     __syncthreads();
-    if (threadIdx.x < kWarps * m) {
+    if (threadIdx.x < NWP * m) {
         const int sg = threadIdx.x / m, i = threadIdx.x - sg * m;
         FF v = {0.0f, 0.0f};
         float hi = -INFINITY, lo = INFINITY;
         bool any = false;
-        for (int ww = 0; ww < kWarps; ++ww)
+        for (int ww = 0; ww < NWP; ++ww)
             if (sm.segof[ww] == sg) {
                 any = true;
                 v = ff_add(v, FF{red[(ww * kMaxM + i) * 4 + 0], red[(ww * kMaxM + i) * 4 + 1]});
@@ -394,24 +397,25 @@ __device__ __forceinline__ void flush_segments32(const SingleArgs &a, int par, i
 // MINB: CTAs per SM the register budget is sized for.  FP64 takes 1 (its
 // element update needs about 250 registers); the mixed kernel comes in both:
 // 1 for problems that fill at most one CTA per SM (no spills), 2 otherwise.
-template <int M, int PREC, int MINB>
-__global__ void __launch_bounds__(kBlock, MINB) single_kernel(SingleArgs a)
+template <int M, int PREC, int MINB, int NT>
+__global__ void __launch_bounds__(NT, MINB) single_kernel(SingleArgs a)
 {
+    constexpr int NWP = NT / 32;
     extern __shared__ double smem[];
     constexpr bool MIXED = PREC != ADMM_FP64;
     constexpr int VW = kMixedVW;
     const int m = a.m, q = a.q, n = a.n, mq = m * q, rs = a.rs;
     const Sm sm = carve(smem, m, q);
-    for (int t = threadIdx.x; t < scal_size(m, q); t += kBlock) smem[t] = a.scal[t];
+    for (int t = threadIdx.x; t < scal_size(m, q); t += NT) smem[t] = a.scal[t];
     __syncthreads();
     if (MIXED)
-        for (int pr = threadIdx.x; pr < mq; pr += kBlock) sm.uoff[pr] = (float)(sm.zeta[pr] + sm.lam[pr]);
+        for (int pr = threadIdx.x; pr < mq; pr += NT) sm.uoff[pr] = (float)(sm.zeta[pr] + sm.lam[pr]);
     __syncthreads();
 
     int64_t c0, c1;
     cta_columns(a, MIXED ? VW : 1, c0, c1);
     const int jf = (int)(c0 / rs), jl = (int)((c1 - 1) / rs);
-    const int prows = pass_rows(c0, c1, rs, jf, jl, MIXED ? VW : 1);
+    const int prows = pass_rows<NWP>(c0, c1, rs, jf, jl, MIXED ? VW : 1);
     unsigned nbar = 0;
     unsigned esc = 0;
     bool ok = true, conv = false;
@@ -432,7 +436,7 @@ __global__ void __launch_bounds__(kBlock, MINB) single_kernel(SingleArgs a)
         // pass every row segment gets its own warps, so its segments run
         // concurrently and one reduction barrier closes them all.
         for (int jb = jf; jb <= jl; jb += prows) {
-            const SegPlan sp = seg_plan(c0, c1, rs, jb, min(jl, jb + prows - 1), threadIdx.x >> 5);
+            const SegPlan sp = seg_plan<NWP>(c0, c1, rs, jb, min(jl, jb + prows - 1), threadIdx.x >> 5);
             const int j = sp.j;
             double *rec = seg_record(a, par, j);
             // row-local column range of the segment (k), and this thread's start and step
@@ -448,7 +452,7 @@ __global__ void __launch_bounds__(kBlock, MINB) single_kernel(SingleArgs a)
                 }
                 for (int k = kb + first; k < ke; k += stride)
                     column64<M>(a, sm, j, k, check, cold, mu_div, gs, dmx, dmn, cm_r, cm_s, rec);
-                flush_segments<M>(a, par, jb, gs, dmx, dmn, check, m, sp, sm);
+                flush_segments<M, NWP>(a, par, jb, gs, dmx, dmn, check, m, sp, sm);
             } else {
                 float ghi[M], glo[M], fmx[M], fmn[M];
 #pragma unroll
@@ -470,13 +474,15 @@ __global__ void __launch_bounds__(kBlock, MINB) single_kernel(SingleArgs a)
                                     a.xmin_mode};
                 const int kn = min(ke, n); // padding columns k >= n are skipped
                 for (int k0 = kb + first * VW; k0 < kn; k0 += stride * VW) {
+                    if constexpr (MINB == 2) // several vectors per thread: fetch the next one into L2
+                        if (k0 + stride * VW < kn) prefetch_vec32<M>(ea, j, k0 + stride * VW, cold);
                     vec32<M, VW, PREC == ADMM_MIXED_FP64CUBIC>(ea, sm.uoff, sm.x1, sm.nu, j, k0, check, cold,
                                                                (float)mu_div, rho1, rho3, rho4, iq, ghi, glo, fmx,
                                                                fmn, fcr, fcs, esc, rec);
                 }
                 fcr_all = fmaxf(fcr_all, fcr);
                 fcs_all = fmaxf(fcs_all, fcs);
-                flush_segments32<M>(a, par, jb, ghi, glo, fmx, fmn, check, m, sp, sm);
+                flush_segments32<M, NWP>(a, par, jb, ghi, glo, fmx, fmn, check, m, sp, sm);
             }
         }
         if (MIXED) {
@@ -485,7 +491,7 @@ __global__ void __launch_bounds__(kBlock, MINB) single_kernel(SingleArgs a)
         }
         if (check) {
             double v[2] = {cm_r, cm_s};
-            block_max<2>(v, sm);
+            block_max<2, NWP>(v, sm);
             if (threadIdx.x == 0) {
                 a.cpart[((size_t)par * a.grid + blockIdx.x) * 4 + 0] = v[0];
                 a.cpart[((size_t)par * a.grid + blockIdx.x) * 4 + 1] = v[1];
@@ -502,7 +508,7 @@ __global__ void __launch_bounds__(kBlock, MINB) single_kernel(SingleArgs a)
         const double rho1 = sm.rho[0], rho2 = sm.rho[1], rho3 = sm.rho[2];
         const double kappa = rho2 / (rho1 + (double)n * rho2);
         double r2m = 0.0, r3m = 0.0, s1m = 0.0, s2m = 0.0;
-        for (int pr = threadIdx.x; pr < mq; pr += kBlock) {
+        for (int pr = threadIdx.x; pr < mq; pr += NT) {
             const int i = pr / q, j = pr - i * q;
             const int nb = row_ctas(a, j);
             const double *rec = a.part + ((size_t)(par * q + j) * a.nbmax) * m * 4 + i * 4;
@@ -539,7 +545,7 @@ __global__ void __launch_bounds__(kBlock, MINB) single_kernel(SingleArgs a)
             sm.x0[pr] = x0;
         }
         __syncthreads();
-        for (int i = threadIdx.x >> 5; i < m; i += kWarps) {        // (c), mean over j: warp i, source i
+        for (int i = threadIdx.x >> 5; i < m; i += NWP) {        // (c), mean over j: warp i, source i
             const int lane = threadIdx.x & 31;
             double sum = 0.0;
             for (int j = lane; j < q; j += 32) sum += sm.x0[i * q + j] - sm.nu[i * q + j];
@@ -548,7 +554,7 @@ __global__ void __launch_bounds__(kBlock, MINB) single_kernel(SingleArgs a)
         }
         __syncthreads();
         double r4m = 0.0;
-        for (int pr = threadIdx.x; pr < mq; pr += kBlock) {          // (h)
+        for (int pr = threadIdx.x; pr < mq; pr += NT) {          // (h)
             const int i = pr / q;
             const double x0 = sm.x0[pr], x1n = sm.x1n[i];
             sm.nu[pr] = sm.nu[pr] + (x1n - x0);
@@ -561,12 +567,12 @@ __global__ void __launch_bounds__(kBlock, MINB) single_kernel(SingleArgs a)
 
         if (check) {
             double r1 = 0.0, s3 = 0.0;
-            for (int b = threadIdx.x; b < a.grid; b += kBlock) {
+            for (int b = threadIdx.x; b < a.grid; b += NT) {
                 r1 = fmax(r1, ldcg(a.cpart + ((size_t)par * a.grid + b) * 4 + 0));
                 s3 = fmax(s3, ldcg(a.cpart + ((size_t)par * a.grid + b) * 4 + 1));
             }
             double v[7] = {r1, r2m, r3m, r4m, s1m, s2m, s3};
-            block_max<7>(v, sm);
+            block_max<7, NWP>(v, sm);
 #pragma unroll
             for (int t = 0; t < 7; ++t) res[t] = v[t];
             const double r = fmax(fmax(v[0], v[1]), fmax(v[2], v[3]));
@@ -583,7 +589,7 @@ __global__ void __launch_bounds__(kBlock, MINB) single_kernel(SingleArgs a)
                 if (ratio > 1.2 * target) f = a.tau;
                 else if (ratio < 0.8 * target) f = 1.0 / a.tau;
                 if (f != 1.0) {
-                    for (int pr = threadIdx.x; pr < mq; pr += kBlock) {
+                    for (int pr = threadIdx.x; pr < mq; pr += NT) {
                         sm.lam[pr] /= f;
                         sm.p[pr] /= f;
                         sm.nu[pr] /= f;
@@ -596,7 +602,7 @@ __global__ void __launch_bounds__(kBlock, MINB) single_kernel(SingleArgs a)
             }
         }
         if (MIXED) {
-            for (int pr = threadIdx.x; pr < mq; pr += kBlock) sm.uoff[pr] = (float)(sm.zeta[pr] + sm.lam[pr]);
+            for (int pr = threadIdx.x; pr < mq; pr += NT) sm.uoff[pr] = (float)(sm.zeta[pr] + sm.lam[pr]);
             __syncthreads();
         }
     }
@@ -605,7 +611,7 @@ __global__ void __launch_bounds__(kBlock, MINB) single_kernel(SingleArgs a)
     // ---- objective (1/q) sum f(x) of eq. (2): one more barrier -----------
     if (ok) {
         double acc = 0.0;
-        for (int64_t cc = c0 + threadIdx.x; cc < c1; cc += kBlock) {
+        for (int64_t cc = c0 + threadIdx.x; cc < c1; cc += NT) {
             const int j = (int)(cc / rs), k = (int)(cc - (int64_t)j * rs);
             if (k >= n) continue;
             for (int i = 0; i < m; ++i) {
@@ -634,7 +640,7 @@ __global__ void __launch_bounds__(kBlock, MINB) single_kernel(SingleArgs a)
         __syncthreads();
         if (threadIdx.x == 0) {
             double t = 0.0, te = 0.0;
-            for (int w = 0; w < kWarps; ++w) {
+            for (int w = 0; w < NWP; ++w) {
                 t += sm.mx[w * 8];
                 te += sm.mx[w * 8 + 1];
             }
@@ -645,7 +651,7 @@ __global__ void __launch_bounds__(kBlock, MINB) single_kernel(SingleArgs a)
         ok = grid_barrier(a.bar, nbar * (unsigned)a.grid, a.status, a.spin_ns, ADMM_ETIMEOUT);
     }
     if (blockIdx.x == 0) {
-        for (int t = threadIdx.x; t < scal_size(m, q); t += kBlock) a.scal[t] = smem[t];
+        for (int t = threadIdx.x; t < scal_size(m, q); t += NT) a.scal[t] = smem[t];
         if (threadIdx.x == 0) {
             double obj = 0.0, escs = 0.0;
             if (ok)
@@ -670,11 +676,12 @@ template <int M> void *single_fn(int precision, int minb)
 {
     switch (precision) {
     case ADMM_MIXED:
-        return minb == 1 ? (void *)single_kernel<M, ADMM_MIXED, 1> : (void *)single_kernel<M, ADMM_MIXED, 2>;
+        return minb == 1 ? (void *)single_kernel<M, ADMM_MIXED, 1, kBlock>
+                         : (void *)single_kernel<M, ADMM_MIXED, 2, kBlock>;
     case ADMM_MIXED_FP64CUBIC:
-        return minb == 1 ? (void *)single_kernel<M, ADMM_MIXED_FP64CUBIC, 1>
-                         : (void *)single_kernel<M, ADMM_MIXED_FP64CUBIC, 2>;
-    default: return (void *)single_kernel<M, ADMM_FP64, 1>;
+        return minb == 1 ? (void *)single_kernel<M, ADMM_MIXED_FP64CUBIC, 1, kBlock>
+                         : (void *)single_kernel<M, ADMM_MIXED_FP64CUBIC, 2, kBlock>;
+    default: return (void *)single_kernel<M, ADMM_FP64, 1, kBlockF64>;
     }
 }
 
@@ -691,10 +698,15 @@ void *pick(int precision, int m, int minb)
 
 int single_mbound(int m) { return m <= 2 ? 2 : (m <= 4 ? 4 : 8); }
 
+// FP64: 12 warps (one CTA per SM, up to 168 registers a thread); the FP64
+// units are shared by the SM, so more warps hide more of their latency.
+int single_threads(int precision) { return precision == ADMM_FP64 ? kBlockF64 : kBlock; }
+
 size_t single_smem_bytes(int m, int q)
 {
     const int mq = m * q;
-    return sizeof(double) * ((size_t)scal_size(m, q) + mq + kMaxM + kWarps * kMaxM * 3 + kWarps * 8 + 16 + kWarps) +
+    return sizeof(double) * ((size_t)scal_size(m, q) + mq + kMaxM + kSingleWarpsMax * kMaxM * 3 +
+                             kSingleWarpsMax * 8 + 16 + kSingleWarpsMax) +
            sizeof(float) * (size_t)mq + 16;
 }
 
@@ -704,7 +716,8 @@ int single_blocks_per_sm(int precision, int m, int minb, size_t smem)
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return 0;
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kBlock, smem) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, single_threads(precision), smem) != cudaSuccess)
+        return 0;
     return nb;
 }
 
@@ -717,7 +730,7 @@ SingleShape single_shape(int precision, int m, int q, int64_t rs, int nsm, size_
     // Contiguous equal column chunks over as many SMs as there are warps of
     // work (FP64 throughput per SM is the scarce resource), one CTA per SM
     // while that covers every column vector in a single pass, two otherwise.
-    sh.minb = (mixed && ncols > (int64_t)nsm * kBlock * unit) ? 2 : 1;
+    sh.minb = (mixed && ncols > (int64_t)nsm * single_threads(precision) * unit) ? 2 : 1;
     int per_sm = single_blocks_per_sm(precision, m, sh.minb, smem);
     if (per_sm < 1 && sh.minb == 2) {
         sh.minb = 1;
@@ -758,7 +771,7 @@ cudaError_t launch_single(int precision, int minb, const SingleArgs &a, size_t s
     if (e != cudaSuccess) return e;
     SingleArgs copy = a;
     void *args[] = {(void *)&copy};
-    return cudaLaunchCooperativeKernel(fn, dim3(a.grid), dim3(kBlock), args, smem, st);
+    return cudaLaunchCooperativeKernel(fn, dim3(a.grid), dim3(single_threads(precision)), args, smem, st);
 }
 
 } // namespace admm_impl
