@@ -369,6 +369,7 @@ def run_serving(args):
     steps = np.zeros(args.count, dtype=np.int64)
     lat_all, it_all, st_all = [], [], []
     submitted = 0
+    busy0 = S.stats()["gpu_busy_s"]
     t_start = time.perf_counter()
     next_t = t_start + rng.exponential(1.0 / args.rate)
     with ClockSampler(local) as clk:
@@ -389,6 +390,7 @@ def run_serving(args):
             st_all.extend(st.tolist())
             time.sleep(0.0005)
         window = time.perf_counter() - t_start
+        busy_window = S.stats()["gpu_busy_s"] - busy0
         finished_in_window = len(lat_all)
         t_end = time.perf_counter()
         while len(lat_all) < submitted and time.perf_counter() - t_end < 120:
@@ -416,6 +418,7 @@ def run_serving(args):
                 "submitted": submitted, "finished": len(lat_all),
                 "iters": {"mean": float(np.mean(it_all)), "max": int(np.max(it_all))} if it_all else None,
                 "ok_frac": float(np.mean(np.array(st_all) == 0)) if st_all else None,
+                "gpu_busy_frac": busy_window / window,
                 "server_stats": stats, "gpu_launches": int(stats["ticks"]), "clocks": clk.summary()}
         print(json.dumps(line))
     return 0

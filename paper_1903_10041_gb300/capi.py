@@ -590,9 +590,9 @@ class Server:
         return t[:k], lat[:k], it[:k], st[:k]
 
     def stats(self) -> dict:
-        buf = (C.c_double * 7)()
-        _check(_lib.admm_server_stats(self.h, buf, 7))
-        keys = ("ticks", "admitted", "finished", "active", "queued", "store_free_frac", "sessions")
+        buf = (C.c_double * 8)()
+        _check(_lib.admm_server_stats(self.h, buf, 8))
+        keys = ("ticks", "admitted", "finished", "active", "queued", "store_free_frac", "sessions", "gpu_busy_s")
         return {k: buf[t] for t, k in enumerate(keys)}
 
     def close(self):

@@ -37,9 +37,22 @@ struct BatchArgs {
     double *out;              // per-instance record [id][kInfo]; [0] iterations so far, [14] finished
     int slice_doubles;        // shared memory per warp-team slice
     int iter_budget;          // > 0: stop every instance after this many more iterations
+    const float *tick_work;   // if non-null (with iter_budget > 0): time-balanced budget, below
     double r_tol, s_tol, tau;
     int max_iter, check_every, xmin_mode, sweep, adapt;
 };
+
+// Time-balanced iteration budget (serving ticks): an instance whose team
+// spends `cost` element updates per thread and iteration runs
+// floor(*tick_work / cost) iterations (at least 1), so every team of a tick
+// works for about the same time and small instances are not held to the
+// pace of the largest one.  The host sets *tick_work to iter_budget times
+// the largest cost in the tick.  Where a tick ends does not change any
+// result: an instance resumes from its saved state bit for bit.
+__host__ __device__ inline float team_iter_cost(int n, int m, int q, int team_threads)
+{
+    return (float)((double)n * m * q / team_threads) + 4.0f; // + per-iteration fixed work
+}
 
 // Kernel variant (register arrays for M sources) of a batch or server: 4 for
 // every m <= 4, else 8.  It must not depend on which instances share a

@@ -168,7 +168,10 @@ template <int KIND, int NW, int M> __device__ void solve_team(const BatchArgs &a
     double res[7] = {out[4], out[5], out[6], out[7], out[8], out[9], out[10]};
     double r_last = out[2], s_last = out[3];
     int it = it0;
-    const int it_end = a.iter_budget > 0 ? min(a.max_iter, it0 + a.iter_budget) : a.max_iter;
+    int budget = a.iter_budget;
+    if (budget > 0 && a.tick_work)
+        budget = (int)fminf(fmaxf(*a.tick_work / team_iter_cost(n, m, q, W * 32), 1.0f), 1.0e9f);
+    const int it_end = budget > 0 ? (int)min((int64_t)a.max_iter, (int64_t)it0 + budget) : a.max_iter;
 
     while (it < it_end) {
         ++it;

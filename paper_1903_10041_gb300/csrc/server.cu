@@ -91,7 +91,8 @@ struct admm_server {
     std::map<int64_t, Session> sessions;
     int64_t next_ticket = 1;
     bool stop = false;
-    double stats[8] = {};
+    double stats[8] = {};      // ticks, admitted, finished, seconds the GPU spent in ticks
+    cudaEvent_t ev[2] = {nullptr, nullptr};
     std::string worker_error;
     std::thread worker;
 };
@@ -358,14 +359,31 @@ void worker_loop(admm_server *S)
         S->h_counts[0] = nX;
         S->h_counts[1] = nL;
         S->h_counts[2] = nS;
+        {   // time-balanced budgets: the largest per-thread cost of the tick sets its length
+            float cmax = 0.0f;
+            const int wc = S->cfg.batch.warps_per_cta * 32;
+            for (int t = 0; t < nX + nL + nS; ++t) {
+                const int s = t < nX ? S->h_order[t] : (t < nX + nL ? S->h_order[maxa + t - nX]
+                                                                    : S->h_order[2 * maxa + t - nX - nL]);
+                const int threads = t < nX ? S->cluster * wc : (t < nX + nL ? wc : 32);
+                cmax = std::max(cmax, team_iter_cost(S->h_inst[s].n, S->h_inst[s].m, S->h_inst[s].q, threads));
+            }
+            const float tw = (float)S->cfg.tick_iters * cmax;
+            std::memcpy(&S->h_counts[3], &tw, sizeof(float));
+        }
         cudaMemcpyAsync(S->d_order, S->h_order, sizeof(int) * nX, cudaMemcpyHostToDevice, S->st);
         cudaMemcpyAsync(S->d_order + maxa, S->h_order + maxa, sizeof(int) * nL, cudaMemcpyHostToDevice, S->st);
         cudaMemcpyAsync(S->d_order + 2 * maxa, S->h_order + 2 * maxa, sizeof(int) * nS, cudaMemcpyHostToDevice, S->st);
-        cudaMemcpyAsync(S->d_counts, S->h_counts, 3 * sizeof(int), cudaMemcpyHostToDevice, S->st);
+        cudaMemcpyAsync(S->d_counts, S->h_counts, 4 * sizeof(int), cudaMemcpyHostToDevice, S->st);
+        cudaEventRecord(S->ev[0], S->st);
         cudaError_t e = cudaGraphLaunch(S->exec, S->st);
+        cudaEventRecord(S->ev[1], S->st);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(S->h_out, S->d_out, sizeof(double) * kInfo * maxa, cudaMemcpyDeviceToHost, S->st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(S->st);
+        float tick_ms = 0.0f;
+        if (e == cudaSuccess && cudaEventElapsedTime(&tick_ms, S->ev[0], S->ev[1]) == cudaSuccess)
+            S->stats[3] += 1e-3 * tick_ms;
         S->stats[0] += 1;
         // retire finished instances
         for (int s : ids) {
@@ -463,6 +481,8 @@ admm_status admm_server_create(const admm_params *prm, const admm_server_config 
         for (void *p : h)
             if (p) cudaFreeHost(p);
         if (S->st) cudaStreamDestroy(S->st);
+        for (cudaEvent_t ev : S->ev)
+            if (ev) cudaEventDestroy(ev);
         delete S;
         return sfail(s, m);
     };
@@ -474,13 +494,13 @@ admm_status admm_server_create(const admm_params *prm, const admm_server_config 
                               (int64_t)maxa * scal_size(cfg->max_m, cfg->max_q), (int64_t)maxa * cfg->max_m);
     if (e == cudaSuccess) e = cudaMalloc(&S->d_inst, sizeof(BatchInst) * maxa);
     if (e == cudaSuccess) e = cudaMalloc(&S->d_order, sizeof(int) * 3 * maxa);
-    if (e == cudaSuccess) e = cudaMalloc(&S->d_counts, sizeof(int) * 3);
+    if (e == cudaSuccess) e = cudaMalloc(&S->d_counts, sizeof(int) * 4); // nX, nL, nS, tick work (float)
     if (e == cudaSuccess) e = cudaMalloc(&S->d_q, sizeof(int) * 3);
     if (e == cudaSuccess) e = cudaMalloc(&S->d_shift, sizeof(int) * maxa);
     if (e == cudaSuccess) e = cudaMalloc(&S->d_out, sizeof(double) * kInfo * maxa);
     if (e == cudaSuccess) e = cudaMallocHost(&S->h_inst, sizeof(BatchInst) * maxa);
     if (e == cudaSuccess) e = cudaMallocHost(&S->h_order, sizeof(int) * 3 * maxa);
-    if (e == cudaSuccess) e = cudaMallocHost(&S->h_counts, sizeof(int) * 3);
+    if (e == cudaSuccess) e = cudaMallocHost(&S->h_counts, sizeof(int) * 4);
     if (e == cudaSuccess) e = cudaMallocHost(&S->h_shift, sizeof(int) * maxa);
     if (e == cudaSuccess) e = cudaMallocHost(&S->h_out, sizeof(double) * kInfo * maxa);
     S->payload_stride = (6 * cfg->max_m * cfg->max_q + 2 * cfg->max_m + cfg->max_q + 3) / 4 * 4;
@@ -489,6 +509,8 @@ admm_status admm_server_create(const admm_params *prm, const admm_server_config 
     if (e == cudaSuccess) e = cudaMalloc(&S->d_payload, sizeof(float) * (size_t)maxa * S->payload_stride);
     if (e == cudaSuccess) e = cudaMallocHost(&S->h_payload, sizeof(float) * (size_t)maxa * S->payload_stride);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreate(&S->ev[0]);
+    if (e == cudaSuccess) e = cudaEventCreate(&S->ev[1]);
     if (e == cudaSuccess) e = cudaMemset(S->d_out, 0, sizeof(double) * kInfo * maxa);
     if (e != cudaSuccess)
         return bail(e == cudaErrorMemoryAllocation ? ADMM_ENOMEM : ADMM_ECUDA, cudaGetErrorString(e));
@@ -525,6 +547,7 @@ admm_status admm_server_create(const admm_params *prm, const admm_server_config 
     a.out = S->d_out;
     a.slice_doubles = (int)S->slice;
     a.iter_budget = cfg->tick_iters;
+    a.tick_work = (const float *)(S->d_counts + 3);
     a.r_tol = prm->r_tol;
     a.s_tol = prm->s_tol;
     a.tau = prm->tau;
@@ -676,7 +699,7 @@ admm_status admm_server_stats(admm_server *S, double *stats, int32_t count)
 {
     if (!S || !stats || count < 1) return sfail(ADMM_EINVAL, "bad argument");
     std::lock_guard<std::mutex> lk(S->mu);
-    double v[8] = {S->stats[0], S->stats[1], S->stats[2], 0.0, (double)S->pending.size(), 0.0, 0.0, 0.0};
+    double v[8] = {S->stats[0], S->stats[1], S->stats[2], 0.0, (double)S->pending.size(), 0.0, 0.0, S->stats[3]};
     for (auto &p : S->active)
         if (p) v[3] += 1;
     v[5] = (double)S->store.ae.free_total() / (double)std::max<int64_t>(1, S->store.ae.capacity());
@@ -703,6 +726,8 @@ admm_status admm_server_destroy(admm_server *S)
     for (void *p : h)
         if (p) cudaFreeHost(p);
     if (S->st) cudaStreamDestroy(S->st);
+    for (cudaEvent_t ev : S->ev)
+        if (ev) cudaEventDestroy(ev);
     delete S;
     return ADMM_OK;
 }
