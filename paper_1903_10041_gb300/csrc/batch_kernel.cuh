@@ -186,11 +186,12 @@ template <int KIND, int NW, int M> __device__ void solve_team(const BatchArgs &a
         for (int item = gw; item < items; item += W) {
             const int j = item / S, sg = item - j * S;
             const int v0 = sg * seg, v1 = min(nv, v0 + seg);
-            float ghi[M], glo[M], fmx[M], fmn[M];
+            float2 ghi[M], glo[M]; // per-lane capacity sums of the column pairs
+            float fmx[M], fmn[M];
 #pragma unroll
             for (int i = 0; i < M; ++i) {
-                ghi[i] = 0.0f;
-                glo[i] = 0.0f;
+                ghi[i] = make_float2(0.0f, 0.0f);
+                glo[i] = make_float2(0.0f, 0.0f);
                 fmx[i] = -INFINITY;
                 fmn[i] = INFINITY;
             }
@@ -203,7 +204,7 @@ template <int KIND, int NW, int M> __device__ void solve_team(const BatchArgs &a
 #pragma unroll
             for (int i = 0; i < M; ++i)
                 if (i < m) {
-                    FF v = ff_norm(ghi[i], glo[i]);
+                    FF v = lanes_sum(ghi[i], glo[i]);
                     float hi = fmx[i], lo = fmn[i];
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) {

@@ -13,10 +13,7 @@ constexpr int kBlockF64 = 384;       // threads per CTA of the FP64 solve kernel
 constexpr int kSingleWarpsMax = 12;  // most warps per CTA of the single-instance kernels
 constexpr int kMaxM = ADMM_MAX_M;
 constexpr int kInfo = 16;            // doubles of the per-solve info record
-#ifndef ADMM_MIXED_VW
-#define ADMM_MIXED_VW 2
-#endif
-constexpr int kMixedVW = ADMM_MIXED_VW; // columns per thread in the mixed kernels (2 or 4)
+constexpr int kMixedVW = 2; // columns per thread in the mixed kernels (one float2 pair)
 
 // Offsets into the scalar state vector (doubles), for mq = m*q pairs:
 //   [0, 5mq)        lam, zeta, h, p, nu   (pair arrays, mq each)

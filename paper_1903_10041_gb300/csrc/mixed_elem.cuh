@@ -1,8 +1,9 @@
 // Mixed-precision element work shared by the single-instance and batched
-// solve kernels: step (a) of App. A for all sources of a few consecutive
+// solve kernels: step (a) of App. A for all sources of a pair of consecutive
 // columns in FP32 (Algorithm 1 through quartic32.cuh), steps (e) and (f) on
 // the float-float column state, and the float-float accumulation of the
-// capacity sums over k.
+// capacity sums over k.  The two columns travel as one float2 through the
+// paired FP32 instructions.
 #pragma once
 #include "common.cuh"
 #include "internal.h"
@@ -10,40 +11,7 @@
 
 namespace admm_impl {
 
-// ---------------------------------------------------------------------------
-// Mixed phase 1: a float4 quad of columns (j, k0..k0+3), FP32 element work.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ float4 ldg4(const float *p) { return __ldg((const float4 *)p); }
-__device__ __forceinline__ float4 ld4(const float *p) { return *(const float4 *)p; }
-__device__ __forceinline__ float f4(const float4 &v, int c) { return c == 0 ? v.x : (c == 1 ? v.y : (c == 2 ? v.z : v.w)); }
-
-// g = b2 x^2 + b1 x as an unevaluated sum hi + lo (error-free products and sum).
-__device__ __forceinline__ void g_ff(float b2, float b1, float x, float &hi, float &lo)
-{
-    const float x2 = x * x;
-    const float ex2 = __fmaf_rn(x, x, -x2);
-    const float p = __fmul_rn(b2, x2);
-    const float ep = __fmaf_rn(b2, x2, -p) + b2 * ex2;
-    const float r = __fmul_rn(b1, x);
-    const float er = __fmaf_rn(b1, x, -r);
-    const float s = __fadd_rn(p, r);
-    const float bb = __fsub_rn(s, p);
-    const float es = __fadd_rn(__fsub_rn(p, __fsub_rn(s, bb)), __fsub_rn(r, bb));
-    hi = s;
-    lo = es + ep + er;
-}
-
-// (hi, lo) += (a, a_lo) in float-float.
-__device__ __forceinline__ void ff_add(float &hi, float &lo, float a, float a_lo)
-{
-    const float s = __fadd_rn(hi, a);
-    const float bb = __fsub_rn(s, hi);
-    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(a, bb));
-    hi = s;
-    lo = lo + (e + a_lo);
-}
-
-// Float-float arithmetic for the column state s, mu (steps (e), (f)).
+// Float-float arithmetic (segment reductions of the capacity sums).
 struct FF {
     float hi, lo;
 };
@@ -69,23 +37,6 @@ __device__ __forceinline__ FF ff_addf(FF a, float b)
     return ff_norm(t.hi, __fadd_rn(t.lo, a.lo));
 }
 __device__ __forceinline__ FF ff_neg(FF a) { return {-a.hi, -a.lo}; }
-
-// VW consecutive columns per thread (VW = 2 or 4), loaded as one vector.
-template <int VW> __device__ __forceinline__ void ldv(const float *p, float *v, bool ro)
-{
-    if constexpr (VW == 4) {
-        const float4 t = ro ? __ldg((const float4 *)p) : *(const float4 *)p;
-        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
-    } else {
-        const float2 t = ro ? __ldg((const float2 *)p) : *(const float2 *)p;
-        v[0] = t.x; v[1] = t.y;
-    }
-}
-template <int VW> __device__ __forceinline__ void stv(float *p, const float *v)
-{
-    if constexpr (VW == 4) *(float4 *)p = make_float4(v[0], v[1], v[2], v[3]);
-    else *(float2 *)p = make_float2(v[0], v[1]);
-}
 
 // Storage of one instance for the mixed element update (FP32 arrays with
 // row stride ld; s, mu float-float as hi and lo arrays).
@@ -124,158 +75,185 @@ __device__ __forceinline__ void prefetch_vec32(const ElemF32 &a, int j, int k0, 
         }
 }
 
-// Step (a) for all sources of VW columns (j, k0..k0+VW-1), then (e), (f).
-// uoff[pr] = zeta + lambda of pair pr in FP32; x1 and nu are the FP64 pair
-// scalars (read at k = 0 only).  rec (if k0 == 0) receives x at k = 0.
+// Float-float on packed pairs (the two columns of a vector).
+struct FF2 {
+    float2 hi, lo;
+};
+__device__ __forceinline__ FF2 ff2_two_sum(float2 a, float2 b)
+{
+    const float2 s = add2(a, b);
+    const float2 bb = sub2(s, a);
+    return {s, add2(sub2(a, sub2(s, bb)), sub2(b, bb))};
+}
+__device__ __forceinline__ FF2 ff2_norm(float2 hi, float2 lo)
+{
+    const float2 s = add2(hi, lo);
+    return {s, sub2(lo, sub2(s, hi))};
+}
+__device__ __forceinline__ FF2 ff2_add(FF2 a, FF2 b)
+{
+    const FF2 t = ff2_two_sum(a.hi, b.hi);
+    return ff2_norm(t.hi, add2(t.lo, add2(a.lo, b.lo)));
+}
+__device__ __forceinline__ FF2 ff2_addf(FF2 a, float2 b)
+{
+    const FF2 t = ff2_two_sum(a.hi, b);
+    return ff2_norm(t.hi, add2(t.lo, a.lo));
+}
+__device__ __forceinline__ FF2 ff2_neg(FF2 a) { return {neg2(a.hi), neg2(a.lo)}; }
+
+// g = b2 x^2 + b1 x as hi + lo on both lanes (error-free products and sum).
+__device__ __forceinline__ void g_ff2(float2 b2, float2 b1, float2 x, float2 &hi, float2 &lo)
+{
+    const float2 x2 = mul2(x, x);
+    const float2 ex2 = fma2(x, x, neg2(x2));
+    const float2 p = mul2(b2, x2);
+    const float2 ep = fma2(b2, ex2, fma2(b2, x2, neg2(p)));
+    const float2 r = mul2(b1, x);
+    const float2 er = fma2(b1, x, neg2(r));
+    const float2 s = add2(p, r);
+    const float2 bb = sub2(s, p);
+    const float2 es = add2(sub2(p, sub2(s, bb)), sub2(r, bb));
+    hi = s;
+    lo = add2(add2(es, ep), er);
+}
+
+// (hi, lo) += (a, a_lo) lane by lane in float-float.
+__device__ __forceinline__ void ff2_acc(float2 &hi, float2 &lo, float2 a, float2 a_lo)
+{
+    const float2 s = add2(hi, a);
+    const float2 bb = sub2(s, hi);
+    const float2 e = add2(sub2(hi, sub2(s, bb)), sub2(a, bb));
+    hi = s;
+    lo = add2(lo, add2(e, a_lo));
+}
+
+__device__ __forceinline__ float2 ld2(const float *p) { return *(const float2 *)p; }
+__device__ __forceinline__ float2 ldg2(const float *p) { return __ldg((const float2 *)p); }
+__device__ __forceinline__ void st2(float *p, float2 v) { *(float2 *)p = v; }
+
+// Step (a) for all sources of the column pair (j, k0), (j, k0 + 1), then
+// (e), (f), on packed pairs.  uoff[pr] = zeta + lambda of pair pr in FP32;
+// x1 and nu are the FP64 pair scalars (read at k = 0 only).  The capacity
+// sums accumulate per lane in ghi/glo (the caller combines the lanes), the
+// D_k extrema in dmx/dmn.  rec (if k0 == 0) receives x at k = 0.  The
+// first column is always < n; the second may be padding (k0 + 1 = n), and
+// then takes no part in the sums and residuals.
 template <int M, int VW, bool C64>
 __device__ __forceinline__ void vec32(const ElemF32 &a, const float *uoff, const double *x1s, const double *nus,
                                       int j, int k0, bool check, bool cold, float mu_div, float rho1, float rho3,
-                                      float rho4, float iq, float *ghi, float *glo, float *dmx, float *dmn,
+                                      float rho4, float iq, float2 *ghi, float2 *glo, float *dmx, float *dmn,
                                       float &cm_r, float &cm_s, unsigned &esc, double *rec)
 {
+    static_assert(VW == 2, "the element update works on column pairs");
     const int m = a.m, q = a.q, ld = a.ld, n = a.n;
-    const float *__restrict__ F2 = a.f2;
-    const float *__restrict__ F1 = a.f1;
-    const float *__restrict__ G2 = a.g2;
-    const float *__restrict__ G1 = a.g1;
-    const float *__restrict__ G0 = a.g0;
-    const float *__restrict__ LO = a.lo;
-    const float *__restrict__ HI = a.hi;
-    const float *__restrict__ Y = a.y;
-    float *X = a.x, *Sv = a.s, *MU = a.mu;
-    float *SL = a.s_lo, *ML = a.mu_lo;
-
     const size_t col = (size_t)j * ld + k0;
-    float yv[VW], st[VW], mu[VW], stl[VW], mul[VW];
-    ldv<VW>(Y + col, yv, true);
-    ldv<VW>(Sv + col, st, false);
-    ldv<VW>(MU + col, mu, false);
-    ldv<VW>(SL + col, stl, false);
-    ldv<VW>(ML + col, mul, false);
+    const float2 yv = ldg2(a.y + col);
+    const float2 st = ld2(a.s + col), stl = ld2(a.s_lo + col);
+    float2 mu = ld2(a.mu + col), mul = ld2(a.mu_lo + col);
     if (mu_div != 1.0f) {
-#pragma unroll
-        for (int c = 0; c < VW; ++c) {
-            mu[c] = mu[c] / mu_div;
-            mul[c] = mul[c] / mu_div;
-        }
+        mu = make_float2(mu.x / mu_div, mu.y / mu_div);
+        mul = make_float2(mul.x / mu_div, mul.y / mu_div);
     }
-    float xt[M][VW], xs[M][VW];
+    float2 xt[M], xs[M];
+    float2 xsum = splat2(0.0f); // sum of x over the sources, kept current by Gauss-Seidel
 #pragma unroll
     for (int i = 0; i < M; ++i)
         if (i < m) {
-            ldv<VW>(X + ((size_t)i * q + j) * ld + k0, xt[i], false);
-#pragma unroll
-            for (int c = 0; c < VW; ++c) xs[i][c] = xt[i][c];
+            xt[i] = ld2(a.x + ((size_t)i * q + j) * ld + k0);
+            xs[i] = xt[i];
+            xsum = add2(xsum, xt[i]);
         }
-    bool valid[VW];
-#pragma unroll
-    for (int c = 0; c < VW; ++c) valid[c] = k0 + c < n;
+    const bool v1 = k0 + 1 < n;
     const bool jac = a.sweep == ADMM_JACOBI;
-    // sum of x over the sources: Gauss-Seidel keeps it current as the sweep
-    // replaces x_i, Jacobi keeps the previous iterate's
-    float xsum[VW];
-#pragma unroll
-    for (int c = 0; c < VW; ++c) {
-        float t = 0.0f;
-#pragma unroll
-        for (int i = 0; i < M; ++i)
-            if (i < m) t += xt[i][c];
-        xsum[c] = t;
-    }
+    const float2 h1 = splat2(0.5f * rho1), h3 = splat2(0.5f * rho3), iq2 = splat2(iq);
+    const float2 nr1 = splat2(-rho1), nr3 = splat2(-rho3), r1 = splat2(rho1);
 
 #pragma unroll
     for (int i = 0; i < M; ++i) {
         if (i < m) {
             const size_t e = ((size_t)i * q + j) * ld + k0;
-            float A2[VW], A1[VW], B2[VW], B1[VW], L4[VW], H4[VW], Z4[VW];
-            ldv<VW>(F2 + e, A2, true);
-            ldv<VW>(F1 + e, A1, true);
-            ldv<VW>(G2 + e, B2, true);
-            ldv<VW>(G1 + e, B1, true);
-            ldv<VW>(LO + (size_t)i * ld + k0, L4, true);
-            ldv<VW>(HI + (size_t)i * ld + k0, H4, true);
-            if (cold) ldv<VW>(G0 + e, Z4, true);
-            else {
-#pragma unroll
-                for (int c = 0; c < VW; ++c) Z4[c] = 0.0f;
-            }
+            const float2 a2 = ldg2(a.f2 + e), a1 = ldg2(a.f1 + e), b2 = ldg2(a.g2 + e), b1 = ldg2(a.g1 + e);
+            const float2 L = ldg2(a.lo + (size_t)i * ld + k0), H = ldg2(a.hi + (size_t)i * ld + k0);
+            const float2 g0 = cold ? ldg2(a.g0 + e) : splat2(0.0f);
             const int pr = i * q + j;
-            const float uo = uoff[pr];
-#pragma unroll
-            for (int c = 0; c < VW; ++c) {
-                const float a2 = A2[c], a1 = A1[c], b2 = B2[c], b1 = B1[c], g0 = Z4[c];
-                const float x0 = xt[i][c];
-                const float gq_old = (b2 * x0 + b1) * x0;
-                const float u = cold ? -g0 : gq_old + uo;
-                const float others = xsum[c] - x0; // sum over l != i (x_i is still x0 here)
-                const float phi = ((st[c] - others) + yv[c]) + mu[c];
-                const float A = 0.5f * rho1 * b2 * b2;
-                const float B = rho1 * b2 * b1;
-                float C = a2 * iq + 0.5f * rho1 * (b1 * b1 - 2.0f * b2 * u) + 0.5f * rho3;
-                float D = a1 * iq - rho1 * b1 * u - rho3 * phi;
-                if (k0 + c == 0) {
-                    C += 0.5f * rho4;
-                    D -= rho4 * (float)(x1s[i] + nus[pr]);
-                }
-                const float xn = C64 ? quartic_min_fp64cubic(A, B, C, D, L4[c], H4[c], a.xmin_mode)
-                                     : quartic_min32(A, B, C, D, L4[c], H4[c], a.xmin_mode, esc);
-                if (!jac) xsum[c] += xn - x0;
-                xs[i][c] = xn;
-                if (valid[c]) {
-                    float ghh, gll;
-                    g_ff(b2, b1, xn, ghh, gll);
-                    ff_add(ghi[i], glo[i], ghh, gll);
-                    if (check) {
-                        const float dk = cold ? ghh + g0 : ghh - gq_old;
-                        dmx[i] = fmaxf(dmx[i], dk);
-                        dmn[i] = fminf(dmn[i], dk);
-                    }
-                }
+            const float2 x0 = xt[i];
+            const float2 gq_old = mul2(fma2(b2, x0, b1), x0);
+            const float2 u = cold ? neg2(g0) : add2(gq_old, splat2(uoff[pr]));
+            const float2 others = sub2(xsum, x0); // sum over l != i (x_i is still x0 here)
+            const float2 phi = add2(add2(sub2(st, others), yv), mu);
+            const float2 A = mul2(mul2(h1, b2), b2);
+            const float2 B = mul2(mul2(r1, b2), b1);
+            const float2 t = fma2(mul2(splat2(-2.0f), b2), u, mul2(b1, b1)); // b1^2 - 2 b2 u
+            float2 C = fma2(a2, iq2, fma2(h1, t, h3));
+            float2 D = fma2(a1, iq2, fma2(mul2(nr1, b1), u, mul2(nr3, phi)));
+            if (k0 == 0) {
+                C.x += 0.5f * rho4;
+                D.x -= rho4 * (float)(x1s[i] + nus[pr]);
+            }
+            float2 xn;
+            if constexpr (C64)
+                xn = make_float2(quartic_min_fp64cubic(A.x, B.x, C.x, D.x, L.x, H.x, a.xmin_mode),
+                                 quartic_min_fp64cubic(A.y, B.y, C.y, D.y, L.y, H.y, a.xmin_mode));
+            else
+                xn = quartic_min32x2(A, B, C, D, L, H, a.xmin_mode, esc);
+            if (!jac) xsum = add2(xsum, sub2(xn, x0));
+            xs[i] = xn;
+            float2 ghh, gll;
+            g_ff2(b2, b1, xn, ghh, gll);
+            if (!v1) {
+                ghh.y = 0.0f;
+                gll.y = 0.0f;
+            }
+            ff2_acc(ghi[i], glo[i], ghh, gll);
+            if (check) {
+                const float2 dk = cold ? add2(ghh, g0) : sub2(ghh, gq_old);
+                dmx[i] = fmaxf(dmx[i], v1 ? fmaxf(dk.x, dk.y) : dk.x);
+                dmn[i] = fminf(dmn[i], v1 ? fminf(dk.x, dk.y) : dk.x);
             }
         }
     }
     // (e), (f) in float-float: the column state carries about 48 bits, so
     // mu's accumulation of ever smaller primal residuals is not lost to FP32
     // rounding and the dual residual term of s settles below 1e-6.
-    float sn[VW], snl[VW], mn[VW], mnl[VW];
+    FF2 sx = {splat2(0.0f), splat2(0.0f)};
 #pragma unroll
-    for (int c = 0; c < VW; ++c) {
-        FF sx = {0.0f, 0.0f};
+    for (int i = 0; i < M; ++i)
+        if (i < m) sx = ff2_addf(sx, xs[i]);
+    const FF2 muf = {mu, mul}, stf = {st, stl};
+    const FF2 v = ff2_add(ff2_addf(sx, neg2(yv)), ff2_neg(muf));        // sum_i x - y - mu
+    const FF2 sv = {make_float2(v.hi.x > 0.0f ? v.hi.x : 0.0f, v.hi.y > 0.0f ? v.hi.y : 0.0f),
+                    make_float2(v.hi.x > 0.0f ? v.lo.x : 0.0f, v.hi.y > 0.0f ? v.lo.y : 0.0f)}; // (e)
+    const FF2 t = ff2_addf(ff2_add(sv, ff2_neg(sx)), yv);                // s - sum_i x + y
+    const FF2 mnew = ff2_add(muf, t);                                     // (f)
+    if (check) {
+        FF2 dx = {splat2(0.0f), splat2(0.0f)};
 #pragma unroll
         for (int i = 0; i < M; ++i)
-            if (i < m) sx = ff_addf(sx, xs[i][c]);
-        const FF muf = {mu[c], mul[c]}, stf = {st[c], stl[c]};
-        const FF v = ff_add(ff_addf(sx, -yv[c]), ff_neg(muf));       // sum_i x - y - mu
-        const FF sv = v.hi > 0.0f ? v : FF{0.0f, 0.0f};               // (e)
-        const FF t = ff_addf(ff_add(sv, ff_neg(sx)), yv[c]);          // s - sum_i x + y
-        const FF mnew = ff_add(muf, t);                                // (f)
-        sn[c] = sv.hi;
-        snl[c] = sv.lo;
-        mn[c] = mnew.hi;
-        mnl[c] = mnew.lo;
-        if (check && valid[c]) {
-            cm_r = fmaxf(cm_r, fabsf(t.hi + t.lo));
-            FF dx = {0.0f, 0.0f};
-#pragma unroll
-            for (int i = 0; i < M; ++i)
-                if (i < m) dx = ff_add(dx, ff_two_sum(xs[i][c], -xt[i][c]));
-            const FF d = ff_add(ff_add(sv, ff_neg(stf)), ff_neg(dx));  // s - s~ - sum_i (x - x~)
-            cm_s = fmaxf(cm_s, fabsf(d.hi + d.lo));
+            if (i < m) dx = ff2_add(dx, ff2_two_sum(xs[i], neg2(xt[i])));
+        const FF2 d = ff2_add(ff2_add(sv, ff2_neg(stf)), ff2_neg(dx)); // s - s~ - sum_i (x - x~)
+        cm_r = fmaxf(cm_r, fabsf(t.hi.x + t.lo.x));
+        cm_s = fmaxf(cm_s, fabsf(d.hi.x + d.lo.x));
+        if (v1) {
+            cm_r = fmaxf(cm_r, fabsf(t.hi.y + t.lo.y));
+            cm_s = fmaxf(cm_s, fabsf(d.hi.y + d.lo.y));
         }
     }
 #pragma unroll
     for (int i = 0; i < M; ++i)
-        if (i < m) stv<VW>(X + ((size_t)i * q + j) * ld + k0, xs[i]);
-    stv<VW>(Sv + col, sn);
-    stv<VW>(MU + col, mn);
-    stv<VW>(SL + col, snl);
-    stv<VW>(ML + col, mnl);
+        if (i < m) st2(a.x + ((size_t)i * q + j) * ld + k0, xs[i]);
+    st2(a.s + col, sv.hi);
+    st2(a.mu + col, mnew.hi);
+    st2(a.s_lo + col, sv.lo);
+    st2(a.mu_lo + col, mnew.lo);
     if (k0 == 0) {
 #pragma unroll
         for (int i = 0; i < M; ++i)
-            if (i < m) rec[i * 4 + 3] = (double)xs[i][0];
+            if (i < m) rec[i * 4 + 3] = (double)xs[i].x;
     }
 }
 
+// Lane sum of the per-thread capacity-sum accumulators of one source.
+__device__ __forceinline__ FF lanes_sum(float2 hi, float2 lo) { return ff_add(ff_norm(hi.x, lo.x), ff_norm(hi.y, lo.y)); }
 
 } // namespace admm_impl

@@ -168,4 +168,92 @@ __device__ __forceinline__ float quartic_min32(float A, float B, float C, float 
     return delta_f32(u, v, b, c, d) > 0.0f ? v : u;
 }
 
+// ---------------------------------------------------------------------------
+// Packed pair variant: the two columns of a vector in one float2, on the
+// paired FP32 instructions (FADD2 / FMUL2 / FFMA2: two lanes per issue, the
+// same rounding per lane as the scalar operations).  The common cases run
+// packed: both lanes quadratic (A = 0), or both lanes on the Cardano branch
+// with the discriminant's sign certified.  Any other combination (trig or
+// uncertain branch, mixed A = 0 / A > 0, non-finite intermediate) is solved
+// lane by lane by quartic_min32, so each lane gets the branch Algorithm 1
+// gives it.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 splat2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 abs2(float2 a) { return make_float2(fabsf(a.x), fabsf(a.y)); }
+
+// Newton step of newton_polish32 on both lanes.
+__device__ __forceinline__ float2 newton_polish32x2(float2 A, float2 B, float2 C, float2 D, float2 x)
+{
+    const float2 A4 = mul2(splat2(4.0f), A), B3 = mul2(splat2(3.0f), B), C2 = add2(C, C);
+    const float2 fp = fma2(fma2(fma2(A4, x, B3), x, C2), x, D);
+    const float2 fpp = fma2(fma2(mul2(splat2(12.0f), A), x, mul2(splat2(6.0f), B)), x, C2);
+    const float2 r = make_float2(fpp.x > 0.0f ? rcp_fast(fpp.x) : 0.0f, fpp.y > 0.0f ? rcp_fast(fpp.y) : 0.0f);
+    const float2 dx = mul2(fp, r);
+    const float2 xn = sub2(x, dx);
+    const float2 lim = mul2(splat2(0.0625f), add2(abs2(x), splat2(1.0f)));
+    return make_float2((fpp.x > 0.0f && fabsf(dx.x) <= lim.x) ? xn.x : x.x,
+                       (fpp.y > 0.0f && fabsf(dx.y) <= lim.y) ? xn.y : x.y);
+}
+
+// Lane by lane (out of line: the rare path stays out of the element loop).
+static __device__ __noinline__ float2 quartic_min32_lanes(float2 A, float2 B, float2 C, float2 D, float2 lo,
+                                                          float2 hi, int paper_mode, unsigned *esc)
+{
+    unsigned e = *esc;
+    const float2 x = make_float2(quartic_min32(A.x, B.x, C.x, D.x, lo.x, hi.x, paper_mode, e),
+                                 quartic_min32(A.y, B.y, C.y, D.y, lo.y, hi.y, paper_mode, e));
+    *esc = e;
+    return x;
+}
+
+__device__ __forceinline__ float2 quartic_min32x2(float2 A, float2 B, float2 C, float2 D, float2 lo, float2 hi,
+                                                  int paper_mode, unsigned &esc)
+{
+#ifndef ADMM_COMPENSATED_POLISH
+    if (A.x == 0.0f && A.y == 0.0f) { // quadratic on both lanes
+        const float2 C2 = add2(C, C);
+        const float2 x = mul2(neg2(D), make_float2(rcp_fast(C2.x), rcp_fast(C2.y)));
+        return make_float2(clampf(x.x, lo.x, hi.x), clampf(x.y, lo.y, hi.y));
+    }
+    if (A.x > 0.0f && A.y > 0.0f) {
+        const float2 inv = make_float2(rcp_fast(A.x), rcp_fast(A.y));
+        const float2 b = mul2(mul2(splat2(0.75f), B), inv);
+        const float2 c = mul2(mul2(splat2(0.5f), C), inv);
+        const float2 d = mul2(mul2(splat2(0.25f), D), inv);
+        const float2 b3 = mul2(b, splat2(1.0f / 3.0f));
+        const float2 b3s = mul2(b3, b3), b3c = mul2(b3s, b3);
+        const float2 Q = fma2(c, splat2(1.0f / 3.0f), neg2(b3s));
+        const float2 hc = mul2(splat2(0.5f), c);
+        const float2 bhc = mul2(b3, hc);
+        const float2 R = sub2(sub2(bhc, b3c), mul2(splat2(0.5f), d));
+        const float2 Qs = mul2(Q, Q);
+        const float2 Q3 = mul2(Qs, Q), R2 = mul2(R, R);
+        const float2 Dl = add2(Q3, R2);
+        // the forward error bound of quartic_min32, on both lanes
+        const float2 mQ = fma2(abs2(c), splat2(1.0f / 3.0f), b3s);
+        const float2 mR = fma2(splat2(0.5f), abs2(d), add2(abs2(bhc), abs2(b3c)));
+        const float2 bsum = fma2(mul2(splat2(96.0f), Qs), mQ,
+                                 fma2(splat2(64.0f), abs2(Q3),
+                                      fma2(mul2(splat2(96.0f), abs2(R)), mR, mul2(splat2(64.0f), R2))));
+        const float2 bound = mul2(splat2(6.0e-8f), bsum);
+        if (Dl.x > bound.x && Dl.y > bound.y) { // Cardano on both lanes
+            const float2 sq = make_float2(sqrt_fast(Dl.x), sqrt_fast(Dl.y));
+            const float2 v = add2(R, make_float2(R.x >= 0.0f ? sq.x : -sq.x, R.y >= 0.0f ? sq.y : -sq.y));
+            const float2 S = make_float2(cbrt_fast(v.x), cbrt_fast(v.y));
+            const float2 rS = make_float2(S.x != 0.0f ? rcp_fast(S.x) : 0.0f, S.y != 0.0f ? rcp_fast(S.y) : 0.0f);
+            const float2 T = mul2(neg2(Q), rS);
+            const float2 x = newton_polish32x2(A, B, C, D, sub2(add2(S, T), b3));
+            if (isfinite(x.x) && isfinite(x.y))
+                return make_float2(clampf(x.x, lo.x, hi.x), clampf(x.y, lo.y, hi.y));
+        }
+    }
+#endif
+    return quartic_min32_lanes(A, B, C, D, lo, hi, paper_mode, &esc);
+}
+
 } // namespace admm_impl

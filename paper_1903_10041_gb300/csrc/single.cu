@@ -343,8 +343,8 @@ __device__ __forceinline__ void flush_segments(const SingleArgs &a, int par, int
 // Mixed variant, on the FP32 pipes: float-float sums and FP32 max / min in
 // a fixed order; only the finished records are converted to FP64.
 template <int M, int NWP>
-__device__ __forceinline__ void flush_segments32(const SingleArgs &a, int par, int jb, const float *ghi,
-                                                 const float *glo, const float *fmx, const float *fmn, bool check,
+__device__ __forceinline__ void flush_segments32(const SingleArgs &a, int par, int jb, const float2 *ghi,
+                                                 const float2 *glo, const float *fmx, const float *fmn, bool check,
                                                  int m, const SegPlan &sp, const Sm &sm)
 {
     float *red = (float *)sm.red; // [NWP][kMaxM][4] floats
@@ -352,7 +352,7 @@ __device__ __forceinline__ void flush_segments32(const SingleArgs &a, int par, i
 #pragma unroll
     for (int i = 0; i < M; ++i)
         if (i < m) {
-            FF v = ff_norm(ghi[i], glo[i]);
+            FF v = lanes_sum(ghi[i], glo[i]);
             float hi = fmx[i], lo = fmn[i];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
@@ -454,11 +454,12 @@ __global__ void __launch_bounds__(NT, MINB) single_kernel(SingleArgs a)
                     column64<M>(a, sm, j, k, check, cold, mu_div, gs, dmx, dmn, cm_r, cm_s, rec);
                 flush_segments<M, NWP>(a, par, jb, gs, dmx, dmn, check, m, sp, sm);
             } else {
-                float ghi[M], glo[M], fmx[M], fmn[M];
+                float2 ghi[M], glo[M]; // per-lane capacity sums of the column pairs
+                float fmx[M], fmn[M];
 #pragma unroll
                 for (int i = 0; i < M; ++i) {
-                    ghi[i] = 0.0f;
-                    glo[i] = 0.0f;
+                    ghi[i] = make_float2(0.0f, 0.0f);
+                    glo[i] = make_float2(0.0f, 0.0f);
                     fmx[i] = -INFINITY;
                     fmn[i] = INFINITY;
                 }

@@ -1,7 +1,9 @@
 """Mixed-precision solves (FP32 storage and element work, FP64 scalars and
 residuals) against the FP64 oracle: at convergence the objective matches
-to 1e-6 relative and the KKT residual of eq. (2) stays within 1e-6 of the
-oracle's own.  Both mixed policies are covered: the FP32 cubic with
+to 1e-6 relative and the KKT residual of eq. (2) stays within r-bar +
+sigma-bar = 2e-6 of the oracle's own (both stop on the termination test of
+Alg. 2 step 3, a few iterations apart, and that test fixes the KKT residual
+only to within its two thresholds).  Both mixed policies are covered: the FP32 cubic with
 FP64-certified branch decisions and the FP64 cubic step."""
 import numpy as np
 import pytest
@@ -11,7 +13,7 @@ from paper_1903_10041_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 OBJ_TOL = 1e-6
-KKT_MARGIN = 1e-6
+KKT_MARGIN = 2e-6  # r-bar + sigma-bar of the termination test
 
 
 @pytest.fixture(scope="module")
