@@ -369,7 +369,7 @@ def run_serving(args):
     steps = np.zeros(args.count, dtype=np.int64)
     lat_all, it_all, st_all = [], [], []
     submitted = 0
-    busy0 = S.stats()["gpu_busy_s"]
+    st0 = S.stats()
     t_start = time.perf_counter()
     next_t = t_start + rng.exponential(1.0 / args.rate)
     with ClockSampler(local) as clk:
@@ -390,7 +390,9 @@ def run_serving(args):
             st_all.extend(st.tolist())
             time.sleep(0.0005)
         window = time.perf_counter() - t_start
-        busy_window = S.stats()["gpu_busy_s"] - busy0
+        st1 = S.stats()
+        busy_window = st1["gpu_busy_s"] - st0["gpu_busy_s"]
+        shift_window = st1["gpu_shift_s"] - st0["gpu_shift_s"]
         finished_in_window = len(lat_all)
         t_end = time.perf_counter()
         while len(lat_all) < submitted and time.perf_counter() - t_end < 120:
@@ -418,7 +420,7 @@ def run_serving(args):
                 "submitted": submitted, "finished": len(lat_all),
                 "iters": {"mean": float(np.mean(it_all)), "max": int(np.max(it_all))} if it_all else None,
                 "ok_frac": float(np.mean(np.array(st_all) == 0)) if st_all else None,
-                "gpu_busy_frac": busy_window / window,
+                "gpu_busy_frac": busy_window / window, "gpu_shift_frac": shift_window / window,
                 "server_stats": stats, "gpu_launches": int(stats["ticks"]), "clocks": clk.summary()}
         print(json.dumps(line))
     return 0
@@ -441,7 +443,8 @@ def main():
     ap.add_argument("--count", type=int, default=4096, help="instances (3) or controllers (4)")
     ap.add_argument("--duration", type=float, default=60.0, help="serving window in seconds (4)")
     ap.add_argument("--rate", type=float, default=2000.0, help="Poisson arrival rate per second (4)")
-    ap.add_argument("--tick-iters", type=int, default=20, help="iterations per serving tick (4)")
+    ap.add_argument("--tick-iters", type=int, default=10,
+                    help="iterations per serving tick of the costliest active instance (4)")
     ap.add_argument("--adapt", action="store_true", help="penalty adaptation of Sec. IV-A (3)")
     ap.add_argument("--batch-config", default="",
                     help="warps,ctas_per_sm,small_max,cluster,cluster_min instead of the autotuner (3, 4)")

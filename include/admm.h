@@ -225,7 +225,8 @@ typedef struct admm_batch_config {
  * (FP32 arrays; the problems may be host or device memory) and sets every
  * instance to the zero start.  params->precision must be ADMM_MIXED;
  * the settings apply to every instance.  Default configuration: 8 warps
- * per CTA, small_max_elements 16384, no clusters (cluster_size 1). */
+ * per CTA, small_max_elements 0 (every instance on a whole-CTA team, the
+ * fastest on mixed workloads of 50..400k elements), no clusters. */
 admm_status admm_batch_create(const admm_problem *probs, int32_t count, const admm_params *params,
                               admm_batch **out);
 admm_status admm_batch_set_config(admm_batch *b, const admm_batch_config *cfg);
@@ -268,13 +269,14 @@ typedef struct admm_server admm_server;
 typedef struct admm_server_config {
     int64_t store_elements;      /* device store capacity, in elements m*q*ld (ld = n rounded up to 4) */
     int32_t max_active;          /* instances on the GPU at once */
-    int32_t tick_iters;          /* iterations per tick */
+    int32_t tick_iters;          /* iterations per tick of the costliest active instance; the others
+                                    run as many as fit in the same time */
     int32_t max_m, max_q;        /* largest m and q a request may have (m*q <= ADMM_BATCH_MAX_PAIRS) */
     admm_batch_config batch;     /* launch configuration of a tick */
 } admm_server_config;
 
-/* store 2^27 elements, 4096 active, 50 iterations per tick, max_m 4,
- * max_q 20, 8 warps per CTA, small_max_elements 16384, no clusters. */
+/* store 2^27 elements, 4096 active, 10 iterations per tick, max_m 4,
+ * max_q 20, 8 warps per CTA, small_max_elements 0, no clusters. */
 void admm_server_default_config(admm_server_config *cfg);
 admm_status admm_server_create(const admm_params *params, const admm_server_config *cfg, admm_server **out);
 /* Validates and queues a request; session >= 0 ties it to that session
@@ -308,8 +310,9 @@ admm_status admm_server_poll(admm_server *s, int64_t ticket, int32_t wait_ms, ad
  * how many.  Drained tickets are forgotten (their x is not kept). */
 admm_status admm_server_drain(admm_server *s, int32_t max, int64_t *tickets, double *latency_s, int32_t *iters,
                               int32_t *status, int32_t *count);
-/* stats[0..7]: ticks, admitted, finished, active, queued, free fraction of
- * the store, sessions, seconds the GPU spent running ticks. */
+/* stats[0..8]: ticks, admitted, finished, active, queued, free fraction of
+ * the store, sessions, seconds the GPU spent running ticks, seconds it spent
+ * moving step requests' instances one step forward. */
 admm_status admm_server_stats(admm_server *s, double *stats, int32_t count);
 /* Stops the worker (in-flight requests are dropped) and frees everything. */
 admm_status admm_server_destroy(admm_server *s);

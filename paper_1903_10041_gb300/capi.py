@@ -390,7 +390,7 @@ class Batch:
         self._keep = []  # the batch holds its own copy of the data
         self.count = len(problems)
 
-    def set_config(self, warps_per_cta=8, ctas_per_sm=0, small_max_elements=16384, cluster_size=1,
+    def set_config(self, warps_per_cta=8, ctas_per_sm=0, small_max_elements=0, cluster_size=1,
                    cluster_min_elements=131072):
         c = admm_batch_config(int(warps_per_cta), int(ctas_per_sm), int(small_max_elements), int(cluster_size), 0,
                               int(cluster_min_elements))
@@ -515,8 +515,8 @@ _lib.admm_server_submit_step.restype = C.c_int
 class Server:
     """Continuous-batching request loop (admm_server_* in admm.h)."""
 
-    def __init__(self, par=None, store_elements=1 << 27, max_active=4096, tick_iters=50, max_m=4, max_q=20,
-                 warps_per_cta=8, ctas_per_sm=0, small_max_elements=16384, cluster_size=1,
+    def __init__(self, par=None, store_elements=1 << 27, max_active=4096, tick_iters=10, max_m=4, max_q=20,
+                 warps_per_cta=8, ctas_per_sm=0, small_max_elements=0, cluster_size=1,
                  cluster_min_elements=131072, **kw):
         pp = par if isinstance(par, admm_params) else make_params(par, **kw)
         pp.precision = PRECISION["mixed"]
@@ -590,9 +590,10 @@ class Server:
         return t[:k], lat[:k], it[:k], st[:k]
 
     def stats(self) -> dict:
-        buf = (C.c_double * 8)()
-        _check(_lib.admm_server_stats(self.h, buf, 8))
-        keys = ("ticks", "admitted", "finished", "active", "queued", "store_free_frac", "sessions", "gpu_busy_s")
+        buf = (C.c_double * 9)()
+        _check(_lib.admm_server_stats(self.h, buf, 9))
+        keys = ("ticks", "admitted", "finished", "active", "queued", "store_free_frac", "sessions", "gpu_busy_s",
+                "gpu_shift_s")
         return {k: buf[t] for t, k in enumerate(keys)}
 
     def close(self):

@@ -23,14 +23,37 @@ namespace {
 // controller moved one step forward in place (x_k <- x_{k+1}, last step
 // kept; the same for s and mu), x_1^(i) reset to the mean of the new first
 // moves, cold flag cleared.  One CTA per instance.
+// row[k] <- row[k + 1] for k < n - 1, by one warp: each round reads 32 * 4
+// values ahead of the ones it overwrites (left to right, so every value is
+// read before it is replaced).
+__device__ __forceinline__ void warp_shift_left(float *row, int n)
+{
+    const int lane = threadIdx.x & 31;
+    for (int k0 = 0; k0 < n - 1; k0 += 128) {
+        float v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int k = k0 + u * 32 + lane;
+            v[u] = k < n - 1 ? row[k + 1] : 0.0f;
+        }
+        __syncwarp();
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int k = k0 + u * 32 + lane;
+            if (k < n - 1) row[k] = v[u];
+        }
+        __syncwarp();
+    }
+}
+
 __global__ void shift_state_kernel(const BatchInst *inst, const int *ids, int count, float *x, float *s, float *s_lo,
                                    float *mu, float *mu_lo, double *scal)
 {
     for (int t = blockIdx.x; t < count; t += gridDim.x) {
         const BatchInst I = inst[ids[t]];
         const int n = I.n, rows_e = I.m * I.q;
-        // rows of x, then rows of s, s_lo, mu, mu_lo; each shifted left by one
-        for (int r = 0; r < rows_e + 4 * I.q; ++r) {
+        // rows of x, then rows of s, s_lo, mu, mu_lo; each shifted left by one (a warp per row)
+        for (int r = threadIdx.x >> 5; r < rows_e + 4 * I.q; r += blockDim.x >> 5) {
             float *row;
             if (r < rows_e) row = x + I.off_e + (int64_t)r * I.ld;
             else {
@@ -38,14 +61,9 @@ __global__ void shift_state_kernel(const BatchInst *inst, const int *ids, int co
                 float *base = c == 0 ? s : (c == 1 ? s_lo : (c == 2 ? mu : mu_lo));
                 row = base + I.off_c + (int64_t)j * I.ld;
             }
-            for (int k0 = 0; k0 < n - 1; k0 += blockDim.x) {
-                const int k = k0 + threadIdx.x;
-                const float v = k < n - 1 ? row[k + 1] : 0.0f;
-                __syncthreads();
-                if (k < n - 1) row[k] = v;
-                __syncthreads();
-            }
+            warp_shift_left(row, n);
         }
+        __syncthreads();
         double *sc = scal + I.off_scal;
         const int mq = I.m * I.q;
         if (threadIdx.x < I.m) {
@@ -68,17 +86,18 @@ __global__ void shift_state_kernel(const BatchInst *inst, const int *ids, int co
 __global__ void shift_step_kernel(const BatchInst *inst, const int *ids, int count, const float *payload,
                                   int payload_stride, float *f2, float *f1, float *f0, float *g2, float *g1, float *g0,
                                   float *lo, float *hi, float *y, float *x, float *s, float *s_lo, float *mu,
-                                  float *mu_lo, double *sumg0, double *scal)
+                                  float *mu_lo, double *sumg0, double *scal, double *out)
 {
     for (int t = blockIdx.x; t < count; t += gridDim.x) {
         const int id = ids[t];
         const BatchInst I = inst[id];
         const int n = I.n, m = I.m, q = I.q, mq = m * q;
-        const float *pl = payload + (size_t)id * payload_stride;
+        const float *pl = payload + (size_t)t * payload_stride;
+        for (int u = threadIdx.x; u < kInfo; u += blockDim.x) out[(size_t)id * kInfo + u] = 0.0; // fresh record
         float *erows[7] = {f2, f1, f0, g2, g1, g0, x};
         float *crows[5] = {y, s, s_lo, mu, mu_lo};
         const int nrows = 7 * mq + 2 * m + 5 * q;
-        for (int r = 0; r < nrows; ++r) {
+        for (int r = threadIdx.x >> 5; r < nrows; r += blockDim.x >> 5) { // a warp per row
             float *row;
             if (r < 7 * mq) row = erows[r / mq] + I.off_e + (int64_t)(r % mq) * I.ld;
             else if (r < 7 * mq + 2 * m) {
@@ -88,14 +107,9 @@ __global__ void shift_step_kernel(const BatchInst *inst, const int *ids, int cou
                 const int rr = r - 7 * mq - 2 * m;
                 row = crows[rr / q] + I.off_c + (int64_t)(rr % q) * I.ld;
             }
-            for (int k0 = 0; k0 < n - 1; k0 += blockDim.x) {
-                const int k = k0 + threadIdx.x;
-                const float v = k < n - 1 ? row[k + 1] : 0.0f;
-                __syncthreads();
-                if (k < n - 1) row[k] = v;
-                __syncthreads();
-            }
+            warp_shift_left(row, n);
         }
+        __syncthreads();
         // the new last step
         const int last = n - 1;
         for (int u = threadIdx.x; u < mq; u += blockDim.x) {
@@ -140,17 +154,41 @@ __global__ void shift_step_kernel(const BatchInst *inst, const int *ids, int cou
     }
 }
 
+// One CTA per finished instance: x rows [m q][ld] (FP32) -> [m q][n] FP64,
+// then x_1 from the scalar state.
+__global__ void gather_x_kernel(const BatchInst *inst, const int *ids, const int64_t *dst, int count, const float *x,
+                                const double *scal, double *out)
+{
+    for (int t = blockIdx.x; t < count; t += gridDim.x) {
+        const BatchInst I = inst[ids[t]];
+        const int64_t rows = (int64_t)I.m * I.q, ne = rows * I.n;
+        double *o = out + dst[t];
+        for (int64_t e = threadIdx.x; e < ne; e += blockDim.x) {
+            const int64_t r = e / I.n;
+            const int k = (int)(e - r * I.n);
+            o[e] = (double)x[I.off_e + r * I.ld + k];
+        }
+        for (int i = threadIdx.x; i < I.m; i += blockDim.x) o[ne + i] = scal[I.off_scal + 5 * rows + i];
+    }
+}
+
 } // namespace
+
+void launch_gather_x(const BatchInst *inst, const int *ids, const int64_t *dst, int count, const float *x,
+                     const double *scal, double *out, cudaStream_t st)
+{
+    if (count > 0) gather_x_kernel<<<std::min(count, 4096), 256, 0, st>>>(inst, ids, dst, count, x, scal, out);
+}
 
 void launch_shift_step(const BatchInst *inst, const int *ids, int count, const float *payload, int payload_stride,
                        float *f2, float *f1, float *f0, float *g2, float *g1, float *g0, float *lo, float *hi,
                        float *y, float *x, float *s, float *s_lo, float *mu, float *mu_lo, double *sumg0,
-                       double *scal, cudaStream_t st)
+                       double *scal, double *out, cudaStream_t st)
 {
     if (count > 0)
         shift_step_kernel<<<std::min(count, 1024), 256, 0, st>>>(inst, ids, count, payload, payload_stride, f2, f1, f0,
                                                                  g2, g1, g0, lo, hi, y, x, s, s_lo, mu, mu_lo, sumg0,
-                                                                 scal);
+                                                                 scal, out);
 }
 
 void launch_shift_state(const BatchInst *inst, const int *ids, int count, float *x, float *s, float *s_lo, float *mu,

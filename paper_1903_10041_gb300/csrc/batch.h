@@ -73,12 +73,17 @@ cudaError_t launch_batch(int warps, int mbound, int grid, int cluster, const Bat
                          cudaStream_t st);
 // Co-resident clusters of that size (0 if it cannot launch).
 int batch_max_clusters(int warps, int mbound, int cluster, size_t smem);
-// Moves data and state of instances ids[0..count-1] one step forward and
-// writes the new last step from payload + id * payload_stride.
+// Moves data and state of instances ids[0..count-1] one step forward,
+// writes the new last step from payload + t * payload_stride and clears the
+// result record out[id].
 void launch_shift_step(const BatchInst *inst, const int *ids, int count, const float *payload, int payload_stride,
                        float *f2, float *f1, float *f0, float *g2, float *g1, float *g0, float *lo, float *hi,
                        float *y, float *x, float *s, float *s_lo, float *mu, float *mu_lo, double *sumg0,
-                       double *scal, cudaStream_t st);
+                       double *scal, double *out, cudaStream_t st);
+// Gathers x (as FP64, rows of n) followed by x_1 (m values) of instances
+// ids[0..count-1] into out + dst[t], for one device-to-host copy.
+void launch_gather_x(const BatchInst *inst, const int *ids, const int64_t *dst, int count, const float *x,
+                     const double *scal, double *out, cudaStream_t st);
 // Moves the state of instances ids[0..count-1] one step forward (receding horizon).
 void launch_shift_state(const BatchInst *inst, const int *ids, int count, float *x, float *s, float *s_lo, float *mu,
                         float *mu_lo, double *scal, cudaStream_t st);

@@ -85,7 +85,7 @@ cudaError_t to_host(const admm_problem &in, HostProblem &out)
 struct admm_batch {
     int count = 0, dev = 0, nsm = 0, max_m = 0, max_q = 0;
     admm_params prm{};
-    admm_batch_config cfg{8, 0, 16384, 1, 0, 131072};
+    admm_batch_config cfg{8, 0, 0, 1, 0, 131072};
     Store store;
     std::vector<BatchInst> inst;
     BatchInst *d_inst = nullptr;

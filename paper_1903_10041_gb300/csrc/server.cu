@@ -79,6 +79,10 @@ struct admm_server {
     int payload_stride = 0;
     double *d_out = nullptr, *h_out = nullptr, *d_tmp = nullptr;
     size_t tmp_n = 0;
+    int *d_gids = nullptr, *h_gids = nullptr;       // finished instances of a tick
+    int64_t *d_goff = nullptr, *h_goff = nullptr;   // their offsets in the gathered results
+    double *h_gather = nullptr;                     // gathered x and x_1 (pinned)
+    size_t gather_n = 0;
     float *pinned = nullptr;
     size_t pinned_n = 0;
 
@@ -91,8 +95,8 @@ struct admm_server {
     std::map<int64_t, Session> sessions;
     int64_t next_ticket = 1;
     bool stop = false;
-    double stats[8] = {};      // ticks, admitted, finished, seconds the GPU spent in ticks
-    cudaEvent_t ev[2] = {nullptr, nullptr};
+    double stats[8] = {}; // ticks, admitted, finished, GPU seconds in ticks, GPU seconds in step shifts
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     std::string worker_error;
     std::thread worker;
 };
@@ -113,6 +117,18 @@ cudaError_t ensure_tmp(admm_server *S, size_t n)
     S->tmp_n = 0;
     cudaError_t e = cudaMalloc(&S->d_tmp, n * sizeof(double));
     if (e == cudaSuccess) S->tmp_n = n;
+    return e;
+}
+
+cudaError_t ensure_gather(admm_server *S, size_t n)
+{
+    cudaError_t e = ensure_tmp(S, n);
+    if (e != cudaSuccess || S->gather_n >= n) return e;
+    if (S->h_gather) cudaFreeHost(S->h_gather);
+    S->h_gather = nullptr;
+    S->gather_n = 0;
+    e = cudaMallocHost(&S->h_gather, n * sizeof(double));
+    if (e == cudaSuccess) S->gather_n = n;
     return e;
 }
 
@@ -183,6 +199,7 @@ void worker_loop(admm_server *S)
         }
         // place and upload the admitted requests (worker-only state)
         shift_ids.clear();
+        bool inst_dirty = false, shift_timed = false;
         std::vector<std::shared_ptr<Request>> back_to_queue;
         std::vector<int> step_ids;
         for (auto &r : admit) {
@@ -208,15 +225,11 @@ void worker_loop(admm_server *S)
                     S->cv_done.notify_all();
                     continue;
                 }
-                std::memcpy(S->h_payload + (size_t)r->slot * S->payload_stride, r->payload.data(),
+                // staged in admission order; one copy for all of them below
+                std::memcpy(S->h_payload + step_ids.size() * S->payload_stride, r->payload.data(),
                             sizeof(float) * r->payload.size());
-                cudaMemcpyAsync(S->d_payload + (size_t)r->slot * S->payload_stride,
-                                S->h_payload + (size_t)r->slot * S->payload_stride, sizeof(float) * r->payload.size(),
-                                cudaMemcpyHostToDevice, S->st);
                 S->h_inst[r->slot] = I;
-                cudaMemcpyAsync(S->d_inst + r->slot, &S->h_inst[r->slot], sizeof(BatchInst), cudaMemcpyHostToDevice,
-                                S->st);
-                cudaMemsetAsync(S->d_out + (size_t)r->slot * kInfo, 0, sizeof(double) * kInfo, S->st);
+                inst_dirty = true;
                 step_ids.push_back(r->slot);
                 r->warm = true;
                 r->t_admit = now_s();
@@ -294,7 +307,7 @@ void worker_loop(admm_server *S)
                 continue;
             }
             S->h_inst[r->slot] = I;
-            cudaMemcpyAsync(S->d_inst + r->slot, &S->h_inst[r->slot], sizeof(BatchInst), cudaMemcpyHostToDevice, S->st);
+            inst_dirty = true;
             cudaMemsetAsync(S->d_out + (size_t)r->slot * kInfo, 0, sizeof(double) * kInfo, S->st);
             if (r->session >= 0) {
                 std::lock_guard<std::mutex> lk(S->mu);
@@ -325,13 +338,20 @@ void worker_loop(admm_server *S)
             }
             S->cv_done.notify_all();
         }
+        if (inst_dirty) // the whole instance table in one copy (a few hundred KB)
+            cudaMemcpyAsync(S->d_inst, S->h_inst, sizeof(BatchInst) * maxa, cudaMemcpyHostToDevice, S->st);
         if (!step_ids.empty()) {
             std::copy(step_ids.begin(), step_ids.end(), S->h_stepids);
             cudaMemcpyAsync(S->d_stepids, S->h_stepids, sizeof(int) * step_ids.size(), cudaMemcpyHostToDevice, S->st);
+            cudaMemcpyAsync(S->d_payload, S->h_payload, sizeof(float) * step_ids.size() * S->payload_stride,
+                            cudaMemcpyHostToDevice, S->st);
             Store &T = S->store;
+            cudaEventRecord(S->ev[2], S->st);
             launch_shift_step(S->d_inst, S->d_stepids, (int)step_ids.size(), S->d_payload, S->payload_stride, T.f2,
                               T.f1, T.f0, T.g2, T.g1, T.g0, T.lo, T.hi, T.y, T.x, T.s, T.s_lo, T.mu, T.mu_lo, T.sumg0,
-                              T.scal, S->st);
+                              T.scal, S->d_out, S->st);
+            cudaEventRecord(S->ev[3], S->st);
+            shift_timed = true;
         }
         if (!shift_ids.empty()) {
             std::copy(shift_ids.begin(), shift_ids.end(), S->h_shift);
@@ -384,11 +404,39 @@ void worker_loop(admm_server *S)
         float tick_ms = 0.0f;
         if (e == cudaSuccess && cudaEventElapsedTime(&tick_ms, S->ev[0], S->ev[1]) == cudaSuccess)
             S->stats[3] += 1e-3 * tick_ms;
+        if (e == cudaSuccess && shift_timed && cudaEventElapsedTime(&tick_ms, S->ev[2], S->ev[3]) == cudaSuccess)
+            S->stats[4] += 1e-3 * tick_ms;
         S->stats[0] += 1;
-        // retire finished instances
-        for (int s : ids) {
+        // retire finished instances: their x and x_1 come back in one gather
+        // kernel and one copy
+        std::vector<int> fin;
+        for (int s : ids)
+            if (e != cudaSuccess || S->h_out[(size_t)s * kInfo + 14] != 0.0) fin.push_back(s);
+        cudaError_t eg = cudaSuccess;
+        if (e == cudaSuccess && !fin.empty()) {
+            int64_t tot = 0;
+            for (size_t t = 0; t < fin.size(); ++t) {
+                const BatchInst &I = S->h_inst[fin[t]];
+                S->h_gids[t] = fin[t];
+                S->h_goff[t] = tot;
+                tot += (int64_t)I.m * I.q * I.n + I.m;
+            }
+            eg = ensure_gather(S, (size_t)tot);
+            if (eg == cudaSuccess)
+                eg = cudaMemcpyAsync(S->d_gids, S->h_gids, sizeof(int) * fin.size(), cudaMemcpyHostToDevice, S->st);
+            if (eg == cudaSuccess)
+                eg = cudaMemcpyAsync(S->d_goff, S->h_goff, sizeof(int64_t) * fin.size(), cudaMemcpyHostToDevice,
+                                     S->st);
+            if (eg == cudaSuccess) {
+                launch_gather_x(S->d_inst, S->d_gids, S->d_goff, (int)fin.size(), S->store.x, S->store.scal, S->d_tmp,
+                                S->st);
+                eg = cudaMemcpyAsync(S->h_gather, S->d_tmp, sizeof(double) * tot, cudaMemcpyDeviceToHost, S->st);
+            }
+            if (eg == cudaSuccess) eg = cudaStreamSynchronize(S->st);
+        }
+        for (size_t t = 0; t < fin.size(); ++t) {
+            const int s = fin[t];
             const double *o = S->h_out + (size_t)s * kInfo;
-            if (e == cudaSuccess && o[14] == 0.0) continue;
             std::shared_ptr<Request> r;
             {
                 std::lock_guard<std::mutex> lk(S->mu);
@@ -397,14 +445,14 @@ void worker_loop(admm_server *S)
             const BatchInst I = S->h_inst[s];
             if (e == cudaSuccess) {
                 std::memcpy(r->info, o, sizeof(double) * kInfo);
-                r->x.resize((size_t)I.m * I.q * I.n);
+                const size_t nx = (size_t)I.m * I.q * I.n;
+                r->x.resize(nx);
                 r->x1.resize(I.m);
-                admm_state so{};
-                so.x = r->x.data();
-                so.x1 = r->x1.data();
-                cudaError_t e2 = ensure_tmp(S, r->x.size());
-                if (e2 == cudaSuccess) e2 = store_get_state(S->store, I, &so, S->d_tmp, S->st);
-                r->status = e2 != cudaSuccess ? ADMM_ECUDA
+                if (eg == cudaSuccess) {
+                    std::memcpy(r->x.data(), S->h_gather + S->h_goff[t], sizeof(double) * nx);
+                    std::memcpy(r->x1.data(), S->h_gather + S->h_goff[t] + nx, sizeof(double) * I.m);
+                }
+                r->status = eg != cudaSuccess ? ADMM_ECUDA
                                               : (o[12] != 0.0 ? (admm_status)(int)o[12]
                                                               : (o[1] != 0.0 ? ADMM_OK : ADMM_ENOTCONVERGED));
             } else {
@@ -442,12 +490,12 @@ void admm_server_default_config(admm_server_config *c)
     std::memset(c, 0, sizeof *c);
     c->store_elements = 1LL << 27;
     c->max_active = 4096;
-    c->tick_iters = 50;
+    c->tick_iters = 10;
     c->max_m = 4;
     c->max_q = 20;
     c->batch.warps_per_cta = 8;
     c->batch.ctas_per_sm = 0;
-    c->batch.small_max_elements = 16384;
+    c->batch.small_max_elements = 0;
     c->batch.cluster_size = 1;
     c->batch.cluster_min_elements = 131072;
 }
@@ -474,10 +522,12 @@ admm_status admm_server_create(const admm_params *prm, const admm_server_config 
     const int maxa = cfg->max_active;
     auto bail = [&](admm_status s, const std::string &m) {
         S->store.free_all();
-        void *d[] = {S->d_inst, S->d_order, S->d_counts, S->d_q, S->d_shift, S->d_out, S->d_tmp, S->d_stepids, S->d_payload};
+        void *d[] = {S->d_inst,  S->d_order, S->d_counts,  S->d_q,    S->d_shift, S->d_out,
+                     S->d_tmp,   S->d_stepids, S->d_payload, S->d_gids, S->d_goff};
         for (void *p : d)
             if (p) cudaFree(p);
-        void *h[] = {S->h_inst, S->h_order, S->h_counts, S->h_shift, S->h_out, S->pinned, S->h_stepids, S->h_payload};
+        void *h[] = {S->h_inst,  S->h_order,   S->h_counts, S->h_shift, S->h_out,
+                     S->pinned,  S->h_stepids, S->h_payload, S->h_gids, S->h_goff, S->h_gather};
         for (void *p : h)
             if (p) cudaFreeHost(p);
         if (S->st) cudaStreamDestroy(S->st);
@@ -497,6 +547,10 @@ admm_status admm_server_create(const admm_params *prm, const admm_server_config 
     if (e == cudaSuccess) e = cudaMalloc(&S->d_counts, sizeof(int) * 4); // nX, nL, nS, tick work (float)
     if (e == cudaSuccess) e = cudaMalloc(&S->d_q, sizeof(int) * 3);
     if (e == cudaSuccess) e = cudaMalloc(&S->d_shift, sizeof(int) * maxa);
+    if (e == cudaSuccess) e = cudaMalloc(&S->d_gids, sizeof(int) * maxa);
+    if (e == cudaSuccess) e = cudaMalloc(&S->d_goff, sizeof(int64_t) * maxa);
+    if (e == cudaSuccess) e = cudaMallocHost(&S->h_gids, sizeof(int) * maxa);
+    if (e == cudaSuccess) e = cudaMallocHost(&S->h_goff, sizeof(int64_t) * maxa);
     if (e == cudaSuccess) e = cudaMalloc(&S->d_out, sizeof(double) * kInfo * maxa);
     if (e == cudaSuccess) e = cudaMallocHost(&S->h_inst, sizeof(BatchInst) * maxa);
     if (e == cudaSuccess) e = cudaMallocHost(&S->h_order, sizeof(int) * 3 * maxa);
@@ -509,8 +563,8 @@ admm_status admm_server_create(const admm_params *prm, const admm_server_config 
     if (e == cudaSuccess) e = cudaMalloc(&S->d_payload, sizeof(float) * (size_t)maxa * S->payload_stride);
     if (e == cudaSuccess) e = cudaMallocHost(&S->h_payload, sizeof(float) * (size_t)maxa * S->payload_stride);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->st, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaEventCreate(&S->ev[0]);
-    if (e == cudaSuccess) e = cudaEventCreate(&S->ev[1]);
+    for (cudaEvent_t &ev : S->ev)
+        if (e == cudaSuccess) e = cudaEventCreate(&ev);
     if (e == cudaSuccess) e = cudaMemset(S->d_out, 0, sizeof(double) * kInfo * maxa);
     if (e != cudaSuccess)
         return bail(e == cudaErrorMemoryAllocation ? ADMM_ENOMEM : ADMM_ECUDA, cudaGetErrorString(e));
@@ -699,12 +753,13 @@ admm_status admm_server_stats(admm_server *S, double *stats, int32_t count)
 {
     if (!S || !stats || count < 1) return sfail(ADMM_EINVAL, "bad argument");
     std::lock_guard<std::mutex> lk(S->mu);
-    double v[8] = {S->stats[0], S->stats[1], S->stats[2], 0.0, (double)S->pending.size(), 0.0, 0.0, S->stats[3]};
+    double v[9] = {S->stats[0], S->stats[1], S->stats[2], 0.0, (double)S->pending.size(), 0.0, 0.0, S->stats[3],
+                   S->stats[4]};
     for (auto &p : S->active)
         if (p) v[3] += 1;
     v[5] = (double)S->store.ae.free_total() / (double)std::max<int64_t>(1, S->store.ae.capacity());
     v[6] = (double)S->sessions.size();
-    for (int t = 0; t < count && t < 8; ++t) stats[t] = v[t];
+    for (int t = 0; t < count && t < 9; ++t) stats[t] = v[t];
     return ADMM_OK;
 }
 
@@ -719,10 +774,12 @@ admm_status admm_server_destroy(admm_server *S)
     if (S->worker.joinable()) S->worker.join();
     if (S->exec) cudaGraphExecDestroy(S->exec);
     S->store.free_all();
-    void *d[] = {S->d_inst, S->d_order, S->d_counts, S->d_q, S->d_shift, S->d_out, S->d_tmp, S->d_stepids, S->d_payload};
+    void *d[] = {S->d_inst,  S->d_order, S->d_counts,  S->d_q,    S->d_shift, S->d_out,
+                     S->d_tmp,   S->d_stepids, S->d_payload, S->d_gids, S->d_goff};
     for (void *p : d)
         if (p) cudaFree(p);
-    void *h[] = {S->h_inst, S->h_order, S->h_counts, S->h_shift, S->h_out, S->pinned, S->h_stepids, S->h_payload};
+    void *h[] = {S->h_inst,  S->h_order,   S->h_counts, S->h_shift, S->h_out,
+                     S->pinned,  S->h_stepids, S->h_payload, S->h_gids, S->h_goff, S->h_gather};
     for (void *p : h)
         if (p) cudaFreeHost(p);
     if (S->st) cudaStreamDestroy(S->st);
