@@ -421,6 +421,7 @@ def run_serving(args):
                 "iters": {"mean": float(np.mean(it_all)), "max": int(np.max(it_all))} if it_all else None,
                 "ok_frac": float(np.mean(np.array(st_all) == 0)) if st_all else None,
                 "gpu_busy_frac": busy_window / window, "gpu_shift_frac": shift_window / window,
+                "mean_active": (st1["instance_ticks"] - st0["instance_ticks"]) / max(1.0, st1["ticks"] - st0["ticks"]),
                 "server_stats": stats, "gpu_launches": int(stats["ticks"]), "clocks": clk.summary()}
         print(json.dumps(line))
     return 0

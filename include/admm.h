@@ -310,9 +310,10 @@ admm_status admm_server_poll(admm_server *s, int64_t ticket, int32_t wait_ms, ad
  * how many.  Drained tickets are forgotten (their x is not kept). */
 admm_status admm_server_drain(admm_server *s, int32_t max, int64_t *tickets, double *latency_s, int32_t *iters,
                               int32_t *status, int32_t *count);
-/* stats[0..8]: ticks, admitted, finished, active, queued, free fraction of
+/* stats[0..9]: ticks, admitted, finished, active, queued, free fraction of
  * the store, sessions, seconds the GPU spent running ticks, seconds it spent
- * moving step requests' instances one step forward. */
+ * moving step requests' instances one step forward, and the sum over ticks
+ * of the instances each tick ran. */
 admm_status admm_server_stats(admm_server *s, double *stats, int32_t count);
 /* Stops the worker (in-flight requests are dropped) and frees everything. */
 admm_status admm_server_destroy(admm_server *s);

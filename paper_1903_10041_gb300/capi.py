@@ -590,10 +590,10 @@ class Server:
         return t[:k], lat[:k], it[:k], st[:k]
 
     def stats(self) -> dict:
-        buf = (C.c_double * 9)()
-        _check(_lib.admm_server_stats(self.h, buf, 9))
+        buf = (C.c_double * 10)()
+        _check(_lib.admm_server_stats(self.h, buf, 10))
         keys = ("ticks", "admitted", "finished", "active", "queued", "store_free_frac", "sessions", "gpu_busy_s",
-                "gpu_shift_s")
+                "gpu_shift_s", "instance_ticks")
         return {k: buf[t] for t, k in enumerate(keys)}
 
     def close(self):

@@ -38,6 +38,9 @@ struct BatchArgs {
     int slice_doubles;        // shared memory per warp-team slice
     int iter_budget;          // > 0: stop every instance after this many more iterations
     const float *tick_work;   // if non-null (with iter_budget > 0): time-balanced budget, below
+    const int *tick_rounds;   // if non-null and > 1: CTA and warp teams take each instance up to this many
+                              // times per launch, in round-robin order (serving ticks, below)
+    int *lock;                // per instance: 1 while a team runs it (round-robin launches)
     double r_tol, s_tol, tau;
     int max_iter, check_every, xmin_mode, sweep, adapt;
 };
@@ -54,6 +57,14 @@ __host__ __device__ inline float team_iter_cost(int n, int m, int q, int team_th
     return (float)((double)n * m * q / team_threads) + 4.0f; // + per-iteration fixed work
 }
 
+// Round-robin ticks: when a tick has more instances than teams, one pass
+// per instance leaves teams idle in the last, partial round.  With
+// *tick_rounds = R > 1 the queue holds every instance R times (instance
+// order repeated), each pass running a slice of the budget, so teams stay
+// busy to within one slice.  A team that draws an instance another team is
+// running skips it; state moves between SMs through L2 (the element update
+// reads mutable state with L1-bypassing loads).
+//
 // Kernel variant (register arrays for M sources) of a batch or server: 4 for
 // every m <= 4, else 8.  It must not depend on which instances share a
 // launch, so that an instance gives the same bits alone and in any mix.

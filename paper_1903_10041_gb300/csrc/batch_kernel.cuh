@@ -149,13 +149,13 @@ template <int KIND, int NW, int M> __device__ void solve_team(const BatchArgs &a
 
     double *gscal = a.scal + I.off_scal;
     double *out = a.out + (size_t)id * kInfo;
-    const bool skip = out[14] != 0.0;
+    const bool skip = __ldcg(out + 14) != 0.0;
     sync_team();
     if (skip) return; // every member read the same flag
-    for (int t = tid; t < scal_size(m, q); t += NTL) scal[t] = gscal[t];
+    for (int t = tid; t < scal_size(m, q); t += NTL) scal[t] = __ldcg(gscal + t);
     sync_local();
     for (int pr = tid; pr < mq; pr += NTL) uoff[pr] = (float)(zeta[pr] + lam[pr]);
-    const int it0 = (int)out[0];
+    const int it0 = (int)__ldcg(out);
     sync_local();
 
     const ElemF32 ea = {a.f2 + I.off_e, a.f1 + I.off_e, a.g2 + I.off_e, a.g1 + I.off_e, a.g0 + I.off_e,
@@ -165,8 +165,9 @@ template <int KIND, int NW, int M> __device__ void solve_team(const BatchArgs &a
     const double *sumg0 = a.sumg0 + I.off_pair;
     unsigned esc = 0;
     bool conv = false;
-    double res[7] = {out[4], out[5], out[6], out[7], out[8], out[9], out[10]};
-    double r_last = out[2], s_last = out[3];
+    double res[7];
+    for (int t = 0; t < 7; ++t) res[t] = __ldcg(out + 4 + t);
+    double r_last = __ldcg(out + 2), s_last = __ldcg(out + 3);
     int it = it0;
     int budget = a.iter_budget;
     if (budget > 0 && a.tick_work)
@@ -372,7 +373,7 @@ template <int KIND, int NW, int M> __device__ void solve_team(const BatchArgs &a
             for (int t = 0; t < 7; ++t) out[4 + t] = res[t];
             if (finished) out[11] = obj / (double)q;
             out[12] = 0.0;
-            out[13] += es;
+            out[13] = __ldcg(out + 13) + es;
             out[14] = finished ? 1.0 : 0.0;
         }
     }
@@ -398,24 +399,57 @@ template <int NW, int M> __global__ void __launch_bounds__(NW * 32, 16 / NW) bat
             solve_team<TEAM_CLUSTER, NW, M>(a, a.orderX[item], smem);
         }
     }
-    // Large instances: the whole CTA is one team.
+    const int R = a.tick_rounds ? max(1, *a.tick_rounds) : 1;
+    // Large instances: the whole CTA is one team.  id -1: the instance is
+    // being run by another team (round-robin launches only).
     for (;;) {
-        if (threadIdx.x == 0) s_item = atomicAdd(a.qL, 1);
+        if (threadIdx.x == 0) {
+            const int item = atomicAdd(a.qL, 1);
+            int id = item < nL * R ? a.orderL[item % max(nL, 1)] : -2;
+            if (id >= 0 && R > 1) {
+                if (atomicCAS(a.lock + id, 0, 1) != 0) id = -1;
+                else __threadfence();
+            }
+            s_item = id;
+        }
         __syncthreads();
-        const int item = s_item;
+        const int id = s_item;
         __syncthreads();
-        if (item >= nL) break;
-        solve_team<TEAM_CTA, NW, M>(a, a.orderL[item], smem);
+        if (id == -2) break;
+        if (id < 0) continue;
+        solve_team<TEAM_CTA, NW, M>(a, id, smem);
+        if (R > 1) {
+            __syncthreads(); // every thread's state writes precede the release
+            if (threadIdx.x == 0) {
+                __threadfence();
+                atomicExch(a.lock + id, 0);
+            }
+        }
     }
     // Small instances: each warp is a team with its own slice.
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     double *slice = smem + (size_t)w * a.slice_doubles;
     for (;;) {
-        int item = 0;
-        if (lane == 0) item = atomicAdd(a.qS, 1);
-        item = __shfl_sync(0xffffffffu, item, 0);
-        if (item >= nS) break;
-        solve_team<TEAM_WARP, NW, M>(a, a.orderS[item], slice);
+        int id = 0;
+        if (lane == 0) {
+            const int item = atomicAdd(a.qS, 1);
+            id = item < nS * R ? a.orderS[item % max(nS, 1)] : -2;
+            if (id >= 0 && R > 1) {
+                if (atomicCAS(a.lock + id, 0, 1) != 0) id = -1;
+                else __threadfence();
+            }
+        }
+        id = __shfl_sync(0xffffffffu, id, 0);
+        if (id == -2) break;
+        if (id < 0) continue;
+        solve_team<TEAM_WARP, NW, M>(a, id, slice);
+        if (R > 1) {
+            __syncwarp();
+            if (lane == 0) {
+                __threadfence();
+                atomicExch(a.lock + id, 0);
+            }
+        }
     }
 }
 

@@ -128,7 +128,9 @@ __device__ __forceinline__ void ff2_acc(float2 &hi, float2 &lo, float2 a, float2
     lo = add2(lo, add2(e, a_lo));
 }
 
-__device__ __forceinline__ float2 ld2(const float *p) { return *(const float2 *)p; }
+// Mutable state (x, s, mu) bypasses L1: in round-robin launches an instance
+// can move to another SM, whose L1 may hold lines of an earlier pass.
+__device__ __forceinline__ float2 ld2(const float *p) { return __ldcg((const float2 *)p); }
 __device__ __forceinline__ float2 ldg2(const float *p) { return __ldg((const float2 *)p); }
 __device__ __forceinline__ void st2(float *p, float2 v) { *(float2 *)p = v; }
 

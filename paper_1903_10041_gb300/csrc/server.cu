@@ -80,6 +80,7 @@ struct admm_server {
     double *d_out = nullptr, *h_out = nullptr, *d_tmp = nullptr;
     size_t tmp_n = 0;
     int *d_gids = nullptr, *h_gids = nullptr;       // finished instances of a tick
+    int *d_lock = nullptr;                          // per slot: a team runs it (round-robin ticks)
     int64_t *d_goff = nullptr, *h_goff = nullptr;   // their offsets in the gathered results
     double *h_gather = nullptr;                     // gathered x and x_1 (pinned)
     size_t gather_n = 0;
@@ -95,7 +96,8 @@ struct admm_server {
     std::map<int64_t, Session> sessions;
     int64_t next_ticket = 1;
     bool stop = false;
-    double stats[8] = {}; // ticks, admitted, finished, GPU seconds in ticks, GPU seconds in step shifts
+    double stats[8] = {}; // ticks, admitted, finished, GPU seconds in ticks, GPU seconds in step shifts,
+                          // sum over ticks of the instances in the tick
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     std::string worker_error;
     std::thread worker;
@@ -388,13 +390,25 @@ void worker_loop(admm_server *S)
                 const int threads = t < nX ? S->cluster * wc : (t < nX + nL ? wc : 32);
                 cmax = std::max(cmax, team_iter_cost(S->h_inst[s].n, S->h_inst[s].m, S->h_inst[s].q, threads));
             }
-            const float tw = (float)S->cfg.tick_iters * cmax;
+            // Round-robin slices when the CTA teams are outnumbered: the tick
+            // keeps the length of ceil(A / teams) passes of the costliest
+            // instance, cut into R slices per instance so no team idles in a
+            // partial last round.
+            int rounds = 1;
+            float tw = (float)S->cfg.tick_iters * cmax;
+            const int teams = S->grid;
+            if (nX == 0 && nS == 0 && nL > teams) {
+                rounds = 4;
+                const int passes = (nL + teams - 1) / teams;
+                tw = (float)((double)tw * passes * teams / ((double)nL * rounds));
+            }
             std::memcpy(&S->h_counts[3], &tw, sizeof(float));
+            S->h_counts[4] = rounds;
         }
         cudaMemcpyAsync(S->d_order, S->h_order, sizeof(int) * nX, cudaMemcpyHostToDevice, S->st);
         cudaMemcpyAsync(S->d_order + maxa, S->h_order + maxa, sizeof(int) * nL, cudaMemcpyHostToDevice, S->st);
         cudaMemcpyAsync(S->d_order + 2 * maxa, S->h_order + 2 * maxa, sizeof(int) * nS, cudaMemcpyHostToDevice, S->st);
-        cudaMemcpyAsync(S->d_counts, S->h_counts, 4 * sizeof(int), cudaMemcpyHostToDevice, S->st);
+        cudaMemcpyAsync(S->d_counts, S->h_counts, 5 * sizeof(int), cudaMemcpyHostToDevice, S->st);
         cudaEventRecord(S->ev[0], S->st);
         cudaError_t e = cudaGraphLaunch(S->exec, S->st);
         cudaEventRecord(S->ev[1], S->st);
@@ -407,6 +421,7 @@ void worker_loop(admm_server *S)
         if (e == cudaSuccess && shift_timed && cudaEventElapsedTime(&tick_ms, S->ev[2], S->ev[3]) == cudaSuccess)
             S->stats[4] += 1e-3 * tick_ms;
         S->stats[0] += 1;
+        S->stats[5] += (double)ids.size();
         // retire finished instances: their x and x_1 come back in one gather
         // kernel and one copy
         std::vector<int> fin;
@@ -523,7 +538,7 @@ admm_status admm_server_create(const admm_params *prm, const admm_server_config 
     auto bail = [&](admm_status s, const std::string &m) {
         S->store.free_all();
         void *d[] = {S->d_inst,  S->d_order, S->d_counts,  S->d_q,    S->d_shift, S->d_out,
-                     S->d_tmp,   S->d_stepids, S->d_payload, S->d_gids, S->d_goff};
+                     S->d_tmp,   S->d_stepids, S->d_payload, S->d_gids, S->d_goff, S->d_lock};
         for (void *p : d)
             if (p) cudaFree(p);
         void *h[] = {S->h_inst,  S->h_order,   S->h_counts, S->h_shift, S->h_out,
@@ -544,7 +559,7 @@ admm_status admm_server_create(const admm_params *prm, const admm_server_config 
                               (int64_t)maxa * scal_size(cfg->max_m, cfg->max_q), (int64_t)maxa * cfg->max_m);
     if (e == cudaSuccess) e = cudaMalloc(&S->d_inst, sizeof(BatchInst) * maxa);
     if (e == cudaSuccess) e = cudaMalloc(&S->d_order, sizeof(int) * 3 * maxa);
-    if (e == cudaSuccess) e = cudaMalloc(&S->d_counts, sizeof(int) * 4); // nX, nL, nS, tick work (float)
+    if (e == cudaSuccess) e = cudaMalloc(&S->d_counts, sizeof(int) * 5); // nX, nL, nS, tick work (float), rounds
     if (e == cudaSuccess) e = cudaMalloc(&S->d_q, sizeof(int) * 3);
     if (e == cudaSuccess) e = cudaMalloc(&S->d_shift, sizeof(int) * maxa);
     if (e == cudaSuccess) e = cudaMalloc(&S->d_gids, sizeof(int) * maxa);
@@ -554,7 +569,9 @@ admm_status admm_server_create(const admm_params *prm, const admm_server_config 
     if (e == cudaSuccess) e = cudaMalloc(&S->d_out, sizeof(double) * kInfo * maxa);
     if (e == cudaSuccess) e = cudaMallocHost(&S->h_inst, sizeof(BatchInst) * maxa);
     if (e == cudaSuccess) e = cudaMallocHost(&S->h_order, sizeof(int) * 3 * maxa);
-    if (e == cudaSuccess) e = cudaMallocHost(&S->h_counts, sizeof(int) * 4);
+    if (e == cudaSuccess) e = cudaMallocHost(&S->h_counts, sizeof(int) * 5);
+    if (e == cudaSuccess) e = cudaMalloc(&S->d_lock, sizeof(int) * maxa);
+    if (e == cudaSuccess) e = cudaMemset(S->d_lock, 0, sizeof(int) * maxa);
     if (e == cudaSuccess) e = cudaMallocHost(&S->h_shift, sizeof(int) * maxa);
     if (e == cudaSuccess) e = cudaMallocHost(&S->h_out, sizeof(double) * kInfo * maxa);
     S->payload_stride = (6 * cfg->max_m * cfg->max_q + 2 * cfg->max_m + cfg->max_q + 3) / 4 * 4;
@@ -602,6 +619,8 @@ admm_status admm_server_create(const admm_params *prm, const admm_server_config 
     a.slice_doubles = (int)S->slice;
     a.iter_budget = cfg->tick_iters;
     a.tick_work = (const float *)(S->d_counts + 3);
+    a.tick_rounds = S->d_counts + 4;
+    a.lock = S->d_lock;
     a.r_tol = prm->r_tol;
     a.s_tol = prm->s_tol;
     a.tau = prm->tau;
@@ -753,13 +772,13 @@ admm_status admm_server_stats(admm_server *S, double *stats, int32_t count)
 {
     if (!S || !stats || count < 1) return sfail(ADMM_EINVAL, "bad argument");
     std::lock_guard<std::mutex> lk(S->mu);
-    double v[9] = {S->stats[0], S->stats[1], S->stats[2], 0.0, (double)S->pending.size(), 0.0, 0.0, S->stats[3],
-                   S->stats[4]};
+    double v[10] = {S->stats[0], S->stats[1], S->stats[2], 0.0, (double)S->pending.size(), 0.0, 0.0, S->stats[3],
+                    S->stats[4], S->stats[5]};
     for (auto &p : S->active)
         if (p) v[3] += 1;
     v[5] = (double)S->store.ae.free_total() / (double)std::max<int64_t>(1, S->store.ae.capacity());
     v[6] = (double)S->sessions.size();
-    for (int t = 0; t < count && t < 9; ++t) stats[t] = v[t];
+    for (int t = 0; t < count && t < 10; ++t) stats[t] = v[t];
     return ADMM_OK;
 }
 
@@ -775,7 +794,7 @@ admm_status admm_server_destroy(admm_server *S)
     if (S->exec) cudaGraphExecDestroy(S->exec);
     S->store.free_all();
     void *d[] = {S->d_inst,  S->d_order, S->d_counts,  S->d_q,    S->d_shift, S->d_out,
-                     S->d_tmp,   S->d_stepids, S->d_payload, S->d_gids, S->d_goff};
+                     S->d_tmp,   S->d_stepids, S->d_payload, S->d_gids, S->d_goff, S->d_lock};
     for (void *p : d)
         if (p) cudaFree(p);
     void *h[] = {S->h_inst,  S->h_order,   S->h_counts, S->h_shift, S->h_out,

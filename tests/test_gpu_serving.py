@@ -128,3 +128,19 @@ def test_step_request_without_a_resident_session_fails_cleanly(capi):
             if res is not None:
                 break
     assert res is not None and res["status"] == capi.ADMM_EINVAL
+
+
+def test_round_robin_ticks_give_the_same_bits(capi):
+    """More instances than CTA teams: each tick takes every instance several
+    times in round-robin slices, moving its state between SMs.  The results
+    equal those of the same requests submitted one at a time."""
+    probs = [W.random_problem(40 + (t % 7) * 13, 2 + t % 3, 1 + t % 4, seed=7000 + t) for t in range(700)]
+    with capi.Server(PAR, tick_iters=10, small_max_elements=0) as S:
+        alone = [wait_all(S, [S.submit(P)])[0] for P in probs[:6]]
+        mix = wait_all(S, [S.submit(P) for P in probs], timeout_s=300.0)
+        stats = S.stats()
+    assert stats["instance_ticks"] / stats["ticks"] > 1.0
+    for t in range(6):
+        assert alone[t]["converged"] and mix[t]["converged"], t
+        assert alone[t]["iters"] == mix[t]["iters"], t
+        assert np.array_equal(alone[t]["x"], mix[t]["x"]), t
