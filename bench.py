@@ -51,6 +51,40 @@ def workload(cfg: int, precision: str):
     return P, par
 
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the solve
+# kernel per iteration, from one ncu capture of each workload (profiles/).
+# It is reported only while the kernel sources hash to the captured build.
+NCU_TRAFFIC = {
+    ("phev n=1000 q=50", "fp64"): {"bytes_per_iter": (7.058688e6 + 0.114432e6) / 3330, "src": "db0d2337e5af9951",
+                                   "capture": "profiles/single_fp64_kernel_config1.md (whole 3330-iteration solve)"},
+    ("config2: plain n=1e5 m=4 q=20", "mixed"): {"bytes_per_iter": (4.302833e9 + 1.365726e9) / 20,
+                                                 "src": "db0d2337e5af9951",
+                                                 "capture": "profiles/single_mixed_kernel_config2.md (20 iterations)"},
+}
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+    import glob
+    files = sorted(glob.glob(os.path.join(ROOT, "paper_1903_10041_gb300", "csrc", "*.cu")) +
+                   glob.glob(os.path.join(ROOT, "paper_1903_10041_gb300", "csrc", "*.cuh")) +
+                   glob.glob(os.path.join(ROOT, "paper_1903_10041_gb300", "csrc", "*.h")) +
+                   glob.glob(os.path.join(ROOT, "include", "*.h")))
+    h = hashlib.sha256()
+    for f in files:
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_per_launch(P, prec: str, iters: int):
+    t = NCU_TRAFFIC.get((P.name, prec))
+    if t is None or t["src"] != kernel_source_hash():
+        return None
+    return t["bytes_per_iter"] * iters
+
+
 def bytes_per_iteration(P, prec: str) -> int:
     """Algorithmic HBM bytes of one iteration (each streamed array once):
     f2, f1, g2, g1 read and x read+write (6 per element), the bounds
@@ -517,7 +551,7 @@ def main():
         flops = iters * (FLOPS_PER_ELEMENT * P.elements + FLOPS_PER_COLUMN * cols)
         achieved = flops / per_launch_s / 1e12
         roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                    "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic_per_launch(P, "fp64", iters),
                     "peak_source": "FP64: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz (derived; measured 1.90 DFMA/clk/SM)",
                     "hbm_achieved_gbs": iters * bytes_per_iteration(P, "fp64") / per_launch_s / 1e9}
     else:
@@ -525,7 +559,7 @@ def main():
             os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"hbm_gbs": 6800.0}
         gbs = iters * bytes_per_iteration(P, args.precision) / per_launch_s / 1e9
         roofline = {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                    "frac": gbs / peaks["hbm_gbs"], "traffic": None}
+                    "frac": gbs / peaks["hbm_gbs"], "traffic": traffic_per_launch(P, args.precision, iters)}
 
     # ---- end to end through the C ABI from pinned host buffers ------------
     e2e = None
