@@ -142,27 +142,36 @@ __device__ __forceinline__ void column64(const SingleArgs &a, const Sm &sm, int 
             const size_t e = ((size_t)i * q + j) * ld + k;
             const double a2 = F2[e], a1 = F1[e], b2 = G2[e], b1 = G1[e];
             const int pr = i * q + j;
-            const double gq_old = b2 * xt[i] * xt[i] + b1 * xt[i];
             const double g0 = cold ? G0[e] : 0.0;
-            // u = theta - beta_0 (theta = z + lambda)
-            const double u = cold ? -g0 : gq_old + (sm.zeta[pr] + sm.lam[pr]);
             double others = 0.0;
 #pragma unroll
             for (int l = 0; l < M; ++l)
                 if (l < m && l != i) others += (a.sweep == ADMM_JACOBI) ? xt[l] : xs[l];
             const double phi = ((st - others) + yv) + mu;
-            const double A = 0.5 * rho1 * b2 * b2;
-            const double B = rho1 * b2 * b1;
-            double C = a2 * iq + 0.5 * rho1 * (b1 * b1 - 2.0 * b2 * u) + 0.5 * rho3;
-            double D = a1 * iq - rho1 * b1 * u - rho3 * phi;
+            double C = a2 * iq + 0.5 * rho3, D = a1 * iq - rho3 * phi;
             if (k == 0) {
                 C += 0.5 * rho4;
                 D -= rho4 * (sm.x1[i] + sm.nu[pr]);
             }
-            const double xn = quartic_min64(A, B, C, D, LO[(size_t)i * ld + k], HI[(size_t)i * ld + k],
-                                            a.xmin_mode);
+            const double lo = LO[(size_t)i * ld + k], hi = HI[(size_t)i * ld + k];
+            double gq_old = 0.0, xn, gq = 0.0;
+            // b2 = b1 = 0 (either sign of zero), tested on the integer pipes
+            if (((__double_as_longlong(b2) | __double_as_longlong(b1)) << 1) == 0) {
+                // no loss on this element (g = beta_0): the terms in beta_2, beta_1
+                // vanish and step (a) is the quadratic case of Algorithm 1
+                xn = clampd(-D * rcp64(2.0 * C), lo, hi);
+            } else {
+                gq_old = b2 * xt[i] * xt[i] + b1 * xt[i];
+                // u = theta - beta_0 (theta = z + lambda)
+                const double u = cold ? -g0 : gq_old + (sm.zeta[pr] + sm.lam[pr]);
+                const double A = 0.5 * rho1 * b2 * b2;
+                const double B = rho1 * b2 * b1;
+                C += 0.5 * rho1 * (b1 * b1 - 2.0 * b2 * u);
+                D -= rho1 * b1 * u;
+                xn = quartic_min64(A, B, C, D, lo, hi, a.xmin_mode);
+                gq = b2 * xn * xn + b1 * xn;
+            }
             xs[i] = xn;
-            const double gq = b2 * xn * xn + b1 * xn;
             gs[i] += gq;
             if (check) {
                 // z_k - z~_k = D_k + (lambda_new - lambda - zeta); D_k = g(x) - g(x~),
