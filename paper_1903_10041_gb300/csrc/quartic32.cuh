@@ -169,6 +169,59 @@ __device__ __forceinline__ float quartic_min32(float A, float B, float C, float 
 }
 
 // ---------------------------------------------------------------------------
+// FP64 minimiser seeded in FP32.  FP64 throughput is 1/64 of FP32 on this
+// GPU, so for the Cardano branch the root is found in FP32 (closed form +
+// Newton step, as in quartic_min32) and then refined by two FP64 Newton steps
+// on the FP64 derivative 4A x^3 + 3B x^2 + 2C x + D (step divisor from an
+// FP32 reciprocal: each step multiplies the relative error by about the
+// FP32 unit roundoff, so two steps reach FP64 rounding).  The FP32 branch
+// test is certified against the FP64 coefficients: the error bound of
+// quartic_min32 is doubled for the rounding of A, B, C, D to FP32.  Anything
+// else (quadratic, trig or uncertain branch, FP32 range, a step that did not
+// settle) takes the FP64 closed form of quartic_min64.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool cardano_seed32(double A64, double B64, double C64, double D64, float &root)
+{
+    const float A = (float)A64, B = (float)B64, C = (float)C64, D = (float)D64;
+    if (!(A > 1.0e-30f && A < 1.0e30f)) return false;
+    const float inv = rcp_fast(A);
+    const float b = 0.75f * B * inv, c = 0.5f * C * inv, d = 0.25f * D * inv;
+    const float b3 = b * (1.0f / 3.0f);
+    const float Q = c * (1.0f / 3.0f) - b3 * b3;
+    const float R = b3 * (0.5f * c) - b3 * b3 * b3 - 0.5f * d;
+    const float Q3 = Q * Q * Q, R2 = R * R;
+    const float Dl = Q3 + R2;
+    const float mQ = fabsf(c) * (1.0f / 3.0f) + b3 * b3;
+    const float mR = fabsf(b3 * 0.5f * c) + fabsf(b3 * b3 * b3) + 0.5f * fabsf(d);
+    const float bound = 1.2e-7f * (96.0f * Q * Q * mQ + 64.0f * fabsf(Q3) + 96.0f * fabsf(R) * mR + 64.0f * R2);
+    if (!(Dl > bound)) return false;
+    const float sq = sqrt_fast(Dl);
+    const float S = cbrt_fast(R >= 0.0f ? R + sq : R - sq);
+    const float T = S != 0.0f ? -Q * rcp_fast(S) : 0.0f;
+    root = newton_polish32(A, B, C, D, S + T - b3);
+    return isfinite(root);
+}
+
+__device__ __forceinline__ double quartic_min64_seeded(double A, double B, double C, double D, double lo, double hi,
+                                                       int paper_mode)
+{
+    float r32;
+    if (A != 0.0 && cardano_seed32(A, B, C, D, r32)) {
+        const double A4 = 4.0 * A, B3 = 3.0 * B, C2 = 2.0 * C, A12 = 12.0 * A, B6 = 6.0 * B;
+        double x = (double)r32, step = 0.0;
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            const double p = ((A4 * x + B3) * x + C2) * x + D;
+            const double pp = (A12 * x + B6) * x + C2;
+            step = p * (double)rcp_approx_f32((float)pp);
+            x -= step;
+        }
+        if (fabs(step) <= 1.0e-12 * (fabs(x) + 1.0)) return clampd(x, lo, hi);
+    }
+    return quartic_min64(A, B, C, D, lo, hi, paper_mode);
+}
+
+// ---------------------------------------------------------------------------
 // Packed pair variant: the two columns of a vector in one float2, on the
 // paired FP32 instructions (FADD2 / FMUL2 / FFMA2: two lanes per issue, the
 // same rounding per lane as the scalar operations).  The common cases run

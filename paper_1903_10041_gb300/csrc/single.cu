@@ -168,7 +168,7 @@ __device__ __forceinline__ void column64(const SingleArgs &a, const Sm &sm, int 
                 const double B = rho1 * b2 * b1;
                 C += 0.5 * rho1 * (b1 * b1 - 2.0 * b2 * u);
                 D -= rho1 * b1 * u;
-                xn = quartic_min64(A, B, C, D, lo, hi, a.xmin_mode);
+                xn = quartic_min64_seeded(A, B, C, D, lo, hi, a.xmin_mode);
                 gq = b2 * xn * xn + b1 * xn;
             }
             xs[i] = xn;
