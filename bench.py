@@ -55,10 +55,10 @@ def workload(cfg: int, precision: str):
 # kernel per iteration, from one ncu capture of each workload (profiles/).
 # It is reported only while the kernel sources hash to the captured build.
 NCU_TRAFFIC = {
-    ("phev n=1000 q=50", "fp64"): {"bytes_per_iter": (7.096576e6 + 0.050432e6) / 3330, "src": "4ca47b2d133155ad",
+    ("phev n=1000 q=50", "fp64"): {"bytes_per_iter": (7.096576e6 + 0.050432e6) / 3330, "src": "094700d60b14e3d8",
                                    "capture": "profiles/single_fp64_kernel_config1.md (whole 3330-iteration solve)"},
     ("config2: plain n=1e5 m=4 q=20", "mixed"): {"bytes_per_iter": (4.302514e9 + 1.364925e9) / 20,
-                                                 "src": "4ca47b2d133155ad",
+                                                 "src": "094700d60b14e3d8",
                                                  "capture": "profiles/single_mixed_kernel_config2.md (20 iterations)"},
 }
 

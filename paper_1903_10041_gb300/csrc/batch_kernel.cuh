@@ -1,32 +1,34 @@
 // Batched solve: thousands of independent instances of uneven n, m, q in one
 // persistent launch (mixed precision).
 //
-// Each instance is solved by one team of threads that runs the whole ADMM
-// loop of App. A for it with team-local synchronisation only: a whole CTA
-// for large instances, or a single warp for small ones (so a CTA of W warps
-// holds W small instances at once).  Teams take work from two global
-// queues of instance ids, large ones first, each sorted by decreasing
-// estimated work (longest-processing-time order), so a CTA that finishes
-// early takes the next instance.  Each instance stops on its own stop test.
+// Each instance is solved by one team of threads that runs the ADMM loop of
+// App. A for it with team-local synchronisation only: a thread-block
+// cluster, a whole CTA, or a single warp (so a CTA of W warps holds W small
+// instances at once), by size thresholds.  Teams take work from three
+// global queues of instance ids (cluster, CTA, warp teams), each sorted by
+// decreasing estimated work (longest-processing-time order), so a team that
+// finishes early takes the next instance.  Each instance stops on its own
+// stop test.
 //
-// The largest instances are solved by a thread-block cluster (2-8 CTAs on
-// neighbouring SMs): each CTA reduces its part of every row into records in
-// its own shared memory, one hardware cluster barrier per iteration follows,
-// and every CTA reads all CTAs' records through distributed shared memory in
-// rank order and runs the scalar steps redundantly.
+// A cluster team (2-8 CTAs on neighbouring SMs): each CTA reduces its part
+// of every row into records in its own shared memory, one hardware cluster
+// barrier per iteration follows, and every CTA reads all CTAs' records
+// through distributed shared memory in rank order and runs the scalar steps
+// redundantly.
 //
-// Per iteration a team sweeps the rows j = 1..q of its instance; within a
-// row its threads take consecutive column vectors (coalesced) and run the
-// element update of mixed_elem.cuh; the row's sums over k are reduced
-// across the team in a fixed order into a record in shared memory, and the
-// per-(i, j) scalar steps, residuals and stop test follow on the team.  The
-// arithmetic and its order depend only on the instance's own shape and its
-// team kind (fixed by the instance's size), so an instance gives the same
-// bits alone and in any mix.
+// Per iteration a team splits the rows j = 1..q of its instance into
+// warp-level (row, segment) work items; within an item a warp takes
+// consecutive column pairs (coalesced) and runs the element update of
+// mixed_elem.cuh; each item is reduced by shuffles into a record in shared
+// memory, one team barrier follows, and the per-(i, j) scalar steps,
+// residuals and stop test run on the team.  The arithmetic and its order
+// depend only on the instance's own shape and its team kind (fixed by the
+// instance's size), so an instance gives the same bits alone and in any mix.
 //
 // An iteration budget lets a launch stop every instance after a given
-// number of iterations with its state saved; the serving loop uses it to
-// run the batch in ticks and admit new instances between ticks.
+// number of iterations with its state saved; the serving loop uses it (with
+// time-balanced budgets and round-robin slices, batch.h) to run the batch in
+// ticks and admit new instances between ticks.
 #pragma once
 #include <cooperative_groups.h>
 

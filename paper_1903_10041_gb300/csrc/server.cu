@@ -5,11 +5,13 @@
 // worker thread runs ticks: it admits queued requests in arrival order
 // while the device store has room and a slot is free (memory-based
 // admission; idle sessions are evicted least-recently-used first when the
-// store is full), replays a CUDA graph that runs `tick_iters` iterations of
-// the batched kernel on every active instance, and retires the instances
-// that finished (converged or out of iterations), copying their results to
-// the host.  Requests that arrive while others are on the GPU join at the
-// next tick.  A session keeps its instance's state resident on the device
+// store is full), replays a CUDA graph that runs the batched kernel on every
+// active instance (the costliest one for `tick_iters` iterations, the others
+// for as many as fit in the same time; in round-robin slices when instances
+// outnumber the CTA teams), and retires the instances that finished
+// (converged or out of iterations), gathering their results to the host
+// with one kernel and one copy.  Requests that arrive while others are on
+// the GPU join at the next tick.  A session keeps its instance's state resident on the device
 // after a solve; the next request of that session is warm-started from it,
 // moved one step forward on the device (the receding horizon of Sec. II and
 // Alg. 2).  An instance's arithmetic depends only on its own shape and team

@@ -27,8 +27,9 @@
 //
 // Precision variants (template PREC):
 //   ADMM_FP64             one column per thread, dense column space (rs = n);
-//   ADMM_MIXED            FP32 storage and element work on vectors of
-//                         kMixedVW columns over a padded column space (rs = ld); the
+//   ADMM_MIXED            FP32 storage and element work on column pairs
+//                         (float2, paired FP32 instructions) over a padded
+//                         column space (rs = ld); the
 //                         capacity sums over k are accumulated per thread in
 //                         float-float (about 48 bits) and reduced in FP64; the
 //                         column state s, mu is stored and updated in
