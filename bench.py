@@ -55,21 +55,22 @@ def workload(cfg: int, precision: str):
 # kernel per iteration, from one ncu capture of each workload (profiles/).
 # It is reported only while the kernel sources hash to the captured build.
 NCU_TRAFFIC = {
-    ("phev n=1000 q=50", "fp64"): {"bytes_per_iter": (7.096576e6 + 0.050432e6) / 3330, "src": "094700d60b14e3d8",
+    ("phev n=1000 q=50", "fp64"): {"bytes_per_iter": (7.096576e6 + 0.050432e6) / 3330, "src": "77d11fd55f249e08",
                                    "capture": "profiles/single_fp64_kernel_config1.md (whole 3330-iteration solve)"},
     ("config2: plain n=1e5 m=4 q=20", "mixed"): {"bytes_per_iter": (4.302514e9 + 1.364925e9) / 20,
-                                                 "src": "094700d60b14e3d8",
+                                                 "src": "77d11fd55f249e08",
                                                  "capture": "profiles/single_mixed_kernel_config2.md (20 iterations)"},
 }
 
 
+# Sources the single-instance solve kernel is compiled from.
+SINGLE_KERNEL_SOURCES = ("single.cu", "quartic32.cuh", "quartic64.cuh", "mixed_elem.cuh", "common.cuh", "internal.h")
+
+
 def kernel_source_hash() -> str:
     import hashlib
-    import glob
-    files = sorted(glob.glob(os.path.join(ROOT, "paper_1903_10041_gb300", "csrc", "*.cu")) +
-                   glob.glob(os.path.join(ROOT, "paper_1903_10041_gb300", "csrc", "*.cuh")) +
-                   glob.glob(os.path.join(ROOT, "paper_1903_10041_gb300", "csrc", "*.h")) +
-                   glob.glob(os.path.join(ROOT, "include", "*.h")))
+    files = sorted([os.path.join(ROOT, "paper_1903_10041_gb300", "csrc", f) for f in SINGLE_KERNEL_SOURCES] +
+                   [os.path.join(ROOT, "include", "admm.h")])
     h = hashlib.sha256()
     for f in files:
         h.update(os.path.basename(f).encode())
