@@ -55,10 +55,10 @@ def workload(cfg: int, precision: str):
 # kernel per iteration, from one ncu capture of each workload (profiles/).
 # It is reported only while the kernel sources hash to the captured build.
 NCU_TRAFFIC = {
-    ("phev n=1000 q=50", "fp64"): {"bytes_per_iter": (7.096576e6 + 0.050432e6) / 3330, "src": "77d11fd55f249e08",
+    ("phev n=1000 q=50", "fp64"): {"bytes_per_iter": (7.096576e6 + 0.050432e6) / 3330, "src": "87d3589338d1ecc0",
                                    "capture": "profiles/single_fp64_kernel_config1.md (whole 3330-iteration solve)"},
     ("config2: plain n=1e5 m=4 q=20", "mixed"): {"bytes_per_iter": (4.302514e9 + 1.364925e9) / 20,
-                                                 "src": "77d11fd55f249e08",
+                                                 "src": "87d3589338d1ecc0",
                                                  "capture": "profiles/single_mixed_kernel_config2.md (20 iterations)"},
 }
 
@@ -469,6 +469,100 @@ def config_dict(P, par, args):
             "l2": "flushed between timed solves (512 MiB write)", "parallelism": f"replicas x{args.gpus}"}
 
 
+def run_quartic(args):
+    """Quartic benchmark of Sec. III-C: Algorithm 1 + clamp on N independent
+    quartics, device-resident and with host copies, FP32 and FP64, beside the
+    oracle's minimiser on 1 and all host cores (a sample)."""
+    import concurrent.futures as cf
+    import ctypes
+    import numpy as np
+    import torch
+    rank, world, local = dist_init(args.gpus)
+    from paper_1903_10041_gb300 import build
+    if rank == 0:
+        build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    from paper_1903_10041_gb300 import capi
+    N = args.quartic
+    g = torch.Generator(device="cuda").manual_seed(1903 + rank)
+
+    def gen(dtype):
+        u = lambda a, b: torch.rand(N, generator=g, device="cuda", dtype=torch.float64) * (b - a) + a
+        A, B, Cc, D = u(0.01, 2.0), u(-2.0, 2.0), u(-3.0, 3.0), u(-2.0, 2.0)
+        c0, w = u(-2.0, 2.0), u(0.0, 3.0)
+        return [t.to(dtype).contiguous() for t in (A, B, Cc, D, c0 - w, c0 + w)]
+
+    stream = torch.cuda.current_stream()
+    out = {}
+    for prec, dtype, width in (("fp32", torch.float32, 4), ("fp64", torch.float64, 8)):
+        dev = gen(dtype)
+        x = torch.empty_like(dev[0])
+        for _ in range(args.warmup):
+            capi.quartic_min(*dev, precision=prec, stream=stream, out=x)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            capi.quartic_min(*dev, precision=prec, stream=stream, out=x)
+        e1.record(stream)
+        e1.synchronize()
+        s_dev = e0.elapsed_time(e1) / 1e3 / args.steps
+        host = [t.cpu().pin_memory().numpy() for t in dev]
+        xh = torch.empty(N, dtype=dtype).pin_memory().numpy()
+        t0 = time.perf_counter()
+        for _ in range(max(1, args.steps // 2)):
+            capi.quartic_min(*host, precision=prec, stream=stream, out=xh)
+        s_e2e = (time.perf_counter() - t0) / max(1, args.steps // 2)
+        out[prec] = {"dev_per_s": N / s_dev, "e2e_per_s": N / s_e2e, "gbs": 7 * width * N / s_dev / 1e9,
+                     "sample": (host, xh)}
+        del dev, x
+    # oracle's Algorithm 1 on the host: a sample, 1 thread and all threads (ctypes drops the GIL)
+    import oracle
+    L = oracle.lib()
+    ns = min(N, 1 << 21)
+    arrs = [np.ascontiguousarray(a[:ns], dtype=np.float64) for a in out["fp64"]["sample"][0]]
+    xo = np.empty(ns)
+    dp = ctypes.POINTER(ctypes.c_double)
+
+    def run(lo_i, hi_i):
+        L.orc_quartic_min_many(hi_i - lo_i, *[a[lo_i:].ctypes.data_as(dp) for a in arrs], 0,
+                               xo[lo_i:].ctypes.data_as(dp), None)
+    t0 = time.perf_counter()
+    run(0, ns)
+    cpu1 = ns / (time.perf_counter() - t0)
+    threads = os.cpu_count() or 1
+    bounds = np.linspace(0, ns, threads + 1).astype(int)
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(threads) as ex:
+        list(ex.map(lambda t: run(bounds[t], bounds[t + 1]), range(threads)))
+    cpun = ns / (time.perf_counter() - t0)
+    x64 = out["fp64"]["sample"][1][:ns]
+    agree = float(np.mean(np.abs(x64 - xo) <= 1e-9 * np.maximum(1.0, np.abs(xo))))
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"hbm_gbs": 6800.0}
+    (vmax,) = barrier_max([-out["fp32"]["dev_per_s"]], world)
+    if rank == 0:
+        f32, f64 = out["fp32"], out["fp64"]
+        line = {"metric": "quartic minimisations/s (Algorithm 1 + clamp, Sec. III-C)", "value": f32["dev_per_s"] * world,
+                "unit": "quartics/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1e3 * N / f32["dev_per_s"], "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded uniform quartics and intervals)",
+                "config": {"workload": f"{N} independent quartics", "n": N},
+                "roofline": {"bound": "hbm", "achieved": f32["gbs"], "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                             "frac": f32["gbs"] / peaks["hbm_gbs"], "traffic": None},
+                "e2e": {"value": f32["e2e_per_s"], "unit": "quartics/s", "h2d_bytes_per_step": 24 * N,
+                        "d2h_bytes_per_step": 4 * N},
+                "fp64": {"dev_per_s": f64["dev_per_s"], "e2e_per_s": f64["e2e_per_s"], "gbs": f64["gbs"],
+                         "frac": f64["gbs"] / peaks["hbm_gbs"], "agree_with_oracle_1e-9": agree},
+                "cpu_baseline": {"value": cpun, "unit": "quartics/s", "cores": threads, "kind": "oracle",
+                                 "one_core": cpu1, "sample": f"{ns} of the quartics, FP64"},
+                "speedup_e2e_fp32_vs_all_cores": f32["e2e_per_s"] / cpun,
+                "gpu_launches": 2 * (args.warmup + args.steps + max(1, args.steps // 2))}
+        print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -489,11 +583,15 @@ def main():
                     help="profiling only: cap the iterations of each solve (the line is then not a benchmark)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--quartic", type=int, default=0,
+                    help="N > 0: the quartic benchmark of Sec. III-C on N quartics instead of a solve")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.quartic > 0:
+        return run_quartic(args)
     if args.config in (3, 4):
         return run_batched(args) if args.config == 3 else run_serving(args)
 

@@ -176,6 +176,27 @@ admm_status admm_destroy(admm_handle *h);
  * path of the bounded device waits without faulting the GPU. */
 admm_status admm_selftest_barrier_timeout(long long spin_ns, int grid, int *status_out);
 
+/* Quartic benchmark of Sec. III-C: Algorithm 1 (Sec. III-B) plus the clamp
+ * of step (a) on `count` independent quartics.  x[t] minimises
+ *   A[t] x^4 + B[t] x^3 + C[t] x^2 + D[t] x   over [lo[t], hi[t]]
+ * (xmin_mode as in admm_params: the constrained minimiser, or the literal
+ * Pi(argmin)).  Arrays are [count], host memory (on_device = 0: copied to
+ * and from the device inside the call, the paper's timing with copies) or
+ * device memory (on_device = 1); the caller owns them.  admm_quartic_min
+ * uses the solver's FP64 minimiser; admm_quartic_min_f32 the mixed
+ * solver's FP32 one (device arrays 8-byte aligned).  Runs on `stream` and
+ * returns after it has finished.  Each element needs A >= 0, C > 0 when
+ * A = 0, lo <= hi and finite coefficients; any other element gets x = NaN
+ * and the call returns ADMM_EINVAL (the others are still solved).
+ * ADMM_EINVAL also for NULL arrays, count < 0 or a bad xmin_mode;
+ * ADMM_ENOMEM / ADMM_ECUDA on device errors. */
+admm_status admm_quartic_min(const double *A, const double *B, const double *C, const double *D, const double *lo,
+                             const double *hi, int64_t count, double *x, int32_t xmin_mode, int32_t on_device,
+                             void *stream);
+admm_status admm_quartic_min_f32(const float *A, const float *B, const float *C, const float *D, const float *lo,
+                                 const float *hi, int64_t count, float *x, int32_t xmin_mode, int32_t on_device,
+                                 void *stream);
+
 /* Solve without any allocation, for callers that cannot allocate device
  * memory: code in host callbacks or real-time control loops where an
  * allocation may block or fail, controllers with a memory budget fixed at

@@ -266,6 +266,39 @@ def admm_selftest_barrier_timeout(spin_ns: int = 20_000_000, grid: int = 4) -> i
     return out.value
 
 
+def quartic_min(A, B, Cc, D, lo, hi, mode: str = "exact", precision: str = "fp64", stream=None, out=None):
+    """Algorithm 1 + clamp on many quartics (admm_quartic_min[_f32]).  The
+    six inputs are 1-D arrays of one length: numpy (host; copied inside the
+    call) or CUDA torch tensors (device).  precision "fp64" (float64 arrays)
+    or "fp32" (float32 arrays).  Returns x (numpy or torch, like the inputs)."""
+    f32 = precision == "fp32"
+    arrs = [A, B, Cc, D, lo, hi]
+    if _is_torch(A):
+        import torch
+        dt = torch.float32 if f32 else torch.float64
+        for a in arrs:
+            if a.dtype != dt or not a.is_contiguous() or not a.is_cuda:
+                raise TypeError("tensors must be contiguous CUDA tensors of the precision's dtype")
+        x = out if out is not None else torch.empty_like(A)
+        ptrs = [C.c_void_p(a.data_ptr()) for a in arrs + [x]]
+        dev = 1
+    else:
+        dt = np.float32 if f32 else np.float64
+        arrs = [np.ascontiguousarray(a, dtype=dt) for a in arrs]
+        x = out if out is not None else np.empty_like(arrs[0])
+        ptrs = [a.ctypes.data_as(C.c_void_p) for a in arrs + [x]]
+        dev = 0
+    n = int(arrs[0].shape[0])
+    sp = None
+    if stream is not None:
+        sp = C.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
+    fn = _lib.admm_quartic_min_f32 if f32 else _lib.admm_quartic_min
+    st = fn(*ptrs[:6], C.c_int64(n), ptrs[6], int(XMIN[mode]), int(dev), sp)
+    if st != ADMM_OK:
+        raise AdmmError(st, admm_last_error())
+    return x
+
+
 class Solver:
     """Owns one handle: ``Solver(problem, params).solve()``."""
 
