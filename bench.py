@@ -43,9 +43,11 @@ FLOPS_PER_ELEMENT = 71
 FLOPS_PER_COLUMN = 12
 
 
-def workload(cfg: int, precision: str):
+def workload(cfg: int, precision: str, coef_shared: bool = False):
     from paper_1903_10041_gb300 import workloads as W
     P = W.config(cfg)
+    if coef_shared:  # the same instance shape with scenario-shared cost and loss maps
+        P = W.shared_problem(P.n, P.m, P.q, name=f"config{cfg} shape, shared maps: n={P.n} m={P.m} q={P.q}")
     rho = (1.0, 1.0, 1.0, 1.0) if cfg == 0 else (1.0, 1.0 / P.n, 1.0, 1.0)
     par = W.Params(rho=rho, precision=precision)
     return P, par
@@ -55,10 +57,10 @@ def workload(cfg: int, precision: str):
 # kernel per iteration, from one ncu capture of each workload (profiles/).
 # It is reported only while the kernel sources hash to the captured build.
 NCU_TRAFFIC = {
-    ("phev n=1000 q=50", "fp64"): {"bytes_per_iter": (7.096576e6 + 0.050432e6) / 3330, "src": "87d3589338d1ecc0",
+    ("phev n=1000 q=50", "fp64"): {"bytes_per_iter": (7.595264e6 + 0.055808e6) / 3330, "src": "b348e97148b128bf",
                                    "capture": "profiles/single_fp64_kernel_config1.md (whole 3330-iteration solve)"},
-    ("config2: plain n=1e5 m=4 q=20", "mixed"): {"bytes_per_iter": (4.302514e9 + 1.364925e9) / 20,
-                                                 "src": "87d3589338d1ecc0",
+    ("config2: plain n=1e5 m=4 q=20", "mixed"): {"bytes_per_iter": (4.317581824e9 + 1.382421760e9) / 20,
+                                                 "src": "b348e97148b128bf",
                                                  "capture": "profiles/single_mixed_kernel_config2.md (20 iterations)"},
 }
 
@@ -93,9 +95,10 @@ def bytes_per_iteration(P, prec: str) -> int:
     each.  Mixed: 4 bytes each, except s and mu, which are float-float
     (8 bytes)."""
     m, q, n = P.m, P.q, P.n
+    coef = 4 * m * n * (1 if getattr(P, "coef_shared", False) else q)  # f2 f1 g2 g1 ([m][n] when shared)
     if prec == "fp64":
-        return 8 * (6 * m * n * q + 2 * m * n + 5 * n * q)
-    return 4 * (6 * m * n * q + 2 * m * n + n * q) + 8 * 4 * n * q
+        return 8 * (coef + 2 * m * n * q + 2 * m * n + 5 * n * q)
+    return 4 * (coef + 2 * m * n * q + 2 * m * n + n * q) + 8 * 4 * n * q
 
 
 class ClockSampler:
@@ -155,6 +158,7 @@ def cpu_baseline(P, par, iters_per_solve: int, budget_s: float = 12.0):
     T iterations of the same solve, scaled to solves/s by the iteration
     count of a full solve."""
     import oracle
+    P = P.dense()  # the oracle takes per-scenario coefficient arrays
     threads = os.cpu_count() or 1
     # size T from a short probe so the sample takes about budget_s seconds
     t0 = time.perf_counter()
@@ -583,6 +587,8 @@ def main():
                     help="profiling only: cap the iterations of each solve (the line is then not a benchmark)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--coef-shared", action="store_true",
+                    help="configs 1-2: scenario-shared cost and loss maps ([m][n] coefficients)")
     ap.add_argument("--quartic", type=int, default=0,
                     help="N > 0: the quartic benchmark of Sec. III-C on N quartics instead of a solve")
     args = ap.parse_args()
@@ -606,7 +612,7 @@ def main():
         torch.distributed.barrier()
     from paper_1903_10041_gb300 import capi
 
-    P, par = workload(args.config, args.precision)
+    P, par = workload(args.config, args.precision, args.coef_shared)
     if args.max_iter:
         par = par.replace(max_iter=args.max_iter)
     stream = torch.cuda.Stream()

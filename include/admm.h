@@ -80,6 +80,8 @@ typedef struct admm_problem {
     const double *y;                 /* [q][n] */
     const double *c;                 /* [m]; +INFINITY = no capacity limit */
     int32_t on_device;               /* 1: device pointers; 0: host pointers */
+    int32_t coef_shared;             /* 1: f2..g0 are [m][n], the same maps for every scenario j
+                                        (single-instance solves only; batches and servers take 0) */
 } admm_problem;
 
 typedef struct admm_params {

@@ -36,7 +36,8 @@ MAX_PAIRS = 1024
 class admm_problem(C.Structure):
     _fields_ = [("n", C.c_int32), ("m", C.c_int32), ("q", C.c_int32),
                 ("f2", _dp), ("f1", _dp), ("f0", _dp), ("g2", _dp), ("g1", _dp), ("g0", _dp),
-                ("x_lo", _dp), ("x_hi", _dp), ("y", _dp), ("c", _dp), ("on_device", C.c_int32)]
+                ("x_lo", _dp), ("x_hi", _dp), ("y", _dp), ("c", _dp), ("on_device", C.c_int32),
+                ("coef_shared", C.c_int32)]
 
 
 class admm_params(C.Structure):
@@ -170,7 +171,8 @@ def make_problem(prob, keep: list) -> admm_problem:
         devs.add(d)
     if len(devs) != 1:
         raise TypeError("problem arrays must be all host or all device")
-    return admm_problem(int(prob.n), int(prob.m), int(prob.q), *ptrs, int(devs.pop()))
+    return admm_problem(int(prob.n), int(prob.m), int(prob.q), *ptrs, int(devs.pop()),
+                        int(bool(getattr(prob, "coef_shared", False))))
 
 
 # ---------------------------------------------------------------------------

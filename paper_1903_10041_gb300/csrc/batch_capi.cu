@@ -278,6 +278,8 @@ admm_status admm_batch_create(const admm_problem *probs, int32_t count, const ad
     for (int t = 0; t < count; ++t) {
         const admm_problem &P = probs[t];
         if (P.n < 1 || P.m < 1 || P.q < 1) return bail(bfail(ADMM_EINVAL, "n, m, q must be >= 1"));
+        if (P.coef_shared != 0)
+            return bail(bfail(ADMM_EUNSUPPORTED, "batched instances take per-scenario coefficients (coef_shared = 0)"));
         if (P.m > ADMM_MAX_M || (int64_t)P.m * P.q > ADMM_BATCH_MAX_PAIRS)
             return bail(bfail(ADMM_EUNSUPPORTED, "instance " + std::to_string(t) + " exceeds m <= 8, m*q <= 256"));
         const InstSizes z = inst_sizes(P.n, P.m, P.q);

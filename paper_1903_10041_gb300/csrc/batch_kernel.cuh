@@ -162,7 +162,8 @@ template <int KIND, int NW, int M> __device__ void solve_team(const BatchArgs &a
 
     const ElemF32 ea = {a.f2 + I.off_e, a.f1 + I.off_e, a.g2 + I.off_e, a.g1 + I.off_e, a.g0 + I.off_e,
                         a.lo + I.off_b, a.hi + I.off_b, a.y + I.off_c,  a.x + I.off_e,  a.s + I.off_c,
-                        a.mu + I.off_c, a.s_lo + I.off_c, a.mu_lo + I.off_c, n, m, q, I.ld, a.sweep, a.xmin_mode};
+                        a.mu + I.off_c, a.s_lo + I.off_c, a.mu_lo + I.off_c, n, m, q, I.ld, a.sweep, a.xmin_mode,
+                        q, 1};
     const double *cc = a.c + I.off_src;
     const double *sumg0 = a.sumg0 + I.off_pair;
     unsigned esc = 0;

@@ -47,7 +47,7 @@ enum : unsigned {
     V_CNAN = 16u        // c is NaN
 };
 
-__global__ void validate_elements(int n, int m, int q, int ld, const double *f2, const double *f1,
+__global__ void validate_elements(int n, int m, int q, int ld, int cq, int cj, const double *f2, const double *f1,
                                   const double *f0, const double *g2, const double *g1, const double *g0,
                                   const double *lo, const double *hi, const double *y, unsigned *flags)
 {
@@ -57,7 +57,7 @@ __global__ void validate_elements(int n, int m, int q, int ld, const double *f2,
         const int k = (int)(t % n);
         const int64_t r = t / n; // i*q + j
         const int i = (int)(r / q), j = (int)(r % q);
-        const size_t e = (size_t)r * ld + k;
+        const size_t e = ((size_t)i * cq + (size_t)j * cj) * ld + k; // coefficient row of (i, j)
         const double v[6] = {f2[e], f1[e], f0[e], g2[e], g1[e], g0[e]};
         for (int u = 0; u < 6; ++u)
             if (!isfinite(v[u])) bits |= V_NONFINITE;
@@ -74,12 +74,13 @@ __global__ void validate_elements(int n, int m, int q, int ld, const double *f2,
 
 // One CTA per pair (i, j): sum_k beta_0 (kept for the solve) and the
 // smallest achievable sum_k g (for the sure-infeasibility check).
-__global__ void pair_sums(int n, int m, int q, int ld, const double *g2, const double *g1, const double *g0,
-                          const double *lo, const double *hi, const double *c, double *sumg0, unsigned *flags)
+__global__ void pair_sums(int n, int m, int q, int ld, int cq, int cj, const double *g2, const double *g1,
+                          const double *g0, const double *lo, const double *hi, const double *c, double *sumg0,
+                          unsigned *flags)
 {
     __shared__ double sh[2][32];
     const int pr = blockIdx.x, i = pr / q;
-    const size_t base = (size_t)pr * ld;
+    const size_t base = ((size_t)i * cq + (size_t)(pr - i * q) * cj) * ld;
     double s0 = 0.0, smin = 0.0;
     for (int k = threadIdx.x; k < n; k += blockDim.x) {
         const double a2 = g2[base + k], a1 = g1[base + k], a0 = g0[base + k];
@@ -173,6 +174,7 @@ struct admm_handle {
     int64_t chunk = 0, ncols = 0;
     int pieces = 0;
     size_t smem = 0;
+    int cshared = 0; // coefficients shared by the scenarios ([m][ld])
 };
 
 namespace {
@@ -359,10 +361,12 @@ admm_status admm_create(const admm_problem *P, const admm_params *prm, admm_hand
     const double *arrs[] = {P->f2, P->f1, P->f0, P->g2, P->g1, P->g0, P->x_lo, P->x_hi, P->y, P->c};
     for (const double *a : arrs)
         if (!a) return fail(ADMM_EINVAL, "a problem array is NULL");
+    if (P->coef_shared != 0 && P->coef_shared != 1) return fail(ADMM_EINVAL, "coef_shared must be 0 or 1");
     if (!params_ok(prm)) return g_err.find("precision") != std::string::npos ? ADMM_EUNSUPPORTED : ADMM_EINVAL;
 
     admm_handle *h = new admm_handle();
     const bool mixed = prm->precision != ADMM_FP64;
+    h->cshared = P->coef_shared;
     h->n = P->n;
     h->m = P->m;
     h->q = P->q;
@@ -389,8 +393,9 @@ admm_status admm_create(const admm_problem *P, const admm_params *prm, admm_hand
     TRY(cudaGetDevice(&h->dev));
     TRY(cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, h->dev));
     const int n = h->n, m = h->m, q = h->q, ld = h->ld, mq = m * q;
-    const size_t ne = (size_t)mq * ld, nb = (size_t)m * ld, nc = (size_t)q * ld;
-    const size_t cnt[9] = {ne, ne, ne, ne, ne, ne, nb, nb, nc};
+    const int crow = h->cshared ? m : mq; // coefficient rows
+    const size_t ne = (size_t)mq * ld, nf = (size_t)crow * ld, nb = (size_t)m * ld, nc = (size_t)q * ld;
+    const size_t cnt[9] = {nf, nf, nf, nf, nf, nf, nb, nb, nc};
     for (int t = 0; t < 9; ++t) {
         TRY(cudaMalloc(&s64[t], cnt[t] * 8));
         TRY(cudaMemset(s64[t], 0, cnt[t] * 8));
@@ -406,16 +411,18 @@ admm_status admm_create(const admm_problem *P, const admm_params *prm, admm_hand
 
     const bool dev = P->on_device != 0;
     const double *src[9] = {P->f2, P->f1, P->f0, P->g2, P->g1, P->g0, P->x_lo, P->x_hi, P->y};
-    const int64_t rows[9] = {mq, mq, mq, mq, mq, mq, m, m, q};
+    const int64_t rows[9] = {crow, crow, crow, crow, crow, crow, m, m, q};
     for (int t = 0; t < 9; ++t) TRY(put_rows(s64[t], ld, src[t], n, rows[t], dev));
     TRY(cudaMemcpy(h->c, P->c, m * 8, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice));
 
     // validation (Assumptions 1 and 3, bounds, sure infeasibility)
     TRY(cudaMemset(h->flags, 0, sizeof(unsigned)));
+    const int cq = h->cshared ? 1 : q, cj = h->cshared ? 0 : 1;
     validate_elements<<<std::max(1, std::min(h->nsm * 8, (int)(ne / 256 + 1))), 256>>>(
-        n, m, q, ld, s64[0], s64[1], s64[2], s64[3], s64[4], s64[5], s64[6], s64[7], s64[8], h->flags);
+        n, m, q, ld, cq, cj, s64[0], s64[1], s64[2], s64[3], s64[4], s64[5], s64[6], s64[7], s64[8], h->flags);
     TRY(cudaGetLastError());
-    pair_sums<<<mq, 256>>>(n, m, q, ld, s64[3], s64[4], s64[5], s64[6], s64[7], h->c, h->sumg0, h->flags);
+    pair_sums<<<mq, 256>>>(n, m, q, ld, cq, cj, s64[3], s64[4], s64[5], s64[6], s64[7], h->c, h->sumg0,
+                           h->flags);
     TRY(cudaGetLastError());
     unsigned flags = 0;
     TRY(cudaMemcpy(&flags, h->flags, sizeof flags, cudaMemcpyDeviceToHost));
@@ -539,6 +546,8 @@ admm_status admm_solve(admm_handle *h, const admm_state *warm, admm_result *out,
     a.ncols = h->ncols;
     a.chunk = h->chunk;
     a.pieces = h->pieces;
+    a.cq = h->cshared ? 1 : h->q;
+    a.cj = h->cshared ? 0 : 1;
     a.nbmax = h->nbmax;
     a.grid = h->grid;
     a.f2 = h->f2;

@@ -29,6 +29,7 @@ inline __host__ __device__ int scal_size(int m, int q) { return 5 * m * q + m + 
 struct SingleArgs {
     int n, m, q, ld;           // ld: padded row stride of the [*][n] arrays
     int rs;                    // row length of the column space: n (FP64) or ld (mixed, padded)
+    int cq, cj;                // coefficient row of pair (i, j): i * cq + j * cj ((q, 1), or (1, 0) when shared)
     int64_t ncols;             // q * rs columns (j, k)
     int64_t chunk;             // flat split: columns per CTA (contiguous in j-major order)
     int pieces;                // > 0: row-aligned split, CTA b takes piece b % pieces of row b / pieces

@@ -44,6 +44,7 @@ struct ElemF32 {
     const float *f2, *f1, *g2, *g1, *g0, *lo, *hi, *y;
     float *x, *s, *mu, *s_lo, *mu_lo;
     int n, m, q, ld, sweep, xmin_mode;
+    int cq, cj; // coefficient row of pair (i, j): i * cq + j * cj
 };
 
 // L2 prefetch of everything vec32 reads for the columns (j, k0..): issued
@@ -64,12 +65,13 @@ __device__ __forceinline__ void prefetch_vec32(const ElemF32 &a, int j, int k0, 
     for (int i = 0; i < M; ++i)
         if (i < a.m) {
             const size_t e = ((size_t)i * a.q + j) * a.ld + k0;
+            const size_t ec = ((size_t)i * a.cq + (size_t)j * a.cj) * a.ld + k0;
             prefetch_l2(a.x + e);
-            prefetch_l2(a.f2 + e);
-            prefetch_l2(a.f1 + e);
-            prefetch_l2(a.g2 + e);
-            prefetch_l2(a.g1 + e);
-            if (cold) prefetch_l2(a.g0 + e);
+            prefetch_l2(a.f2 + ec);
+            prefetch_l2(a.f1 + ec);
+            prefetch_l2(a.g2 + ec);
+            prefetch_l2(a.g1 + ec);
+            if (cold) prefetch_l2(a.g0 + ec);
             prefetch_l2(a.lo + (size_t)i * a.ld + k0);
             prefetch_l2(a.hi + (size_t)i * a.ld + k0);
         }
@@ -174,7 +176,7 @@ __device__ __forceinline__ void vec32(const ElemF32 &a, const float *uoff, const
 #pragma unroll
     for (int i = 0; i < M; ++i) {
         if (i < m) {
-            const size_t e = ((size_t)i * q + j) * ld + k0;
+            const size_t e = ((size_t)i * a.cq + (size_t)j * a.cj) * ld + k0; // coefficient element
             const float2 a2 = ldg2(a.f2 + e), a1 = ldg2(a.f1 + e), b2 = ldg2(a.g2 + e), b1 = ldg2(a.g1 + e);
             const float2 L = ldg2(a.lo + (size_t)i * ld + k0), H = ldg2(a.hi + (size_t)i * ld + k0);
             const float2 g0 = cold ? ldg2(a.g0 + e) : splat2(0.0f);

@@ -170,6 +170,7 @@ extern "C" admm_status admm_solve_noalloc(const admm_problem *P, const admm_para
     if (!P->on_device || !st->on_device)
         return nfail(ADMM_EINVAL, "problem and state arrays must be device memory (on_device = 1)");
     if (P->n < 1 || P->m < 1 || P->q < 1) return nfail(ADMM_EINVAL, "n, m, q must be >= 1");
+    if (P->coef_shared != 0) return nfail(ADMM_EUNSUPPORTED, "coef_shared is not available here");
     if (P->m > ADMM_MAX_M) return nfail(ADMM_EUNSUPPORTED, "m exceeds ADMM_MAX_M");
     if ((int64_t)P->m * P->q > ADMM_MAX_PAIRS) return nfail(ADMM_EUNSUPPORTED, "m*q exceeds ADMM_MAX_PAIRS");
     const double *arrs[] = {P->f2, P->f1, P->f0, P->g2, P->g1, P->g0, P->x_lo, P->x_hi, P->y, P->c,
@@ -247,6 +248,8 @@ extern "C" admm_status admm_solve_noalloc(const admm_problem *P, const admm_para
     a.ncols = ncols;
     a.chunk = chunk;
     a.pieces = sh.pieces;
+    a.cq = q;
+    a.cj = 1;
     a.nbmax = nbmax;
     a.grid = grid;
     a.f2 = P->f2;

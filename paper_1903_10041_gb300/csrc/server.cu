@@ -653,6 +653,8 @@ admm_status admm_server_submit(admm_server *S, const admm_problem *P, int64_t se
     clear_last_error();
     if (!S || !P || !ticket) return sfail(ADMM_EINVAL, "NULL argument");
     if (P->on_device) return sfail(ADMM_EINVAL, "server requests take host arrays (on_device = 0)");
+    if (P->coef_shared != 0)
+        return sfail(ADMM_EUNSUPPORTED, "server requests take per-scenario coefficients (coef_shared = 0)");
     if (P->m > S->cfg.max_m || P->q > S->cfg.max_q)
         return sfail(ADMM_EUNSUPPORTED, "instance exceeds the server's max_m or max_q");
     auto r = std::make_shared<Request>();

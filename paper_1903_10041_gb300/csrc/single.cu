@@ -140,7 +140,7 @@ __device__ __forceinline__ void column64(const SingleArgs &a, const Sm &sm, int 
 #pragma unroll
     for (int i = 0; i < M; ++i) {
         if (i < m) {
-            const size_t e = ((size_t)i * q + j) * ld + k;
+            const size_t e = ((size_t)i * a.cq + (size_t)j * a.cj) * ld + k; // coefficient element
             const double a2 = F2[e], a1 = F1[e], b2 = G2[e], b1 = G1[e];
             const int pr = i * q + j;
             const double g0 = cold ? G0[e] : 0.0;
@@ -482,7 +482,7 @@ __global__ void __launch_bounds__(NT, MINB) single_kernel(SingleArgs a)
                                     (float *)a.s,        (float *)a.mu,       (float *)a.s_lo,
                                     (float *)a.mu_lo,    a.n,                 a.m,
                                     a.q,                 a.ld,                a.sweep,
-                                    a.xmin_mode};
+                                    a.xmin_mode,         a.cq,                a.cj};
                 const int kn = min(ke, n); // padding columns k >= n are skipped
                 for (int k0 = kb + first * VW; k0 < kn; k0 += stride * VW) {
                     if constexpr (MINB == 2) // several vectors per thread: fetch the next one into L2
@@ -627,16 +627,17 @@ __global__ void __launch_bounds__(NT, MINB) single_kernel(SingleArgs a)
             if (k >= n) continue;
             for (int i = 0; i < m; ++i) {
                 const size_t e = ((size_t)i * q + j) * a.ld + k;
+                const size_t ec = ((size_t)i * a.cq + (size_t)j * a.cj) * a.ld + k; // coefficient element
                 double f2, f1, f0, x;
                 if constexpr (MIXED) {
-                    f2 = ((const float *)a.f2)[e];
-                    f1 = ((const float *)a.f1)[e];
-                    f0 = ((const float *)a.f0)[e];
+                    f2 = ((const float *)a.f2)[ec];
+                    f1 = ((const float *)a.f1)[ec];
+                    f0 = ((const float *)a.f0)[ec];
                     x = ((const float *)a.x)[e];
                 } else {
-                    f2 = ((const double *)a.f2)[e];
-                    f1 = ((const double *)a.f1)[e];
-                    f0 = ((const double *)a.f0)[e];
+                    f2 = ((const double *)a.f2)[ec];
+                    f1 = ((const double *)a.f1)[ec];
+                    f0 = ((const double *)a.f0)[ec];
                     x = ((const double *)a.x)[e];
                 }
                 acc += f2 * x * x + f1 * x + f0;

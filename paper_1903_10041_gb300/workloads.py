@@ -87,10 +87,19 @@ class Problem:
     y: np.ndarray
     c: np.ndarray
     name: str = ""
+    coef_shared: bool = False     # f2..g0 are [m][n], the same maps for every scenario
 
     @property
     def elements(self) -> int:
         return self.m * self.q * self.n
+
+    def dense(self) -> "Problem":
+        """The same problem with per-scenario coefficient arrays [m][q][n]."""
+        if not self.coef_shared:
+            return self
+        rep = {k: np.ascontiguousarray(np.broadcast_to(getattr(self, k)[:, None, :], (self.m, self.q, self.n)))
+               for k in ("f2", "f1", "f0", "g2", "g1", "g0")}
+        return dataclasses.replace(self, coef_shared=False, **rep)
 
     def arrays(self):
         return dict(f2=self.f2, f1=self.f1, f0=self.f0, g2=self.g2, g1=self.g1, g0=self.g0,
@@ -143,6 +152,23 @@ def random_problem(n: int, m: int, q: int, seed: int = SEED, name: str = "") -> 
     y = _u(seed, (T_Y,), (q, n), 0.5, 2.0)
     c = _capacity(g2, g1, g0, 2.0)
     return Problem(n, m, q, f2, f1, f0, g2, g1, g0, lo, hi, y, c, name or f"plain n={n} m={m} q={q}")
+
+
+def shared_problem(n: int, m: int, q: int, seed: int = SEED, name: str = "") -> Problem:
+    """The plain recipe with scenario-shared cost and loss maps: f and g are
+    drawn per (i, k) ([m][n]) and only the demand y differs by scenario."""
+    sh = (m, n)
+    f2 = _u(seed, (T_F2,), sh, 0.1, 1.0)
+    f1 = _u(seed, (T_F1,), sh, -1.0, 1.0)
+    g2 = _u(seed, (T_G2,), sh, 0.01, 0.1)
+    g1 = np.ones(sh)
+    z = np.zeros(sh)
+    lo = np.full((m, n), -1.0)
+    hi = np.full((m, n), 2.0)
+    y = _u(seed, (T_Y,), (q, n), 0.5, 2.0)
+    c = _capacity(g2[:, None, :], g1[:, None, :], z[:, None, :], 2.0)
+    return Problem(n, m, q, f2, f1, z.copy(), g2, g1, z.copy(), lo, hi, y, c,
+                   name or f"shared n={n} m={m} q={q}", coef_shared=True)
 
 
 def phev_problem(n: int = 1000, q: int = 50, seed: int = SEED) -> Problem:
