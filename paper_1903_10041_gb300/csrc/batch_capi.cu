@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "store.h"
+#include "trace.h"
 
 using namespace admm_impl;
 
@@ -256,6 +257,7 @@ extern "C" {
 
 admm_status admm_batch_create(const admm_problem *probs, int32_t count, const admm_params *prm, admm_batch **out)
 {
+    TraceRange trace_("admm_batch_create");
     clear_last_error();
     if (!out) return bfail(ADMM_EINVAL, "out is NULL");
     *out = nullptr;
@@ -360,6 +362,7 @@ admm_status admm_batch_get_config(admm_batch *b, admm_batch_config *cfg)
 
 admm_status admm_batch_solve(admm_batch *b, void *stream)
 {
+    TraceRange trace_("admm_batch_solve");
     clear_last_error();
     if (!b) return bfail(ADMM_EINVAL, "batch is NULL");
     admm_status s = ensure_graph(b);
@@ -440,6 +443,7 @@ admm_status admm_batch_reset(admm_batch *b)
 
 admm_status admm_batch_autotune(admm_batch *b, int32_t trial_iters, admm_batch_config *chosen)
 {
+    TraceRange trace_("admm_batch_autotune");
     clear_last_error();
     if (!b || trial_iters < 1) return bfail(ADMM_EINVAL, "bad argument");
     const admm_batch_config keep = b->cfg;

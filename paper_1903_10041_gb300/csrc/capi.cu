@@ -12,6 +12,7 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "trace.h"
 
 using namespace admm_impl;
 
@@ -350,6 +351,7 @@ const char *admm_status_string(admm_status s)
 
 admm_status admm_create(const admm_problem *P, const admm_params *prm, admm_handle **out)
 {
+    TraceRange trace_("admm_create");
     g_err.clear();
     if (!out) return fail(ADMM_EINVAL, "out is NULL");
     *out = nullptr;
@@ -529,6 +531,7 @@ static admm_status load_state(admm_handle *h, const admm_state *w, cudaStream_t 
 
 admm_status admm_solve(admm_handle *h, const admm_state *warm, admm_result *out, void *stream)
 {
+    TraceRange trace_("admm_solve");
     g_err.clear();
     if (!h) return fail(ADMM_EINVAL, "handle is NULL");
     DeviceGuard dg(h->dev);

@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 
 #include "internal.h"
+#include "trace.h"
 #include "quartic32.cuh"
 
 using namespace admm_impl;
@@ -86,6 +87,7 @@ template <class T>
 admm_status quartic_min_impl(const T *A, const T *B, const T *C, const T *D, const T *lo, const T *hi, int64_t count,
                              T *x, int32_t xmin_mode, int32_t on_device, void *stream)
 {
+    TraceRange trace_("admm_quartic_min");
     clear_last_error();
     if (count < 0 || (count > 0 && (!A || !B || !C || !D || !lo || !hi || !x)))
         return set_last_error("NULL array or negative count"), ADMM_EINVAL;

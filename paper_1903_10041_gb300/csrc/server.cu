@@ -30,6 +30,7 @@
 #include <vector>
 
 #include "store.h"
+#include "trace.h"
 
 using namespace admm_impl;
 
@@ -363,6 +364,7 @@ void worker_loop(admm_server *S)
             launch_shift_state(S->d_inst, S->d_shift, (int)shift_ids.size(), S->store.x, S->store.s, S->store.s_lo,
                                S->store.mu, S->store.mu_lo, S->store.scal, S->st);
         }
+        TraceRange trace_("admm_server_tick");
         // queues of the active instances for this tick
         int nX = 0, nL = 0, nS = 0;
         std::vector<int> ids;
