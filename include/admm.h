@@ -48,7 +48,8 @@ typedef enum admm_status {
     ADMM_ETIMEOUT = 4,       /* a bounded device-side wait gave up */
     ADMM_ENOTCONVERGED = 5,  /* max_iter reached; the result is still filled */
     ADMM_EUNSUPPORTED = 6,   /* sizes beyond this build's limits */
-    ADMM_EPENDING = 7        /* a served request has not finished yet */
+    ADMM_EPENDING = 7,       /* a served request has not finished yet */
+    ADMM_ECANCELLED = 8      /* a served request was cancelled (admm_server_cancel) */
 } admm_status;
 
 /* Arithmetic of the per-element work (the stored state follows it). */
@@ -338,6 +339,12 @@ admm_status admm_server_drain(admm_server *s, int32_t max, int64_t *tickets, dou
  * moving step requests' instances one step forward, and the sum over ticks
  * of the instances each tick ran. */
 admm_status admm_server_stats(admm_server *s, double *stats, int32_t count);
+/* Cancels a request.  A queued request leaves the queue at once; a running
+ * one leaves at the next tick boundary (its session keeps the state reached
+ * so far for the next warm start).  Either way it finishes with status
+ * ADMM_ECANCELLED and no x.  A finished request is left as it is.
+ * ADMM_EINVAL for an unknown ticket. */
+admm_status admm_server_cancel(admm_server *s, int64_t ticket);
 /* Stops the worker (in-flight requests are dropped) and frees everything. */
 admm_status admm_server_destroy(admm_server *s);
 

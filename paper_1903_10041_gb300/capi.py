@@ -514,7 +514,9 @@ class Batch:
 # serving
 # ---------------------------------------------------------------------------
 ADMM_EPENDING = 7
+ADMM_ECANCELLED = 8
 STATUS_NAMES[7] = "EPENDING"
+STATUS_NAMES[8] = "ECANCELLED"
 
 
 class admm_server_config(C.Structure):
@@ -588,6 +590,10 @@ class Server:
         if session >= 0:
             self._session_n[int(session)] = int(prob.n)
         return t.value
+
+    def cancel(self, ticket: int) -> None:
+        """admm_server_cancel: the request finishes with ADMM_ECANCELLED."""
+        _check(_lib.admm_server_cancel(self.h, C.c_int64(int(ticket))))
 
     def poll(self, ticket: int, wait_ms: int = 0, want_x: bool = False):
         """None while pending; else a result dict (with x, x1 if want_x)."""

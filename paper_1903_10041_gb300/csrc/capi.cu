@@ -180,6 +180,25 @@ struct admm_handle {
 
 namespace {
 
+// Host-side fault injection for the failure paths of admm_create: with the
+// environment variable ADMM_FAULT_ALLOC = k (k >= 1), the k-th device
+// allocation of each admm_create call reports cudaErrorMemoryAllocation
+// instead of allocating.  Unset (the normal case) it costs one getenv.
+struct AllocFault {
+    long long fail_at = 0, count = 0;
+    AllocFault()
+    {
+        const char *v = std::getenv("ADMM_FAULT_ALLOC");
+        fail_at = v ? std::atoll(v) : 0;
+    }
+};
+
+template <class T> cudaError_t dev_malloc(AllocFault &af, T **p, size_t bytes)
+{
+    if (af.fail_at > 0 && ++af.count == af.fail_at) return cudaErrorMemoryAllocation;
+    return cudaMalloc((void **)p, bytes);
+}
+
 template <class T> void dfree(T *&p)
 {
     if (p) cudaFree((void *)p);
@@ -345,6 +364,8 @@ const char *admm_status_string(admm_status s)
     case ADMM_ETIMEOUT: return "device wait timed out";
     case ADMM_ENOTCONVERGED: return "not converged";
     case ADMM_EUNSUPPORTED: return "unsupported size or mode";
+    case ADMM_EPENDING: return "pending";
+    case ADMM_ECANCELLED: return "cancelled";
     }
     return "unknown status";
 }
@@ -367,6 +388,7 @@ admm_status admm_create(const admm_problem *P, const admm_params *prm, admm_hand
     if (!params_ok(prm)) return g_err.find("precision") != std::string::npos ? ADMM_EUNSUPPORTED : ADMM_EINVAL;
 
     admm_handle *h = new admm_handle();
+    AllocFault af;
     const bool mixed = prm->precision != ADMM_FP64;
     h->cshared = P->coef_shared;
     h->n = P->n;
@@ -379,8 +401,7 @@ admm_status admm_create(const admm_problem *P, const admm_params *prm, admm_hand
     // FP64 staging copies of the problem (the final arrays in FP64 mode)
     double *s64[9] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     auto bail = [&](admm_status s) {
-        if (mixed)
-            for (double *&p : s64) dfree(p);
+        for (double *&p : s64) dfree(p); // staging copies not yet owned by the handle
         free_all(h);
         delete h;
         return s;
@@ -399,16 +420,16 @@ admm_status admm_create(const admm_problem *P, const admm_params *prm, admm_hand
     const size_t ne = (size_t)mq * ld, nf = (size_t)crow * ld, nb = (size_t)m * ld, nc = (size_t)q * ld;
     const size_t cnt[9] = {nf, nf, nf, nf, nf, nf, nb, nb, nc};
     for (int t = 0; t < 9; ++t) {
-        TRY(cudaMalloc(&s64[t], cnt[t] * 8));
+        TRY(dev_malloc(af, &s64[t], cnt[t] * 8));
         TRY(cudaMemset(s64[t], 0, cnt[t] * 8));
     }
-    TRY(cudaMalloc(&h->c, m * 8));
-    TRY(cudaMalloc(&h->sumg0, mq * 8));
-    TRY(cudaMalloc(&h->scal, scal_size(m, q) * 8));
-    TRY(cudaMalloc(&h->info, kInfo * 8));
-    TRY(cudaMalloc(&h->bar, sizeof(unsigned)));
-    TRY(cudaMalloc(&h->flags, sizeof(unsigned)));
-    TRY(cudaMalloc(&h->status, sizeof(int)));
+    TRY(dev_malloc(af, &h->c, m * 8));
+    TRY(dev_malloc(af, &h->sumg0, mq * 8));
+    TRY(dev_malloc(af, &h->scal, scal_size(m, q) * 8));
+    TRY(dev_malloc(af, &h->info, kInfo * 8));
+    TRY(dev_malloc(af, &h->bar, sizeof(unsigned)));
+    TRY(dev_malloc(af, &h->flags, sizeof(unsigned)));
+    TRY(dev_malloc(af, &h->status, sizeof(int)));
     TRY(cudaMallocHost(&h->info_host, kInfo * 8));
 
     const bool dev = P->on_device != 0;
@@ -443,20 +464,20 @@ admm_status admm_create(const admm_problem *P, const admm_params *prm, admm_hand
             *dst[t] = s64[t];
             s64[t] = nullptr;
         }
-        TRY(cudaMalloc(&h->x, ne * 8));
-        TRY(cudaMalloc(&h->s, nc * 8));
-        TRY(cudaMalloc(&h->mu, nc * 8));
+        TRY(dev_malloc(af, &h->x, ne * 8));
+        TRY(dev_malloc(af, &h->s, nc * 8));
+        TRY(dev_malloc(af, &h->mu, nc * 8));
     } else {
         for (int t = 0; t < 9; ++t) {
-            TRY(cudaMalloc(dst[t], cnt[t] * 4));
+            TRY(dev_malloc(af, dst[t], cnt[t] * 4));
             convert_rows_f64_to_f32((float *)*dst[t], ld, s64[t], ld, ld, rows[t], 0);
             TRY(cudaGetLastError());
         }
         TRY(cudaDeviceSynchronize());
         for (double *&p : s64) dfree(p);
-        TRY(cudaMalloc(&h->x, ne * 4));
-        TRY(cudaMalloc(&h->s, nc * 8));   // float-float: hi rows then lo rows
-        TRY(cudaMalloc(&h->mu, nc * 8));
+        TRY(dev_malloc(af, &h->x, ne * 4));
+        TRY(dev_malloc(af, &h->s, nc * 8));   // float-float: hi rows then lo rows
+        TRY(dev_malloc(af, &h->mu, nc * 8));
         h->s_lo = (float *)h->s + nc;
         h->mu_lo = (float *)h->mu + nc;
         TRY(cudaMemset(h->x, 0, ne * 4));
@@ -473,8 +494,8 @@ admm_status admm_create(const admm_problem *P, const admm_params *prm, admm_hand
     h->grid = sh.grid;
     h->nbmax = sh.nbmax;
     h->minb = sh.minb;
-    TRY(cudaMalloc(&h->part, sizeof(double) * 2 * (size_t)q * h->nbmax * m * 4));
-    TRY(cudaMalloc(&h->cpart, sizeof(double) * 2 * (size_t)h->grid * 4));
+    TRY(dev_malloc(af, &h->part, sizeof(double) * 2 * (size_t)q * h->nbmax * m * 4));
+    TRY(dev_malloc(af, &h->cpart, sizeof(double) * 2 * (size_t)h->grid * 4));
     st = reset_state(h);
     if (st != ADMM_OK) return bail(st);
 #undef TRY

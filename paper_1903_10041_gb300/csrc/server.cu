@@ -50,7 +50,7 @@ struct Request {
     std::vector<float> payload;  // step data: f2 f1 f0 g2 g1 g0 [m][q], lo hi [m], y [q]
     double t_submit = 0, t_admit = 0, t_finish = 0;
     int slot = -1;
-    bool warm = false, done = false;
+    bool warm = false, done = false, cancel = false;
     admm_status status = ADMM_OK;
     double info[kInfo] = {};
     std::vector<double> x, x1;
@@ -365,6 +365,29 @@ void worker_loop(admm_server *S)
                                S->store.mu, S->store.mu_lo, S->store.scal, S->st);
         }
         TraceRange trace_("admm_server_tick");
+        // cancelled requests leave at the tick boundary
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            bool any = false;
+            for (int s = 0; s < maxa; ++s) {
+                std::shared_ptr<Request> r = S->active[s];
+                if (!r || !r->cancel) continue;
+                if (r->session >= 0) {
+                    Session &ss = S->sessions[r->session];
+                    ss.busy = false;
+                    ss.last_used = now_s();
+                } else {
+                    S->store.release(S->h_inst[s]);
+                }
+                S->active[s] = nullptr;
+                S->free_slots.push_back(s);
+                r->status = ADMM_ECANCELLED;
+                r->t_finish = now_s();
+                r->done = true;
+                any = true;
+            }
+            if (any) S->cv_done.notify_all();
+        }
         // queues of the active instances for this tick
         int nX = 0, nL = 0, nS = 0;
         std::vector<int> ids;
@@ -716,6 +739,27 @@ admm_status admm_server_submit_step(admm_server *S, int64_t session, const admm_
     S->pending.push_back(r);
     *ticket = r->ticket;
     S->cv_work.notify_one();
+    return ADMM_OK;
+}
+
+admm_status admm_server_cancel(admm_server *S, int64_t ticket)
+{
+    clear_last_error();
+    if (!S) return sfail(ADMM_EINVAL, "server is NULL");
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto it = S->reqs.find(ticket);
+    if (it == S->reqs.end()) return sfail(ADMM_EINVAL, "unknown ticket");
+    std::shared_ptr<Request> r = it->second;
+    if (r->done) return ADMM_OK;
+    r->cancel = true;
+    auto q = std::find(S->pending.begin(), S->pending.end(), r);
+    if (q != S->pending.end()) { // not admitted yet
+        S->pending.erase(q);
+        r->status = ADMM_ECANCELLED;
+        r->t_finish = now_s();
+        r->done = true;
+        S->cv_done.notify_all();
+    }
     return ADMM_OK;
 }
 

@@ -144,3 +144,21 @@ def test_round_robin_ticks_give_the_same_bits(capi):
         assert alone[t]["converged"] and mix[t]["converged"], t
         assert alone[t]["iters"] == mix[t]["iters"], t
         assert np.array_equal(alone[t]["x"], mix[t]["x"]), t
+
+
+def test_cancel_a_queued_and_a_running_request(capi):
+    long_par = PAR.replace(r_tol=0.0, s_tol=0.0, max_iter=5000)  # runs to the iteration cap
+    with capi.Server(long_par, max_active=1, tick_iters=5) as S:
+        running = S.submit(W.random_problem(4000, 3, 8, seed=91))
+        queued = S.submit(W.random_problem(300, 2, 2, seed=92))
+        time.sleep(0.2)
+        S.cancel(queued)
+        rq = S.poll(queued, wait_ms=2000)
+        assert rq is not None and rq["status"] == capi.ADMM_ECANCELLED
+        S.cancel(running)
+        rr = S.poll(running, wait_ms=10000)
+        assert rr is not None and rr["status"] == capi.ADMM_ECANCELLED
+    with capi.Server(PAR, max_active=1) as S:  # the server keeps serving after cancellations
+        t = S.submit(W.random_problem(300, 2, 2, seed=93))
+        r = wait_all(S, [t])[0]
+        assert r["converged"]
