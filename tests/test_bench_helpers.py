@@ -1,0 +1,44 @@
+"""Host-side helpers of bench.py: the algorithmic byte model (dense and
+scenario-shared maps) and the rule that ncu traffic is reported only for the
+kernel sources it was captured on."""
+import importlib.util
+import os
+
+from paper_1903_10041_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _bench():
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def test_bytes_per_iteration_counts_each_streamed_array_once():
+    b = _bench()
+    P = W.random_problem(1000, 3, 4)
+    m, q, n = 3, 4, 1000
+    assert b.bytes_per_iteration(P, "fp64") == 8 * (6 * m * q * n + 2 * m * n + 5 * q * n)
+    assert b.bytes_per_iteration(P, "mixed") == 4 * (6 * m * q * n + 2 * m * n + q * n) + 32 * q * n
+    S = W.shared_problem(1000, 3, 4)
+    # shared maps: f2 f1 g2 g1 once per (i, k) instead of per (i, j, k)
+    assert b.bytes_per_iteration(P, "fp64") - b.bytes_per_iteration(S, "fp64") == 8 * 4 * m * n * (q - 1)
+
+
+def test_traffic_is_reported_only_for_the_captured_sources():
+    b = _bench()
+    P = W.config(1)
+    key = (P.name, "fp64")
+    assert key in b.NCU_TRAFFIC
+    expect = b.NCU_TRAFFIC[key]["bytes_per_iter"] * 3330
+    if b.NCU_TRAFFIC[key]["src"] == b.kernel_source_hash():
+        assert b.traffic_per_launch(P, "fp64", 3330) == expect
+    saved = b.NCU_TRAFFIC[key]["src"]
+    try:
+        b.NCU_TRAFFIC[key]["src"] = "0" * 16  # a kernel changed since the capture
+        assert b.traffic_per_launch(P, "fp64", 3330) is None
+    finally:
+        b.NCU_TRAFFIC[key]["src"] = saved
+    assert b.traffic_per_launch(W.config(0), "fp64", 100) is None  # never captured
