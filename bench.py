@@ -47,7 +47,7 @@ def workload(cfg: int, precision: str, coef_shared: bool = False):
     from paper_1903_10041_gb300 import workloads as W
     P = W.config(cfg)
     if coef_shared:  # the same instance shape with scenario-shared cost and loss maps
-        P = W.shared_problem(P.n, P.m, P.q, name=f"config{cfg} shape, shared maps: n={P.n} m={P.m} q={P.q}")
+        P = W.shared_problem(P.n, P.m, P.q, name=f"shared maps n={P.n} m={P.m} q={P.q}")
     rho = (1.0, 1.0, 1.0, 1.0) if cfg == 0 else (1.0, 1.0 / P.n, 1.0, 1.0)
     par = W.Params(rho=rho, precision=precision)
     return P, par
@@ -58,10 +58,10 @@ def workload(cfg: int, precision: str, coef_shared: bool = False):
 # It is reported only while the kernel sources hash to the captured build.
 NCU_TRAFFIC = {
     ("phev n=1000 q=50", "fp64"): {"bytes_per_iter": (7.595264e6 + 0.055808e6) / 3330, "src": "1766275275686cf8",
-                                   "capture": "profiles/single_fp64_kernel_config1.md (whole 3330-iteration solve)"},
-    ("config2: plain n=1e5 m=4 q=20", "mixed"): {"bytes_per_iter": (4.317581824e9 + 1.382421760e9) / 20,
+                                   "capture": "profiles/single_fp64_kernel_phev_n1000_q50.md (whole 3330-iteration solve)"},
+    ("plain n=1e5 m=4 q=20", "mixed"): {"bytes_per_iter": (4.317581824e9 + 1.382421760e9) / 20,
                                                  "src": "1766275275686cf8",
-                                                 "capture": "profiles/single_mixed_kernel_config2.md (20 iterations)"},
+                                                 "capture": "profiles/single_mixed_kernel_plain_n1e5_m4_q20.md (20 iterations)"},
 }
 
 
@@ -110,7 +110,9 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.idx = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        import tempfile
+        out_dir = os.environ.get("ADMM_CLOCKS_DIR", tempfile.gettempdir())  # where the samples are kept
+        self.path = os.path.join(out_dir, f"clocks_rank{gpu_index}.csv")
 
     def __enter__(self):
         try:
@@ -258,7 +260,7 @@ def oracle_sample_errors(probs, par, results, states, idx, oracle):
 
 
 def run_batched(args):
-    """configs[3]: `count` instances of uneven n, m, q in one launch (mixed)."""
+    """The batched workload: `count` instances of uneven n, m, q in one launch (mixed)."""
     import numpy as np
     import torch
     rank, world, local = dist_init(args.gpus)
@@ -374,7 +376,7 @@ def run_batched(args):
 
 
 def run_serving(args):
-    """configs[4]: Poisson arrivals of receding-horizon re-solves of `count`
+    """The serving workload: Poisson arrivals of receding-horizon re-solves of `count`
     controllers sized as the batched workload; continuous batching."""
     import numpy as np
     import torch

@@ -248,9 +248,9 @@ def receding_step(p: Problem, step: int, seed: int = SEED) -> Problem:
 
 
 CONFIGS = {
-    0: lambda: random_problem(100, 2, 1, name="config0: plain n=100 m=2 q=1"),
+    0: lambda: random_problem(100, 2, 1, name="plain n=100 m=2 q=1"),
     1: lambda: phev_problem(1000, 50),
-    2: lambda: random_problem(100_000, 4, 20, name="config2: plain n=1e5 m=4 q=20"),
+    2: lambda: random_problem(100_000, 4, 20, name="plain n=1e5 m=4 q=20"),
 }
 
 

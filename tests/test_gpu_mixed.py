@@ -40,7 +40,7 @@ def _kkt(oracle, P, par, st, rho):
 
 
 CASES = {
-    "config0": lambda: (W.config(0), W.Params()),
+    "plain_n100_m2_q1": lambda: (W.config(0), W.Params()),
     "phev_n400_q12": lambda: (W.phev_problem(400, 12), W.Params(rho=(1.0, 1.0 / 400, 1.0, 1.0))),
     "plain_n2000_m4_q20": lambda: (W.random_problem(2000, 4, 20),
                                    W.Params(rho=(1.0, 1.0 / 2000, 1.0, 1.0))),

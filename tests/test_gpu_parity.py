@@ -74,7 +74,7 @@ def compare_states(P, st_o, rep_o, st_g, res, tol=TOL, check_res=True):
 
 
 @pytest.mark.parametrize("T", [1, 10, 100, 1000])
-def test_config0_fixed_iterations(capi, oracle_lib, T):
+def test_plain_n100_fixed_iterations(capi, oracle_lib, T):
     P = W.config(0)
     par = W.Params(max_iter=T, r_tol=0.0, s_tol=0.0)
     st_o, rep_o, st_g, res = run_both(capi, oracle_lib, P, par)
@@ -82,7 +82,7 @@ def test_config0_fixed_iterations(capi, oracle_lib, T):
     compare_states(P, st_o, rep_o, st_g, res)
 
 
-def test_config0_to_convergence(capi, oracle_lib):
+def test_plain_n100_to_convergence(capi, oracle_lib):
     P = W.config(0)
     par = W.Params()
     st_o, rep_o, st_g, res = run_both(capi, oracle_lib, P, par)
