@@ -47,7 +47,7 @@ typedef enum admm_status {
     ADMM_ECUDA = 3,          /* a CUDA runtime call failed */
     ADMM_ETIMEOUT = 4,       /* a bounded device-side wait gave up */
     ADMM_ENOTCONVERGED = 5,  /* max_iter reached; the result is still filled */
-    ADMM_EUNSUPPORTED = 6,   /* sizes beyond this build's limits */
+    ADMM_EUNSUPPORTED = 6,   /* sizes beyond the compiled limits (ADMM_MAX_M, ...) */
     ADMM_EPENDING = 7,       /* a served request has not finished yet */
     ADMM_ECANCELLED = 8      /* a served request was cancelled (admm_server_cancel) */
 } admm_status;
