@@ -171,9 +171,19 @@ def cpu_baseline(P, par, iters_per_solve: int, budget_s: float = 12.0):
     oracle.solve(P, par.replace(max_iter=T, r_tol=0.0, s_tol=0.0), threads=threads)
     dt = time.perf_counter() - t0
     sec_per_solve = dt / T * iters_per_solve
+    # the same on one core, on a shorter sample (about a quarter of the budget)
+    t0 = time.perf_counter()
+    oracle.solve(P, par.replace(max_iter=3, r_tol=0.0, s_tol=0.0), threads=1)
+    per_it1 = (time.perf_counter() - t0) / 3
+    T1 = max(5, min(iters_per_solve, int(0.25 * budget_s / max(per_it1, 1e-9))))
+    t0 = time.perf_counter()
+    oracle.solve(P, par.replace(max_iter=T1, r_tol=0.0, s_tol=0.0), threads=1)
+    dt1 = time.perf_counter() - t0
     return {"value": 1.0 / sec_per_solve, "unit": "solves/s", "cores": threads, "kind": "oracle",
+            "one_core": T1 / (dt1 * iters_per_solve),
             "sample": f"{T} of the {iters_per_solve} iterations of one solve ({dt:.2f} s), "
-                      f"scaled to a full solve; OpenMP over columns, {threads} threads"}
+                      f"scaled to a full solve; OpenMP over columns, {threads} threads "
+                      f"(one core: {T1} iterations, {dt1:.2f} s)"}
 
 
 def dist_init(n_gpus: int):
