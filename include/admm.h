@@ -185,7 +185,8 @@ admm_status admm_selftest_barrier_timeout(long long spin_ns, int grid, int *stat
  * (xmin_mode as in admm_params: the constrained minimiser, or the literal
  * Pi(argmin)).  Arrays are [count], host memory (on_device = 0: copied to
  * and from the device inside the call, the paper's timing with copies) or
- * device memory (on_device = 1); the caller owns them.  admm_quartic_min
+ * device memory (on_device = 1, checked: other pointers give ADMM_EINVAL);
+ * the caller owns them.  admm_quartic_min
  * uses the solver's FP64 minimiser; admm_quartic_min_f32 the mixed
  * solver's FP32 one (device arrays 8-byte aligned).  Runs on `stream` and
  * returns after it has finished.  Each element needs A >= 0, C > 0 when

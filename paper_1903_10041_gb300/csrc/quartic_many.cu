@@ -94,6 +94,17 @@ admm_status quartic_min_impl(const T *A, const T *B, const T *C, const T *D, con
     if (xmin_mode != ADMM_XMIN_EXACT && xmin_mode != ADMM_XMIN_PAPER)
         return set_last_error("bad xmin_mode"), ADMM_EINVAL;
     if (count == 0) return ADMM_OK;
+    if (on_device) { // the kernel dereferences these: they must be device-accessible
+        const void *ptrs[7] = {A, B, C, D, lo, hi, x};
+        for (const void *ptr : ptrs) {
+            cudaPointerAttributes at{};
+            if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess ||
+                (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)) {
+                cudaGetLastError(); // clear a sticky query error
+                return set_last_error("on_device = 1 but an array is not device memory"), ADMM_EINVAL;
+            }
+        }
+    }
     if (sizeof(T) == 4 && on_device &&
         ((uintptr_t)A | (uintptr_t)B | (uintptr_t)C | (uintptr_t)D | (uintptr_t)lo | (uintptr_t)hi | (uintptr_t)x) % 8)
         return set_last_error("FP32 device arrays must be 8-byte aligned"), ADMM_EINVAL;
