@@ -23,9 +23,10 @@ if not os.path.exists(LIB_PATH):
 _lib = C.CDLL(LIB_PATH)
 _dp = C.POINTER(C.c_double)
 
-ADMM_OK, ADMM_EINVAL, ADMM_ENOMEM, ADMM_ECUDA, ADMM_ETIMEOUT, ADMM_ENOTCONVERGED, ADMM_EUNSUPPORTED = range(7)
+(ADMM_OK, ADMM_EINVAL, ADMM_ENOMEM, ADMM_ECUDA, ADMM_ETIMEOUT, ADMM_ENOTCONVERGED, ADMM_EUNSUPPORTED,
+ ADMM_EPENDING, ADMM_ECANCELLED) = range(9)
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "ENOTCONVERGED",
-                6: "EUNSUPPORTED"}
+                6: "EUNSUPPORTED", 7: "EPENDING", 8: "ECANCELLED"}
 PRECISION = {"fp64": 0, "mixed": 1, "mixed_fp64cubic": 2}
 XMIN = {"exact": 0, "paper": 1}
 SWEEP = {"gauss_seidel": 0, "jacobi": 1}
@@ -513,12 +514,6 @@ class Batch:
 # ---------------------------------------------------------------------------
 # serving
 # ---------------------------------------------------------------------------
-ADMM_EPENDING = 7
-ADMM_ECANCELLED = 8
-STATUS_NAMES[7] = "EPENDING"
-STATUS_NAMES[8] = "ECANCELLED"
-
-
 class admm_server_config(C.Structure):
     _fields_ = [("store_elements", C.c_int64), ("max_active", C.c_int32), ("tick_iters", C.c_int32),
                 ("max_m", C.c_int32), ("max_q", C.c_int32), ("batch", admm_batch_config)]
@@ -550,7 +545,21 @@ _lib.admm_server_submit_step.restype = C.c_int
 
 
 class Server:
-    """Continuous-batching request loop (admm_server_* in admm.h)."""
+    """Continuous-batching request loop (admm_server_* in admm.h).
+
+    Requests are whole problems (``submit``) or receding-horizon steps of a
+    session whose instance stays resident on the device (``submit_step``).
+    A worker thread admits queued requests in arrival order into a device
+    store of ``store_elements`` elements (an instance takes m*q*ld, ld = n
+    rounded up to 4; at most ``max_active`` instances at once) and runs
+    ticks: one launch of the batched kernel over every active instance, in
+    which the costliest instance runs ``tick_iters`` iterations and the
+    others a time-balanced share.  Finished instances leave at the tick
+    boundary, so a request's result does not depend on which others shared
+    its ticks.  ``cancel`` ends a request with ADMM_ECANCELLED; ``poll`` and
+    ``drain`` return results; ``stats`` reports counters and GPU time.
+    Requests solve in the mixed-precision path.
+    """
 
     def __init__(self, par=None, store_elements=1 << 27, max_active=4096, tick_iters=10, max_m=4, max_q=20,
                  warps_per_cta=8, ctas_per_sm=0, small_max_elements=0, cluster_size=1,
