@@ -6,9 +6,11 @@ the PHEV-shaped robust instance (n = 1000 steps, m = 2 sources, q = 50
 scenarios; synthetic data, FP64), the whole loop in one persistent kernel.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--config 0|1|2] [--precision fp64|mixed|mixed_fp64cubic]
+                  [--config 0|1|2|3|4] [--precision fp64|mixed|mixed_fp64cubic]
+                  [--q-sweep 5,10,20,50,100,200,500] [--quartic N]
 
-Prints one JSON line.  `value` times K solves with inputs resident in HBM
+Prints one JSON line (one per scenario count with --q-sweep, the runtime
+against q comparison of Sec. IV-B).  `value` times K solves with inputs resident in HBM
 (CUDA events on the launch stream, L2 flushed between solves);
 `e2e` times the same solves through the public C ABI from pinned host
 buffers (create + solve + copy-out + destroy).  Under torchrun each rank
@@ -481,7 +483,7 @@ def run_serving(args):
 def config_dict(P, par, args):
     return {"workload": P.name + f" ({args.precision})", "n": P.n, "m": P.m, "q": P.q,
             "elements": P.elements, "rho": list(par.rho), "r_tol": par.r_tol, "s_tol": par.s_tol,
-            "check_every": par.check_every, "max_iter": par.max_iter,
+            "check_every": par.check_every, "max_iter": par.max_iter, "adapt_rho": bool(par.adapt_rho),
             "l2": "flushed between timed solves (512 MiB write)", "parallelism": f"replicas x{args.gpus}"}
 
 
@@ -591,7 +593,7 @@ def main():
     ap.add_argument("--rate", type=float, default=2000.0, help="Poisson arrival rate per second (4)")
     ap.add_argument("--tick-iters", type=int, default=10,
                     help="iterations per serving tick of the costliest active instance (4)")
-    ap.add_argument("--adapt", action="store_true", help="penalty adaptation of Sec. IV-A (3)")
+    ap.add_argument("--adapt", action="store_true", help="penalty adaptation of Sec. IV-A (3, --q-sweep)")
     ap.add_argument("--batch-config", default="",
                     help="warps,ctas_per_sm,small_max,cluster,cluster_min instead of the autotuner (3, 4)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "mixed_fp64cubic"])
@@ -601,6 +603,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--coef-shared", action="store_true",
                     help="--config 1 or 2: scenario-shared cost and loss maps ([m][n] coefficients)")
+    ap.add_argument("--q-sweep", default="",
+                    help="comma-separated scenario counts (e.g. 5,10,20,50,100,200,500): one line per q for the "
+                         "n=1000 PHEV instance, runtime against q as in Sec. IV-B")
     ap.add_argument("--quartic", type=int, default=0,
                     help="N > 0: the quartic benchmark of Sec. III-C on N quartics instead of a solve")
     args = ap.parse_args()
@@ -613,7 +618,6 @@ def main():
     if args.config in (3, 4):
         return run_batched(args) if args.config == 3 else run_serving(args)
 
-    import numpy as np
     import torch
     rank, world, local = dist_init(args.gpus)
     assert torch.cuda.is_available(), "bench.py needs a CUDA GPU"
@@ -622,9 +626,38 @@ def main():
         build.build()
     if world > 1:
         torch.distributed.barrier()
-    from paper_1903_10041_gb300 import capi
+    if args.q_sweep:
+        for P, par in sweep_workloads(args.q_sweep, args.precision, args.adapt):
+            run_single(args, P, par, rank, world, local)
+    else:
+        P, par = workload(args.config, args.precision, args.coef_shared)
+        run_single(args, P, par, rank, world, local)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
 
-    P, par = workload(args.config, args.precision, args.coef_shared)
+
+def sweep_workloads(spec: str, precision: str, adapt: bool):
+    """The PHEV-shaped instance (n = 1000, m = 2) at each scenario count of a
+    comma-separated list, with the penalties of the q = 50 case: the runtime
+    against q sweep of Sec. IV-B (q from 5 to 500 there)."""
+    from paper_1903_10041_gb300 import workloads as W
+    out = []
+    for tok in spec.split(","):
+        q = int(tok)
+        if q < 1:
+            raise ValueError(f"scenario count {q} < 1")
+        P = W.phev_problem(1000, q)
+        out.append((P, W.Params(rho=(1.0, 1.0 / P.n, 1.0, 1.0), precision=precision, adapt_rho=adapt)))
+    return out
+
+
+def run_single(args, P, par, rank, world, local):
+    """Times K single-instance solves of P (one persistent-kernel launch
+    each) and prints one JSON line."""
+    import numpy as np
+    import torch
+    from paper_1903_10041_gb300 import capi
     if args.max_iter:
         par = par.replace(max_iter=args.max_iter)
     stream = torch.cuda.Stream()
@@ -704,8 +737,8 @@ def main():
                "d2h_bytes_per_step": d2h}
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.config != 2:
-        cpu = cpu_baseline(P, par, iters)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and (args.config != 2 or args.q_sweep):
+        cpu = cpu_baseline(P, par, iters, budget_s=4.0 if args.q_sweep else 12.0)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
@@ -719,11 +752,8 @@ def main():
                 "gpu_launches": args.steps,
                 "profiling_cap": args.max_iter or None,
                 "clocks": clk.summary()}
-        print(json.dumps(line))
+        print(json.dumps(line), flush=True)
     solver.close()
-    if world > 1:
-        torch.distributed.destroy_process_group()
-    return 0
 
 
 if __name__ == "__main__":

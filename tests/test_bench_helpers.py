@@ -42,3 +42,22 @@ def test_traffic_is_reported_only_for_the_captured_sources():
     finally:
         b.NCU_TRAFFIC[key]["src"] = saved
     assert b.traffic_per_launch(W.config(0), "fp64", 100) is None  # never captured
+
+
+def test_q_sweep_workloads_are_the_phev_instance_at_each_scenario_count():
+    import numpy as np
+    import pytest
+    b = _bench()
+    sweep = b.sweep_workloads("5,50,500", "fp64", True)
+    assert [P.q for P, _ in sweep] == [5, 50, 500]
+    for P, par in sweep:
+        assert (P.n, P.m) == (1000, 2) and P.f2.shape == (2, P.q, 1000)
+        assert par.adapt_rho and par.rho == (1.0, 1e-3, 1.0, 1.0)
+    # q = 50 is the headline PHEV instance itself, with its penalties
+    P50, par50 = sweep[1]
+    C1, cpar = b.workload(1, "fp64")
+    assert P50.name == C1.name and par50.rho == cpar.rho
+    for k, v in C1.arrays().items():
+        np.testing.assert_array_equal(getattr(P50, k), v)
+    with pytest.raises(ValueError):
+        b.sweep_workloads("5,0", "fp64", False)
