@@ -55,3 +55,26 @@ def test_struct_layouts_match_the_header(lib):
     assert ctypes.sizeof(capi.admm_params) == 8 * 7 + 4 * 6 + 4 * 4
     assert ctypes.sizeof(capi.admm_problem) == 16 + 8 * 10 + 8
     assert ctypes.sizeof(capi.admm_state) == 8 * 9 + 8 * 4 + 8
+
+
+def test_binding_refuses_to_load_without_the_library(tmp_path):
+    """No CPU fallback: the binding raises ImportError when libadmm.so is
+    absent beside it, instead of running anything else."""
+    import importlib.util
+    import shutil
+    src = os.path.join(ROOT, "paper_1903_10041_gb300", "capi.py")
+    shutil.copy(src, tmp_path / "capi.py")
+    spec = importlib.util.spec_from_file_location("capi_without_lib", tmp_path / "capi.py")
+    mod = importlib.util.module_from_spec(spec)
+    with pytest.raises(ImportError, match="no fallback"):
+        spec.loader.exec_module(mod)
+
+
+def test_status_codes_match_the_header():
+    from paper_1903_10041_gb300 import capi
+    txt = open(os.path.join(ROOT, "include", "admm.h")).read()
+    codes = {m.group(1): int(m.group(2)) for m in re.finditer(r"\b(ADMM_[A-Z]+)\s*=\s*(\d+)", txt)}
+    for name in ("ADMM_OK", "ADMM_EINVAL", "ADMM_ENOMEM", "ADMM_ECUDA", "ADMM_ETIMEOUT", "ADMM_ENOTCONVERGED",
+                 "ADMM_EUNSUPPORTED", "ADMM_EPENDING", "ADMM_ECANCELLED"):
+        assert getattr(capi, name) == codes[name], name
+        assert capi.STATUS_NAMES[codes[name]] == name[len("ADMM_"):]

@@ -283,3 +283,21 @@ def test_dual_residual_bounds_z_stationarity_violation(oracle_lib):
         assert rep["sigma"] >= viol * (1 - 1e-9) - 1e-14
         equal += abs(rep["sigma"] - viol) <= 1e-9 * viol
     assert equal >= 1
+
+
+def test_penalty_change_keeps_a_fixed_point(oracle_lib):
+    """The scaled duals lambda, p, mu, nu carry a factor 1/rho, so the
+    rescaling that goes with a Sec. IV-A penalty change (reading R11) keeps
+    the unscaled multipliers, and with them a fixed point of the iteration:
+    once converged, further iterations under repeated penalty changes leave x
+    where it is.  A missing or inverted rescaling moves it by O(1)."""
+    P = W.random_problem(60, 2, 3, seed=17)
+    par = W.Params(rho=(1.0, 1.0 / 60, 1.0, 1.0), r_tol=1e-11, s_tol=1e-11, max_iter=200000)
+    st, rep = oracle_lib.solve(P, par)
+    assert rep["converged"]
+    # thresholds that are never met, so the ratio test changes rho at every check
+    cont = par.replace(adapt_rho=True, r_tol=1e-30, s_tol=1e-30, check_every=1, max_iter=40)
+    st2, rep2 = oracle_lib.solve(P, cont, state=st)
+    assert abs(math.log(rep2["rho"][0])) > 5 * math.log(1.1)  # several changes took place
+    assert np.abs(st2["x"] - st["x"]).max() < 1e-8
+    assert rep2["r"] < 1e-10 and rep2["sigma"] < 1e-10
