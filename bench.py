@@ -37,12 +37,33 @@ L2_FLUSH_BYTES = 512 << 20  # > 126 MB L2
 # FP64 peak of GB300 derived from unit counts and clock: 152 SMs x 2 DFMA/clk
 # per SM x 2 flop x 2.07 GHz (the measured DFMA rate is 1.90/clk/SM).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
-# Conventional FP64 flop count of one element update of the FP64 kernel on
-# the Cardano branch (each +, -, *, /, sqrt, cbrt counts 1, an FMA 2); the
-# breakdown is in the design doc.
-FLOPS_PER_ELEMENT = 71
-# column work shared by the m elements of a column (sums, s, mu, residuals)
-FLOPS_PER_COLUMN = 12
+# Conventional FP64 flops of one iteration of the FP64 kernel, counted from
+# its element update (each +, -, *, /, sqrt and cube root counts 1, an FMA 2;
+# comparisons and clamps 0):
+#   every element: the sum over the other sources (m - 1), phi (3), the
+#     lossless parts of C and D (6), its share of the column sums of x and
+#     x - x~ (3);
+#   an element with losses (beta_2 or beta_1 nonzero) adds g(x~), u, A, B
+#     and the loss terms of C and D (21), Algorithm 1 on its Cardano branch
+#     (29: one division, the scaled coefficients b, c, d, Q, R, Delta, the
+#     square root, the cube root with its reciprocal, S + T - b/3) and g(x)
+#     with its sum over k (5); the trig branch costs more and is counted as
+#     Cardano;
+#   a lossless element (g = beta_0) takes the quadratic case x = -D / 2C (3);
+#   every column: v and mu of steps (e), (f) (5).
+FLOPS_LOSS_TERMS = 21 + 29 + 5
+FLOPS_QUADRATIC = 3
+FLOPS_PER_COLUMN = 5
+
+
+def fp64_flops_per_iteration(P) -> int:
+    import numpy as np
+    lossy = int(np.count_nonzero((np.asarray(P.g2) != 0) | (np.asarray(P.g1) != 0)))
+    if getattr(P, "coef_shared", False):  # maps given once per (i, k) for every scenario
+        lossy *= P.q
+    common = (P.m - 1) + 3 + 6 + 3
+    return (P.elements * common + lossy * FLOPS_LOSS_TERMS + (P.elements - lossy) * FLOPS_QUADRATIC
+            + FLOPS_PER_COLUMN * P.q * P.n)
 
 
 def workload(cfg: int, precision: str, coef_shared: bool = False):
@@ -696,9 +717,8 @@ def run_single(args, P, par, rank, world, local):
 
     # ---- roofline of the solve kernel (one launch = one solve) ------------
     per_launch_s = total_ms / args.steps / 1e3
-    cols = P.q * P.n
     if args.precision == "fp64":
-        flops = iters * (FLOPS_PER_ELEMENT * P.elements + FLOPS_PER_COLUMN * cols)
+        flops = iters * fp64_flops_per_iteration(P)
         achieved = flops / per_launch_s / 1e12
         roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic_per_launch(P, "fp64", iters),

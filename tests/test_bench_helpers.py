@@ -61,3 +61,15 @@ def test_q_sweep_workloads_are_the_phev_instance_at_each_scenario_count():
         np.testing.assert_array_equal(getattr(P50, k), v)
     with pytest.raises(ValueError):
         b.sweep_workloads("5,0", "fp64", False)
+
+
+def test_fp64_flop_count_follows_the_branch_each_element_takes():
+    """Elements with losses run Algorithm 1 (68 counted flops at m = 2);
+    lossless ones (the PHEV engine, g = 0) the quadratic case (16)."""
+    b = _bench()
+    P = W.config(1)  # engine lossless, battery lossy
+    assert b.fp64_flops_per_iteration(P) == 68 * 50_000 + 16 * 50_000 + 5 * 50 * 1000
+    Q = W.random_problem(100, 2, 3)  # every element has losses
+    assert b.fp64_flops_per_iteration(Q) == 68 * 600 + 5 * 300
+    S = W.shared_problem(100, 3, 4)
+    assert b.fp64_flops_per_iteration(S) == b.fp64_flops_per_iteration(S.dense())
