@@ -116,3 +116,24 @@ def test_paper_mode_clamps_the_global_minimiser(oracle_lib):
     xp, _ = oracle_lib.quartic_min(A, B, Cc, D, -2.0, 3.0, mode="paper")
     xe, _ = oracle_lib.quartic_min(A, B, Cc, D, -2.0, 3.0, mode="exact")
     assert abs(xp - 2.0) < 1e-12 and xp == xe
+
+
+def _golden_quartics():
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "quartic_cases.txt")
+    rows = [line.split() for line in open(path) if line.strip() and not line.startswith("#")]
+    br = np.array([int(r[0]) for r in rows])
+    v = np.array([[float(t) for t in r[1:]] for r in rows])
+    return br, v
+
+
+def test_golden_quartics_with_exact_minimisers(oracle_lib):
+    """tests/golden/quartic_cases.txt: minimisers fixed by factorised
+    derivatives in exact arithmetic, every branch of Algorithm 1 with and
+    without clamping, and the exact tie of the symmetric double well."""
+    br, v = _golden_quartics()
+    assert set(br.tolist()) == {0, 1, 2, 3} and len(br) >= 60
+    x, branch = oracle_lib.quartic_min(*[v[:, t] for t in range(6)])
+    want = v[:, 6]
+    assert np.array_equal(branch, br)
+    assert np.abs(x - want).max() <= 1e-12 * max(1.0, np.abs(want).max())
