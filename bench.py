@@ -80,10 +80,10 @@ def workload(cfg: int, precision: str, coef_shared: bool = False):
 # kernel per iteration, from one ncu capture of each workload (profiles/).
 # It is reported only while the kernel sources hash to the captured build.
 NCU_TRAFFIC = {
-    ("phev n=1000 q=50", "fp64"): {"bytes_per_iter": (7.595264e6 + 0.055808e6) / 3330, "src": "4e081105e8d7e187",
+    ("phev n=1000 q=50", "fp64"): {"bytes_per_iter": (7.595264e6 + 0.055808e6) / 3330, "src": "965ff8b0533d4c28",
                                    "capture": "profiles/single_fp64_kernel_phev_n1000_q50.md (whole 3330-iteration solve)"},
     ("plain n=1e5 m=4 q=20", "mixed"): {"bytes_per_iter": (4.317581824e9 + 1.382421760e9) / 20,
-                                                 "src": "4e081105e8d7e187",
+                                                 "src": "965ff8b0533d4c28",
                                                  "capture": "profiles/single_mixed_kernel_plain_n1e5_m4_q20.md (20 iterations)"},
 }
 

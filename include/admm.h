@@ -254,7 +254,13 @@ typedef struct admm_batch_config {
  * fastest on mixed workloads of 50..400k elements), no clusters. */
 admm_status admm_batch_create(const admm_problem *probs, int32_t count, const admm_params *params,
                               admm_batch **out);
+/* Replaces the launch configuration (used from the next admm_batch_solve;
+ * instance state is kept).  ADMM_EINVAL for warps_per_cta not 4, 8 or 16,
+ * cluster_size not 1, 2, 4 or 8, a negative setting or reserved != 0;
+ * ADMM_EUNSUPPORTED if clusters of that size cannot be co-resident. */
 admm_status admm_batch_set_config(admm_batch *b, const admm_batch_config *cfg);
+/* The configuration in use; ctas_per_sm reports the resident CTAs per SM
+ * actually launched. */
 admm_status admm_batch_get_config(admm_batch *b, admm_batch_config *cfg);
 /* Times each candidate configuration (warps per CTA x team thresholds x
  * cluster size) on
@@ -270,11 +276,15 @@ admm_status admm_batch_solve(admm_batch *b, void *stream);
 admm_status admm_batch_wait(admm_batch *b, void *stream, admm_result *results);
 /* Per-instance record as in admm_get_info (valid after admm_batch_wait). */
 admm_status admm_batch_get_info(admm_batch *b, int32_t idx, double *info, int32_t count);
+/* Copies instance idx's state into `out` as FP64 arrays (layouts as in
+ * admm_state; host or device buffers by out->on_device; NULL arrays are
+ * skipped).  Synchronous.  ADMM_EINVAL for a bad idx. */
 admm_status admm_batch_get_state(admm_batch *b, int32_t idx, admm_state *out);
 /* Loads a state (e.g. a warm start) into instance idx and marks it unfinished. */
 admm_status admm_batch_set_state(admm_batch *b, int32_t idx, const admm_state *in);
 /* Every instance back to the zero start; records cleared. */
 admm_status admm_batch_reset(admm_batch *b);
+/* Frees everything the batch owns; NULL is accepted. */
 admm_status admm_batch_destroy(admm_batch *b);
 
 /* ---- Serving: continuous batching of re-solves --------------------------
@@ -303,6 +313,13 @@ typedef struct admm_server_config {
 /* store 2^27 elements, 4096 active, 10 iterations per tick, max_m 4,
  * max_q 20, 8 warps per CTA, small_max_elements 0, no clusters. */
 void admm_server_default_config(admm_server_config *cfg);
+/* Allocates the device store and tables and starts the worker thread on
+ * the current device.  ADMM_EUNSUPPORTED unless params->precision is
+ * ADMM_MIXED; ADMM_EINVAL for rho <= 0 or a configuration out of range
+ * (max_active, tick_iters, max_m, max_q < 1; m*q > ADMM_BATCH_MAX_PAIRS;
+ * store_elements < 1024; batch settings as in admm_batch_set_config);
+ * ADMM_ENOMEM / ADMM_ECUDA if an allocation or CUDA call fails, with
+ * nothing left allocated. */
 admm_status admm_server_create(const admm_params *params, const admm_server_config *cfg, admm_server **out);
 /* Validates and queues a request; session >= 0 ties it to that session
  * (warm start from the session's resident state when the shapes match),
@@ -346,11 +363,14 @@ admm_status admm_server_stats(admm_server *s, double *stats, int32_t count);
  * ADMM_ECANCELLED and no x.  A finished request is left as it is.
  * ADMM_EINVAL for an unknown ticket. */
 admm_status admm_server_cancel(admm_server *s, int64_t ticket);
-/* Stops the worker (in-flight requests are dropped) and frees everything. */
+/* Stops the worker (in-flight requests are dropped) and frees everything;
+ * NULL is accepted. */
 admm_status admm_server_destroy(admm_server *s);
 
 /* Message of the last failing call on this thread ("" if none). */
 const char *admm_last_error(void);
+/* Short English description of a status code ("ok", "invalid argument",
+ * ...); a static string. */
 const char *admm_status_string(admm_status s);
 
 #ifdef __cplusplus

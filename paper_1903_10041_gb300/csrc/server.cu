@@ -556,6 +556,9 @@ admm_status admm_server_create(const admm_params *prm, const admm_server_config 
     if (cfg->batch.cluster_size != 1 && cfg->batch.cluster_size != 2 && cfg->batch.cluster_size != 4 &&
         cfg->batch.cluster_size != 8)
         return sfail(ADMM_EINVAL, "cluster_size must be 1, 2, 4 or 8");
+    if (cfg->batch.ctas_per_sm < 0 || cfg->batch.small_max_elements < 0 || cfg->batch.cluster_min_elements < 0)
+        return sfail(ADMM_EINVAL, "negative setting");
+    if (cfg->batch.reserved) return sfail(ADMM_EINVAL, "reserved must be 0");
     for (int t = 0; t < 4; ++t)
         if (!(prm->rho[t] > 0.0)) return sfail(ADMM_EINVAL, "rho must be > 0");
     admm_server *S = new admm_server();

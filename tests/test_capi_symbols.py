@@ -78,3 +78,32 @@ def test_status_codes_match_the_header():
                  "ADMM_EUNSUPPORTED", "ADMM_EPENDING", "ADMM_ECANCELLED"):
         assert getattr(capi, name) == codes[name], name
         assert capi.STATUS_NAMES[codes[name]] == name[len("ADMM_"):]
+
+
+def test_batch_and_server_creation_validate_on_the_host():
+    """Bad arguments are refused before any device call (no GPU needed)."""
+    from paper_1903_10041_gb300 import capi
+    p = capi.admm_default_params()
+    p.precision = capi.PRECISION["mixed"]
+    cfg = capi.admm_server_config()
+    capi._lib.admm_server_default_config(ctypes.byref(cfg))
+    h = capi._S()
+    assert capi._lib.admm_server_create(None, ctypes.byref(cfg), ctypes.byref(h)) == capi.ADMM_EINVAL
+    for field, bad in (("reserved", 1), ("small_max_elements", -1), ("cluster_size", 3), ("warps_per_cta", 6)):
+        c2 = capi.admm_server_config()
+        ctypes.pointer(c2)[0] = cfg
+        setattr(c2.batch, field, bad)
+        assert capi._lib.admm_server_create(ctypes.byref(p), ctypes.byref(c2), ctypes.byref(h)) == capi.ADMM_EINVAL
+        assert not h.value
+    for field, bad in (("max_active", 0), ("tick_iters", 0), ("max_m", capi.MAX_M + 1)):
+        c2 = capi.admm_server_config()
+        ctypes.pointer(c2)[0] = cfg
+        setattr(c2, field, bad)
+        assert capi._lib.admm_server_create(ctypes.byref(p), ctypes.byref(c2), ctypes.byref(h)) == capi.ADMM_EINVAL
+    p64 = capi.admm_default_params()  # FP64: the server runs the mixed path only
+    assert capi._lib.admm_server_create(ctypes.byref(p64), ctypes.byref(cfg), ctypes.byref(h)) == \
+        capi.ADMM_EUNSUPPORTED
+    b = capi._B()
+    assert capi._lib.admm_batch_create(None, 1, ctypes.byref(p), ctypes.byref(b)) == capi.ADMM_EINVAL
+    assert capi._lib.admm_batch_destroy(None) == capi.ADMM_OK
+    assert capi._lib.admm_server_destroy(None) == capi.ADMM_OK
