@@ -301,3 +301,46 @@ def test_penalty_change_keeps_a_fixed_point(oracle_lib):
     assert abs(math.log(rep2["rho"][0])) > 5 * math.log(1.1)  # several changes took place
     assert np.abs(st2["x"] - st["x"]).max() < 1e-8
     assert rep2["r"] < 1e-10 and rep2["sigma"] < 1e-10
+
+
+def test_kkt_residual_reports_each_kind_of_violation(oracle_lib):
+    """The KKT residual is the bar the mixed-precision results are held to,
+    so each of its terms must respond to the violation it measures: starting
+    from a converged iterate, break one condition of eq. (2) or one dual
+    condition at a time and check that its term (and the max) rises."""
+    P = W.random_problem(25, 2, 5, seed=34)
+    par = W.Params(rho=(1.0, 1.0 / 25, 1.0, 1.0), r_tol=1e-9, s_tol=1e-9, max_iter=200000)
+    st, rep = oracle_lib.solve(P, par)
+    assert rep["converged"]
+    k0, t0 = oracle_lib.kkt(P, par, st)
+    assert k0 < 1e-7, t0
+    sx = st["x"].sum(axis=0)                               # [q, n]
+    gsum = (P.g2 * st["x"] ** 2 + P.g1 * st["x"] + P.g0).sum(axis=2)  # [m, q]
+
+    def term(t, st2=None, P2=None):
+        k, tt = oracle_lib.kkt(P2 or P, par, st2 or st)
+        assert k >= tt[t] and k == tt.max()
+        return tt[t]
+
+    def edit(**arrs):
+        s2 = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in st.items()}
+        for k, f in arrs.items():
+            f(s2[k])
+        return s2
+
+    lo, hi = P.lo[:, None, :], P.hi[:, None, :]
+    i, j, k = np.argwhere((st["x"] > lo + 0.05) & (st["x"] < hi - 0.05) &
+                          (np.arange(P.n)[None, None, :] > 0))[0]
+    assert term(0, edit(x=lambda a: a.__setitem__((i, j, k), a[i, j, k] + 0.02))) > 1e-4   # stationarity
+    jb, kb = np.argwhere(st["mu"] > 1e-3)[0]                # a binding demand (eta > 0)
+    assert term(1, edit(x=lambda a: a.__setitem__((slice(None), jb, kb), a[:, jb, kb] - 0.05))) > 0.05
+    P2 = P.copy()
+    P2.c = 0.5 * gsum.min(axis=1)
+    assert term(2, P2=P2) > 0.1                             # capacity infeasible
+    assert term(3, edit(x=lambda a: a.__setitem__((0, 1, 0), a[0, 1, 0] + 0.1))) > 0.09     # copies differ
+    js, ks = np.argwhere(sx - P.y > 0.05)[0]                # a slack demand
+    assert term(4, edit(mu=lambda a: a.__setitem__((js, ks), 1.0))) > 0.04                 # eta (sum x - y) != 0
+    ic, jc = np.argwhere(gsum < P.c[:, None] - 0.05)[0]     # a slack capacity
+    assert term(5, edit(p=lambda a: a.__setitem__((ic, jc), -25.0))) > 0.04               # gamma (c - sum g) != 0
+    assert term(6, edit(mu=lambda a: a.__setitem__((0, 0), -0.5))) >= 0.5                  # eta < 0
+    assert term(7, edit(nu=lambda a: a.__setitem__((0, 0), a[0, 0] + 0.5))) >= 0.5 - 1e-12  # sum_j omega != 0
