@@ -344,3 +344,30 @@ def test_kkt_residual_reports_each_kind_of_violation(oracle_lib):
     assert term(5, edit(p=lambda a: a.__setitem__((ic, jc), -25.0))) > 0.04               # gamma (c - sum g) != 0
     assert term(6, edit(mu=lambda a: a.__setitem__((0, 0), -0.5))) >= 0.5                  # eta < 0
     assert term(7, edit(nu=lambda a: a.__setitem__((0, 0), a[0, 0] + 0.5))) >= 0.5 - 1e-12  # sum_j omega != 0
+
+
+def test_residual_terms_equal_the_dual_increments(oracle_lib, small):
+    """In scaled form each dual step adds the residual of its constraint
+    (steps (f)-(i)), so the primal residual terms of App. A are the largest
+    dual increments of the same iteration: demand |s - sum x + y| = |d mu|,
+    losses |z - g(x)| = |d lambda|, capacity copies |h - 1'z| = |d p|, x_1
+    copies |x_1^(i,j) - x_1^(i)| = |d nu|; and the demand dual-residual term
+    rho3 |d s - sum d x| = rho3 |d mu - d mu_prev| (the change between two
+    consecutive increments of mu, since y is fixed)."""
+    rho = (1.3, 0.4, 0.7, 1.1)
+    par = W.Params(rho=rho, max_iter=1, r_tol=0.0, s_tol=0.0, check_every=1)
+    P = small.copy()
+    P.c = 0.3 * P.c  # binding capacities, so that h is clipped and p moves
+    st0 = _random_state(P, 77)
+    st1, _ = oracle_lib.solve(P, par, state=st0)
+    st2, rep = oracle_lib.solve(P, par, state=st1)
+    r_mu, r_lam, r_p, r_nu = rep["r_terms"]
+    d = {k: st2[k] - st1[k] for k in ("mu", "lam", "p", "nu")}
+    assert r_mu == pytest.approx(np.abs(d["mu"]).max(), rel=1e-12, abs=1e-14)
+    assert r_lam == pytest.approx(np.abs(d["lam"]).max(), rel=1e-12, abs=1e-14)
+    assert r_p == pytest.approx(np.abs(d["p"]).max(), rel=1e-12, abs=1e-14)
+    assert r_nu == pytest.approx(np.abs(d["nu"]).max(), rel=1e-12, abs=1e-14)
+    assert min(r_mu, r_lam, r_p, r_nu) > 1e-6  # a non-trivial iterate
+    second = (st2["mu"] - st1["mu"]) - (st1["mu"] - st0["mu"])
+    assert rep["s_terms"][2] == pytest.approx(rho[2] * np.abs(second).max(), rel=1e-12, abs=1e-14)
+    assert rep["s_terms"][2] > 1e-6
