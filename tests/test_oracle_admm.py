@@ -371,3 +371,21 @@ def test_residual_terms_equal_the_dual_increments(oracle_lib, small):
     second = (st2["mu"] - st1["mu"]) - (st1["mu"] - st0["mu"])
     assert rep["s_terms"][2] == pytest.approx(rho[2] * np.abs(second).max(), rel=1e-12, abs=1e-14)
     assert rep["s_terms"][2] > 1e-6
+
+
+@pytest.mark.parametrize("band", ["grow", "hold", "shrink"])
+def test_penalty_adaptation_follows_the_ratio_rule(oracle_lib, band):
+    """Sec. IV-A: every rho_t grows by tau when r / sigma > 1.2 rbar/sbar,
+    shrinks by tau when r / sigma < 0.8 rbar/sbar, and stays in between.  The
+    first check (after 10 iterations) decides the penalties used from
+    iteration 11 on; thresholds far below reach are chosen so that no stop
+    intervenes, with rbar/sbar placed relative to the observed ratio."""
+    P = W.random_problem(30, 2, 3, seed=21)
+    rho0 = (1.0, 1.0 / 30, 1.0, 1.0)
+    base = W.Params(rho=rho0, r_tol=1e-30, s_tol=1e-30, check_every=10, adapt_rho=True, tau=1.1)
+    _, rep10 = oracle_lib.solve(P, base.replace(max_iter=10))  # the last iteration never adapts
+    assert rep10["rho"] == list(rho0)
+    ratio = rep10["r"] / rep10["sigma"]
+    target, f = {"grow": (ratio / 1.5, 1.1), "hold": (ratio, 1.0), "shrink": (ratio / 0.6, 1.0 / 1.1)}[band]
+    _, rep20 = oracle_lib.solve(P, base.replace(max_iter=20, r_tol=target * 1e-30))
+    assert rep20["rho"] == pytest.approx([f * r for r in rho0], rel=1e-15)
