@@ -27,11 +27,6 @@ def capi():
     return capi
 
 
-def _oracle_state_of(st):
-    """GPU state -> the oracle's dense state (z, lambda rebuilt from zeta, lam)."""
-    return st
-
-
 def _kkt(oracle, P, par, st, rho):
     m, q, n = P.m, P.q, P.n
     dense = {"x": st["x"], "z": np.zeros((m, q, n)), "lam": np.broadcast_to(st["lam"][:, :, None], (m, q, n)).copy(),
