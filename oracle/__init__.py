@@ -15,7 +15,6 @@ check_every, xmin_mode, sweep) will do.
 from __future__ import annotations
 
 import ctypes as C
-import os
 
 import numpy as np
 
