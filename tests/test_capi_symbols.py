@@ -107,3 +107,21 @@ def test_batch_and_server_creation_validate_on_the_host():
     assert capi._lib.admm_batch_create(None, 1, ctypes.byref(p), ctypes.byref(b)) == capi.ADMM_EINVAL
     assert capi._lib.admm_batch_destroy(None) == capi.ADMM_OK
     assert capi._lib.admm_server_destroy(None) == capi.ADMM_OK
+
+
+def test_plain_c_client_builds_and_runs(lib, tmp_path):
+    """The boundary is usable from C99 alone: tests/c_abi_host.c compiles
+    against include/admm.h, links libadmm.so and makes the host-only calls."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    so = lib._name
+    exe = tmp_path / "c_abi_host"
+    subprocess.run([cc, "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
+                    os.path.join(ROOT, "tests", "c_abi_host.c"), so, "-lm",
+                    "-Wl,-rpath," + os.path.dirname(so), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert out.returncode == 0, out.stderr
+    assert "c client ok" in out.stdout
