@@ -389,3 +389,34 @@ def test_penalty_adaptation_follows_the_ratio_rule(oracle_lib, band):
     target, f = {"grow": (ratio / 1.5, 1.1), "hold": (ratio, 1.0), "shrink": (ratio / 0.6, 1.0 / 1.1)}[band]
     _, rep20 = oracle_lib.solve(P, base.replace(max_iter=20, r_tol=target * 1e-30))
     assert rep20["rho"] == pytest.approx([f * r for r in rho0], rel=1e-15)
+
+
+def test_objective_invariances(oracle_lib):
+    """The objective of eq. (2) is the scenario mean of the nominal cost (1):
+    q identical scenarios give the nominal value; shifting every f0 by d
+    shifts it by n m d; it is linear in (f2, f1, f0) jointly."""
+    rng = np.random.default_rng(5)
+    P1 = W.random_problem(40, 3, 1, seed=61)
+    x1 = rng.uniform(P1.lo[:, None, :], P1.hi[:, None, :], (3, 1, 40))
+    q = 7
+    Pq = P1.copy()
+    for k in ("f2", "f1", "f0", "g2", "g1", "g0"):
+        setattr(Pq, k, np.repeat(getattr(P1, k), q, axis=1))
+    Pq.y = np.repeat(P1.y, q, axis=0)
+    Pq.q = q
+    xq = np.repeat(x1, q, axis=1)
+    v1 = oracle_lib.objective(P1, x1)
+    assert oracle_lib.objective(Pq, xq) == pytest.approx(v1, rel=1e-13)
+    Ps = Pq.copy()
+    Ps.f0 = Pq.f0 + 0.25
+    assert oracle_lib.objective(Ps, xq) - oracle_lib.objective(Pq, xq) == pytest.approx(40 * 3 * 0.25, rel=1e-12)
+    P2 = Pq.copy()
+    P2.f2, P2.f1, P2.f0 = 2 * Pq.f2, 2 * Pq.f1, 2 * Pq.f0
+    assert oracle_lib.objective(P2, xq) == pytest.approx(2 * oracle_lib.objective(Pq, xq), rel=1e-13)
+    assert abs(v1) > 1.0  # non-trivial value
+    # a quadratic in every element: the second difference along a uniform
+    # shift h is 2 h^2 sum(f2) / q, whatever the point
+    h = 0.5
+    d2 = (oracle_lib.objective(Pq, xq + h) - 2 * oracle_lib.objective(Pq, xq) +
+          oracle_lib.objective(Pq, xq - h))
+    assert d2 == pytest.approx(2 * h * h * Pq.f2.sum() / q, rel=1e-10)
