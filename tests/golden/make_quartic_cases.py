@@ -6,6 +6,7 @@ follows from the mathematics, not from any solver:
     f(x) = A x^4 + B x^3 + C x^2 + D x,   f'(x) = 4A x^3 + 3B x^2 + 2C x + D.
 
 - three real roots r1 < r2 < r3:  f'(x) = 4A (x - r1)(x - r2)(x - r3);
+- a double root r and a simple t: f'(x) = 4A (x - r)^2 (x - t);
 - one real root r:                f'(x) = 4A (x - r)(x^2 + p x + s), p^2 < 4s;
 - triple root r:                  f(x) = A (x - r)^4 minus its constant;
 - quadratic (A = B = 0):          f(x) = C x^2 + D x, C > 0.
@@ -17,7 +18,9 @@ roots of f' inside the interval; equal values keep the smaller point (the
 tie rule of Algorithm 1, Sec. III-B, kept after clamping).  The branch
 column names the case of Algorithm 1 the cubic f'/4A falls in: 0 one real
 root (Delta > 0, Cardano), 1 triple root (Q = R = 0), 2 three real roots
-(trigonometric form), 3 quadratic (A = 0).
+(trigonometric form), 3 quadratic (A = 0), -1 a double root (Delta = 0 in
+exact arithmetic, so rounding sends it to either the Cardano or the
+trigonometric branch).
 
 Run from the repository root:  python tests/golden/make_quartic_cases.py
 """
@@ -82,6 +85,17 @@ def main():
         A = 3 * al
         lo, hi = interval((r,))
         n1 += add(0, A, 4 * al * (p - r), 6 * al * (s - r * p), -12 * al * r * s, lo, hi, (r,))
+    n2 = 0
+    while n2 < 24:  # a double root of f' (a saddle of f) and a simple one (the minimum)
+        r, t = dy(rng, -3, 3, 8), dy(rng, -3, 3, 8)
+        if abs(r - t) < Fr(1, 4):
+            continue
+        al = Fr(rng.randint(1, 8), 4)
+        A = 3 * al
+        # f'(x) = 4A (x - r)^2 (x - t): roots r (double), t
+        e1, e2, e3 = 2 * r + t, r * r + 2 * r * t, r * r * t
+        lo, hi = interval((r, t))
+        n2 += add(-1, A, -4 * al * e1, 6 * al * e2, -12 * al * e3, lo, hi, (r, t))
     for _ in range(8):  # triple root: A (x - r)^4, A a power of two
         r, A = dy(rng, -3, 3, 4), Fr(2) ** rng.randint(-2, 2)
         lo, hi = interval((r,))
