@@ -125,3 +125,48 @@ def test_plain_c_client_builds_and_runs(lib, tmp_path):
     out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
     assert out.returncode == 0, out.stderr
     assert "c client ok" in out.stdout
+
+
+def test_create_refuses_bad_sizes_and_settings_on_the_host():
+    """Empty and oversized instances and bad settings are refused by
+    admm_create before it touches a device (no GPU needed), with the
+    status the header documents."""
+    from paper_1903_10041_gb300 import capi
+    from paper_1903_10041_gb300 import workloads as W
+
+    def create(prob, par=None, edit=None):
+        keep: list = []
+        cp = capi.make_problem(prob, keep)
+        if edit:
+            edit(cp)
+        pp = par or capi.admm_default_params()
+        h = capi._H()
+        st = capi._lib.admm_create(ctypes.byref(cp), ctypes.byref(pp), ctypes.byref(h))
+        assert not h.value
+        return st
+
+    P = W.random_problem(4, 2, 1, seed=3)
+    assert create(P, edit=lambda c: setattr(c, "n", 0)) == capi.ADMM_EINVAL       # empty horizon
+    assert create(P, edit=lambda c: setattr(c, "q", 0)) == capi.ADMM_EINVAL       # no scenario
+    assert create(W.random_problem(3, capi.MAX_M + 1, 1, seed=3)) == capi.ADMM_EUNSUPPORTED
+    assert create(W.random_problem(2, 1, capi.MAX_PAIRS + 1, seed=3)) == capi.ADMM_EUNSUPPORTED
+    assert create(P, edit=lambda c: setattr(c, "y", None)) == capi.ADMM_EINVAL
+    assert create(P, edit=lambda c: setattr(c, "coef_shared", 2)) == capi.ADMM_EINVAL
+
+    def par(**kw):
+        p = capi.admm_default_params()
+        for k, v in kw.items():
+            if k == "rho1":
+                p.rho[1] = v
+            elif k == "reserved":
+                p.reserved[0] = v
+            else:
+                setattr(p, k, v)
+        return p
+
+    for kw in ({"rho1": 0.0}, {"rho1": float("inf")}, {"r_tol": float("nan")}, {"max_iter": 0},
+               {"check_every": 0}, {"xmin_mode": 5}, {"sweep": 3}, {"adapt_rho": 1, "tau": 1.0},
+               {"reserved": 1}):
+        assert create(P, par(**kw)) == capi.ADMM_EINVAL, kw
+    assert create(P, par(precision=9)) == capi.ADMM_EUNSUPPORTED
+    assert "precision" in capi.admm_last_error()
