@@ -420,3 +420,31 @@ def test_objective_invariances(oracle_lib):
     d2 = (oracle_lib.objective(Pq, xq + h) - 2 * oracle_lib.objective(Pq, xq) +
           oracle_lib.objective(Pq, xq - h))
     assert d2 == pytest.approx(2 * h * h * Pq.f2.sum() / q, rel=1e-10)
+
+
+def test_open_loop_variant_is_the_nominal_problem_on_the_largest_demand(oracle_lib):
+    """Sec. II's open-loop formulation (one sequence per source against
+    max_j y_k^(j)) is problem (1) with that demand, so it is solved as q = 1.
+    Repeated over the scenarios, its solution is feasible for eq. (2) (same
+    first move, every scenario's demand met, same capacities), so the
+    receding-horizon optimum of eq. (2) costs no more than it."""
+    P = W.shared_problem(30, 2, 4, seed=71).dense()  # cost and loss maps shared by the scenarios
+    par = W.Params(rho=(1.0, 1.0 / 30, 1.0, 1.0), r_tol=1e-9, s_tol=1e-9, max_iter=200000)
+    st_r, rep_r = oracle_lib.solve(P, par)
+    assert rep_r["converged"]
+    ol = P.copy()
+    for k in ("f2", "f1", "f0", "g2", "g1", "g0"):
+        setattr(ol, k, np.ascontiguousarray(getattr(P, k)[:, :1, :]))
+    ol.y = P.y.max(axis=0, keepdims=True)
+    ol.q = 1
+    st_o, rep_o = oracle_lib.solve(ol, par)
+    assert rep_o["converged"]
+    x_rep = np.repeat(st_o["x"], P.q, axis=1)
+    assert (x_rep.sum(axis=0) >= P.y - 1e-6).all()                                   # demand of every scenario
+    gsum = (P.g2 * x_rep ** 2 + P.g1 * x_rep + P.g0).sum(axis=2)
+    assert (gsum <= P.c[:, None] + 1e-6).all()                                        # capacities
+    obj_ol = oracle_lib.objective(P, x_rep)
+    assert obj_ol == pytest.approx(oracle_lib.objective(ol, st_o["x"]), rel=1e-12)
+    obj_r = oracle_lib.objective(P, st_r["x"])
+    assert obj_r <= obj_ol + 1e-6
+    assert obj_r < obj_ol - 1e-3  # scenario feedback after the first move pays on this instance
