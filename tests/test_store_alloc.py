@@ -1,0 +1,35 @@
+"""The device store's range allocator (host code of the batched and serving
+solvers) against a per-cell occupancy model: tests/range_alloc_check.cpp,
+compiled here and linked to libadmm.so.  CPU only."""
+import os
+import shutil
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _cuda_include():
+    for base in (os.environ.get("CUDA_HOME"), os.path.dirname(os.path.dirname(shutil.which("nvcc") or "")),
+                 "/usr/local/cuda"):
+        if base and os.path.exists(os.path.join(base, "include", "cuda_runtime.h")):
+            return os.path.join(base, "include")
+    return None
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_range_allocator_is_first_fit_and_coalesces(tmp_path, seed):
+    cxx, inc = shutil.which("g++"), _cuda_include()
+    if cxx is None or inc is None:
+        pytest.skip("needs g++ and the CUDA headers")
+    from paper_1903_10041_gb300 import build
+    so = build.build()
+    exe = tmp_path / "range_alloc_check"
+    subprocess.run([cxx, "-std=c++17", "-O1", "-Wall", "-I", os.path.join(ROOT, "include"),
+                    "-I", os.path.join(ROOT, "paper_1903_10041_gb300", "csrc"), "-I", inc,
+                    os.path.join(ROOT, "tests", "range_alloc_check.cpp"), so,
+                    "-Wl,-rpath," + os.path.dirname(so), "-o", str(exe)], check=True)
+    r = subprocess.run([str(exe), str(seed)], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stderr
+    assert "range allocator ok" in r.stdout
