@@ -495,7 +495,17 @@ def run_serving(args):
                 "ok_frac": float(np.mean(np.array(st_all) == 0)) if st_all else None,
                 "gpu_busy_frac": busy_window / window, "gpu_shift_frac": shift_window / window,
                 "mean_active": (st1["instance_ticks"] - st0["instance_ticks"]) / max(1.0, st1["ticks"] - st0["ticks"]),
-                "server_stats": stats, "gpu_launches": int(stats["ticks"]), "clocks": clk.summary()}
+                "server_stats": stats,
+                # the batched kernel once per tick of the window; a tick with step requests or finished
+                # instances adds one shift or one gather kernel
+                "gpu_launches": int(st1["ticks"] - st0["ticks"]),
+                # requests go in and results come out through the public API from host memory, so the
+                # served rate is itself end to end: a step request carries f, g [m][q], bounds [m] and
+                # y [q] in FP64; a drained result is its ticket, latency, iterations and status
+                "e2e": {"value": value * world, "unit": "solves/s",
+                        "h2d_bytes_per_step": float(np.mean([8 * (6 * m * q + 2 * m + q) for _, m, q in shapes])),
+                        "d2h_bytes_per_step": 8 + 8 + 4 + 4},
+                "roofline": None, "cpu_baseline": None, "clocks": clk.summary()}
         print(json.dumps(line))
     return 0
 
