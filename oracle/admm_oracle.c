@@ -20,7 +20,7 @@
  *     iterations as in Sec. IV-B.
  *   - The objective (1/q) sum f of eq. (2) and a KKT residual of eq. (2).
  *
- * Readings of points the paper leaves open (each is listed in the design doc):
+ * Readings of points the paper leaves open, numbered R1..R14 wherever they are cited:
  *   R1  step (c) averages: x_1^(i) = (1/q) sum_j (x_1^(i,j) - nu^(i,j)).
  *   R2  theta_k^(i,j) = z_k^(i,j) + lambda_k^(i,j) (the paper prints
  *       lambda_k^(i)); y in L is y^(j).
