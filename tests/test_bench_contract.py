@@ -63,6 +63,9 @@ def test_default_line_has_every_contract_key(monkeypatch, capsys):
     monkeypatch.setattr(torch, "empty", lambda *a, device=None, **k: real_empty(*a, **k))
     monkeypatch.setattr(torch.Tensor, "pin_memory", lambda self: self)
     import paper_1903_10041_gb300 as pkg
+    from paper_1903_10041_gb300 import build
+    build.build()
+    import paper_1903_10041_gb300.capi  # noqa: F401  (the real binding is what the patches restore)
     fake = types.ModuleType("paper_1903_10041_gb300.capi")
     fake.Solver = _Solver
     monkeypatch.setitem(__import__("sys").modules, "paper_1903_10041_gb300.capi", fake)
