@@ -244,6 +244,7 @@ def run_reference(args):
     from oracle import build as ob
     ob.build()
     P, par = workload(args.config, "fp64")
+    par = par.replace(adapt_rho=args.adapt)
     # iterations of a full solve: the oracle's own count (cached per run)
     st, rep = oracle.solve(P, par, threads=os.cpu_count() or 1) if args.config != 2 else (None, {"iters": 2600})
     iters = rep["iters"]
@@ -637,7 +638,7 @@ def main():
     ap.add_argument("--rate", type=float, default=2000.0, help="Poisson arrival rate per second (4)")
     ap.add_argument("--tick-iters", type=int, default=10,
                     help="iterations per serving tick of the costliest active instance (4)")
-    ap.add_argument("--adapt", action="store_true", help="penalty adaptation of Sec. IV-A (3, --q-sweep)")
+    ap.add_argument("--adapt", action="store_true", help="penalty adaptation of Sec. IV-A (0, 1, 2, 3, --q-sweep)")
     ap.add_argument("--batch-config", default="",
                     help="warps,ctas_per_sm,small_max,cluster,cluster_min instead of the autotuner (3, 4)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "mixed_fp64cubic"])
@@ -676,7 +677,7 @@ def main():
             run_single(args, P, par, rank, world, local)
     else:
         P, par = workload(args.config, args.precision, args.coef_shared)
-        run_single(args, P, par, rank, world, local)
+        run_single(args, P, par.replace(adapt_rho=args.adapt), rank, world, local)
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
