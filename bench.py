@@ -784,7 +784,7 @@ def run_single(args, P, par, rank, world, local):
                "d2h_bytes_per_step": d2h}
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and (args.config != 2 or args.q_sweep):
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(P, par, iters, budget_s=4.0 if args.q_sweep else 12.0)
 
     if rank == 0:
