@@ -6,16 +6,21 @@ the PHEV-shaped robust instance (n = 1000 steps, m = 2 sources, q = 50
 scenarios; synthetic data, FP64), the whole loop in one persistent kernel.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--config 0|1|2|3|4] [--precision fp64|mixed|mixed_fp64cubic]
-                  [--q-sweep 5,10,20,50,100,200,500] [--quartic N]
+                  [--config 0|1|2|3|4] [--precision fp64|mixed|mixed_fp64cubic] [--adapt]
+                  [--q-sweep 5,10,20,50,100,200,500] [--quartic N[,N2,...]]
 
-Prints one JSON line (one per scenario count with --q-sweep, the runtime
-against q comparison of Sec. IV-B).  `value` times K solves with inputs resident in HBM
-(CUDA events on the launch stream, L2 flushed between solves);
-`e2e` times the same solves through the public C ABI from pinned host
-buffers (create + solve + copy-out + destroy).  Under torchrun each rank
-solves its own replica (weak scaling, no collective on the data path).
-`--impl reference` times the FP64 CPU oracle on the host cores instead.
+Workloads: 0 and 1 and 2 are single instances (n=100 m=2 q=1; the PHEV
+n=1000 q=50 default; n=1e5 m=4 q=20), 3 the 4096-instance batch, 4 the
+served Poisson stream of re-solves; --q-sweep and --quartic are the
+runtime-against-q (Sec. IV-B) and quartic (Sec. III-C) comparisons.
+
+Prints one JSON line (one per q or N for the sweeps).  `value` times K
+solves with inputs resident in HBM (CUDA events on the launch stream, L2
+flushed between solves); `e2e` times the same solves through the public C
+ABI from pinned host buffers (create + solve + copy-out + destroy).  Under
+torchrun each rank solves its own instances (weak scaling, no collective
+on the data path).  `--impl reference` times the FP64 CPU oracle on the
+host cores instead.
 """
 from __future__ import annotations
 
