@@ -9,7 +9,7 @@ scenarios; synthetic data, FP64), the whole loop in one persistent kernel.
                   [--config 0|1|2|3|4] [--precision fp64|mixed|mixed_fp64cubic] [--adapt]
                   [--q-sweep 5,10,20,50,100,200,500] [--quartic N[,N2,...]]
 
-Workloads: 0 and 1 and 2 are single instances (n=100 m=2 q=1; the PHEV
+Workloads: 0, 1 and 2 are single instances (n=100 m=2 q=1; the PHEV
 n=1000 q=50 default; n=1e5 m=4 q=20), 3 the 4096-instance batch, 4 the
 served Poisson stream of re-solves; --q-sweep and --quartic are the
 runtime-against-q (Sec. IV-B) and quartic (Sec. III-C) comparisons.
