@@ -606,6 +606,8 @@ class Server:
 
     def poll(self, ticket: int, wait_ms: int = 0, want_x: bool = False):
         """None while pending; else a result dict (with x, x1 if want_x)."""
+        if ticket not in self._shapes:
+            raise AdmmError(ADMM_EINVAL, f"unknown or already returned ticket {ticket}")
         n, m, q = self._shapes[ticket]
         res = admm_result()
         x = x1 = None

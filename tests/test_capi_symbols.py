@@ -170,3 +170,14 @@ def test_create_refuses_bad_sizes_and_settings_on_the_host():
         assert create(P, par(**kw)) == capi.ADMM_EINVAL, kw
     assert create(P, par(precision=9)) == capi.ADMM_EUNSUPPORTED
     assert "precision" in capi.admm_last_error()
+
+
+def test_server_poll_of_an_unknown_ticket_is_an_error():
+    """A ticket the binding never issued (or already returned) is refused
+    before any call into the library."""
+    from paper_1903_10041_gb300 import capi
+    s = object.__new__(capi.Server)
+    s.h, s._shapes, s._session_n = None, {}, {}
+    with pytest.raises(capi.AdmmError) as e:
+        s.poll(12345)
+    assert e.value.status == capi.ADMM_EINVAL
