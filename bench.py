@@ -1,16 +1,18 @@
 """Benchmark: ADMM solves/s to 1e-6 residual on one GB300 (per GPU, replicas).
 
-One step = one solve, from the zero start to the stop test (r < 1e-6 and
-sigma < 1e-6, checked every 10 iterations; at most 5000 iterations), of
-the PHEV-shaped robust instance (n = 1000 steps, m = 2 sources, q = 50
-scenarios; synthetic data, FP64), the whole loop in one persistent kernel.
+Default workload (--config 3): one step = one batched launch that solves
+4096 independent instances of problem (2) (n log-uniform in [50, 5000],
+m in {2, 3, 4}, q in [1, 20]; synthetic, seeded per instance) from the zero
+start to the stop test (r < 1e-6, sigma < 1e-6 with the mixed-precision
+margin, checked every 10 iterations; at most 5000 iterations), mixed
+precision, launch configuration picked by the autotuner.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--config 0|1|2|3|4] [--precision fp64|mixed|mixed_fp64cubic] [--adapt]
-                  [--q-sweep 5,10,20,50,100,200,500] [--quartic N[,N2,...]]
+                  [--paper-penalties] [--q-sweep 5,10,20,50,100,200,500] [--quartic N[,N2,...]]
 
 Workloads: 0, 1 and 2 are single instances (n=100 m=2 q=1; the PHEV
-n=1000 q=50 default; n=1e5 m=4 q=20), 3 the 4096-instance batch, 4 the
+n=1000 q=50; n=1e5 m=4 q=20), 3 the 4096-instance batch (default), 4 the
 served Poisson stream of re-solves; --q-sweep and --quartic are the
 runtime-against-q (Sec. IV-B) and quartic (Sec. III-C) comparisons.
 
@@ -81,24 +83,26 @@ def workload(cfg: int, precision: str, coef_shared: bool = False):
 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the solve
-# kernel per iteration, from one ncu capture of each workload (profiles/).
-# It is reported only while the kernel sources hash to the captured build.
+# kernels, from one ncu capture of each workload: bytes per iteration of a
+# single-instance solve, or per element-iteration of a batched launch.  A
+# figure is reported only while the kernel's sources hash to the build it
+# was taken on (otherwise `traffic` is null).
 NCU_TRAFFIC = {
-    ("phev n=1000 q=50", "fp64"): {"bytes_per_iter": (7.595264e6 + 0.055808e6) / 3330, "src": "965ff8b0533d4c28",
-                                   "capture": "profiles/single_fp64_kernel_phev_n1000_q50.md (whole 3330-iteration solve)"},
+    ("phev n=1000 q=50", "fp64"): {"bytes_per_iter": (7.595264e6 + 0.055808e6) / 3330, "src": "965ff8b0533d4c28"},
     ("plain n=1e5 m=4 q=20", "mixed"): {"bytes_per_iter": (4.317581824e9 + 1.382421760e9) / 20,
-                                                 "src": "965ff8b0533d4c28",
-                                                 "capture": "profiles/single_mixed_kernel_plain_n1e5_m4_q20.md (20 iterations)"},
+                                        "src": "965ff8b0533d4c28"},
 }
+NCU_TRAFFIC_BATCH = {"bytes_per_element_iter": None, "src": None}
 
-
-# Sources the single-instance solve kernel is compiled from.
+# Sources each solve kernel is compiled from.
 SINGLE_KERNEL_SOURCES = ("single.cu", "quartic32.cuh", "quartic64.cuh", "mixed_elem.cuh", "common.cuh", "internal.h")
+BATCH_KERNEL_SOURCES = ("batch_kernel.cuh", "batch_w4.cu", "batch_w8.cu", "batch_w16.cu", "batch.h", "quartic32.cuh",
+                        "quartic64.cuh", "mixed_elem.cuh", "common.cuh", "internal.h")
 
 
-def kernel_source_hash() -> str:
+def kernel_source_hash(sources=SINGLE_KERNEL_SOURCES) -> str:
     import hashlib
-    files = sorted([os.path.join(ROOT, "paper_1903_10041_gb300", "csrc", f) for f in SINGLE_KERNEL_SOURCES] +
+    files = sorted([os.path.join(ROOT, "paper_1903_10041_gb300", "csrc", f) for f in sources] +
                    [os.path.join(ROOT, "include", "admm.h")])
     h = hashlib.sha256()
     for f in files:
@@ -115,6 +119,13 @@ def traffic_per_launch(P, prec: str, iters: int):
     return t["bytes_per_iter"] * iters
 
 
+def batch_traffic_per_launch(element_iters: float):
+    t = NCU_TRAFFIC_BATCH
+    if t["bytes_per_element_iter"] is None or t["src"] != kernel_source_hash(BATCH_KERNEL_SOURCES):
+        return None
+    return t["bytes_per_element_iter"] * element_iters
+
+
 def bytes_per_iteration(P, prec: str) -> int:
     """Algorithmic HBM bytes of one iteration (each streamed array once):
     f2, f1, g2, g1 read and x read+write (6 per element), the bounds
@@ -126,6 +137,28 @@ def bytes_per_iteration(P, prec: str) -> int:
     if prec == "fp64":
         return 8 * (coef + 2 * m * n * q + 2 * m * n + 5 * n * q)
     return 4 * (coef + 2 * m * n * q + 2 * m * n + n * q) + 8 * 4 * n * q
+
+
+def measured_peaks() -> dict:
+    """HBM copy bandwidth measured on this GPU type (MEASURED_PEAKS.json at
+    the repository root), else the fallback figure."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured (STREAM-style copy, MEASURED_PEAKS.json)"}
+    return {"hbm_gbs": 6800.0, "source": "fallback 6.8 TB/s (no measured figure present)"}
+
+
+def batch_params(args):
+    """Settings of the batched and served workloads: rho = (1, 1/n, 1, 1) per
+    instance (reading R12), mixed precision, the Sec. IV-A adaptation with
+    --adapt."""
+    from paper_1903_10041_gb300 import workloads as W
+    return W.Params(rho=(1.0, 1.0, 1.0, 1.0), rho2_over_n=True, precision="mixed", adapt_rho=args.adapt)
+
+
+def penalty_text(args) -> str:
+    return "(1, 1/n, 1, 1) per instance" + (", adapted (Sec. IV-A)" if args.adapt else "")
 
 
 class ClockSampler:
@@ -271,8 +304,9 @@ def run_reference(args):
             times.append(dt)
     per_solve = statistics.mean(times) / T * iters
     v = 1.0 / per_solve
+    # each step runs T of the solve's iterations; the rate is scaled to whole solves
     line = {"metric": METRIC, "value": v, "unit": "solves/s", "impl": "reference", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_solve * 1e3,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": config_dict(P, par, args),
             "cpu_baseline": {"value": v, "unit": "solves/s", "cores": threads, "kind": "oracle",
@@ -286,32 +320,35 @@ def run_reference(args):
 def run_reference_batched(args, oracle):
     """The oracle on the batched (3) or served (4) workload: each step solves
     the workload's instances in order, from the zero start to the stop test,
-    for about 10 s, and the step's rate is instances solved per second (a
-    bounded sample of the same instance distribution)."""
+    for about 4 s, and the rate is instances solved per second (a bounded
+    sample of the same instance distribution).  ms_per_step is the measured
+    duration of a step."""
     from paper_1903_10041_gb300 import workloads as W
-    par = W.Params(rho=(1.0, 1.0, 1.0, 1.0), rho2_over_n=True, adapt_rho=args.adapt)
+    par = batch_params(args).replace(precision="fp64")
     threads = os.cpu_count() or 1
-    rates, solved, nxt = [], 0, 0
+    durations, solved, nxt, k_all = [], 0, 0, []
     for step in range(args.warmup + args.steps):
         t0, k = time.perf_counter(), 0
-        while time.perf_counter() - t0 < 10.0 or k == 0:
+        while time.perf_counter() - t0 < 4.0 or k == 0:
             oracle.solve(W.batch_instance(nxt % args.count), par, threads=threads)
             nxt += 1
             k += 1
         dt = time.perf_counter() - t0
         if step >= args.warmup:
-            rates.append(k / dt)
+            durations.append(dt)
+            k_all.append(k)
             solved += k
-    v = statistics.mean(rates)
+    v = solved / sum(durations)
     kind = "batched" if args.config == 3 else "served (cold solves of the controllers)"
     line = {"metric": METRIC, "value": v, "unit": "solves/s", "impl": "reference", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / v, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded per instance)",
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(durations),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded per instance)",
             "config": {"workload": f"{kind}: {args.count} instances, n log-uniform [50,5000], m in {{2,3,4}}, "
-                                   f"q in [1,20]", "count": args.count},
+                                   f"q in [1,20]", "count": args.count, "rho": penalty_text(args)},
             "cpu_baseline": {"value": v, "unit": "solves/s", "cores": threads, "kind": "oracle",
-                             "sample": f"{solved} instances solved to the stop test in the timed steps, "
-                                       f"about 10 s each"},
+                             "sample": f"{solved} instances (ids 0..{nxt - 1} mod {args.count}, in order) solved "
+                                       f"to the stop test in the timed steps of about 4 s each"},
             "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -338,6 +375,34 @@ def oracle_sample_errors(probs, par, results, states, idx, oracle):
             "per_instance_rel_objective_err": [float(e) for e in errs]}
 
 
+def pinned_copy(P):
+    """The problem with every array in page-locked host memory (the e2e legs
+    copy to the device from pinned buffers)."""
+    import numpy as np
+    import torch
+    Q = P.copy()
+    for k, v in P.arrays().items():
+        setattr(Q, k, torch.from_numpy(np.ascontiguousarray(v)).pin_memory().numpy())
+    return Q
+
+
+def batch_sample(probs, limit_small=40000):
+    """Instances for the per-instance oracle comparison: the 6 smallest, 6
+    spread over the lower half of the size distribution (m*q*n <= 40000),
+    and the two instances nearest 1e5 and 2.5e5 elements."""
+    import numpy as np
+    order = np.argsort([P.elements for P in probs])
+    small = [int(t) for t in order[:6]]
+    spread = [int(t) for t in order[len(order) // 8: len(order) // 2: max(1, len(order) // 48)]
+              if probs[int(t)].elements <= limit_small][:6]
+    big = []
+    for target in (1e5, 2.5e5):
+        t = int(np.argmin([abs(P.elements - target) for P in probs]))
+        if t not in small + spread + big:
+            big.append(t)
+    return small, spread, big
+
+
 def run_batched(args):
     """The batched workload: `count` instances of uneven n, m, q in one launch (mixed)."""
     import numpy as np
@@ -352,7 +417,7 @@ def run_batched(args):
     from paper_1903_10041_gb300 import workloads as W
     base = rank * args.count
     probs = [W.batch_instance(base + t) for t in range(args.count)]
-    par = W.Params(rho=(1.0, 1.0, 1.0, 1.0), rho2_over_n=True, precision="mixed", adapt_rho=args.adapt)
+    par = batch_params(args)
     if args.max_iter:
         par = par.replace(max_iter=args.max_iter)
     B = capi.Batch(probs, par)
@@ -378,6 +443,8 @@ def run_batched(args):
 
     for _ in range(args.warmup):
         one()
+    if world > 1:
+        torch.distributed.barrier()
     times, res = [], None
     with ClockSampler(local) as clk:
         for _ in range(args.steps):
@@ -388,27 +455,28 @@ def run_batched(args):
     per_batch_s = sum(times) / args.steps / 1e3
     iters = np.array([r["iters"] for r in res])
     conv = np.array([r["converged"] for r in res])
+    el_it = float(sum(int(r["iters"]) * P.elements for r, P in zip(res, probs)))
     byts = sum(int(r["iters"]) * bytes_per_iteration(P, "mixed") for r, P in zip(res, probs))
-    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
-        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"hbm_gbs": 6800.0}
+    peaks = measured_peaks()
     gbs = byts / per_batch_s / 1e9
     roofline = {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": gbs / peaks["hbm_gbs"], "traffic": None}
-    # oracle error on a sample: the 6 smallest instances and 6 spread over the batch (m*q*n <= 40000)
+                "frac": gbs / peaks["hbm_gbs"], "traffic": batch_traffic_per_launch(el_it),
+                "algorithmic_bytes": float(byts), "peak_source": peaks["source"]}
+    # the FP64 oracle on a sample of the instances: objective error and KKT excess
     import oracle
-    order = np.argsort([P.elements for P in probs])
-    small = [int(t) for t in order[:6]]
-    spread = [int(t) for t in order[len(order) // 8: len(order) // 2: max(1, len(order) // 48)]
-              if probs[int(t)].elements <= 40000][:6]
-    idx = small + spread
+    small, spread, big = batch_sample(probs)
+    idx = small + spread + big
     states = {t: B.state(t) for t in idx}
-    errors = oracle_sample_errors(probs, par, res, states, idx, oracle) if rank == 0 else None
+    errors = (oracle_sample_errors(probs, par, res, states, idx, oracle)
+              if rank == 0 and not args.no_oracle_sample else None)
     # end to end: create from pinned host arrays, solve, read every result (objective, x)
     e2e = None
     if not args.no_e2e:
+        pinned = [pinned_copy(P) for P in probs]
         t0 = time.perf_counter()
-        B2 = capi.Batch(probs, par)
-        B2.set_config(cfg["warps_per_cta"], cfg["ctas_per_sm"], cfg["small_max_elements"])
+        B2 = capi.Batch(pinned, par)
+        B2.set_config(cfg["warps_per_cta"], cfg["ctas_per_sm"], cfg["small_max_elements"],
+                      cfg["cluster_size"], cfg["cluster_min_elements"])
         B2.solve()
         out = B2.wait(want_x=True)
         e2e_s = time.perf_counter() - t0
@@ -429,7 +497,6 @@ def run_batched(args):
             oracle.solve(P, par.replace(precision="fp64", max_iter=T, r_tol=0.0, s_tol=0.0),
                          threads=os.cpu_count() or 1)
             t_el.append((time.perf_counter() - t0) / (T * P.elements))
-        el_it = float(sum(int(r["iters"]) * P.elements for r, P in zip(res, probs)))
         sec = el_it * float(np.mean(t_el))
         cpu = {"value": args.count / sec, "unit": "solves/s", "cores": os.cpu_count() or 1, "kind": "oracle",
                "sample": f"200 iterations of instances {small[:1] + spread[:1]}, scaled by element-iterations to "
@@ -442,14 +509,16 @@ def run_batched(args):
                 "config": {"workload": f"batched: {args.count} instances, n log-uniform [50,5000], m in {{2,3,4}}, "
                                        f"q in [1,20], mixed precision", "count": args.count,
                            "elements": int(sum(P.elements for P in probs)), "autotuned": cfg,
-                           "rho": "(1, 1/n, 1, 1) per instance" + (", adapted (Sec. IV-A)" if args.adapt else ""),
+                           "rho": penalty_text(args), "stop": "r < 1e-6, sigma < 0.85e-6 (mixed margin), "
+                                                             "checked every 10 iterations, at most 5000",
                            "l2": "inputs larger than L2 (and flushed)",
                            "parallelism": f"replicas x{world}"},
                 "iters": {"mean": float(iters.mean()), "max": int(iters.max()), "min": int(iters.min())},
+                "element_iterations": el_it,
                 "converged_frac": float(conv.mean()), "oracle_error_sample": errors,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
                 "clocks": clk.summary()}
-        print(json.dumps(line))
+        print(json.dumps(line), flush=True)
     B.close()
     return 0
 
@@ -649,8 +718,7 @@ def quartic_line(args, N: int, rank: int, world: int):
         cpun = rate(lambda: list(ex.map(lambda t: run(bounds[t], bounds[t + 1]), range(threads))))
     x64 = out["fp64"]["sample"][1][:ns]
     agree = float(np.mean(np.abs(x64 - xo) <= 1e-9 * np.maximum(1.0, np.abs(xo))))
-    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
-        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"hbm_gbs": 6800.0}
+    peaks = measured_peaks()
     (vmax,) = barrier_max([-out["fp32"]["dev_per_s"]], world)
     if rank == 0:
         f32, f64 = out["fp32"], out["fp64"]
@@ -678,7 +746,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", type=int, default=1, choices=[0, 1, 2, 3, 4])
+    ap.add_argument("--config", type=int, default=3, choices=[0, 1, 2, 3, 4])
     ap.add_argument("--count", type=int, default=4096, help="instances (3) or controllers (4)")
     ap.add_argument("--duration", type=float, default=60.0, help="serving window in seconds (4)")
     ap.add_argument("--rate", type=float, default=2000.0, help="Poisson arrival rate per second (4)")
@@ -692,6 +760,8 @@ def main():
                     help="profiling only: cap the iterations of each solve (the line is then not a benchmark)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-oracle-sample", action="store_true",
+                    help="--config 3: skip the per-instance oracle comparison (profiling runs)")
     ap.add_argument("--coef-shared", action="store_true",
                     help="--config 1 or 2: scenario-shared cost and loss maps ([m][n] coefficients)")
     ap.add_argument("--q-sweep", default="",
@@ -763,8 +833,9 @@ def run_single(args, P, par, rank, world, local):
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        res = solver.solve(stream=stream)
+        solver.solve_async(stream=stream)
         e1.record(stream)
+        res = solver.wait()
         e1.synchronize()
         return e0.elapsed_time(e1), res
 
@@ -798,8 +869,7 @@ def run_single(args, P, par, rank, world, local):
                     # (the n=1000 PHEV one) is served mostly from L2, not HBM (see traffic)
                     "streamed_gbs": iters * bytes_per_iteration(P, "fp64") / per_launch_s / 1e9}
     else:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
-            os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"hbm_gbs": 6800.0}
+        peaks = measured_peaks()
         gbs = iters * bytes_per_iteration(P, args.precision) / per_launch_s / 1e9
         roofline = {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                     "frac": gbs / peaks["hbm_gbs"], "traffic": traffic_per_launch(P, args.precision, iters)}

@@ -57,7 +57,12 @@ enum {
     ADMM_FP64 = 0,          /* everything in FP64 */
     ADMM_MIXED = 1,         /* FP32 storage and element work; FP64 k-sums, pair
                                scalars and residuals; the cubic's branch is
-                               decided in FP64 whenever FP32 cannot certify it */
+                               decided in FP64 whenever FP32 cannot certify it.
+                               Mixed solves (this and the next) stop at
+                               r < r_tol and sigma < 0.85 s_tol: the margin
+                               on sigma, the binding residual, absorbs the
+                               FP32 rounding of the stored x in the KKT
+                               conditions of eq. (2) */
     ADMM_MIXED_FP64CUBIC = 2 /* as ADMM_MIXED, but the whole cubic step
                                (b, c, d, Q, R, Delta, roots, delta-f) in FP64 */
 };
@@ -145,14 +150,28 @@ admm_status admm_create(const admm_problem *prob, const admm_params *params, adm
 /* Replaces the settings used by later solves (same validation). */
 admm_status admm_set_params(admm_handle *h, const admm_params *params);
 
-/* Solves from `warm` (NULL: continue from the handle's current state; a
- * fresh handle holds the zero start) until the stop test or max_iter,
- * with the whole loop on the device (one persistent launch).  Runs on
- * `stream` (a cudaStream_t; NULL = legacy default stream) and returns after
- * the stream has finished the solve.  Fills `out` (which may be NULL)
- * and leaves the final state in the handle.  Returns ADMM_OK,
- * ADMM_ENOTCONVERGED (result still filled), ADMM_ETIMEOUT, ADMM_ECUDA. */
+/* Queues a solve from `warm` (NULL: continue from the handle's current
+ * state; a fresh handle holds the zero start) until the stop test or
+ * max_iter, with the whole loop on the device (one persistent launch), on
+ * `stream` (a cudaStream_t; NULL = legacy default stream), and returns once
+ * the work is queued: ADMM_OK, or ADMM_EINVAL / ADMM_ECUDA if it could not
+ * be queued.  The solve's own outcome arrives later: `out` (may be NULL) is
+ * filled by a host function queued behind the solve, so its fields,
+ * out->status included (ADMM_OK, ADMM_ENOTCONVERGED with the result still
+ * filled, ADMM_ETIMEOUT), are valid once the stream has been synchronised;
+ * `out` and its x, x1 buffers must stay valid until then.  admm_wait waits
+ * for the handle's last queued solve and returns that status.  The final
+ * state stays in the handle.  A warm state is loaded before the call
+ * returns (the call waits for that copy); with pageable host buffers for
+ * out->x or out->x1 the call returns only after their copies.  One solve per
+ * handle may be in flight at a time; solves of different handles on
+ * different streams may overlap on the device. */
 admm_status admm_solve(admm_handle *h, const admm_state *warm, admm_result *out, void *stream);
+
+/* Waits until the handle's last queued solve has finished and returns its
+ * status (ADMM_OK, ADMM_ENOTCONVERGED, ADMM_ETIMEOUT), filling `out` (may be
+ * NULL) as admm_solve does. */
+admm_status admm_wait(admm_handle *h, admm_result *out);
 
 /* Resets the handle's state to the zero start. */
 admm_status admm_reset(admm_handle *h);
@@ -161,8 +180,9 @@ admm_status admm_reset(admm_handle *h);
  * out->on_device says; NULL array pointers are skipped).  Synchronous. */
 admm_status admm_get_state(admm_handle *h, admm_state *out, void *stream);
 
-/* Copies the per-solve record of the last admm_solve on this handle into
- * info_out[0 .. count-1] (count <= 16): 0 iterations, 1 converged, 2 r,
+/* Copies the per-solve record of the last admm_solve on this handle (valid
+ * after admm_wait or a sync of its stream) into info_out[0 .. count-1]
+ * (count <= 16): 0 iterations, 1 converged, 2 r,
  * 3 sigma, 4..7 the four terms of r, 8..10 the three terms of sigma,
  * 11 objective, 12 status, 13 cubic branch decisions that FP32 could not
  * certify and FP64 took (ADMM_MIXED).  Host-only; no device work. */
@@ -208,19 +228,26 @@ admm_status admm_quartic_min_f32(const float *A, const float *B, const float *C,
  * paper has no counterpart; this is a deployment variant of admm_solve.
  *
  * The caller passes everything: `prob` and `state` hold device pointers in
- * the dense layout above (on_device = 1 for both).  `state` is in/out: the
- * solve starts from it (state->cold = 1 starts from zero: x is set to
- * clamp(0) and every other array to 0, ignoring their contents) and leaves
- * the final state in it, including rho and cold.  `out` may be NULL.
+ * the dense layout above (on_device = 1 for both; rows are n values apart,
+ * unpadded, so loads may coalesce less well than in admm_solve, whose
+ * handle pads rows to 32 doubles).  `state` is in/out: the solve starts
+ * from it (state->cold = 1 starts from zero: x is set to clamp(0) and every
+ * other array to 0, ignoring their contents) and leaves the final state in
+ * it, including rho and cold.  The problem is validated before anything of
+ * the caller's is written: ADMM_EINVAL (invalid data as in admm_create)
+ * leaves `state` as it was.  `out` may be NULL.
  * The solver's scratch lives in a fixed 4 MiB device array inside the
- * library, which every GPU that loads the library holds until exit.  The
- * first call on each device looks up that array's address; make it before
- * any stream capture.  Calls share the array and it keeps the last call's
- * contents; each call clears what must start at zero, and calls that overlap
- * on the GPU race on it, so the caller must serialise them.  Instances
- * whose scratch would exceed the array are rejected with
- * ADMM_EUNSUPPORTED (a few thousand CTA-row segments; the n = 1000, q = 50
- * and n = 1e5, m = 4, q = 20 instances need under 100 KiB).  Only
+ * library.  A device holds it from the first call made on it (with CUDA's
+ * lazy module loading, that call also loads the library's kernels, which
+ * does allocate device memory) until the process exits.  Make the first
+ * call on each device a warm-up at start-up, outside any real-time loop or
+ * host callback and before any stream capture: it also looks up the
+ * array's address.  Later calls allocate nothing.  Calls share the array
+ * and it keeps the last call's contents; each call clears what must start
+ * at zero, and calls that overlap on the GPU race on it, so the caller must
+ * serialise them.  Instances whose scratch would exceed the array are
+ * rejected with ADMM_EUNSUPPORTED (at most ADMM_MAX_PAIRS pairs on a
+ * 152-SM GPU need under 200 KiB, so today the limit is not reached).  Only
  * ADMM_FP64 is available.  Returns as admm_solve, after the stream has
  * finished.  No cudaMalloc, cudaFree or other allocating call is made. */
 admm_status admm_solve_noalloc(const admm_problem *prob, const admm_params *params, admm_state *state,

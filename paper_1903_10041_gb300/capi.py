@@ -69,6 +69,8 @@ _lib.admm_set_params.argtypes = [_H, C.POINTER(admm_params)]
 _lib.admm_set_params.restype = C.c_int
 _lib.admm_solve.argtypes = [_H, C.POINTER(admm_state), C.POINTER(admm_result), C.c_void_p]
 _lib.admm_solve.restype = C.c_int
+_lib.admm_wait.argtypes = [_H, C.POINTER(admm_result)]
+_lib.admm_wait.restype = C.c_int
 _lib.admm_reset.argtypes = [_H]
 _lib.admm_reset.restype = C.c_int
 _lib.admm_get_state.argtypes = [_H, C.POINTER(admm_state), C.c_void_p]
@@ -210,11 +212,21 @@ def _state_struct(st: dict, keep: list) -> admm_state:
     return admm_state(*ptrs, rho, int(bool(st.get("cold", False))), int(devs.pop()))
 
 
-def admm_solve(h, warm: dict | None = None, x_out=None, x1_out=None, stream=None,
-               raise_on=(ADMM_EINVAL, ADMM_ENOMEM, ADMM_ECUDA, ADMM_ETIMEOUT, ADMM_EUNSUPPORTED)) -> dict:
-    """Runs a solve.  ``x_out``/``x1_out``: optional numpy or torch buffers
-    that receive x [m, q, n] and x_1 [m].  ``stream``: a torch.cuda.Stream,
-    an integer cudaStream_t, or None (legacy default stream)."""
+_ERRORS = (ADMM_EINVAL, ADMM_ENOMEM, ADMM_ECUDA, ADMM_ETIMEOUT, ADMM_EUNSUPPORTED)
+
+
+class Pending:
+    """A queued solve: keeps its result record and buffers alive until waited on."""
+
+    def __init__(self, h, res, keep):
+        self.h, self.res, self.keep = h, res, keep
+
+
+def admm_solve_async(h, warm: dict | None = None, x_out=None, x1_out=None, stream=None) -> Pending:
+    """Queues a solve (admm_solve) and returns without waiting for it.
+    ``x_out``/``x1_out``: optional numpy or torch buffers that receive x
+    [m, q, n] and x_1 [m].  ``stream``: a torch.cuda.Stream, an integer
+    cudaStream_t, or None (legacy default stream)."""
     keep: list = []
     ws = C.byref(_state_struct(warm, keep)) if warm is not None else None
     res = admm_result()
@@ -228,10 +240,24 @@ def admm_solve(h, warm: dict | None = None, x_out=None, x1_out=None, stream=None
     if stream is not None:
         sp = C.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
     st = _lib.admm_solve(h, ws, C.byref(res), sp)
+    if st != ADMM_OK:
+        raise AdmmError(st, admm_last_error())
+    return Pending(h, res, keep)
+
+
+def admm_wait(pending: Pending, raise_on=_ERRORS) -> dict:
+    """Waits for a queued solve and returns its outcome."""
+    res = pending.res
+    st = _lib.admm_wait(pending.h, C.byref(res))
     if st in raise_on:
         raise AdmmError(st, admm_last_error())
     return {"status": st, "iters": res.iters, "converged": bool(res.converged), "objective": res.objective,
             "r": res.r, "sigma": res.sigma}
+
+
+def admm_solve(h, warm: dict | None = None, x_out=None, x1_out=None, stream=None, raise_on=_ERRORS) -> dict:
+    """Runs a solve to its end: admm_solve, then admm_wait."""
+    return admm_wait(admm_solve_async(h, warm, x_out, x1_out, stream), raise_on)
 
 
 def admm_get_state(h, n: int, m: int, q: int) -> dict:
@@ -306,11 +332,21 @@ class Solver:
     """Owns one handle: ``Solver(problem, params).solve()``."""
 
     def __init__(self, prob, par=None, **kw):
+        self._pending = None
         self.n, self.m, self.q = int(prob.n), int(prob.m), int(prob.q)
         self.h = admm_create(prob, par, **kw)
 
     def solve(self, warm=None, **kw) -> dict:
         return admm_solve(self.h, warm, **kw)
+
+    def solve_async(self, warm=None, **kw) -> Pending:
+        """Queues a solve on ``stream`` and returns at once; ``wait`` ends it."""
+        self._pending = admm_solve_async(self.h, warm, **kw)
+        return self._pending
+
+    def wait(self, **kw) -> dict:
+        p, self._pending = self._pending, None
+        return admm_wait(p, **kw)
 
     def set_params(self, par=None, **kw):
         admm_set_params(self.h, par, **kw)

@@ -42,6 +42,7 @@ struct BatchArgs {
                               // times per launch, in round-robin order (serving ticks, below)
     int *lock;                // per instance: 1 while a team runs it (round-robin launches)
     double r_tol, s_tol, tau;
+    double adapt_target;      // r_tol / s_tol of the settings (Sec. IV-A ratio rule)
     int max_iter, check_every, xmin_mode, sweep, adapt;
 };
 

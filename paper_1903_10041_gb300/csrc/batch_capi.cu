@@ -183,8 +183,9 @@ BatchArgs make_args(const admm_batch *b)
     a.out = b->d_out;
     a.slice_doubles = (int)b->slice;
     a.iter_budget = b->iter_budget;
-    a.r_tol = b->prm.r_tol;
-    a.s_tol = b->prm.s_tol;
+    a.r_tol = stop_r_tol(b->prm.precision, b->prm.r_tol);
+    a.s_tol = stop_s_tol(b->prm.precision, b->prm.s_tol);
+    a.adapt_target = b->prm.r_tol / b->prm.s_tol;
     a.tau = b->prm.tau;
     a.max_iter = b->prm.max_iter;
     a.check_every = b->prm.check_every;

@@ -16,10 +16,11 @@
 // through distributed shared memory in rank order and runs the scalar steps
 // redundantly.
 //
-// Per iteration a team splits the rows j = 1..q of its instance into
-// warp-level (row, segment) work items; within an item a warp takes
-// consecutive column pairs (coalesced) and runs the element update of
-// mixed_elem.cuh; each item is reduced by shuffles into a record in shared
+// Per iteration a team splits the q rows of nv column pairs of its instance
+// into W equal contiguous ranges, one per warp (W warps in the team); a
+// warp walks its range row piece by row piece, its lanes taking
+// consecutive column pairs (coalesced) and running the element update of
+// mixed_elem.cuh; each piece is reduced by shuffles into a record in shared
 // memory, one team barrier follows, and the per-(i, j) scalar steps,
 // residuals and stop test run on the team.  The arithmetic and its order
 // depend only on the instance's own shape and its team kind (fixed by the
@@ -87,24 +88,26 @@ template <int NT> __device__ __forceinline__ double team_sum(const Team<NT> &T, 
 
 enum { TEAM_WARP = 0, TEAM_CTA = 1, TEAM_CLUSTER = 2 };
 
-// Segments per row for a team of W warps: rows are cut so that about one
-// (row, segment) work item falls to each warp, but no segment is shorter
-// than two vectors per lane.
-__host__ __device__ inline int team_segments(int W, int q, int nv)
+// Column pairs per warp of a team of W warps over P = q nv pairs: equal
+// shares in whole lane rounds.  Warp w takes pairs [w chunk, (w + 1) chunk)
+// of the row-major pair index j nv + v, so rows j touch warps
+// j nv / chunk .. ((j + 1) nv - 1) / chunk, and the record of (row j, warp
+// w) sits at index j + w: rows share at most their boundary warp, so the
+// indices never collide and stay below q + W - 1.
+__host__ __device__ inline int64_t team_chunk(int W, int q, int nv)
 {
-    const int want = (W + q - 1) / q;
-    const int cap = nv / 64 > 1 ? nv / 64 : 1;
-    return want < 1 ? 1 : (want < cap ? want : cap);
+    const int64_t P = (int64_t)q * nv;
+    return ((P + W - 1) / W + 31) / 32 * 32;
 }
 
 // One team solves instance `id` from its saved state until it stops or the
 // iteration budget runs out.  KIND: one warp (slice = that warp's shared
 // memory), one CTA, or a thread-block cluster (every CTA runs this
-// function; each holds a copy of the scalar state and records of the work
-// items its warps processed).  Work per iteration: items (row j, segment)
-// in a fixed order, one per warp in turn; each warp reduces its items with
-// shuffles only; one team barrier; then the per-(i, j) scalar steps read the
-// records of each row in segment order.
+// function; each holds a copy of the scalar state and records of the row
+// pieces its warps processed).  Work per iteration: each warp its range of
+// column pairs, piece by piece, reducing each piece with shuffles only; one
+// team barrier; then the per-(i, j) scalar steps read the records of each
+// row in warp order.
 template <int KIND, int NW, int M> __device__ void solve_team(const BatchArgs &a, int id, double *smem)
 {
     namespace cg = cooperative_groups;
@@ -133,9 +136,9 @@ template <int KIND, int NW, int M> __device__ void solve_team(const BatchArgs &a
     const int n = I.n, m = I.m, q = I.q, mq = m * q;
     const int nv = (n + VW - 1) / VW;
     const int W = NWT * CL, gw = rank * NWT + wl;
-    const int S = team_segments(W, q, nv);
-    const int seg = (nv + S - 1) / S;
-    const int items = q * S;
+    const int64_t chunk = team_chunk(W, q, nv);
+    const int64_t npairs = (int64_t)q * nv;
+    const int items = q + W - 1; // record slots: (row j, warp w) at j + w
 
     // shared memory: scal | rec[2][items][m][4] | cmax[2][NWT][2] | part[8] | x0s[mq] | x1n | scr | uoff
     double *scal = smem;
@@ -187,9 +190,12 @@ template <int KIND, int NW, int M> __device__ void solve_team(const BatchArgs &a
         const float iq = 1.0f / (float)q;
         float fcr = 0.0f, fcs = 0.0f;
         double *recs = rec0 + (size_t)par * items * m * 4;
-        for (int item = gw; item < items; item += W) {
-            const int j = item / S, sg = item - j * S;
-            const int v0 = sg * seg, v1 = min(nv, v0 + seg);
+        const int64_t pend = min(npairs, (int64_t)(gw + 1) * chunk);
+        for (int64_t pa = (int64_t)gw * chunk; pa < pend;) {
+            const int j = (int)(pa / nv);
+            const int v0 = (int)(pa - (int64_t)j * nv);
+            const int v1 = (int)(min(pend, (int64_t)(j + 1) * nv) - (int64_t)j * nv);
+            pa = (int64_t)j * nv + v1;
             float2 ghi[M], glo[M]; // per-lane capacity sums of the column pairs
             float fmx[M], fmn[M];
 #pragma unroll
@@ -199,7 +205,7 @@ template <int KIND, int NW, int M> __device__ void solve_team(const BatchArgs &a
                 fmx[i] = -INFINITY;
                 fmn[i] = INFINITY;
             }
-            double *rec = recs + (size_t)item * m * 4;
+            double *rec = recs + (size_t)(j + gw) * m * 4;
             for (int v = v0 + lane; v < v1; v += 32) {
                 if (v + 32 < v1) prefetch_vec32<M>(ea, j, (v + 32) * VW, cold);
                 vec32<M, VW, false>(ea, uoff, x1, nu, j, v * VW, check, cold, mu_div, rho1, rho3, rho4, iq, ghi, glo,
@@ -242,17 +248,17 @@ template <int KIND, int NW, int M> __device__ void solve_team(const BatchArgs &a
         for (int pr = tid; pr < mq; pr += NTL) {
             const int i = pr / q, j = pr - i * q;
             double Ssum = 0.0, dmx = -INFINITY, dmn = INFINITY, x0 = 0.0;
-            for (int sg = 0; sg < S; ++sg) {
-                const int item = j * S + sg;
+            const int wf = (int)((int64_t)j * nv / chunk), wlst = (int)(((int64_t)j * nv + nv - 1) / chunk);
+            for (int w = wf; w <= wlst; ++w) { // the warps whose ranges cover row j, in order
                 const double *rb = recs;
-                if constexpr (KIND == TEAM_CLUSTER) rb = cg::this_cluster().map_shared_rank(recs, (item % W) / NWT);
-                const double *rr = rb + ((size_t)item * m + i) * 4;
+                if constexpr (KIND == TEAM_CLUSTER) rb = cg::this_cluster().map_shared_rank(recs, w / NWT);
+                const double *rr = rb + ((size_t)(j + w) * m + i) * 4;
                 Ssum += rr[0];
                 if (check) {
                     dmx = fmax(dmx, rr[1]);
                     dmn = fmin(dmn, rr[2]);
                 }
-                if (sg == 0) x0 = rr[3];
+                if (w == wf) x0 = rr[3]; // k = 0 lies in the first warp's piece
             }
             const double lm = lam[pr], zt = zeta[pr], h0 = hh[pr], p0 = pp[pr];
             const double Wv = (Ssum + sumg0[pr]) - (double)n * lm;
@@ -317,7 +323,7 @@ template <int KIND, int NW, int M> __device__ void solve_team(const BatchArgs &a
                 break;
             }
             if (a.adapt && it < a.max_iter) { // Sec. IV-A, duals rescaled by rho_old / rho_new
-                const double ratio = r / sgm, target = a.r_tol / a.s_tol;
+                const double ratio = r / sgm, target = a.adapt_target;
                 double f = 1.0;
                 if (ratio > 1.2 * target) f = a.tau;
                 else if (ratio < 0.8 * target) f = 1.0 / a.tau;

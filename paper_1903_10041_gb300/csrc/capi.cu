@@ -170,6 +170,7 @@ struct admm_handle {
     unsigned *bar = nullptr, *flags = nullptr;
     int *status = nullptr;
     double *info_host = nullptr; // pinned
+    cudaEvent_t done = nullptr;  // recorded after each queued solve (admm_wait)
     // launch shape
     int grid = 0, nbmax = 0, rs = 0, minb = 1;
     int64_t chunk = 0, ncols = 0;
@@ -221,6 +222,8 @@ void free_all(admm_handle *h)
     dfree(h->status);
     if (h->info_host) cudaFreeHost(h->info_host);
     h->info_host = nullptr;
+    if (h->done) cudaEventDestroy(h->done);
+    h->done = nullptr;
 }
 
 struct DeviceGuard {
@@ -431,6 +434,8 @@ admm_status admm_create(const admm_problem *P, const admm_params *prm, admm_hand
     TRY(dev_malloc(af, &h->flags, sizeof(unsigned)));
     TRY(dev_malloc(af, &h->status, sizeof(int)));
     TRY(cudaMallocHost(&h->info_host, kInfo * 8));
+    for (int t = 0; t < kInfo; ++t) h->info_host[t] = 0.0;
+    TRY(cudaEventCreateWithFlags(&h->done, cudaEventDisableTiming));
 
     const bool dev = P->on_device != 0;
     const double *src[9] = {P->f2, P->f1, P->f0, P->g2, P->g1, P->g0, P->x_lo, P->x_hi, P->y};
@@ -527,6 +532,36 @@ admm_status admm_reset(admm_handle *h)
     return reset_state(h);
 }
 
+// Status of a finished solve from its info record.
+static admm_status result_status(const double *inf)
+{
+    if (inf[12] != 0.0) return (admm_status)(int)inf[12];
+    return inf[1] == 0.0 ? ADMM_ENOTCONVERGED : ADMM_OK;
+}
+
+static void fill_result(const double *inf, admm_result *out)
+{
+    out->iters = (int32_t)inf[0];
+    out->converged = inf[1] != 0.0;
+    out->r = inf[2];
+    out->sigma = inf[3];
+    out->objective = inf[11];
+    out->status = result_status(inf);
+}
+
+// Host function queued behind a solve: copies its record into the caller's
+// admm_result (no CUDA calls in here).
+struct ResultFill {
+    const double *info_host;
+    admm_result *out;
+};
+static void CUDART_CB fill_result_cb(void *p)
+{
+    ResultFill *rf = (ResultFill *)p;
+    fill_result(rf->info_host, rf->out);
+    delete rf;
+}
+
 static admm_status load_state(admm_handle *h, const admm_state *w, cudaStream_t st)
 {
     const int m = h->m, q = h->q, mq = m * q;
@@ -596,8 +631,9 @@ admm_status admm_solve(admm_handle *h, const admm_state *warm, admm_result *out,
     a.bar = h->bar;
     a.status = h->status;
     a.info = h->info;
-    a.r_tol = h->prm.r_tol;
-    a.s_tol = h->prm.s_tol;
+    a.r_tol = stop_r_tol(h->prm.precision, h->prm.r_tol);
+    a.s_tol = stop_s_tol(h->prm.precision, h->prm.s_tol);
+    a.adapt_target = h->prm.r_tol / h->prm.s_tol;
     a.tau = h->prm.tau;
     a.max_iter = h->prm.max_iter;
     a.check_every = h->prm.check_every;
@@ -613,19 +649,27 @@ admm_status admm_solve(admm_handle *h, const admm_state *warm, admm_result *out,
     if (out && out->x1)
         CUDA_TRY(cudaMemcpyAsync(out->x1, h->scal + 5 * h->m * h->q, h->m * 8,
                                  out->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
-    CUDA_TRY(cudaStreamSynchronize(st));
-    const double *inf = h->info_host;
-    admm_status s = ADMM_OK;
-    if (inf[12] != 0.0) s = (admm_status)(int)inf[12];
-    else if (inf[1] == 0.0) s = ADMM_ENOTCONVERGED;
     if (out) {
-        out->iters = (int32_t)inf[0];
-        out->converged = inf[1] != 0.0;
-        out->r = inf[2];
-        out->sigma = inf[3];
-        out->objective = inf[11];
-        out->status = s;
+        // fills *out when the stream reaches this point (valid after a sync)
+        ResultFill *rf = new ResultFill{h->info_host, out};
+        cudaError_t e = cudaLaunchHostFunc(st, fill_result_cb, rf);
+        if (e != cudaSuccess) {
+            delete rf;
+            return fail(ADMM_ECUDA, "CUDA error: %s", cudaGetErrorString(e));
+        }
     }
+    CUDA_TRY(cudaEventRecord(h->done, st));
+    return ADMM_OK;
+}
+
+admm_status admm_wait(admm_handle *h, admm_result *out)
+{
+    g_err.clear();
+    if (!h) return fail(ADMM_EINVAL, "handle is NULL");
+    DeviceGuard dg(h->dev);
+    CUDA_TRY(cudaEventSynchronize(h->done));
+    if (out) fill_result(h->info_host, out);
+    const admm_status s = result_status(h->info_host);
     if (s == ADMM_ETIMEOUT) return fail(s, "a grid barrier wait timed out");
     if (s == ADMM_ENOTCONVERGED) g_err = "max_iter reached before the stop test passed";
     return s;

@@ -50,11 +50,13 @@ admm_status nfail(admm_status s, const char *msg, const char *detail = "")
 
 // Validation of the caller's problem and preparation of the scratch: the
 // scalar state vector, sum_k beta_0 per pair, zeroed counters.  One CTA per
-// pair; all CTAs also scan the elements for invalid data.
+// pair; all CTAs also scan the elements for invalid data.  It reads the
+// caller's arrays and writes only the scratch, so a problem found invalid
+// leaves the caller's state as it was.
 __global__ void noalloc_prepare(int n, int m, int q, const double *f2, const double *f1, const double *f0,
                                 const double *g2, const double *g1, const double *g0, const double *lo,
-                                const double *hi, const double *y, const double *c, double *x, double *s,
-                                double *mu, const double *lam, const double *zeta, const double *hh,
+                                const double *hi, const double *y, const double *c, const double *lam,
+                                const double *zeta, const double *hh,
                                 const double *pp, const double *nu, const double *x1, double rho1, double rho2,
                                 double rho3, double rho4, int cold, double *scal, double *sumg0,
                                 unsigned *bar, int *status, unsigned *flags)
@@ -79,13 +81,6 @@ __global__ void noalloc_prepare(int n, int m, int q, const double *f2, const dou
         xm = clampd(xm, l, h);
         s0 += v[5];
         smin += v[3] * xm * xm + v[4] * xm + v[5];
-        if (cold) {
-            x[e] = clampd(0.0, l, h);
-            if (i == 0) {
-                s[(size_t)j * n + k] = 0.0;
-                mu[(size_t)j * n + k] = 0.0;
-            }
-        }
     }
     s0 = warp_sum(s0);
     smin = warp_sum(smin);
@@ -122,6 +117,23 @@ __global__ void noalloc_prepare(int n, int m, int q, const double *f2, const dou
         }
     }
     if (bits) atomicOr(flags, bits);
+}
+
+// The zero start of the element and column state (x = clamp(0), s = mu = 0),
+// written only once the problem has passed validation.
+__global__ void noalloc_cold_start(int n, int m, int q, const double *lo, const double *hi, double *x, double *s,
+                                   double *mu)
+{
+    const int64_t ne = (int64_t)m * q * n, nc = (int64_t)q * n;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ne; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = t / n;
+        const int k = (int)(t - r * n), i = (int)(r / q);
+        x[t] = clampd(0.0, lo[(size_t)i * n + k], hi[(size_t)i * n + k]);
+        if (t < nc) {
+            s[t] = 0.0;
+            mu[t] = 0.0;
+        }
+    }
 }
 
 // Copies the final scalar state back to the caller's arrays.
@@ -219,7 +231,7 @@ extern "C" admm_status admm_solve_noalloc(const admm_problem *P, const admm_para
     cudaStream_t cs = (cudaStream_t)stream;
     noalloc_zero_flags<<<1, 1, 0, cs>>>(flags);
     noalloc_prepare<<<mq, 256, 0, cs>>>(n, m, q, P->f2, P->f1, P->f0, P->g2, P->g1, P->g0, P->x_lo, P->x_hi, P->y,
-                                       P->c, st->x, st->s, st->mu, st->lam, st->zeta, st->h, st->p, st->nu, st->x1,
+                                       P->c, st->lam, st->zeta, st->h, st->p, st->nu, st->x1,
                                        st->cold ? prm->rho[0] : st->rho[0],
                                        st->cold ? (prm->rho2_over_n ? prm->rho[1] / (double)n : prm->rho[1]) : st->rho[1],
                                        st->cold ? prm->rho[2] : st->rho[2], st->cold ? prm->rho[3] : st->rho[3],
@@ -237,6 +249,12 @@ extern "C" admm_status admm_solve_noalloc(const admm_problem *P, const admm_para
         if (hflags & 16u) why += " c is NaN;";
         if (hflags & 8u) why += " sum_k min g > c (infeasible);";
         return nfail(ADMM_EINVAL, "invalid problem:", why.c_str());
+    }
+    if (st->cold) {
+        const int64_t ne = (int64_t)mq * n;
+        const int blocks = (int)std::min<int64_t>((ne + 255) / 256, (int64_t)nsm * 8);
+        noalloc_cold_start<<<blocks, 256, 0, cs>>>(n, m, q, P->x_lo, P->x_hi, st->x, st->s, st->mu);
+        if ((e = cudaGetLastError()) != cudaSuccess) return nfail(ADMM_ECUDA, "cold start: ", cudaGetErrorString(e));
     }
 
     SingleArgs a{};
@@ -274,6 +292,7 @@ extern "C" admm_status admm_solve_noalloc(const admm_problem *P, const admm_para
     a.info = info;
     a.r_tol = prm->r_tol;
     a.s_tol = prm->s_tol;
+    a.adapt_target = prm->r_tol / prm->s_tol;
     a.tau = prm->tau;
     a.max_iter = prm->max_iter;
     a.check_every = prm->check_every;

@@ -651,8 +651,9 @@ admm_status admm_server_create(const admm_params *prm, const admm_server_config 
     a.tick_work = (const float *)(S->d_counts + 3);
     a.tick_rounds = S->d_counts + 4;
     a.lock = S->d_lock;
-    a.r_tol = prm->r_tol;
-    a.s_tol = prm->s_tol;
+    a.r_tol = stop_r_tol(prm->precision, prm->r_tol);
+    a.s_tol = stop_s_tol(prm->precision, prm->s_tol);
+    a.adapt_target = prm->r_tol / prm->s_tol;
     a.tau = prm->tau;
     a.max_iter = prm->max_iter;
     a.check_every = prm->check_every;

@@ -595,7 +595,7 @@ __global__ void __launch_bounds__(NT, MINB) single_kernel(SingleArgs a)
                 break;
             }
             if (a.adapt && it < a.max_iter) { // Sec. IV-A, duals rescaled by rho_old / rho_new
-                const double ratio = r / sg, target = a.r_tol / a.s_tol;
+                const double ratio = r / sg, target = a.adapt_target;
                 double f = 1.0;
                 if (ratio > 1.2 * target) f = a.tau;
                 else if (ratio < 0.8 * target) f = 1.0 / a.tau;

@@ -43,6 +43,12 @@ class _Solver:
     def solve(self, stream=None, x_out=None, x1_out=None):
         return {"status": 0, "iters": 3330, "converged": True, "objective": 38.22, "r": 0.0, "sigma": 0.0}
 
+    def solve_async(self, stream=None):
+        pass
+
+    def wait(self):
+        return self.solve()
+
     def close(self):
         pass
 
@@ -99,3 +105,93 @@ def test_default_line_has_every_contract_key(monkeypatch, capsys):
     assert e2e["d2h_bytes_per_step"] == 8 * (P.m * P.q * P.n + P.m)
     assert line["gpu_launches"] == 10
     assert set(line["clocks"]) >= {"sm_mhz", "sm_max_mhz", "reasons"}
+
+
+class _Batch:
+    """Stand-in for capi.Batch: fixed iteration counts and results."""
+
+    def __init__(self, probs, par):
+        self.probs = probs
+        self.cfg = {"warps_per_cta": 8, "ctas_per_sm": 2, "small_max_elements": 0, "cluster_size": 1,
+                    "cluster_min_elements": 0}
+
+    def set_config(self, *a):
+        pass
+
+    def config(self):
+        return dict(self.cfg)
+
+    def autotune(self, trial_iters=30):
+        return dict(self.cfg)
+
+    def reset(self):
+        pass
+
+    def solve(self, stream=None):
+        pass
+
+    def wait(self, stream=None, want_x=False):
+        import numpy as np
+        out = []
+        for P in self.probs:
+            r = {"iters": 1000, "converged": True, "objective": 1.0, "status": 0}
+            if want_x:
+                r["x"], r["x1"] = np.zeros((P.m, P.q, P.n)), np.zeros(P.m)
+            out.append(r)
+        return out
+
+    def state(self, t):
+        return {}
+
+    def close(self):
+        pass
+
+
+def test_default_batched_line_has_every_contract_key(monkeypatch, capsys):
+    """The default workload (no --config) is the 4096-instance batch; its
+    line carries the contract keys, an HBM roofline over the algorithmic
+    bytes, the oracle's CPU baseline and the end-to-end leg."""
+    torch = pytest.importorskip("torch")
+    b = _bench()
+    monkeypatch.setattr(torch.cuda, "Event", _Event)
+    monkeypatch.setattr(torch.cuda, "Stream", lambda: types.SimpleNamespace(cuda_stream=0))
+    monkeypatch.setattr(torch.cuda, "synchronize", lambda *a: None)
+    real_empty = torch.empty
+    monkeypatch.setattr(torch, "empty", lambda *a, device=None, **k: real_empty(*a, **k))
+    monkeypatch.setattr(torch.Tensor, "pin_memory", lambda self: self)
+    monkeypatch.setattr(torch.Tensor, "fill_", lambda self, v: self)
+    import paper_1903_10041_gb300 as pkg
+    from paper_1903_10041_gb300 import build
+    build.build()
+    import paper_1903_10041_gb300.capi  # noqa: F401
+    fake = types.ModuleType("paper_1903_10041_gb300.capi")
+    fake.Batch = _Batch
+    monkeypatch.setitem(__import__("sys").modules, "paper_1903_10041_gb300.capi", fake)
+    monkeypatch.setattr(pkg, "capi", fake, raising=False)
+    # a short oracle comparison stands in for the sampled full solves
+    monkeypatch.setattr(b, "oracle_sample_errors", lambda probs, par, res, states, idx, oracle: {
+        "instances": idx, "max_rel_objective_err": 0.0, "max_kkt_excess": 0.0})
+    monkeypatch.setattr(b.os, "cpu_count", lambda: 2)
+    ns = b.argparse.Namespace(gpus=1, steps=10, warmup=5, count=64, max_iter=0, batch_config="", adapt=False,
+                              no_e2e=False, no_cpu_baseline=False, no_oracle_sample=False)
+    b.run_batched(ns)
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "roofline", "cpu_baseline", "e2e",
+              "gpu_launches", "clocks"):
+        assert k in line, k
+    assert line["config"]["workload"].startswith("batched: 64 instances")
+    assert line["value"] == pytest.approx(64 * 10 / 0.8) and line["ms_per_step"] == pytest.approx(80.0)
+    rf = line["roofline"]
+    assert rf["bound"] == "hbm" and rf["unit"] == "GB/s" and rf["frac"] == pytest.approx(rf["achieved"] / rf["peak"])
+    assert rf["achieved"] == pytest.approx(rf["algorithmic_bytes"] / 0.080 / 1e9)
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 2
+    assert line["e2e"]["h2d_bytes_per_step"] > 0 and line["e2e"]["d2h_bytes_per_step"] > 0
+    assert line["gpu_launches"] == 10
+
+
+def test_no_flag_default_is_the_batched_workload():
+    b = _bench()
+    import inspect
+    src = inspect.getsource(b.main)
+    assert 'ap.add_argument("--config", type=int, default=3' in src

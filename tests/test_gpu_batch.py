@@ -1,6 +1,6 @@
 """Batched solves (one persistent launch, one team per instance, mixed
 precision): every instance matches the FP64 oracle (objective to 1e-6
-relative, KKT within r-bar + sigma-bar = 2e-6 of the oracle's), gives the same bits alone and
+relative, KKT residual at most the oracle's plus 1e-6), gives the same bits alone and
 in the mix, and keeps doing so under every launch configuration the
 autotuner may pick."""
 import numpy as np
@@ -63,7 +63,7 @@ def test_batch_matches_the_oracle_per_instance(capi, oracle_lib):
         obj_o = oracle_lib.objective(P, st_o["x"])
         assert abs(res[t]["objective"] - obj_o) <= 1e-6 * max(1.0, abs(obj_o)), (t, res[t]["objective"], obj_o)
         k_o = oracle_lib.kkt(P, par, st_o)[0]
-        assert _kkt(oracle_lib, P, par, states[t]) <= k_o + 2e-6, t
+        assert _kkt(oracle_lib, P, par, states[t]) <= k_o + 1e-6, t
     assert kinds["small"] > 0 and kinds["large"] > 0 and kinds["cluster"] > 0
 
 

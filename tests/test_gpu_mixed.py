@@ -1,9 +1,10 @@
 """Mixed-precision solves (FP32 storage and element work, FP64 scalars and
 residuals) against the FP64 oracle: at convergence the objective matches
-to 1e-6 relative and the KKT residual of eq. (2) stays within r-bar +
-sigma-bar = 2e-6 of the oracle's own (both stop on the termination test of
-Alg. 2 step 3, a few iterations apart, and that test fixes the KKT residual
-only to within its two thresholds).  Both mixed policies are covered: the FP32 cubic with
+to 1e-6 relative and the KKT residual of eq. (2) is at most the oracle's
+own plus 1e-6.  Mixed solves stop at sigma < 0.85 sigma-bar (and r < r-bar)
+in the termination test of Alg. 2 step 3: the margin on sigma, the
+binding residual, absorbs the FP32 rounding of the stored x; the extra
+iterations this costs are printed beside the oracle's count.  Both mixed policies are covered: the FP32 cubic with
 FP64-certified branch decisions and the FP64 cubic step."""
 import numpy as np
 import pytest
@@ -13,7 +14,7 @@ from paper_1903_10041_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 OBJ_TOL = 1e-6
-KKT_MARGIN = 2e-6  # r-bar + sigma-bar of the termination test
+KKT_MARGIN = 1e-6
 
 
 @pytest.fixture(scope="module")
@@ -60,6 +61,8 @@ def test_mixed_converges_to_the_oracle_solution(capi, oracle_lib, case, precisio
     rel_obj = abs(res["objective"] - obj_o) / max(1.0, abs(obj_o))
     assert rel_obj <= OBJ_TOL, (rel_obj, res["objective"], obj_o)
     k_g, terms = _kkt(oracle_lib, P, par, st, st["rho"])
+    print(f"{case} {precision}: iterations {res['iters']} (oracle {rep_o['iters']}), KKT {k_g:.3e} "
+          f"(oracle {k_o:.3e}), objective error {rel_obj:.1e}")
     assert k_g <= k_o + KKT_MARGIN, (k_g, k_o, terms)
     assert info["fp64_escalations"] >= 0
 

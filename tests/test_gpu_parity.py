@@ -61,7 +61,7 @@ def compare_states(P, st_o, rep_o, st_g, res, tol=TOL, check_res=True):
         "p": rel(st_g["p"], st_o["p"]),
         "nu": rel(st_g["nu"], st_o["nu"]),
         "x1": rel(st_g["x1"], st_o["x1"]),
-        "lam": rel(st_g["lam"], st_o["lam"][:, :, 0]),
+        "lam": rel(np.broadcast_to(st_g["lam"][:, :, None], st_o["lam"].shape), st_o["lam"]),  # every k
     }
     gx = P.g2 * st_g["x"] ** 2 + P.g1 * st_g["x"] + P.g0
     errs["z"] = rel(gx + st_g["zeta"][:, :, None], st_o["z"])
@@ -117,7 +117,14 @@ def test_double_well_trig_branch(capi, oracle_lib, mode, sweep):
     with capi.Solver(P, par) as s:
         res = s.solve(raise_on=(1, 2, 3, 4, 6))
         st_g = s.state()
-    compare_states(P, st_o, rep_o, st_g, res, tol=1e-8)
+    # a near-tie in delta-f (or a near-double root) could choose the other
+    # local minimum on one side; such an element would differ by O(1).  Count
+    # them: none occur on this trajectory, so every element is held to 1e-9.
+    scale = max(1.0, np.abs(st_o["x"]).max())
+    flips = int(np.count_nonzero(np.abs(st_g["x"] - st_o["x"]) > 1e-6 * scale))
+    print(f"{mode} {sweep}: trig-branch updates {rep_o['branch_count'][2]}, elements on the other minimum {flips}")
+    assert flips == 0
+    compare_states(P, st_o, rep_o, st_g, res)
 
 
 def test_phev_shape_with_infinite_capacity(capi, oracle_lib):
@@ -240,3 +247,40 @@ def test_rho2_over_n_equals_explicit_rho2(capi, oracle_lib):
     assert np.array_equal(sa["x"], sb["x"]) and sa["rho"] == sb["rho"]
     st_o, _ = oracle_lib.solve(P, a, threads=8)
     assert rel(sa["x"], st_o["x"]) <= TOL
+
+
+def test_solve_returns_once_queued_and_two_handles_overlap(capi, oracle_lib):
+    """admm_solve queues the solve on the caller's stream and returns; the
+    result record is valid after the stream is synchronised.  Two handles on
+    two streams: both calls return before either solve ends, and each result
+    equals the same solve run alone."""
+    import time
+    import torch
+    P1, P2 = W.config(1), W.random_problem(2000, 3, 6, seed=97)
+    par1 = W.Params(rho=(1.0, 1.0 / P1.n, 1.0, 1.0), max_iter=1500, r_tol=0.0, s_tol=0.0)
+    par2 = W.Params(rho=(1.0, 1.0 / P2.n, 1.0, 1.0), max_iter=1500, r_tol=0.0, s_tol=0.0)
+    alone = []
+    for P, par in ((P1, par1), (P2, par2)):
+        with capi.Solver(P, par) as s:
+            t0 = time.perf_counter()
+            s.solve(raise_on=(1, 2, 3, 4, 6))
+            alone.append((time.perf_counter() - t0, s.state()))
+    s1, s2 = capi.Solver(P1, par1), capi.Solver(P2, par2)
+    st1, st2 = torch.cuda.Stream(), torch.cuda.Stream()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s1.solve_async(stream=st1)
+    s2.solve_async(stream=st2)
+    queued = time.perf_counter() - t0
+    assert queued < 0.5 * min(alone[0][0], alone[1][0]), (queued, alone[0][0], alone[1][0])
+    st1.synchronize()
+    st2.synchronize()
+    rec1, rec2 = s1._pending.res, s2._pending.res       # filled by the time the streams are synchronised
+    assert rec1.iters == 1500 and rec2.iters == 1500 and rec1.status == capi.ADMM_ENOTCONVERGED
+    r1, r2 = s1.wait(raise_on=()), s2.wait(raise_on=())
+    assert r1["iters"] == 1500 and r2["iters"] == 1500
+    for s, (_, ref) in ((s1, alone[0]), (s2, alone[1])):
+        got = s.state()
+        for k in ("x", "s", "mu", "lam", "h", "p", "nu", "x1"):
+            assert np.array_equal(got[k], ref[k]), k
+        s.close()
