@@ -284,7 +284,7 @@ def run_reference(args):
     if args.config in (3, 4):
         return run_reference_batched(args, oracle)
     P, par = workload(args.config, "fp64")
-    par = par.replace(adapt_rho=args.adapt)
+    par = paper_penalties(P) if args.paper_penalties else par.replace(adapt_rho=args.adapt)
     # iterations of a full solve: the oracle's own count.  For the n=1e5, m=4, q=20 instance a full
     # oracle solve takes about 10 minutes on 8 cores, so its count (2650 with fixed penalties, run once)
     # is used; with the adaptation it is counted here like the others.
@@ -523,6 +523,63 @@ def run_batched(args):
     return 0
 
 
+def shifted_oracle_state(P_new, P_old, st):
+    """The receding-horizon warm start the server applies, written on the
+    oracle's dense state: x, s, mu and the offsets z - g(x) move one step
+    forward (last step kept), x at the new last step is clamped to its new
+    bounds, x_1 is the mean of the new first moves; lambda, h, p, nu are
+    kept."""
+    import numpy as np
+    sh = lambda a: np.concatenate([a[..., 1:], a[..., -1:]], axis=-1)
+    g = lambda Q, x: Q.g2 * x * x + Q.g1 * x + Q.g0
+    x = sh(st["x"])
+    x[:, :, -1] = np.clip(x[:, :, -1], P_new.lo[:, None, -1], P_new.hi[:, None, -1])
+    d = sh(st["z"] - g(P_old, st["x"]))
+    return {"x": x, "z": g(P_new, x) + d, "lam": st["lam"].copy(), "s": sh(st["s"]), "mu": sh(st["mu"]),
+            "h": st["h"].copy(), "p": st["p"].copy(), "nu": st["nu"].copy(), "x1": x[:, :, 0].mean(axis=1)}
+
+
+def serving_cpu_baseline(trace, par, budget_s: float = 12.0, max_elements: int = 40000):
+    """The oracle replaying the request trace serially on the host cores: the
+    controllers of the first requests (those with at most `max_elements`
+    elements) are solved cold (untimed), then their requests in trace order
+    are solved warm-started from the shifted previous state, each timed, for
+    about `budget_s` seconds.  Service times only: a serial CPU cannot keep
+    up with the arrival rate, so there is no queueing model."""
+    import numpy as np
+    import oracle
+    from paper_1903_10041_gb300 import workloads as W
+    threads = os.cpu_count() or 1
+    po = par.replace(precision="fp64")
+    cur, states, times, iters = {}, {}, [], []
+    spent = 0.0
+    for c, step in trace:
+        if spent > budget_s:
+            break
+        if c not in cur:
+            P0 = W.batch_instance(c)
+            if P0.elements > max_elements:
+                continue
+            states[c] = oracle.solve(P0, po, threads=threads)[0]
+            cur[c] = P0
+        P_new = W.receding_step(cur[c], step, seed=W.SEED * (1 << 32) + c)
+        warm = shifted_oracle_state(P_new, cur[c], states[c])
+        t0 = time.perf_counter()
+        st, rep = oracle.solve(P_new, po, state=warm, threads=threads)
+        dt = time.perf_counter() - t0
+        spent += dt
+        times.append(dt)
+        iters.append(rep["iters"])
+        cur[c], states[c] = P_new, st
+    t = np.array(times) * 1e3
+    return {"value": len(t) / (t.sum() / 1e3), "unit": "solves/s", "cores": threads, "kind": "oracle",
+            "latency_ms": {"p50": float(np.percentile(t, 50)), "p99": float(np.percentile(t, 99)),
+                           "mean": float(t.mean())},
+            "sample": f"{len(t)} re-solves of {len(cur)} controllers (m*q*n <= {max_elements}) in trace order, "
+                      f"warm-started from the shifted previous state, timed one by one (service time, "
+                      f"no queueing); mean {np.mean(iters):.0f} iterations"}
+
+
 def run_serving(args):
     """The serving workload: Poisson arrivals of receding-horizon re-solves of `count`
     controllers sized as the batched workload; continuous batching."""
@@ -536,7 +593,7 @@ def run_serving(args):
         torch.distributed.barrier()
     from paper_1903_10041_gb300 import capi
     from paper_1903_10041_gb300 import workloads as W
-    par = W.Params(rho=(1.0, 1.0, 1.0, 1.0), rho2_over_n=True, precision="mixed")
+    par = batch_params(args)
     base = rank * args.count
     shapes = [W.batch_shape(base + c) for c in range(args.count)]
     total_el = sum(((n + 3) // 4 * 4) * m * q for n, m, q in shapes)
@@ -556,7 +613,16 @@ def run_serving(args):
         time.sleep(0.001)
     rng = np.random.default_rng(1903 + rank)
     steps = np.zeros(args.count, dtype=np.int64)
-    lat_all, it_all, st_all = [], [], []
+    owner, trace = {}, []
+    lat_all, it_all, st_all, ctl_all = [], [], [], []
+
+    def take():
+        t, lat, it, st = S.drain()
+        lat_all.extend(lat.tolist())
+        it_all.extend(it.tolist())
+        st_all.extend(st.tolist())
+        ctl_all.extend(owner.pop(int(k)) for k in t)
+
     submitted = 0
     st0 = S.stats()
     t_start = time.perf_counter()
@@ -570,13 +636,12 @@ def run_serving(args):
                 c = int(rng.integers(args.count))
                 steps[c] += 1
                 n, m, q = shapes[c]
-                S.submit_step(c, W.step_data(m, q, int(steps[c]), seed=W.SEED * (1 << 32) + base + c))
+                tk = S.submit_step(c, W.step_data(m, q, int(steps[c]), seed=W.SEED * (1 << 32) + base + c))
+                owner[tk] = c
+                trace.append((base + c, int(steps[c])))
                 submitted += 1
                 next_t += rng.exponential(1.0 / args.rate)
-            t, lat, it, st = S.drain()
-            lat_all.extend(lat.tolist())
-            it_all.extend(it.tolist())
-            st_all.extend(st.tolist())
+            take()
             time.sleep(0.0005)
         window = time.perf_counter() - t_start
         st1 = S.stats()
@@ -585,30 +650,42 @@ def run_serving(args):
         finished_in_window = len(lat_all)
         t_end = time.perf_counter()
         while len(lat_all) < submitted and time.perf_counter() - t_end < 120:
-            t, lat, it, st = S.drain()
-            lat_all.extend(lat.tolist())
-            it_all.extend(it.tolist())
-            st_all.extend(st.tolist())
+            take()
             time.sleep(0.001)
     stats = S.stats()
     S.close()
     lat = np.array(lat_all) * 1e3
     value = finished_in_window / window
     (vmin,) = barrier_max([-value], world)
+    # algorithmic bytes of the finished re-solves: iterations x the mixed per-iteration count of each shape
+    from types import SimpleNamespace as NS
+    bpi = lambda c: bytes_per_iteration(NS(n=shapes[c][0], m=shapes[c][1], q=shapes[c][2]), "mixed")
+    byts = float(sum(i * bpi(c) for i, c in zip(it_all, ctl_all)))
+    peaks = measured_peaks()
+    gbs = byts / window / 1e9
+    d2h = float(np.mean([8 * (n * m * q + m) for n, m, q in (shapes[c] for c in ctl_all)])) + 24 if ctl_all else 0.0
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = serving_cpu_baseline(trace, par)
     if rank == 0:
+        ok = np.array(st_all) == 0
         line = {"metric": METRIC, "value": value * world, "unit": "solves/s", "n_gpus": world,
-                "steps": submitted, "warmup": args.count, "ms_per_step": float(np.mean(lat)) if len(lat) else None,
+                "steps": finished_in_window, "warmup": args.count,
+                "ms_per_step": 1e3 * window / max(1, finished_in_window),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
                 "data": "synthetic (seeded receding-horizon steps per controller)",
                 "config": {"workload": f"serving: Poisson {args.rate:g}/s re-solves of {args.count} controllers "
                                        f"sized as the batched workload, {args.duration:g} s window",
-                           "tick_iters": args.tick_iters, "rho": "(1, 1/n, 1, 1) per instance",
+                           "tick_iters": args.tick_iters, "rho": penalty_text(args),
+                           "steps": "requests finished in the window; warmup = the controllers' cold solves",
                            "parallelism": f"replicas x{world}"},
                 "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                                "mean": float(np.mean(lat)), "max": float(np.max(lat))} if len(lat) else None,
-                "submitted": submitted, "finished": len(lat_all),
-                "iters": {"mean": float(np.mean(it_all)), "max": int(np.max(it_all))} if it_all else None,
-                "ok_frac": float(np.mean(np.array(st_all) == 0)) if st_all else None,
+                "window_s": window, "submitted": submitted, "finished": len(lat_all),
+                "iters": {"mean": float(np.mean(it_all)), "p99": float(np.percentile(it_all, 99)),
+                          "max": int(np.max(it_all)), "at_cap_frac": float(np.mean(np.array(it_all) >= par.max_iter))}
+                if it_all else None,
+                "ok_frac": float(np.mean(ok)) if st_all else None,
                 "gpu_busy_frac": busy_window / window, "gpu_shift_frac": shift_window / window,
                 "mean_active": (st1["instance_ticks"] - st0["instance_ticks"]) / max(1.0, st1["ticks"] - st0["ticks"]),
                 "server_stats": stats,
@@ -617,12 +694,18 @@ def run_serving(args):
                 "gpu_launches": int(st1["ticks"] - st0["ticks"]),
                 # requests go in and results come out through the public API from host memory, so the
                 # served rate is itself end to end: a step request carries f, g [m][q], bounds [m] and
-                # y [q] in FP64; a drained result is its ticket, latency, iterations and status
+                # y [q] in FP64; each finished request's x [m][q][n] and x_1 [m] come back in FP64
+                # (the server gathers them every tick) with its 24-byte record
                 "e2e": {"value": value * world, "unit": "solves/s",
                         "h2d_bytes_per_step": float(np.mean([8 * (6 * m * q + 2 * m + q) for _, m, q in shapes])),
-                        "d2h_bytes_per_step": 8 + 8 + 4 + 4},
-                "roofline": None, "cpu_baseline": None, "clocks": clk.summary()}
-        print(json.dumps(line))
+                        "d2h_bytes_per_step": d2h},
+                "roofline": {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                             "frac": gbs / peaks["hbm_gbs"], "traffic": None, "algorithmic_bytes": byts,
+                             "over": "the whole window (GPU idle time included)",
+                             "achieved_while_busy": byts / max(busy_window, 1e-9) / 1e9,
+                             "peak_source": peaks["source"]},
+                "cpu_baseline": cpu, "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
     return 0
 
 
@@ -753,6 +836,9 @@ def main():
     ap.add_argument("--tick-iters", type=int, default=10,
                     help="iterations per serving tick of the costliest active instance (4)")
     ap.add_argument("--adapt", action="store_true", help="penalty adaptation of Sec. IV-A (0, 1, 2, 3, --q-sweep)")
+    ap.add_argument("--paper-penalties", action="store_true",
+                    help="--config 1 or --q-sweep: the PHEV settings of Sec. IV-A (rho = 1e-4, 2e-6, 5e-6, 5e-6; "
+                         "r-bar = 1e-6 dE, sigma-bar = 1e-2; adaptation on)")
     ap.add_argument("--batch-config", default="",
                     help="warps,ctas_per_sm,small_max,cluster,cluster_min instead of the autotuner (3, 4)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "mixed_fp64cubic"])
@@ -789,20 +875,32 @@ def main():
     if world > 1:
         torch.distributed.barrier()
     if args.q_sweep:
-        for P, par in sweep_workloads(args.q_sweep, args.precision, args.adapt):
+        for P, par in sweep_workloads(args.q_sweep, args.precision, args.adapt, args.paper_penalties):
             run_single(args, P, par, rank, world, local)
     else:
         P, par = workload(args.config, args.precision, args.coef_shared)
-        run_single(args, P, par.replace(adapt_rho=args.adapt), rank, world, local)
+        par = paper_penalties(P, args.precision) if args.paper_penalties else par.replace(adapt_rho=args.adapt)
+        run_single(args, P, par, rank, world, local)
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
 
 
-def sweep_workloads(spec: str, precision: str, adapt: bool):
+def paper_penalties(P, precision: str = "fp64"):
+    """The settings of the PHEV study (Sec. IV-A): initial penalties rho_1 =
+    1e-4, rho_2 = 2e-6, rho_3 = rho_4 = 5e-6, thresholds r-bar = 1e-6 dE
+    (dE: the battery capacity, c of the second source) and sigma-bar = 1e-2,
+    with the penalty adaptation on."""
+    from paper_1903_10041_gb300 import workloads as W
+    dE = float(P.c[1])
+    return W.Params(rho=(1e-4, 2e-6, 5e-6, 5e-6), r_tol=1e-6 * dE, s_tol=1e-2, adapt_rho=True, precision=precision)
+
+
+def sweep_workloads(spec: str, precision: str, adapt: bool, paper: bool = False):
     """The PHEV-shaped instance (n = 1000, m = 2) at each scenario count of a
-    comma-separated list, with the penalties of the q = 50 case: the runtime
-    against q sweep of Sec. IV-B (q from 5 to 500 there)."""
+    comma-separated list, with the penalties of the q = 50 case (or, with
+    `paper`, the settings of Sec. IV-A): the runtime against q sweep of
+    Sec. IV-B (q from 5 to 500 there)."""
     from paper_1903_10041_gb300 import workloads as W
     out = []
     for tok in spec.split(","):
@@ -810,7 +908,9 @@ def sweep_workloads(spec: str, precision: str, adapt: bool):
         if q < 1:
             raise ValueError(f"scenario count {q} < 1")
         P = W.phev_problem(1000, q)
-        out.append((P, W.Params(rho=(1.0, 1.0 / P.n, 1.0, 1.0), precision=precision, adapt_rho=adapt)))
+        par = (paper_penalties(P, precision) if paper else
+               W.Params(rho=(1.0, 1.0 / P.n, 1.0, 1.0), precision=precision, adapt_rho=adapt))
+        out.append((P, par))
     return out
 
 

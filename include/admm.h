@@ -290,9 +290,14 @@ admm_status admm_batch_set_config(admm_batch *b, const admm_batch_config *cfg);
  * actually launched. */
 admm_status admm_batch_get_config(admm_batch *b, admm_batch_config *cfg);
 /* Times each candidate configuration (warps per CTA x team thresholds x
- * cluster size) on
- * `trial_iters` iterations of this batch, keeps the fastest, and resets
- * every instance to the zero start.  *chosen (may be NULL) receives it. */
+ * cluster size) on this batch, keeps the fastest, and resets every instance
+ * to the zero start.  trial_iters > 0: each candidate runs that many
+ * iterations (throughput; 4, 8, 16 warps x warp-team thresholds 0, 8192,
+ * 32768 x clusters off, of 4 or 8 CTAs); trial_iters = 0: each candidate
+ * runs the whole solve, so the time includes the tail of the slowest
+ * instances (8 or 16 warps, no warp teams, clusters off or of 2 or 4 CTAs
+ * for instances above 6e4 or 1.5e5 elements).  *chosen (may be NULL)
+ * receives the choice.  ADMM_EINVAL for trial_iters < 0. */
 admm_status admm_batch_autotune(admm_batch *b, int32_t trial_iters, admm_batch_config *chosen);
 /* Enqueues the solve of every unfinished instance from its current state
  * on `stream` (asynchronous; replays a CUDA graph captured on first use). */

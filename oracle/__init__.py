@@ -70,6 +70,12 @@ def lib():
         L.orc_objective.argtypes = [C.POINTER(_Problem), _dp]
         L.orc_kkt.restype = C.c_double
         L.orc_kkt.argtypes = [C.POINTER(_Problem), C.POINTER(_Params), C.POINTER(_State), _dp]
+        L.orc_shard_phase_a.restype = None
+        L.orc_shard_phase_a.argtypes = [C.POINTER(_Problem), C.POINTER(_Params), C.POINTER(_State), C.c_int,
+                                        _dp, _dp, _dp, _dp, _dp]
+        L.orc_shard_phase_b.restype = None
+        L.orc_shard_phase_b.argtypes = [C.POINTER(_Problem), C.POINTER(_Params), C.POINTER(_State), C.c_int,
+                                        _dp, _dp, _dp, _dp, _dp]
         _lib = L
     return _lib
 
@@ -176,3 +182,35 @@ def kkt(prob, par, state: dict):
     t = np.zeros(8)
     v = lib().orc_kkt(C.byref(H.c), C.byref(_params(par, n=H.n)), C.byref(_state_struct(st)), _ptr(t))
     return v, t
+
+
+def shard_phase_a(prob, par, state: dict, k0: int, xprev, sprev, threads: int = 1, n_total: int | None = None):
+    """Phase A of the column-sharded iteration on a worker's slice ``prob``
+    (its columns [k0, k0 + prob.n)): step (a), steps (e), (f), and the
+    worker's record [2 m q + 2] (see orc_shard_phase_a).  ``state`` holds
+    the worker's columns and every pair scalar; it is updated in place.
+    Returns (g(x) [m, q, n_s], record)."""
+    H = _Holder(prob)
+    m, q, n = H.m, H.q, H.n
+    gx = np.empty((m, q, n))
+    colsum = np.empty((q, n))
+    rec = np.empty(2 * m * q + 2)
+    xp, sp = _f64(xprev), _f64(sprev)
+    lib().orc_shard_phase_a(C.byref(H.c), C.byref(_params(par, threads, n=n_total or n)),
+                            C.byref(_state_struct(state)), int(k0), _ptr(xp), _ptr(sp), _ptr(gx), _ptr(colsum),
+                            _ptr(rec))
+    return gx, rec
+
+
+def shard_phase_b(prob, par, state: dict, n_total: int, tot, gx, zprev, hprev):
+    """Phase B of the column-sharded iteration with the combined record
+    ``tot``: steps (b), (g) on the worker's columns and (c), (d), (h), (i)
+    on the pair scalars (see orc_shard_phase_b).  Returns the residual terms
+    [|z - g(x)| max, |z - z~| max (the worker's), |h - 1'z|, copies,
+    |h - h~| (every worker's)]."""
+    H = _Holder(prob)
+    res = np.empty(5)
+    t, g, zp, hp = _f64(tot), _f64(gx), _f64(zprev), _f64(hprev)
+    lib().orc_shard_phase_b(C.byref(H.c), C.byref(_params(par, n=n_total)), C.byref(_state_struct(state)),
+                            int(n_total), _ptr(t), _ptr(g), _ptr(zp), _ptr(hp), _ptr(res))
+    return res

@@ -229,17 +229,17 @@ static void step_a_coeffs(const orc_problem *P, const orc_params *pr, size_t e, 
 
 static double amax(double a, double b) { return a > b ? a : b; }
 
-/* One ADMM iteration (a)-(i).  `xprev` holds x at the start of the iteration
- * (for Jacobi and the residuals).  Returns nothing; residuals are computed
- * by the caller from the saved previous iterate. */
-static void admm_iteration(const orc_problem *P, const orc_params *pr, orc_state *S,
-                           const double *xprev, double *gx, double *colsum, orc_report *rep)
+/* Step (a) of App. A on the columns of P: the x-update source by source;
+ * for a fixed i the (j, k) updates are independent (Sec. II), so they may
+ * run in any order.  k0 is the global index of P's first column (nonzero
+ * only for a shard of columns, see orc_shard_phase_a): the copy term of
+ * step (a) applies at global k = 0.  `xprev` holds x at the start of the
+ * iteration (Jacobi sweep). */
+static void step_a(const orc_problem *P, const orc_params *pr, orc_state *S, const double *xprev, int k0,
+                   orc_report *rep)
 {
     int n = P->n, m = P->m, q = P->q;
     long long differs = 0, br0 = 0, br1 = 0, br2 = 0, br3 = 0;
-
-    /* (a) x-update, source by source; for a fixed i the (j, k) updates are
-     * independent (Sec. II), so they may run in any order. */
     for (int i = 0; i < m; ++i) {
 #pragma omp parallel for collapse(2) reduction(+ : differs, br0, br1, br2, br3)
         for (int j = 0; j < q; ++j)
@@ -253,7 +253,7 @@ static void admm_iteration(const orc_problem *P, const orc_params *pr, orc_state
                 double phi = S->s[IDX2(j, k)] - others + P->y[IDX2(j, k)] + S->mu[IDX2(j, k)];
                 double psi = S->x1[i] + S->nu[(size_t)i * q + j];
                 double A, B, C, D;
-                step_a_coeffs(P, pr, e, theta, phi, k == 0, psi, &A, &B, &C, &D);
+                step_a_coeffs(P, pr, e, theta, phi, k + k0 == 0, psi, &A, &B, &C, &D);
                 int br = 0;
                 double lo = P->lo[IDX2(i, k)], hi = P->hi[IDX2(i, k)];
                 double xn = orc_quartic_min(A, B, C, D, lo, hi, pr->xmin_mode, &br);
@@ -264,11 +264,43 @@ static void admm_iteration(const orc_problem *P, const orc_params *pr, orc_state
                 S->x[e] = xn;
             }
     }
-    for (size_t e = 0; e < (size_t)m * q * n; ++e)
-        gx[e] = g_at(P, e, S->x[e]);
     rep->literal_differs += differs;
     rep->branch_count[0] += br0; rep->branch_count[1] += br1;
     rep->branch_count[2] += br2; rep->branch_count[3] += br3;
+}
+
+/* Steps (e) and (f) on the columns of P (colsum receives sum_i x). */
+static void steps_e_f(const orc_problem *P, orc_state *S, double *colsum)
+{
+    int n = P->n, m = P->m, q = P->q;
+    /* (e) s-update: projection of sum_i x - y - mu onto [0, inf) */
+    for (int j = 0; j < q; ++j)
+        for (int k = 0; k < n; ++k) {
+            double sx = 0.0;
+            for (int i = 0; i < m; ++i)
+                sx += S->x[IDX3(i, j, k)];
+            colsum[IDX2(j, k)] = sx;
+            double v = sx - P->y[IDX2(j, k)] - S->mu[IDX2(j, k)];
+            S->s[IDX2(j, k)] = v > 0.0 ? v : 0.0;
+        }
+    /* (f) mu-update */
+    for (int j = 0; j < q; ++j)
+        for (int k = 0; k < n; ++k)
+            S->mu[IDX2(j, k)] += S->s[IDX2(j, k)] - colsum[IDX2(j, k)] + P->y[IDX2(j, k)];
+}
+
+/* One ADMM iteration (a)-(i).  `xprev` holds x at the start of the iteration
+ * (for Jacobi and the residuals).  Returns nothing; residuals are computed
+ * by the caller from the saved previous iterate. */
+static void admm_iteration(const orc_problem *P, const orc_params *pr, orc_state *S,
+                           const double *xprev, double *gx, double *colsum, orc_report *rep)
+{
+    int n = P->n, m = P->m, q = P->q;
+
+    /* (a) x-update */
+    step_a(P, pr, S, xprev, 0, rep);
+    for (size_t e = 0; e < (size_t)m * q * n; ++e)
+        gx[e] = g_at(P, e, S->x[e]);
 
     double kappa = pr->rho2 / (pr->rho1 + (double)n * pr->rho2);
     /* (b) z-update: z = g(x) - lambda + kappa 1 (h + p - 1'(g(x) - lambda)) */
@@ -298,20 +330,8 @@ static void admm_iteration(const orc_problem *P, const orc_params *pr, orc_state
             double v = sz - S->p[(size_t)i * q + j];
             S->h[(size_t)i * q + j] = v < P->c[i] ? v : P->c[i];
         }
-    /* (e) s-update: projection of sum_i x - y - mu onto [0, inf) */
-    for (int j = 0; j < q; ++j)
-        for (int k = 0; k < n; ++k) {
-            double sx = 0.0;
-            for (int i = 0; i < m; ++i)
-                sx += S->x[IDX3(i, j, k)];
-            colsum[IDX2(j, k)] = sx;
-            double v = sx - P->y[IDX2(j, k)] - S->mu[IDX2(j, k)];
-            S->s[IDX2(j, k)] = v > 0.0 ? v : 0.0;
-        }
-    /* (f) mu-update */
-    for (int j = 0; j < q; ++j)
-        for (int k = 0; k < n; ++k)
-            S->mu[IDX2(j, k)] += S->s[IDX2(j, k)] - colsum[IDX2(j, k)] + P->y[IDX2(j, k)];
+    /* (e), (f) */
+    steps_e_f(P, S, colsum);
     /* (g) lambda-update */
     for (int i = 0; i < m; ++i)
         for (int j = 0; j < q; ++j)
@@ -425,6 +445,122 @@ int orc_solve(const orc_problem *P, const orc_params *pr_in, orc_state *S, orc_r
     rep->rho[0] = prm.rho1; rep->rho[1] = prm.rho2; rep->rho[2] = prm.rho3; rep->rho[3] = prm.rho4;
     free(xp); free(zp); free(gx); free(sp); free(colsum); free(hp);
     return 0;
+}
+
+/* ---- The iteration split over workers that own columns k ----------------
+ * Step (a) and steps (e), (f), (g) act on one column (j, k) at a time
+ * (Sec. II: the (j, k) updates are independent); the coupling along k is
+ * the per-(i, j) sum of g(x) - lambda that steps (b), (d) and (i) use, and x
+ * at k = 0 that steps (c) and (h) use (App. A).  A worker that owns the
+ * columns [k0, k0 + n_s) of every row runs phase A on them; the partial
+ * records of all workers are combined (sums; x at k = 0 from its owner;
+ * maxima of the column residual terms); every worker then runs phase B with
+ * the combined record.  Steps (d) and (i) take 1'z = sum_k (g(x) - lambda)
+ * + n t, the value the monolithic iteration sums from the new z (equal up to
+ * rounding).  P is the worker's slice of the problem (n = n_s columns; c
+ * whole); S holds the worker's columns of x, z, lambda, s, mu and every
+ * h, p, nu, x_1. */
+
+/* Phase A: step (a), g(x), steps (e) and (f) on the worker's columns, then
+ * its record rec[2mq + 2]: [0, mq) sum over its columns of g(x) - lambda
+ * per pair (i, j); [mq, 2mq) x at the global k = 0 when k0 = 0, else 0;
+ * [2mq] the largest demand residual |s - sum_i x + y| of its columns;
+ * [2mq + 1] the largest |s - s~ - sum_i (x - x~)| (xprev, sprev: x and s
+ * before the iteration). */
+void orc_shard_phase_a(const orc_problem *P, const orc_params *pr, orc_state *S, int k0, const double *xprev,
+                       const double *sprev, double *gx, double *colsum, double *rec)
+{
+    int n = P->n, m = P->m, q = P->q;
+    orc_report scratch;
+    memset(&scratch, 0, sizeof scratch);
+    step_a(P, pr, S, xprev, k0, &scratch);
+    for (size_t e = 0; e < (size_t)m * q * n; ++e)
+        gx[e] = g_at(P, e, S->x[e]);
+    steps_e_f(P, S, colsum);
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < q; ++j) {
+            double sum = 0.0;
+            for (int k = 0; k < n; ++k)
+                sum += gx[IDX3(i, j, k)] - S->lam[IDX3(i, j, k)];
+            rec[(size_t)i * q + j] = sum;
+            rec[(size_t)m * q + (size_t)i * q + j] = k0 == 0 ? S->x[IDX3(i, j, 0)] : 0.0;
+        }
+    double r1 = 0.0, s3 = 0.0;
+    for (int j = 0; j < q; ++j)
+        for (int k = 0; k < n; ++k) {
+            double sx = 0.0, dx = 0.0;
+            for (int i = 0; i < m; ++i) {
+                sx += S->x[IDX3(i, j, k)];
+                dx += S->x[IDX3(i, j, k)] - xprev[IDX3(i, j, k)];
+            }
+            r1 = amax(r1, fabs(S->s[IDX2(j, k)] - sx + P->y[IDX2(j, k)]));
+            s3 = amax(s3, fabs(S->s[IDX2(j, k)] - sprev[IDX2(j, k)] - dx));
+        }
+    rec[2 * (size_t)m * q] = r1;
+    rec[2 * (size_t)m * q + 1] = s3;
+}
+
+/* Phase B: with the combined record `tot`, step (b) on the worker's columns,
+ * steps (c), (d), (h), (i) on the pair scalars (the same on every worker)
+ * and step (g) on its columns; n_total is the instance's n.  res[0], res[1]
+ * receive the worker's largest |z - g(x)| and |z - z~| (zprev: z before the
+ * iteration); res[2..4] the largest |h - 1'z|, |x_1^(i,j) - x_1^(i)| and
+ * |h - h~| over the pairs (hprev: h before), the same on every worker. */
+void orc_shard_phase_b(const orc_problem *P, const orc_params *pr, orc_state *S, int n_total, const double *tot,
+                       const double *gx, const double *zprev, const double *hprev, double *res)
+{
+    int n = P->n, m = P->m, q = P->q;
+    size_t mq = (size_t)m * q;
+    double kappa = pr->rho2 / (pr->rho1 + (double)n_total * pr->rho2);
+    double r2 = 0.0, s1 = 0.0, r3 = 0.0, r4 = 0.0, s2 = 0.0;
+    double *sz = malloc(sizeof(double) * mq);
+    /* (b) z = g(x) - lambda + kappa (h + p - 1'(g(x) - lambda)) 1 */
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < q; ++j) {
+            size_t pr_ = (size_t)i * q + j;
+            double t = kappa * (S->h[pr_] + S->p[pr_] - tot[pr_]);
+            for (int k = 0; k < n; ++k) {
+                size_t e = IDX3(i, j, k);
+                S->z[e] = gx[e] - S->lam[e] + t;
+            }
+            sz[pr_] = tot[pr_] + (double)n_total * t;
+        }
+    /* (c) x_1-update (R1) */
+    for (int i = 0; i < m; ++i) {
+        double sum = 0.0;
+        for (int j = 0; j < q; ++j)
+            sum += tot[mq + (size_t)i * q + j] - S->nu[(size_t)i * q + j];
+        S->x1[i] = sum / (double)q;
+    }
+    /* (d) h-update */
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < q; ++j) {
+            size_t pr_ = (size_t)i * q + j;
+            double v = sz[pr_] - S->p[pr_];
+            S->h[pr_] = v < P->c[i] ? v : P->c[i];
+        }
+    /* (g) lambda-update on the worker's columns, with the residual terms of z */
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < q; ++j)
+            for (int k = 0; k < n; ++k) {
+                size_t e = IDX3(i, j, k);
+                r2 = amax(r2, fabs(S->z[e] - gx[e]));
+                s1 = amax(s1, fabs(S->z[e] - zprev[e]));
+                S->lam[e] += S->z[e] - gx[e];
+            }
+    /* (h) nu-update, (i) p-update, and the pair residual terms */
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < q; ++j) {
+            size_t pr_ = (size_t)i * q + j;
+            double x0 = tot[mq + pr_];
+            S->nu[pr_] += S->x1[i] - x0;
+            S->p[pr_] += S->h[pr_] - sz[pr_];
+            r3 = amax(r3, fabs(S->h[pr_] - sz[pr_]));
+            r4 = amax(r4, fabs(x0 - S->x1[i]));
+            s2 = amax(s2, fabs(S->h[pr_] - hprev[pr_]));
+        }
+    free(sz);
+    res[0] = r2; res[1] = s1; res[2] = r3; res[3] = r4; res[4] = s2;
 }
 
 /* Objective of eq. (2): (1/q) sum_{i,j,k} f_k^{(i,j)}(x_k^{(i,j)}). */

@@ -143,7 +143,9 @@ admm_status build_queues(admm_batch *b)
     BTRY(cudaMemcpy(b->d_order, all.data(), sizeof(int) * std::max<size_t>(all.size(), 1), cudaMemcpyHostToDevice));
     // launch shape: as many co-resident CTAs (clusters) as fit
     const int mb = batch_mbound(b->max_m);
-    b->smem = std::max(batch_smem_bytes(b->cfg.warps_per_cta, b->slice),
+    // per-warp slices only when some instance runs on a one-warp team: the
+    // shared memory left unclaimed serves as L1
+    b->smem = std::max(b->nS > 0 ? batch_smem_bytes(b->cfg.warps_per_cta, b->slice) : 0,
                        sizeof(double) * batch_cluster_team_doubles(b->max_m, b->max_q, b->cfg.warps_per_cta,
                                                                    clusters ? b->cfg.cluster_size : 1));
     const int per_sm = batch_blocks_per_sm(b->cfg.warps_per_cta, mb, b->smem);
@@ -446,11 +448,20 @@ admm_status admm_batch_autotune(admm_batch *b, int32_t trial_iters, admm_batch_c
 {
     TraceRange trace_("admm_batch_autotune");
     clear_last_error();
-    if (!b || trial_iters < 1) return bfail(ADMM_EINVAL, "bad argument");
+    if (!b || trial_iters < 0) return bfail(ADMM_EINVAL, "bad argument");
     const admm_batch_config keep = b->cfg;
-    const int64_t thresholds[] = {0, 8192, 32768};
-    const int warps[] = {4, 8, 16};
-    const struct { int32_t size; int64_t min_el; } clus[] = {{1, 0}, {4, 131072}, {8, 131072}, {8, 32768}};
+    // trial_iters > 0: throughput over that many iterations; 0: whole solves,
+    // whose time includes the tail of the slowest instances (where multi-CTA
+    // cluster teams for the largest instances pay)
+    const bool whole = trial_iters == 0;
+    const std::vector<int64_t> thresholds = whole ? std::vector<int64_t>{0} : std::vector<int64_t>{0, 8192, 32768};
+    const std::vector<int> warps = whole ? std::vector<int>{8, 16} : std::vector<int>{4, 8, 16};
+    struct Clus {
+        int32_t size;
+        int64_t min_el;
+    };
+    const std::vector<Clus> clus = whole ? std::vector<Clus>{{1, 0}, {2, 60000}, {2, 150000}, {4, 60000}, {4, 150000}}
+                                         : std::vector<Clus>{{1, 0}, {4, 131072}, {8, 131072}, {8, 32768}};
     cudaEvent_t e0, e1;
     BTRY(cudaEventCreate(&e0));
     BTRY(cudaEventCreate(&e1));
@@ -459,7 +470,7 @@ admm_status admm_batch_autotune(admm_batch *b, int32_t trial_iters, admm_batch_c
     b->iter_budget = trial_iters;
     for (int w : warps)
         for (int64_t th : thresholds)
-            for (auto cc : clus) {
+            for (const Clus &cc : clus) {
                 if (cc.size > 1 && cc.min_el < th) continue;
                 admm_batch_config c{w, 0, th, cc.size, 0, cc.min_el};
                 b->cfg = c;

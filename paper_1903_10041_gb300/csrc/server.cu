@@ -619,7 +619,7 @@ admm_status admm_server_create(const admm_params *prm, const admm_server_config 
     // launch shape of a tick: kernel and slices for the configured max m, q
     S->mbound = batch_mbound(cfg->max_m);
     S->slice = batch_slice_doubles(cfg->max_m, cfg->max_q);
-    S->smem = std::max(batch_smem_bytes(cfg->batch.warps_per_cta, S->slice),
+    S->smem = std::max(cfg->batch.small_max_elements > 0 ? batch_smem_bytes(cfg->batch.warps_per_cta, S->slice) : 0,
                        sizeof(double) * batch_cluster_team_doubles(cfg->max_m, cfg->max_q, cfg->batch.warps_per_cta,
                                                                    std::max(1, cfg->batch.cluster_size)));
     const int per_sm = batch_blocks_per_sm(cfg->batch.warps_per_cta, S->mbound, S->smem);

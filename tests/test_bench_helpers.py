@@ -73,3 +73,16 @@ def test_fp64_flop_count_follows_the_branch_each_element_takes():
     assert b.fp64_flops_per_iteration(Q) == 68 * 600 + 5 * 300
     S = W.shared_problem(100, 3, 4)
     assert b.fp64_flops_per_iteration(S) == b.fp64_flops_per_iteration(S.dense())
+
+
+def test_paper_penalties_are_the_settings_of_the_phev_study():
+    """Sec. IV-A: rho = (1e-4, 2e-6, 5e-6, 5e-6), r-bar = 1e-6 dE with dE the
+    battery capacity, sigma-bar = 1e-2, adaptation on; the q sweep uses them
+    at every q with --paper-penalties."""
+    b = _bench()
+    P = W.phev_problem(1000, 5)
+    par = b.paper_penalties(P)
+    assert par.rho == (1e-4, 2e-6, 5e-6, 5e-6) and par.adapt_rho
+    assert par.r_tol == 1e-6 * float(P.c[1]) and par.s_tol == 1e-2
+    sweep = b.sweep_workloads("5,500", "fp64", False, paper=True)
+    assert [q.rho for _, q in sweep] == [(1e-4, 2e-6, 5e-6, 5e-6)] * 2

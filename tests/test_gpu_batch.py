@@ -101,6 +101,26 @@ def test_batch_autotune_picks_a_valid_config_and_still_solves(capi, oracle_lib):
         assert abs(res[t]["objective"] - obj_o) <= 1e-6 * max(1.0, abs(obj_o))
 
 
+def test_batch_autotune_on_whole_solves(capi, oracle_lib):
+    """trial_iters = 0 times whole solves (the tail included); the choice is
+    one of the documented candidates and the batch still solves to the
+    oracle's objective."""
+    probs = small_batch(12, seed=12)
+    par = W.Params(rho=(1.0, 1.0 / 600, 1.0, 1.0), precision="mixed", adapt_rho=True)
+    with capi.Batch(probs, par) as B:
+        cfg = B.autotune(trial_iters=0)
+        assert cfg["warps_per_cta"] in (8, 16) and cfg["small_max_elements"] == 0
+        assert (cfg["cluster_size"], cfg["cluster_min_elements"]) in ((1, 0), (2, 60000), (2, 150000), (4, 60000),
+                                                                      (4, 150000))
+        B.solve()
+        res = B.wait()
+    for t in (0, 5):
+        st_o, _ = oracle_lib.solve(probs[t], par.replace(precision="fp64"), threads=16)
+        obj_o = oracle_lib.objective(probs[t], st_o["x"])
+        assert res[t]["converged"]
+        assert abs(res[t]["objective"] - obj_o) <= 1e-6 * max(1.0, abs(obj_o))
+
+
 def test_batch_equals_its_graph_replay_and_reset(capi):
     probs = small_batch(10, seed=13)
     par = W.Params(rho=(1.0, 1.0 / 600, 1.0, 1.0), precision="mixed")

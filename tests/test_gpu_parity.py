@@ -284,3 +284,19 @@ def test_solve_returns_once_queued_and_two_handles_overlap(capi, oracle_lib):
         for k in ("x", "s", "mu", "lam", "h", "p", "nu", "x1"):
             assert np.array_equal(got[k], ref[k]), k
         s.close()
+
+
+def test_paper_penalty_settings_match(capi, oracle_lib):
+    """The PHEV settings of Sec. IV-A: initial penalties rho = (1e-4, 2e-6,
+    5e-6, 5e-6), thresholds r-bar = 1e-6 dE and sigma-bar = 1e-2, with the
+    penalty adaptation on (rho grows by about 1e5 over the solve).  FP64 on
+    the GPU takes the same adaptation steps and iterations as the oracle."""
+    P = W.phev_problem(n=200, q=6)
+    dE = float(P.c[1])
+    par = W.Params(rho=(1e-4, 2e-6, 5e-6, 5e-6), r_tol=1e-6 * dE, s_tol=1e-2, adapt_rho=True)
+    st_o, rep_o, st_g, res = run_both(capi, oracle_lib, P, par)
+    assert rep_o["converged"] and res["converged"]
+    assert res["iters"] == rep_o["iters"]
+    assert np.allclose(st_g["rho"], rep_o["rho"], rtol=1e-12, atol=0)
+    assert rep_o["rho"][0] > 100 * par.rho[0]          # the adaptation acted
+    compare_states(P, st_o, rep_o, st_g, res)

@@ -70,3 +70,16 @@ def test_device_arrays_and_invalid_elements(capi, oracle_lib):
     with pytest.raises(capi.AdmmError) as ei:
         capi.quartic_min(A_bad, B, Cc, D, lo, hi)
     assert ei.value.status == capi.ADMM_EINVAL
+
+
+@pytest.mark.parametrize("mode", ["exact", "paper"])
+def test_fp64_acos_clamp_case(capi, oracle_lib, mode):
+    """The cubic of the oracle's acos-clamp pin (subnormal R^2, the computed
+    argument of acos 1 + 5e-10): the GPU's FP64 minimiser clamps it too and
+    returns the oracle's finite minimiser."""
+    from tests.test_oracle_quartic import ACOS_CLAMP_CUBIC
+    b, c, d = ACOS_CLAMP_CUBIC
+    args = [np.array([v]) for v in (0.25, b, c / 2.0, d, -1.0, 1.0)]
+    x = capi.quartic_min(*args, mode=mode, precision="fp64")
+    xo, br = oracle_lib.quartic_min(*[a[0] for a in args], mode=mode)
+    assert br == 2 and np.isfinite(x[0]) and abs(x[0] - float(xo)) <= 1e-9 * abs(float(xo)), (x[0], xo)

@@ -448,3 +448,23 @@ def test_open_loop_variant_is_the_nominal_problem_on_the_largest_demand(oracle_l
     obj_r = oracle_lib.objective(P, st_r["x"])
     assert obj_r <= obj_ol + 1e-6
     assert obj_r < obj_ol - 1e-3  # scenario feedback after the first move pays on this instance
+
+
+def test_start_point_does_not_change_the_solution(oracle_lib):
+    """Reading R8 starts from x = Pi(0), the paper gives no start.  The start
+    fixes the trajectory only: with f strictly convex (f2 > 0) eq. (2) has
+    one minimiser, and solves from Pi(0), from x = 0 outside the bounds and
+    from a random iterate reach it."""
+    P = W.random_problem(60, 2, 3, seed=23)
+    P.lo = np.full_like(P.lo, 0.25)       # 0 lies outside [lo, hi]: Pi(0) != 0
+    par = W.Params(rho=(1.0, 1.0 / 60, 1.0, 1.0), r_tol=1e-9, s_tol=1e-9, max_iter=200000)
+    st_a, rep_a = oracle_lib.solve(P, par)
+    assert np.all(oracle_lib.init_state(P)["x"] == 0.25)
+    zero = {k: np.zeros_like(v) for k, v in oracle_lib.init_state(P).items()}
+    st_b, rep_b = oracle_lib.solve(P, par, state=zero)
+    st_c, rep_c = oracle_lib.solve(P, par, state=_random_state(P, 29))
+    assert rep_a["converged"] and rep_b["converged"] and rep_c["converged"]
+    assert rep_a["iters"] != rep_b["iters"] or np.abs(st_a["x"] - st_b["x"]).max() > 0.0
+    for st in (st_b, st_c):
+        assert np.abs(st["x"] - st_a["x"]).max() < 1e-6
+        assert abs(oracle_lib.objective(P, st["x"]) - oracle_lib.objective(P, st_a["x"])) < 1e-8

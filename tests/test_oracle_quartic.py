@@ -1,5 +1,6 @@
 """Pins of the oracle's quartic minimiser (Algorithm 1, Sec. III-B) against
 closed forms, constructed roots and brute force.  CPU only."""
+import math
 from fractions import Fraction
 
 import numpy as np
@@ -140,3 +141,33 @@ def test_golden_quartics_with_exact_minimisers(oracle_lib):
     assert np.array_equal(branch[fixed], br[fixed])
     assert np.isin(branch[~fixed], (0, 2)).all()
     assert np.abs(x - want).max() <= 1e-12 * max(1.0, np.abs(want).max())
+
+
+# A cubic x^3 + b x^2 + c x + d whose computed Delta is 0 (trig branch) while
+# R / sqrt(-Q^3) rounds to 1 + 5e-10: R^2 and Q^3 lie in the subnormal range.
+# In binary64 with correctly rounded square root and division the argument
+# cannot pass +-1 when the computed Delta <= 0 unless R^2 or Q^3 is
+# subnormal (fl(sqrt(fl(x*x))) = |x| otherwise), so the case has to sit there.
+ACOS_CLAMP_CUBIC = (0.0, -3.3729653494511964e-105, -7.539906031043884e-158)
+
+
+def test_acos_argument_clamp_is_needed_in_the_subnormal_range(oracle_lib):
+    """Reading R6: the argument of acos in the trig branch of Algorithm 1 is
+    clamped to [-1, 1].  On this cubic the unclamped argument exceeds 1 in
+    binary64, so without the clamp the roots are NaN; with it they are the
+    double root -sqrt(-Q) and the simple root 2 sqrt(-Q) (theta = 0)."""
+    b, c, d = ACOS_CLAMP_CUBIC
+    # the case really exercises the clamp (Python floats are binary64)
+    Q = c / 3.0 - b * b / 9.0
+    R = b * c / 6.0 - b * b * b / 27.0 - d / 2.0
+    assert Q * Q * Q + R * R <= 0.0 and abs(R / math.sqrt(-Q * Q * Q)) > 1.0
+    roots, branch = oracle_lib.cubic_roots(b, c, d)
+    assert branch == 2 and np.all(np.isfinite(roots)), roots
+    s = math.sqrt(-Q)
+    np.testing.assert_allclose(np.sort(roots), [-s, -s, 2.0 * s], rtol=1e-7)
+    # each root makes the cubic vanish to the rounding of its terms
+    for r in roots:
+        assert abs(r ** 3 + c * r + d) <= 1e-6 * abs(d)
+    # the quartic with this derivative (A = 1/4: b = B, c = 2 C, d = D) has a finite minimiser
+    x, br = oracle_lib.quartic_min(0.25, b, c / 2.0, d, -1.0, 1.0)
+    assert br == 2 and math.isfinite(float(x)) and abs(float(x) - 2.0 * s) <= 1e-7 * s

@@ -1,6 +1,7 @@
 """Batched parity at the full size of the batched workload (4096 instances,
 n log-uniform in [50, 5000], m in {2, 3, 4}, q in [1, 20], mixed precision,
-rho = (1, 1/n, 1, 1) per instance): seven of its instances, the three
+rho = (1, 1/n, 1, 1) per instance, fixed or adapted as in Sec. IV-A): seven
+of its instances, the three
 largest shapes among them (n near 5000, m = 4, q near 20), solved in one
 batch through the C ABI and each compared with a full FP64 oracle solve of
 the same instance: objective within 1e-6 relative and KKT residual of
@@ -47,11 +48,12 @@ def _kkt(oracle, P, par, st):
     return oracle.kkt(P, par.replace(rho=tuple(st["rho"]), rho2_over_n=False), dense)[0]
 
 
-def test_full_size_batched_instances_match_the_oracle(capi, oracle_lib):
+@pytest.mark.parametrize("adapt", [False, True])
+def test_full_size_batched_instances_match_the_oracle(capi, oracle_lib, adapt):
     ids = list(INSTANCES)
     probs = [W.batch_instance(t) for t in ids]
     assert [(P.n, P.m, P.q) for P in probs] == [INSTANCES[t] for t in ids]
-    par = W.Params(rho=(1.0, 1.0, 1.0, 1.0), rho2_over_n=True, precision="mixed")
+    par = W.Params(rho=(1.0, 1.0, 1.0, 1.0), rho2_over_n=True, precision="mixed", adapt_rho=adapt)
     with capi.Batch(probs, par) as B:
         B.solve()
         res = B.wait()
@@ -66,7 +68,7 @@ def test_full_size_batched_instances_match_the_oracle(capi, oracle_lib):
         k_g = _kkt(oracle_lib, P, po, states[t])
         err = abs(res[t]["objective"] - obj_o) / max(1.0, abs(obj_o))
         rows.append((ids[t], P.n, P.m, P.q, res[t]["iters"], rep_o["iters"], err, k_g - k_o))
-        print(f"instance {ids[t]} (n={P.n}, m={P.m}, q={P.q}): iterations {res[t]['iters']} (oracle "
+        print(f"{'adapted' if adapt else 'fixed'} rho, instance {ids[t]} (n={P.n}, m={P.m}, q={P.q}): iterations {res[t]['iters']} (oracle "
               f"{rep_o['iters']}), objective error {err:.1e}, KKT {k_g:.2e} (oracle {k_o:.2e})")
         assert rep_o["converged"] and res[t]["converged"], rows[-1]
         assert err <= 1e-6, rows[-1]
