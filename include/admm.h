@@ -295,8 +295,8 @@ admm_status admm_batch_get_config(admm_batch *b, admm_batch_config *cfg);
  * iterations (throughput; 4, 8, 16 warps x warp-team thresholds 0, 8192,
  * 32768 x clusters off, of 4 or 8 CTAs); trial_iters = 0: each candidate
  * runs the whole solve, so the time includes the tail of the slowest
- * instances (8 or 16 warps, no warp teams, clusters off or of 2 or 4 CTAs
- * for instances above 6e4 or 1.5e5 elements).  *chosen (may be NULL)
+ * instances (8 or 16 warps, no warp teams; clusters off, of 2 CTAs for
+ * instances above 1e5, 1.5e5 or 2.5e5 elements, or of 4 above 2.5e5).  *chosen (may be NULL)
  * receives the choice.  ADMM_EINVAL for trial_iters < 0. */
 admm_status admm_batch_autotune(admm_batch *b, int32_t trial_iters, admm_batch_config *chosen);
 /* Enqueues the solve of every unfinished instance from its current state

@@ -36,6 +36,7 @@ struct BatchArgs {
     double *scal;             // per-instance scalar state (in/out)
     double *out;              // per-instance record [id][kInfo]; [0] iterations so far, [14] finished
     int slice_doubles;        // shared memory per warp-team slice
+    int stage_off;            // bytes from the CTA's shared memory to its coefficient stages (m <= 4 kernels)
     int iter_budget;          // > 0: stop every instance after this many more iterations
     const float *tick_work;   // if non-null (with iter_budget > 0): time-balanced budget, below
     const int *tick_rounds;   // if non-null and > 1: CTA and warp teams take each instance up to this many
@@ -79,6 +80,15 @@ void *batch_fn_w16(int mbound);
 // Shared memory (doubles) a CTA or cluster team needs in each of its CTAs.
 size_t batch_cluster_team_doubles(int max_m, int max_q, int warps, int cluster);
 size_t batch_smem_bytes(int warps, size_t slice_doubles);
+// Dynamic shared memory of one CTA: the CTA or cluster team's region, then
+// (m <= 4 kernel) two coefficient stages per warp at byte offset stage_off;
+// the per-warp slices of one-warp teams, when used, overlap both (a CTA runs
+// its one-warp teams only after its CTA-team work).
+struct BatchSmem {
+    size_t bytes;
+    int stage_off;
+};
+BatchSmem batch_cta_smem(int max_m, int max_q, int warps, int cluster, bool warp_teams, size_t slice_doubles);
 int batch_blocks_per_sm(int warps, int mbound, size_t smem);
 // Launch with clusters of `cluster` CTAs (1 = no clusters); grid is a multiple of it.
 cudaError_t launch_batch(int warps, int mbound, int grid, int cluster, const BatchArgs &a, size_t smem,

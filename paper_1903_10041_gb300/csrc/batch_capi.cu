@@ -96,6 +96,7 @@ struct admm_batch {
     double *d_tmp = nullptr;
     int nX = 0, nL = 0, nS = 0, cluster = 1;
     size_t slice = 0, smem = 0;
+    int stage_off = 0;       // byte offset of the coefficient stages in a CTA's shared memory
     int grid = 0;
     cudaStream_t cap = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -145,9 +146,10 @@ admm_status build_queues(admm_batch *b)
     const int mb = batch_mbound(b->max_m);
     // per-warp slices only when some instance runs on a one-warp team: the
     // shared memory left unclaimed serves as L1
-    b->smem = std::max(b->nS > 0 ? batch_smem_bytes(b->cfg.warps_per_cta, b->slice) : 0,
-                       sizeof(double) * batch_cluster_team_doubles(b->max_m, b->max_q, b->cfg.warps_per_cta,
-                                                                   clusters ? b->cfg.cluster_size : 1));
+    const BatchSmem bs = batch_cta_smem(b->max_m, b->max_q, b->cfg.warps_per_cta, clusters ? b->cfg.cluster_size : 1,
+                                        b->nS > 0, b->slice);
+    b->smem = bs.bytes;
+    b->stage_off = bs.stage_off;
     const int per_sm = batch_blocks_per_sm(b->cfg.warps_per_cta, mb, b->smem);
     if (per_sm < 1) return bfail(ADMM_EUNSUPPORTED, "batched kernel cannot be resident with this configuration");
     const int use = b->cfg.ctas_per_sm > 0 ? std::min(b->cfg.ctas_per_sm, per_sm) : per_sm;
@@ -184,6 +186,7 @@ BatchArgs make_args(const admm_batch *b)
     a.f0 = b->store.f0;
     a.out = b->d_out;
     a.slice_doubles = (int)b->slice;
+    a.stage_off = b->stage_off;
     a.iter_budget = b->iter_budget;
     a.r_tol = stop_r_tol(b->prm.precision, b->prm.r_tol);
     a.s_tol = stop_s_tol(b->prm.precision, b->prm.s_tol);
@@ -460,7 +463,7 @@ admm_status admm_batch_autotune(admm_batch *b, int32_t trial_iters, admm_batch_c
         int32_t size;
         int64_t min_el;
     };
-    const std::vector<Clus> clus = whole ? std::vector<Clus>{{1, 0}, {2, 60000}, {2, 150000}, {4, 60000}, {4, 150000}}
+    const std::vector<Clus> clus = whole ? std::vector<Clus>{{1, 0}, {2, 100000}, {2, 150000}, {2, 250000}, {4, 250000}}
                                          : std::vector<Clus>{{1, 0}, {4, 131072}, {8, 131072}, {8, 32768}};
     cudaEvent_t e0, e1;
     BTRY(cudaEventCreate(&e0));

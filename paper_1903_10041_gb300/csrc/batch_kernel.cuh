@@ -136,6 +136,9 @@ template <int KIND, int NW, int M> __device__ void solve_team(const BatchArgs &a
     const int n = I.n, m = I.m, q = I.q, mq = m * q;
     const int nv = (n + VW - 1) / VW;
     const int W = NWT * CL, gw = rank * NWT + wl;
+    // coefficients staged in shared memory by cp.async (CTA and cluster teams of the m <= 4 kernel)
+    constexpr bool STG = KIND != TEAM_WARP && M == 4;
+    float2 *stage = (float2 *)((char *)smem + a.stage_off);
     const int64_t chunk = team_chunk(W, q, nv);
     const int64_t npairs = (int64_t)q * nv;
     const int items = q + W - 1; // record slots: (row j, warp w) at j + w
@@ -206,10 +209,31 @@ template <int KIND, int NW, int M> __device__ void solve_team(const BatchArgs &a
                 fmn[i] = INFINITY;
             }
             double *rec = recs + (size_t)(j + gw) * m * 4;
-            for (int v = v0 + lane; v < v1; v += 32) {
-                if (v + 32 < v1) prefetch_vec32<M>(ea, j, (v + 32) * VW, cold);
-                vec32<M, VW, false>(ea, uoff, x1, nu, j, v * VW, check, cold, mu_div, rho1, rho3, rho4, iq, ghi, glo,
-                                    fmx, fmn, fcr, fcs, esc, rec);
+            if constexpr (STG) {
+                // two stages per warp; round r of the piece reads stage r & 1
+                // while the copies of round r + 1 fill the other
+                float2 *stw = stage + (size_t)wl * 2 * stage_slots<M>() * 32 + lane;
+                int v = v0 + lane;
+                if (v < v1) stage_vec32<M>(ea, j, v * VW, stw);
+                cp_async_commit();
+                for (int r = 0; v < v1; v += 32, ++r) {
+                    float2 *cur = stw + (r & 1) * stage_slots<M>() * 32;
+                    if (v + 32 < v1) {
+                        stage_vec32<M>(ea, j, (v + 32) * VW, stw + ((r + 1) & 1) * stage_slots<M>() * 32);
+                        prefetch_mutable<M>(ea, j, (v + 32) * VW);
+                    }
+                    cp_async_commit();
+                    cp_async_wait1(); // this round's copies have landed
+                    vec32<M, VW, false, true>(ea, uoff, x1, nu, j, v * VW, check, cold, mu_div, rho1, rho3, rho4,
+                                              iq, ghi, glo, fmx, fmn, fcr, fcs, esc, rec, cur);
+                }
+                cp_async_wait0();
+            } else {
+                for (int v = v0 + lane; v < v1; v += 32) {
+                    if (v + 32 < v1) prefetch_vec32<M>(ea, j, (v + 32) * VW, cold);
+                    vec32<M, VW, false>(ea, uoff, x1, nu, j, v * VW, check, cold, mu_div, rho1, rho3, rho4, iq, ghi,
+                                        glo, fmx, fmn, fcr, fcs, esc, rec);
+                }
             }
 #pragma unroll
             for (int i = 0; i < M; ++i)

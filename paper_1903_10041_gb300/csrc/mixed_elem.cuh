@@ -77,6 +77,58 @@ __device__ __forceinline__ void prefetch_vec32(const ElemF32 &a, int j, int k0, 
         }
 }
 
+// Shared-memory staging of the read-only coefficients (batched kernel):
+// each lane copies the f2, f1, g2, g1 of every source and y of its next
+// column pair into its own slots of a per-warp stage with 8-byte cp.async
+// copies, one pair ahead, and reads the current pair from the other stage.
+// A lane reads only the slots it filled, so cp.async.wait_group orders it;
+// no other synchronisation is needed.  Slot s of a stage holds 32 float2
+// (one per lane): slot 0 y, slots 1 + 4 i + {0, 1, 2, 3} f2, f1, g2, g1 of
+// source i.
+template <int M> __host__ __device__ constexpr int stage_slots() { return 4 * M + 1; }
+__device__ __forceinline__ void cp_async8(float2 *dst, const float *src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Copies the staged arrays of the column pair (j, k0) into the lane's slots
+// (dst = stage base + lane).
+template <int M> __device__ __forceinline__ void stage_vec32(const ElemF32 &a, int j, int k0, float2 *dst)
+{
+    cp_async8(dst, a.y + (size_t)j * a.ld + k0);
+#pragma unroll
+    for (int i = 0; i < M; ++i)
+        if (i < a.m) {
+            const size_t d = ((size_t)i * a.cq + (size_t)j * a.cj) * a.ld + k0;
+            cp_async8(dst + (1 + 4 * i) * 32, a.f2 + d);
+            cp_async8(dst + (2 + 4 * i) * 32, a.f1 + d);
+            cp_async8(dst + (3 + 4 * i) * 32, a.g2 + d);
+            cp_async8(dst + (4 + 4 * i) * 32, a.g1 + d);
+        }
+}
+
+// L2 prefetch of what the staged element update still reads from global
+// memory: x, the bounds and the column state s, mu.
+template <int M> __device__ __forceinline__ void prefetch_mutable(const ElemF32 &a, int j, int k0)
+{
+    const size_t col = (size_t)j * a.ld + k0;
+    prefetch_l2(a.s + col);
+    prefetch_l2(a.mu + col);
+    prefetch_l2(a.s_lo + col);
+    prefetch_l2(a.mu_lo + col);
+#pragma unroll
+    for (int i = 0; i < M; ++i)
+        if (i < a.m) {
+            prefetch_l2(a.x + ((size_t)i * a.q + j) * a.ld + k0);
+            prefetch_l2(a.lo + (size_t)i * a.ld + k0);
+            prefetch_l2(a.hi + (size_t)i * a.ld + k0);
+        }
+}
+
 // Float-float on packed pairs (the two columns of a vector).
 struct FF2 {
     float2 hi, lo;
@@ -143,16 +195,17 @@ __device__ __forceinline__ void st2(float *p, float2 v) { *(float2 *)p = v; }
 // D_k extrema in dmx/dmn.  rec (if k0 == 0) receives x at k = 0.  The
 // first column is always < n; the second may be padding (k0 + 1 = n), and
 // then takes no part in the sums and residuals.
-template <int M, int VW, bool C64>
+template <int M, int VW, bool C64, bool STAGED = false>
 __device__ __forceinline__ void vec32(const ElemF32 &a, const float *uoff, const double *x1s, const double *nus,
                                       int j, int k0, bool check, bool cold, float mu_div, float rho1, float rho3,
                                       float rho4, float iq, float2 *ghi, float2 *glo, float *dmx, float *dmn,
-                                      float &cm_r, float &cm_s, unsigned &esc, double *rec)
+                                      float &cm_r, float &cm_s, unsigned &esc, double *rec,
+                                      const float2 *stg = nullptr)
 {
     static_assert(VW == 2, "the element update works on column pairs");
     const int m = a.m, q = a.q, ld = a.ld, n = a.n;
     const size_t col = (size_t)j * ld + k0;
-    const float2 yv = ldg2(a.y + col);
+    const float2 yv = STAGED ? stg[0] : ldg2(a.y + col);
     const float2 st = ld2(a.s + col), stl = ld2(a.s_lo + col);
     float2 mu = ld2(a.mu + col), mul = ld2(a.mu_lo + col);
     if (mu_div != 1.0f) {
@@ -177,7 +230,10 @@ __device__ __forceinline__ void vec32(const ElemF32 &a, const float *uoff, const
     for (int i = 0; i < M; ++i) {
         if (i < m) {
             const size_t e = ((size_t)i * a.cq + (size_t)j * a.cj) * ld + k0; // coefficient element
-            const float2 a2 = ldg2(a.f2 + e), a1 = ldg2(a.f1 + e), b2 = ldg2(a.g2 + e), b1 = ldg2(a.g1 + e);
+            const float2 a2 = STAGED ? stg[(1 + 4 * i) * 32] : ldg2(a.f2 + e);
+            const float2 a1 = STAGED ? stg[(2 + 4 * i) * 32] : ldg2(a.f1 + e);
+            const float2 b2 = STAGED ? stg[(3 + 4 * i) * 32] : ldg2(a.g2 + e);
+            const float2 b1 = STAGED ? stg[(4 + 4 * i) * 32] : ldg2(a.g1 + e);
             const float2 L = ldg2(a.lo + (size_t)i * ld + k0), H = ldg2(a.hi + (size_t)i * ld + k0);
             const float2 g0 = cold ? ldg2(a.g0 + e) : splat2(0.0f);
             const int pr = i * q + j;

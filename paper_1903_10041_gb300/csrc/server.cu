@@ -70,6 +70,7 @@ struct admm_server {
     admm_server_config cfg{};
     int dev = 0, nsm = 0, grid = 0, mbound = 8, cluster = 1;
     size_t slice = 0, smem = 0;
+    int stage_off = 0;       // byte offset of the coefficient stages in a CTA's shared memory
     Store store;
     cudaStream_t st = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -619,9 +620,11 @@ admm_status admm_server_create(const admm_params *prm, const admm_server_config 
     // launch shape of a tick: kernel and slices for the configured max m, q
     S->mbound = batch_mbound(cfg->max_m);
     S->slice = batch_slice_doubles(cfg->max_m, cfg->max_q);
-    S->smem = std::max(cfg->batch.small_max_elements > 0 ? batch_smem_bytes(cfg->batch.warps_per_cta, S->slice) : 0,
-                       sizeof(double) * batch_cluster_team_doubles(cfg->max_m, cfg->max_q, cfg->batch.warps_per_cta,
-                                                                   std::max(1, cfg->batch.cluster_size)));
+    const BatchSmem bs = batch_cta_smem(cfg->max_m, cfg->max_q, cfg->batch.warps_per_cta,
+                                        std::max(1, cfg->batch.cluster_size), cfg->batch.small_max_elements > 0,
+                                        S->slice);
+    S->smem = bs.bytes;
+    S->stage_off = bs.stage_off;
     const int per_sm = batch_blocks_per_sm(cfg->batch.warps_per_cta, S->mbound, S->smem);
     if (per_sm < 1) return bail(ADMM_EUNSUPPORTED, "tick kernel cannot be resident");
     const int use = cfg->batch.ctas_per_sm > 0 ? std::min(cfg->batch.ctas_per_sm, per_sm) : per_sm;
@@ -647,6 +650,7 @@ admm_status admm_server_create(const admm_params *prm, const admm_server_config 
     a.f0 = S->store.f0;
     a.out = S->d_out;
     a.slice_doubles = (int)S->slice;
+    a.stage_off = S->stage_off;
     a.iter_budget = cfg->tick_iters;
     a.tick_work = (const float *)(S->d_counts + 3);
     a.tick_rounds = S->d_counts + 4;

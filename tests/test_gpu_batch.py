@@ -110,8 +110,8 @@ def test_batch_autotune_on_whole_solves(capi, oracle_lib):
     with capi.Batch(probs, par) as B:
         cfg = B.autotune(trial_iters=0)
         assert cfg["warps_per_cta"] in (8, 16) and cfg["small_max_elements"] == 0
-        assert (cfg["cluster_size"], cfg["cluster_min_elements"]) in ((1, 0), (2, 60000), (2, 150000), (4, 60000),
-                                                                      (4, 150000))
+        assert (cfg["cluster_size"], cfg["cluster_min_elements"]) in ((1, 0), (2, 100000), (2, 150000), (2, 250000),
+                                                                      (4, 250000))
         B.solve()
         res = B.wait()
     for t in (0, 5):
