@@ -391,6 +391,34 @@ def oracle_sample_errors(probs, par, results, states, idx, oracle):
             "bar": "distance to the optimum <= oracle's + 1e-6 and KKT <= oracle's + 1e-6", "per_instance": rows}
 
 
+def pinned_copy(P):
+    """The problem with every array in page-locked host memory (the e2e legs
+    copy to the device from pinned buffers)."""
+    import numpy as np
+    import torch
+    Q = P.copy()
+    for k, v in P.arrays().items():
+        setattr(Q, k, torch.from_numpy(np.ascontiguousarray(v)).pin_memory().numpy())
+    return Q
+
+
+def batch_sample(probs, limit_small=40000):
+    """Instances for the per-instance oracle comparison: the 6 smallest, 6
+    spread over the lower half of the size distribution (m*q*n <= 40000),
+    and the two instances nearest 1e5 and 2.5e5 elements."""
+    import numpy as np
+    order = np.argsort([P.elements for P in probs])
+    small = [int(t) for t in order[:6]]
+    spread = [int(t) for t in order[len(order) // 8: len(order) // 2: max(1, len(order) // 48)]
+              if probs[int(t)].elements <= limit_small][:6]
+    big = []
+    for target in (1e5, 2.5e5):
+        t = int(np.argmin([abs(P.elements - target) for P in probs]))
+        if t not in small + spread + big:
+            big.append(t)
+    return small, spread, big
+
+
 def run_batched(args):
     """The batched workload: `count` instances of uneven n, m, q in one launch (mixed)."""
     import numpy as np
