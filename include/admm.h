@@ -49,7 +49,10 @@ typedef enum admm_status {
     ADMM_ENOTCONVERGED = 5,  /* max_iter reached; the result is still filled */
     ADMM_EUNSUPPORTED = 6,   /* sizes beyond the compiled limits (ADMM_MAX_M, ...) */
     ADMM_EPENDING = 7,       /* a served request has not finished yet */
-    ADMM_ECANCELLED = 8      /* a served request was cancelled (admm_server_cancel) */
+    ADMM_ECANCELLED = 8,     /* a served request was cancelled (admm_server_cancel) */
+    ADMM_EBOUNDS = 9         /* bounds-checked build only: an element access of the mixed
+                                element update fell outside its instance's arrays (it was
+                                redirected inside them; the results are not valid) */
 } admm_status;
 
 /* Arithmetic of the per-element work (the stored state follows it). */
@@ -87,7 +90,8 @@ typedef struct admm_problem {
     const double *c;                 /* [m]; +INFINITY = no capacity limit */
     int32_t on_device;               /* 1: device pointers; 0: host pointers */
     int32_t coef_shared;             /* 1: f2..g0 are [m][n], the same maps for every scenario j
-                                        (single-instance solves only; batches and servers take 0) */
+                                        (single-instance, batched and served solves; admm_solve_noalloc
+                                        takes 0) */
 } admm_problem;
 
 typedef struct admm_params {
@@ -198,6 +202,15 @@ admm_status admm_destroy(admm_handle *h);
  * device stays usable.  No counterpart in the paper: it tests the failure
  * path of the bounded device waits without faulting the GPU. */
 admm_status admm_selftest_barrier_timeout(long long spin_ns, int grid, int *status_out);
+
+/* Diagnostics of the bounds-checked build (libadmm_debug.so, compiled with
+ * -DADMM_DEBUG_BOUNDS; see ADMM_EBOUNDS): checks an element index that lies
+ * past a 16-element device buffer with the same check the element update
+ * uses; the check must record it (without any access outside the buffer).
+ * *status_out receives ADMM_EBOUNDS and *index_out the recorded index (20).
+ * A release build returns ADMM_EUNSUPPORTED.  No counterpart in the paper:
+ * it tests the failure path of the checked build without a fault. */
+admm_status admm_selftest_bounds(int *status_out, long long *index_out);
 
 /* Quartic benchmark of Sec. III-C: Algorithm 1 (Sec. III-B) plus the clamp
  * of step (a) on `count` independent quartics.  x[t] minimises
@@ -358,7 +371,9 @@ admm_status admm_server_create(const admm_params *params, const admm_server_conf
  * -1 for a one-off solve.  *ticket identifies it for admm_server_poll. */
 admm_status admm_server_submit(admm_server *s, const admm_problem *prob, int64_t session, int64_t *ticket);
 /* The newest sampling step of a receding horizon: its data at the new
- * last step k = n-1 (f, g [m][q], bounds [m], demand [q]; host memory). */
+ * last step k = n-1 (f, g [m][q], bounds [m], demand [q]; host memory).  A
+ * session whose problem has scenario-shared maps (coef_shared = 1) takes
+ * the new step's maps from scenario j = 0. */
 typedef struct admm_step {
     int32_t m, q;
     const double *f2, *f1, *f0, *g2, *g1, *g0; /* [m][q] */

@@ -14,7 +14,8 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libadmm.so")
+# ADMM_LIB=debug loads the bounds-checked build (libadmm_debug.so) instead
+LIB_PATH = os.path.join(HERE, "libadmm_debug.so" if os.environ.get("ADMM_LIB") == "debug" else "libadmm.so")
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"{LIB_PATH} is missing: build it with paper_1903_10041_gb300.build.build() "
@@ -24,9 +25,9 @@ _lib = C.CDLL(LIB_PATH)
 _dp = C.POINTER(C.c_double)
 
 (ADMM_OK, ADMM_EINVAL, ADMM_ENOMEM, ADMM_ECUDA, ADMM_ETIMEOUT, ADMM_ENOTCONVERGED, ADMM_EUNSUPPORTED,
- ADMM_EPENDING, ADMM_ECANCELLED) = range(9)
+ ADMM_EPENDING, ADMM_ECANCELLED, ADMM_EBOUNDS) = range(10)
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "ENOTCONVERGED",
-                6: "EUNSUPPORTED", 7: "EPENDING", 8: "ECANCELLED"}
+                6: "EUNSUPPORTED", 7: "EPENDING", 8: "ECANCELLED", 9: "EBOUNDS"}
 PRECISION = {"fp64": 0, "mixed": 1, "mixed_fp64cubic": 2}
 XMIN = {"exact": 0, "paper": 1}
 SWEEP = {"gauss_seidel": 0, "jacobi": 1}
@@ -85,6 +86,8 @@ _lib.admm_get_info.argtypes = [_H, _dp, C.c_int]
 _lib.admm_get_info.restype = C.c_int
 _lib.admm_selftest_barrier_timeout.argtypes = [C.c_longlong, C.c_int, C.POINTER(C.c_int)]
 _lib.admm_selftest_barrier_timeout.restype = C.c_int
+_lib.admm_selftest_bounds.argtypes = [C.POINTER(C.c_int), C.POINTER(C.c_longlong)]
+_lib.admm_selftest_bounds.restype = C.c_int
 
 
 class AdmmError(RuntimeError):
@@ -293,6 +296,13 @@ def admm_selftest_barrier_timeout(spin_ns: int = 20_000_000, grid: int = 4) -> i
     out = C.c_int(-1)
     _check(_lib.admm_selftest_barrier_timeout(int(spin_ns), int(grid), C.byref(out)))
     return out.value
+
+
+def admm_selftest_bounds():
+    """(status, index) of the checked build's bounds self-test (admm.h)."""
+    st, ix = C.c_int(-1), C.c_longlong(-1)
+    _check(_lib.admm_selftest_bounds(C.byref(st), C.byref(ix)))
+    return st.value, ix.value
 
 
 def quartic_min(A, B, Cc, D, lo, hi, mode: str = "exact", precision: str = "fp64", stream=None, out=None):

@@ -80,7 +80,9 @@ __global__ void shift_state_kernel(const BatchInst *inst, const int *ids, int co
 // Receding-horizon step request: the whole instance (coefficients, bounds,
 // demand, x, s, mu) moves one step forward in place; the new last step's
 // data comes from `payload` (per instance, FP32: f2 f1 f0 g2 g1 g0 [m][q],
-// lo hi [m], y [q]); x at the new last step is clamped to its new bounds;
+// lo hi [m], y [q]; an instance with scenario-shared maps takes scenario
+// 0's maps for every scenario); x at the new last step is clamped to its
+// new bounds;
 // sum_k beta_0 is recomputed; x_1^(i) = mean of the new first moves; cold
 // flag cleared.  One CTA per instance.
 __global__ void shift_step_kernel(const BatchInst *inst, const int *ids, int count, const float *payload,
@@ -110,16 +112,17 @@ __global__ void shift_step_kernel(const BatchInst *inst, const int *ids, int cou
             warp_shift_left(row, n);
         }
         __syncthreads();
-        // the new last step
+        // the new last step (shared maps: scenario 0's maps of the step data in every scenario's row)
         const int last = n - 1;
         for (int u = threadIdx.x; u < mq; u += blockDim.x) {
             const int64_t e = I.off_e + (int64_t)u * I.ld + last;
-            f2[e] = pl[0 * mq + u];
-            f1[e] = pl[1 * mq + u];
-            f0[e] = pl[2 * mq + u];
-            g2[e] = pl[3 * mq + u];
-            g1[e] = pl[4 * mq + u];
-            g0[e] = pl[5 * mq + u];
+            const int v = I.cs ? u / q * q : u;
+            f2[e] = pl[0 * mq + v];
+            f1[e] = pl[1 * mq + v];
+            f0[e] = pl[2 * mq + v];
+            g2[e] = pl[3 * mq + v];
+            g1[e] = pl[4 * mq + v];
+            g0[e] = pl[5 * mq + v];
         }
         for (int i = threadIdx.x; i < m; i += blockDim.x) {
             lo[I.off_b + (int64_t)i * I.ld + last] = pl[6 * mq + i];

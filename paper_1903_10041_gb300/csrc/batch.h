@@ -19,7 +19,8 @@ struct BatchInst {
     int off_pair;             // sumg0: [m*q] at off_pair
     int off_scal;             // scalar state: scal_size(m, q) doubles at off_scal
     int off_src;              // c: [m] at off_src
-    int pad;
+    int cs;                   // 1: f2..g0 shared by the scenarios (stored repeated; a step request
+                              //    writes scenario 0's new maps to every scenario's row)
 };
 
 struct BatchArgs {
@@ -37,6 +38,7 @@ struct BatchArgs {
     double *out;              // per-instance record [id][kInfo]; [0] iterations so far, [14] finished
     int slice_doubles;        // shared memory per warp-team slice
     int stage_off;            // bytes from the CTA's shared memory to its coefficient stages (m <= 4 kernels)
+    unsigned long long *dbg;  // bounds record of checked builds (see ADMM_IDX), else unused
     int iter_budget;          // > 0: stop every instance after this many more iterations
     const float *tick_work;   // if non-null (with iter_budget > 0): time-balanced budget, below
     const int *tick_rounds;   // if non-null and > 1: CTA and warp teams take each instance up to this many

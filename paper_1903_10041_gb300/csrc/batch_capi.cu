@@ -66,7 +66,9 @@ cudaError_t to_host(const admm_problem &in, HostProblem &out)
 {
     out.P = in;
     if (!in.on_device) return cudaSuccess;
-    const size_t ne = (size_t)in.m * in.q * in.n, nb = (size_t)in.m * in.n, nc = (size_t)in.q * in.n;
+    // coefficient arrays: [m][q][n], or [m][n] when shared by the scenarios
+    const size_t ne = (size_t)in.m * (in.coef_shared ? 1 : in.q) * in.n, nb = (size_t)in.m * in.n,
+                 nc = (size_t)in.q * in.n;
     const double *src[10] = {in.f2, in.f1, in.f0, in.g2, in.g1, in.g0, in.x_lo, in.x_hi, in.y, in.c};
     const size_t cnt[10] = {ne, ne, ne, ne, ne, ne, nb, nb, nc, (size_t)in.m};
     const double **dst[10] = {&out.P.f2, &out.P.f1, &out.P.f0, &out.P.g2, &out.P.g1, &out.P.g0,
@@ -182,6 +184,7 @@ BatchArgs make_args(const admm_batch *b)
     a.qX = b->d_q;
     a.qL = b->d_q + 1;
     a.qS = b->d_q + 2;
+    a.dbg = (unsigned long long *)(b->d_q + 4);
     b->store.fill_args(a);
     a.f0 = b->store.f0;
     a.out = b->d_out;
@@ -208,7 +211,7 @@ admm_status ensure_graph(admm_batch *b)
     const BatchArgs a = make_args(b);
     cudaGraph_t g = nullptr;
     BTRY(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = cudaMemsetAsync(b->d_q, 0, 3 * sizeof(int), b->cap);
+    cudaError_t e = cudaMemsetAsync(b->d_q, 0, 4 * sizeof(int) + sizeof(unsigned long long), b->cap);
     if (e == cudaSuccess)
         e = launch_batch(b->cfg.warps_per_cta, batch_mbound(b->max_m), b->grid, b->cluster, a, b->smem, b->cap);
     cudaError_t e2 = cudaStreamEndCapture(b->cap, &g);
@@ -286,8 +289,6 @@ admm_status admm_batch_create(const admm_problem *probs, int32_t count, const ad
     for (int t = 0; t < count; ++t) {
         const admm_problem &P = probs[t];
         if (P.n < 1 || P.m < 1 || P.q < 1) return bail(bfail(ADMM_EINVAL, "n, m, q must be >= 1"));
-        if (P.coef_shared != 0)
-            return bail(bfail(ADMM_EUNSUPPORTED, "batched instances take per-scenario coefficients (coef_shared = 0)"));
         if (P.m > ADMM_MAX_M || (int64_t)P.m * P.q > ADMM_BATCH_MAX_PAIRS)
             return bail(bfail(ADMM_EUNSUPPORTED, "instance " + std::to_string(t) + " exceeds m <= 8, m*q <= 256"));
         const InstSizes z = inst_sizes(P.n, P.m, P.q);
@@ -305,7 +306,7 @@ admm_status admm_batch_create(const admm_problem *probs, int32_t count, const ad
     e = b->store.allocate(tot.e, tot.b, tot.c, tot.p, tot.s, tot.m);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_inst, sizeof(BatchInst) * count);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_order, sizeof(int) * count);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_q, 3 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_q, 4 * sizeof(int) + sizeof(unsigned long long)); // + bounds record
     if (e == cudaSuccess) e = cudaMalloc(&b->d_out, sizeof(double) * kInfo * count);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_tmp, sizeof(double) * std::max<size_t>(max_dense, 1));
     if (e == cudaSuccess) e = cudaMallocHost(&b->h_out, sizeof(double) * kInfo * count);
@@ -329,6 +330,7 @@ admm_status admm_batch_create(const admm_problem *probs, int32_t count, const ad
             cudaFreeHost(pinned);
             return bail(bfail(ADMM_ENOMEM, "store is full"));
         }
+        b->inst[t].cs = S.cs;
         e = b->store.upload(b->inst[t], S, b->prm, pinned, max_floats, b->cap);
     }
     cudaFreeHost(pinned);
@@ -383,7 +385,12 @@ admm_status admm_batch_wait(admm_batch *b, void *stream, admm_result *results)
     if (!b) return bfail(ADMM_EINVAL, "batch is NULL");
     cudaStream_t st = (cudaStream_t)stream;
     BTRY(cudaMemcpyAsync(b->h_out, b->d_out, sizeof(double) * kInfo * b->count, cudaMemcpyDeviceToHost, st));
+    unsigned long long rec = 0; // bounds record of checked builds
+    BTRY(cudaMemcpyAsync(&rec, b->d_q + 4, sizeof rec, cudaMemcpyDeviceToHost, st));
     BTRY(cudaStreamSynchronize(st));
+    if (rec != 0)
+        return bfail(ADMM_EBOUNDS, "element access out of bounds: array " + std::to_string((int)(rec >> 56) - 1) +
+                                       ", index " + std::to_string((long long)(rec & 0x00FFFFFFFFFFFFFFull)));
     admm_status worst = ADMM_OK;
     for (int t = 0; t < b->count; ++t) {
         const double *o = b->h_out + (size_t)t * kInfo;

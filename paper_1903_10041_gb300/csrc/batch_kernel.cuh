@@ -169,7 +169,7 @@ template <int KIND, int NW, int M> __device__ void solve_team(const BatchArgs &a
     const ElemF32 ea = {a.f2 + I.off_e, a.f1 + I.off_e, a.g2 + I.off_e, a.g1 + I.off_e, a.g0 + I.off_e,
                         a.lo + I.off_b, a.hi + I.off_b, a.y + I.off_c,  a.x + I.off_e,  a.s + I.off_c,
                         a.mu + I.off_c, a.s_lo + I.off_c, a.mu_lo + I.off_c, n, m, q, I.ld, a.sweep, a.xmin_mode,
-                        q, 1};
+                        q, 1, a.dbg};
     const double *cc = a.c + I.off_src;
     const double *sumg0 = a.sumg0 + I.off_pair;
     unsigned esc = 0;
@@ -377,7 +377,7 @@ template <int KIND, int NW, int M> __device__ void solve_team(const BatchArgs &a
         for (int64_t t = (int64_t)rank * NTL + tid; t < tot; t += (int64_t)CL * NTL) {
             const int64_t r = t / n;
             const int k = (int)(t - r * n);
-            const size_t e = (size_t)r * I.ld + k;
+            const size_t e = ADMM_IDX((size_t)r * I.ld + k, 1, ea.len_x(), a.dbg, DBG_X);
             const double x = ea.x[e];
             acc += (double)F2[e] * x * x + (double)F1[e] * x + (double)F0[e];
         }

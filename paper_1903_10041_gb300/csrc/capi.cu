@@ -226,6 +226,18 @@ void free_all(admm_handle *h)
     h->done = nullptr;
 }
 
+#ifdef ADMM_DEBUG_BOUNDS
+// Self-test of the bounds check: index 20 of a 16-float buffer is recorded
+// and redirected to 0 (the access stays inside the buffer).
+__global__ void bounds_selftest_kernel(float *buf, unsigned long long *rec)
+{
+    if (threadIdx.x == 0) {
+        const size_t k = ADMM_IDX((size_t)20, 1, (size_t)16, rec, DBG_SELFTEST);
+        buf[k] += 1.0f;
+    }
+}
+#endif
+
 struct DeviceGuard {
     int prev = -1;
     explicit DeviceGuard(int dev)
@@ -369,6 +381,7 @@ const char *admm_status_string(admm_status s)
     case ADMM_EUNSUPPORTED: return "unsupported size or mode";
     case ADMM_EPENDING: return "pending";
     case ADMM_ECANCELLED: return "cancelled";
+    case ADMM_EBOUNDS: return "element access out of bounds (checked build)";
     }
     return "unknown status";
 }
@@ -532,9 +545,13 @@ admm_status admm_reset(admm_handle *h)
     return reset_state(h);
 }
 
-// Status of a finished solve from its info record.
+// Status of a finished solve from its info record ([15]: the bounds record
+// of checked builds, as raw bits).
 static admm_status result_status(const double *inf)
 {
+    unsigned long long rec;
+    std::memcpy(&rec, inf + 15, sizeof rec);
+    if (rec != 0) return ADMM_EBOUNDS;
     if (inf[12] != 0.0) return (admm_status)(int)inf[12];
     return inf[1] == 0.0 ? ADMM_ENOTCONVERGED : ADMM_OK;
 }
@@ -643,6 +660,8 @@ admm_status admm_solve(admm_handle *h, const admm_state *warm, admm_result *out,
     a.spin_ns = spin_limit_ns();
     CUDA_TRY(cudaMemsetAsync(h->bar, 0, sizeof(unsigned), st));
     CUDA_TRY(cudaMemsetAsync(h->status, 0, sizeof(int), st));
+    CUDA_TRY(cudaMemsetAsync(h->info + 15, 0, sizeof(double), st));
+    a.dbg = (unsigned long long *)(h->info + 15);
     CUDA_TRY(launch_single(h->prm.precision, h->minb, a, h->smem, st));
     CUDA_TRY(cudaMemcpyAsync(h->info_host, h->info, kInfo * 8, cudaMemcpyDeviceToHost, st));
     if (out && out->x) CUDA_TRY(export_rows(h, out->x, out->on_device != 0, h->x, (int64_t)h->m * h->q, st));
@@ -671,6 +690,12 @@ admm_status admm_wait(admm_handle *h, admm_result *out)
     if (out) fill_result(h->info_host, out);
     const admm_status s = result_status(h->info_host);
     if (s == ADMM_ETIMEOUT) return fail(s, "a grid barrier wait timed out");
+    if (s == ADMM_EBOUNDS) {
+        unsigned long long rec;
+        std::memcpy(&rec, h->info_host + 15, sizeof rec);
+        return fail(s, "element access out of bounds: array %d, index %lld", (int)(rec >> 56) - 1,
+                    (long long)(rec & 0x00FFFFFFFFFFFFFFull));
+    }
     if (s == ADMM_ENOTCONVERGED) g_err = "max_iter reached before the stop test passed";
     return s;
 }
@@ -725,6 +750,34 @@ admm_status admm_destroy(admm_handle *h)
     }
     delete h;
     return ADMM_OK;
+}
+
+admm_status admm_selftest_bounds(int *status_out, long long *index_out)
+{
+    g_err.clear();
+    if (!status_out || !index_out) return fail(ADMM_EINVAL, "NULL argument");
+#ifdef ADMM_DEBUG_BOUNDS
+    float *buf = nullptr;
+    unsigned long long *rec = nullptr;
+    CUDA_TRY(cudaMalloc(&buf, 16 * sizeof(float) + sizeof(unsigned long long)));
+    rec = (unsigned long long *)(buf + 16);
+    cudaError_t e = cudaMemset(buf, 0, 16 * sizeof(float) + sizeof(unsigned long long));
+    if (e == cudaSuccess) {
+        bounds_selftest_kernel<<<1, 32>>>(buf, rec);
+        e = cudaGetLastError();
+    }
+    unsigned long long h = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&h, rec, sizeof h, cudaMemcpyDeviceToHost);
+    cudaFree(buf);
+    if (e != cudaSuccess) return fail(ADMM_ECUDA, "CUDA error: %s", cudaGetErrorString(e));
+    *status_out = (h != 0 && (int)(h >> 56) - 1 == DBG_SELFTEST) ? ADMM_EBOUNDS : ADMM_OK;
+    *index_out = (long long)(h & 0x00FFFFFFFFFFFFFFull);
+    return ADMM_OK;
+#else
+    *status_out = ADMM_OK;
+    *index_out = -1;
+    return fail(ADMM_EUNSUPPORTED, "built without bounds checks (build with debug_bounds for libadmm_debug.so)");
+#endif
 }
 
 admm_status admm_selftest_barrier_timeout(long long spin_ns, int grid, int *status_out)

@@ -25,6 +25,27 @@ __device__ __forceinline__ int ld_volatile_i32(const int *p)
     return *(const volatile int *)p;
 }
 
+// Bounds-checked builds (compiled with -DADMM_DEBUG_BOUNDS, libadmm_debug.so):
+// an element-array index is checked against the instance's range of that
+// array before the access; an index outside it is recorded in *rec (array
+// id in the top byte, the index below; the first violation wins) and
+// replaced by 0, so the access stays inside the allocation and the kernel
+// carries on.  The host turns a record into ADMM_EBOUNDS.  Release builds
+// use the index as it is.
+#ifdef ADMM_DEBUG_BOUNDS
+__device__ __forceinline__ size_t dbg_index(size_t idx, size_t need, size_t len, unsigned long long *rec, int id)
+{
+    if (idx + need <= len) return idx;
+    if (rec) atomicCAS(rec, 0ull, ((unsigned long long)(id + 1) << 56) | (idx & 0x00FFFFFFFFFFFFFFull));
+    return 0;
+}
+#define ADMM_IDX(idx, need, len, rec, id) ::admm_impl::dbg_index((idx), (need), (len), (rec), (id))
+#else
+#define ADMM_IDX(idx, need, len, rec, id) (idx)
+#endif
+// array ids of the bounds records
+enum { DBG_COL = 0, DBG_X = 1, DBG_COEF = 2, DBG_BOUND = 3, DBG_SELFTEST = 15 };
+
 // Loads that bypass L1: data written by other SMs since this SM last cached it.
 __device__ __forceinline__ double ldcg(const double *p) { return __ldcg(p); }
 

@@ -63,6 +63,7 @@ struct SingleArgs {
     unsigned *bar;             // barrier counter (zeroed before the launch)
     int *status;               // 0 or an admm_status set by a device wait
     double *info;              // out [kInfo]
+    unsigned long long *dbg;   // bounds record of checked builds (see ADMM_IDX), else unused
     double r_tol, s_tol, tau;
     double adapt_target;       // r_tol / s_tol of the settings (Sec. IV-A ratio rule)
     int max_iter, check_every, xmin_mode, sweep, adapt;

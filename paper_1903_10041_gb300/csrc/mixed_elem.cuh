@@ -45,6 +45,13 @@ struct ElemF32 {
     float *x, *s, *mu, *s_lo, *mu_lo;
     int n, m, q, ld, sweep, xmin_mode;
     int cq, cj; // coefficient row of pair (i, j): i * cq + j * cj
+    unsigned long long *dbg = nullptr; // bounds record (checked builds)
+    // lengths of the instance's ranges: columns [q][ld], x [m][q][ld],
+    // coefficients [m][ld] when shared else [m][q][ld], bounds [m][ld]
+    __device__ __forceinline__ size_t len_col() const { return (size_t)q * ld; }
+    __device__ __forceinline__ size_t len_x() const { return (size_t)m * q * ld; }
+    __device__ __forceinline__ size_t len_coef() const { return (size_t)m * (cj ? q : 1) * ld; }
+    __device__ __forceinline__ size_t len_bound() const { return (size_t)m * ld; }
 };
 
 // L2 prefetch of everything vec32 reads for the columns (j, k0..): issued
@@ -55,7 +62,7 @@ __device__ __forceinline__ void prefetch_l2(const void *p) { asm volatile("prefe
 template <int M>
 __device__ __forceinline__ void prefetch_vec32(const ElemF32 &a, int j, int k0, bool cold)
 {
-    const size_t col = (size_t)j * a.ld + k0;
+    const size_t col = ADMM_IDX((size_t)j * a.ld + k0, 2, a.len_col(), a.dbg, DBG_COL);
     prefetch_l2(a.y + col);
     prefetch_l2(a.s + col);
     prefetch_l2(a.mu + col);
@@ -64,16 +71,18 @@ __device__ __forceinline__ void prefetch_vec32(const ElemF32 &a, int j, int k0, 
 #pragma unroll
     for (int i = 0; i < M; ++i)
         if (i < a.m) {
-            const size_t e = ((size_t)i * a.q + j) * a.ld + k0;
-            const size_t ec = ((size_t)i * a.cq + (size_t)j * a.cj) * a.ld + k0;
+            const size_t e = ADMM_IDX(((size_t)i * a.q + j) * a.ld + k0, 2, a.len_x(), a.dbg, DBG_X);
+            const size_t ec = ADMM_IDX(((size_t)i * a.cq + (size_t)j * a.cj) * a.ld + k0, 2, a.len_coef(), a.dbg,
+                                       DBG_COEF);
+            const size_t eb = ADMM_IDX((size_t)i * a.ld + k0, 2, a.len_bound(), a.dbg, DBG_BOUND);
             prefetch_l2(a.x + e);
             prefetch_l2(a.f2 + ec);
             prefetch_l2(a.f1 + ec);
             prefetch_l2(a.g2 + ec);
             prefetch_l2(a.g1 + ec);
             if (cold) prefetch_l2(a.g0 + ec);
-            prefetch_l2(a.lo + (size_t)i * a.ld + k0);
-            prefetch_l2(a.hi + (size_t)i * a.ld + k0);
+            prefetch_l2(a.lo + eb);
+            prefetch_l2(a.hi + eb);
         }
 }
 
@@ -99,11 +108,12 @@ __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_g
 // (dst = stage base + lane).
 template <int M> __device__ __forceinline__ void stage_vec32(const ElemF32 &a, int j, int k0, float2 *dst)
 {
-    cp_async8(dst, a.y + (size_t)j * a.ld + k0);
+    cp_async8(dst, a.y + ADMM_IDX((size_t)j * a.ld + k0, 2, a.len_col(), a.dbg, DBG_COL));
 #pragma unroll
     for (int i = 0; i < M; ++i)
         if (i < a.m) {
-            const size_t d = ((size_t)i * a.cq + (size_t)j * a.cj) * a.ld + k0;
+            const size_t d = ADMM_IDX(((size_t)i * a.cq + (size_t)j * a.cj) * a.ld + k0, 2, a.len_coef(), a.dbg,
+                                      DBG_COEF);
             cp_async8(dst + (1 + 4 * i) * 32, a.f2 + d);
             cp_async8(dst + (2 + 4 * i) * 32, a.f1 + d);
             cp_async8(dst + (3 + 4 * i) * 32, a.g2 + d);
@@ -115,7 +125,7 @@ template <int M> __device__ __forceinline__ void stage_vec32(const ElemF32 &a, i
 // memory: x, the bounds and the column state s, mu.
 template <int M> __device__ __forceinline__ void prefetch_mutable(const ElemF32 &a, int j, int k0)
 {
-    const size_t col = (size_t)j * a.ld + k0;
+    const size_t col = ADMM_IDX((size_t)j * a.ld + k0, 2, a.len_col(), a.dbg, DBG_COL);
     prefetch_l2(a.s + col);
     prefetch_l2(a.mu + col);
     prefetch_l2(a.s_lo + col);
@@ -123,9 +133,10 @@ template <int M> __device__ __forceinline__ void prefetch_mutable(const ElemF32 
 #pragma unroll
     for (int i = 0; i < M; ++i)
         if (i < a.m) {
-            prefetch_l2(a.x + ((size_t)i * a.q + j) * a.ld + k0);
-            prefetch_l2(a.lo + (size_t)i * a.ld + k0);
-            prefetch_l2(a.hi + (size_t)i * a.ld + k0);
+            prefetch_l2(a.x + ADMM_IDX(((size_t)i * a.q + j) * a.ld + k0, 2, a.len_x(), a.dbg, DBG_X));
+            const size_t eb = ADMM_IDX((size_t)i * a.ld + k0, 2, a.len_bound(), a.dbg, DBG_BOUND);
+            prefetch_l2(a.lo + eb);
+            prefetch_l2(a.hi + eb);
         }
 }
 
@@ -204,7 +215,7 @@ __device__ __forceinline__ void vec32(const ElemF32 &a, const float *uoff, const
 {
     static_assert(VW == 2, "the element update works on column pairs");
     const int m = a.m, q = a.q, ld = a.ld, n = a.n;
-    const size_t col = (size_t)j * ld + k0;
+    const size_t col = ADMM_IDX((size_t)j * ld + k0, 2, a.len_col(), a.dbg, DBG_COL);
     const float2 yv = STAGED ? stg[0] : ldg2(a.y + col);
     const float2 st = ld2(a.s + col), stl = ld2(a.s_lo + col);
     float2 mu = ld2(a.mu + col), mul = ld2(a.mu_lo + col);
@@ -217,7 +228,7 @@ __device__ __forceinline__ void vec32(const ElemF32 &a, const float *uoff, const
 #pragma unroll
     for (int i = 0; i < M; ++i)
         if (i < m) {
-            xt[i] = ld2(a.x + ((size_t)i * q + j) * ld + k0);
+            xt[i] = ld2(a.x + ADMM_IDX(((size_t)i * q + j) * ld + k0, 2, a.len_x(), a.dbg, DBG_X));
             xs[i] = xt[i];
             xsum = add2(xsum, xt[i]);
         }
@@ -229,12 +240,14 @@ __device__ __forceinline__ void vec32(const ElemF32 &a, const float *uoff, const
 #pragma unroll
     for (int i = 0; i < M; ++i) {
         if (i < m) {
-            const size_t e = ((size_t)i * a.cq + (size_t)j * a.cj) * ld + k0; // coefficient element
+            const size_t e = ADMM_IDX(((size_t)i * a.cq + (size_t)j * a.cj) * ld + k0, 2, a.len_coef(), a.dbg,
+                                      DBG_COEF); // coefficient element
+            const size_t eb = ADMM_IDX((size_t)i * ld + k0, 2, a.len_bound(), a.dbg, DBG_BOUND);
             const float2 a2 = STAGED ? stg[(1 + 4 * i) * 32] : ldg2(a.f2 + e);
             const float2 a1 = STAGED ? stg[(2 + 4 * i) * 32] : ldg2(a.f1 + e);
             const float2 b2 = STAGED ? stg[(3 + 4 * i) * 32] : ldg2(a.g2 + e);
             const float2 b1 = STAGED ? stg[(4 + 4 * i) * 32] : ldg2(a.g1 + e);
-            const float2 L = ldg2(a.lo + (size_t)i * ld + k0), H = ldg2(a.hi + (size_t)i * ld + k0);
+            const float2 L = ldg2(a.lo + eb), H = ldg2(a.hi + eb);
             const float2 g0 = cold ? ldg2(a.g0 + e) : splat2(0.0f);
             const int pr = i * q + j;
             const float2 x0 = xt[i];
@@ -301,7 +314,7 @@ __device__ __forceinline__ void vec32(const ElemF32 &a, const float *uoff, const
     }
 #pragma unroll
     for (int i = 0; i < M; ++i)
-        if (i < m) st2(a.x + ((size_t)i * q + j) * ld + k0, xs[i]);
+        if (i < m) st2(a.x + ADMM_IDX(((size_t)i * q + j) * ld + k0, 2, a.len_x(), a.dbg, DBG_X), xs[i]);
     st2(a.s + col, sv.hi);
     st2(a.mu + col, mnew.hi);
     st2(a.s_lo + col, sv.lo);

@@ -250,7 +250,8 @@ void worker_loop(admm_server *S)
             if (r->session >= 0) {
                 std::lock_guard<std::mutex> lk(S->mu);
                 Session &ss = S->sessions[r->session];
-                if (ss.resident && ss.inst.n == sg.n && ss.inst.m == sg.m && ss.inst.q == sg.q) {
+                if (ss.resident && ss.inst.n == sg.n && ss.inst.m == sg.m && ss.inst.q == sg.q &&
+                    ss.inst.cs == sg.cs) {
                     I = ss.inst;
                     reuse = true;
                 }
@@ -259,6 +260,7 @@ void worker_loop(admm_server *S)
                 back_to_queue.push_back(r); // store full: wait for a later tick
                 continue;
             }
+            I.cs = sg.cs;
             const InstSizes z = inst_sizes(sg.n, sg.m, sg.q);
             cudaError_t e = ensure_pinned(S, 7 * (size_t)z.e + 2 * (size_t)z.b + (size_t)z.c);
             if (e == cudaSuccess) {
@@ -686,8 +688,6 @@ admm_status admm_server_submit(admm_server *S, const admm_problem *P, int64_t se
     clear_last_error();
     if (!S || !P || !ticket) return sfail(ADMM_EINVAL, "NULL argument");
     if (P->on_device) return sfail(ADMM_EINVAL, "server requests take host arrays (on_device = 0)");
-    if (P->coef_shared != 0)
-        return sfail(ADMM_EUNSUPPORTED, "server requests take per-scenario coefficients (coef_shared = 0)");
     if (P->m > S->cfg.max_m || P->q > S->cfg.max_q)
         return sfail(ADMM_EUNSUPPORTED, "instance exceeds the server's max_m or max_q");
     auto r = std::make_shared<Request>();

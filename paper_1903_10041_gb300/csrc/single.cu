@@ -482,7 +482,8 @@ __global__ void __launch_bounds__(NT, MINB) single_kernel(SingleArgs a)
                                     (float *)a.s,        (float *)a.mu,       (float *)a.s_lo,
                                     (float *)a.mu_lo,    a.n,                 a.m,
                                     a.q,                 a.ld,                a.sweep,
-                                    a.xmin_mode,         a.cq,                a.cj};
+                                    a.xmin_mode,         a.cq,                a.cj,
+                                    a.dbg};
                 const int kn = min(ke, n); // padding columns k >= n are skipped
                 for (int k0 = kb + first * VW; k0 < kn; k0 += stride * VW) {
                     if constexpr (MINB == 2) // several vectors per thread: fetch the next one into L2

@@ -81,6 +81,11 @@ bool stage_instance(const admm_problem &P, Staged &S, std::string &why)
     S.m = m;
     S.q = q;
     S.ld = ld;
+    if (P.coef_shared != 0 && P.coef_shared != 1) {
+        why = "coef_shared must be 0 or 1";
+        return false;
+    }
+    S.cs = P.coef_shared;
     const size_t ne = (size_t)m * q * ld, nb = (size_t)m * ld, nc = (size_t)q * ld;
     for (auto &v : S.e) v.assign(ne, 0.0f);
     for (auto &v : S.b) v.assign(nb, 0.0f);
@@ -119,7 +124,10 @@ bool stage_instance(const admm_problem &P, Staged &S, std::string &why)
         for (int j = 0; j < q; ++j) {
             double s0 = 0.0, smin = 0.0;
             for (int k = 0; k < n; ++k) {
-                const size_t e = ((size_t)i * q + j) * n + k, d = ((size_t)i * q + j) * ld + k;
+                // scenario-shared maps: read once per source and stored in every
+                // scenario's row (the batched kernel indexes coefficients like x)
+                const size_t e = (S.cs ? (size_t)i : (size_t)i * q + j) * n + k;
+                const size_t d = ((size_t)i * q + j) * ld + k, dc = d;
                 double v[6];
                 for (int t = 0; t < 6; ++t) {
                     v[t] = src[t][e];
@@ -127,7 +135,7 @@ bool stage_instance(const admm_problem &P, Staged &S, std::string &why)
                         why = "non-finite coefficient";
                         return false;
                     }
-                    S.e[t][d] = (float)v[t];
+                    S.e[t][dc] = (float)v[t];
                 }
                 if (v[0] < 0.0 || v[3] < 0.0) {
                     why = "f2 < 0 or g2 < 0 (Assumption 1 needs convex f, g)";
@@ -223,7 +231,7 @@ bool Store::place(int n, int m, int q, BatchInst &I)
     I.off_pair = (int)op;
     I.off_scal = (int)os;
     I.off_src = (int)om;
-    I.pad = 0;
+    I.cs = 0;
     return true;
 }
 

@@ -37,6 +37,7 @@ InstSizes inst_sizes(int n, int m, int q);
 // false with a message on invalid data.
 struct Staged {
     int n = 0, m = 0, q = 0, ld = 0;
+    int cs = 0;                // 1: f2..g0 given once per source ([m][n]), repeated over the scenarios here
     std::vector<float> e[7];   // f2 f1 f0 g2 g1 g0 x0   [m][q][ld]
     std::vector<float> b[2];   // lo hi                  [m][ld]
     std::vector<float> y;      // [q][ld]

@@ -38,6 +38,15 @@ def test_every_declared_symbol_is_exported(lib):
     assert not missing, missing
 
 
+def test_bounds_checked_build_exports_the_same_symbols():
+    """libadmm_debug.so (-DADMM_DEBUG_BOUNDS) is the same boundary with the
+    element accesses checked."""
+    from paper_1903_10041_gb300 import build
+    dbg = ctypes.CDLL(build.build(debug_bounds=True))
+    missing = [n for n in sorted(_declared()) if not hasattr(dbg, n)]
+    assert not missing, missing
+
+
 def test_host_only_calls_work_without_a_gpu():
     from paper_1903_10041_gb300 import capi
     p = capi.admm_default_params()
@@ -75,7 +84,7 @@ def test_status_codes_match_the_header():
     txt = open(os.path.join(ROOT, "include", "admm.h")).read()
     codes = {m.group(1): int(m.group(2)) for m in re.finditer(r"\b(ADMM_[A-Z]+)\s*=\s*(\d+)", txt)}
     for name in ("ADMM_OK", "ADMM_EINVAL", "ADMM_ENOMEM", "ADMM_ECUDA", "ADMM_ETIMEOUT", "ADMM_ENOTCONVERGED",
-                 "ADMM_EUNSUPPORTED", "ADMM_EPENDING", "ADMM_ECANCELLED"):
+                 "ADMM_EUNSUPPORTED", "ADMM_EPENDING", "ADMM_ECANCELLED", "ADMM_EBOUNDS"):
         assert getattr(capi, name) == codes[name], name
         assert capi.STATUS_NAMES[codes[name]] == name[len("ADMM_"):]
 
