@@ -88,11 +88,13 @@ def workload(cfg: int, precision: str, coef_shared: bool = False):
 # figure is reported only while the kernel's sources hash to the build it
 # was taken on (otherwise `traffic` is null).
 NCU_TRAFFIC = {
-    ("phev n=1000 q=50", "fp64"): {"bytes_per_iter": (7.595264e6 + 0.055808e6) / 3330, "src": "965ff8b0533d4c28"},
-    ("plain n=1e5 m=4 q=20", "mixed"): {"bytes_per_iter": (4.317581824e9 + 1.382421760e9) / 20,
-                                        "src": "965ff8b0533d4c28"},
+    ("phev n=1000 q=50", "fp64"): {"bytes_per_iter": (7670528 + 57856) / 3330, "src": "8f897a19c7a6fd75"},
 }
-NCU_TRAFFIC_BATCH = {"bytes_per_element_iter": None, "src": None}
+NCU_TRAFFIC_BATCH = {"bytes_per_element_iter": (1883104666112 + 660502484224) / 76360828990.0, "src": "f5cc893436019ddd"}
+# FP64 pipe utilisation (sm__pipe_fp64_cycles_active, % of peak over the active cycles) of the FP64 solve
+# kernel on the PHEV instance, from an ncu capture of the same build: the counted-flop fraction leaves out
+# the Newton steps of the FP32-seeded roots, conversions, comparisons and the per-pair scalar phase.
+NCU_FP64_PIPE = {("phev n=1000 q=50", "fp64"): {"pct": 60.85, "src": "8f897a19c7a6fd75"}}
 
 # Sources each solve kernel is compiled from.
 SINGLE_KERNEL_SOURCES = ("single.cu", "quartic32.cuh", "quartic64.cuh", "mixed_elem.cuh", "common.cuh", "internal.h")
@@ -117,6 +119,13 @@ def traffic_per_launch(P, prec: str, iters: int):
     if t is None or t["src"] != kernel_source_hash():
         return None
     return t["bytes_per_iter"] * iters
+
+
+def fp64_pipe_busy(P):
+    t = NCU_FP64_PIPE.get((P.name, "fp64"))
+    if t is None or t["pct"] is None or t["src"] != kernel_source_hash():
+        return None
+    return t["pct"] / 100.0
 
 
 def batch_traffic_per_launch(element_iters: float):
@@ -988,6 +997,7 @@ def run_single(args, P, par, rank, world, local):
         roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic_per_launch(P, "fp64", iters),
                     "peak_source": "FP64: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz (derived; measured 1.90 DFMA/clk/SM)",
+                    "fp64_pipe_busy": fp64_pipe_busy(P),
                     # algorithmic bytes streamed per second; an instance that fits in L2
                     # (the n=1000 PHEV one) is served mostly from L2, not HBM (see traffic)
                     "streamed_gbs": iters * bytes_per_iteration(P, "fp64") / per_launch_s / 1e9}
