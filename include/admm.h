@@ -291,7 +291,10 @@ typedef struct admm_batch_config {
  * instance to the zero start.  params->precision must be ADMM_MIXED;
  * the settings apply to every instance.  Default configuration: 8 warps
  * per CTA, small_max_elements 0 (every instance on a whole-CTA team, the
- * fastest on mixed workloads of 50..400k elements), no clusters. */
+ * fastest on mixed workloads of 50..400k elements), no clusters.
+ * ADMM_EUNSUPPORTED if the packed arrays would exceed 2^32 - 1 elements
+ * each (sum over the instances of m*q*ld; the kernel indexes them with
+ * 32-bit offsets): split such a batch into several. */
 admm_status admm_batch_create(const admm_problem *probs, int32_t count, const admm_params *params,
                               admm_batch **out);
 /* Replaces the launch configuration (used from the next admm_batch_solve;
@@ -363,8 +366,9 @@ void admm_server_default_config(admm_server_config *cfg);
  * ADMM_MIXED; ADMM_EINVAL for rho <= 0 or a configuration out of range
  * (max_active, tick_iters, max_m, max_q < 1; m*q > ADMM_BATCH_MAX_PAIRS;
  * store_elements < 1024; batch settings as in admm_batch_set_config);
- * ADMM_ENOMEM / ADMM_ECUDA if an allocation or CUDA call fails, with
- * nothing left allocated. */
+ * ADMM_EUNSUPPORTED for store_elements > 2^32 - 1 (32-bit array offsets
+ * in the kernel); ADMM_ENOMEM / ADMM_ECUDA if an allocation or CUDA call
+ * fails, with nothing left allocated. */
 admm_status admm_server_create(const admm_params *params, const admm_server_config *cfg, admm_server **out);
 /* Validates and queues a request; session >= 0 ties it to that session
  * (warm start from the session's resident state when the shapes match),

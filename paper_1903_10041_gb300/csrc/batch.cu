@@ -206,7 +206,7 @@ void launch_shift_state(const BatchInst *inst, const int *ids, int count, float 
 static size_t team_doubles(int m, int q, int items, int nwt)
 {
     const int mq = m * q;
-    return (size_t)scal_size(m, q) + 2 * (size_t)items * m * 4 + 4 * (size_t)nwt + 8 + mq + kMaxM + kWarpsMax * 8 +
+    return (size_t)scal_size(m, q) + 2 * (size_t)items * m * 4 + 4 * (size_t)nwt + 24 + mq + kMaxM + kWarpsMax * 8 +
            (mq + 1) / 2 + 8;
 }
 

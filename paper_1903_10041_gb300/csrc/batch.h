@@ -9,6 +9,9 @@
 namespace admm_impl {
 
 constexpr int kWarpsMax = 16; // largest CTA of the batched kernel, in warps
+// Elements per array of a batch or server store: the kernel indexes the
+// arrays with 32-bit unsigned offsets from their bases.
+constexpr int64_t kBatchArrayMax = 0xFFFFFFFFll;
 
 // One instance of a batch: sizes and offsets into the packed arrays.
 struct BatchInst {

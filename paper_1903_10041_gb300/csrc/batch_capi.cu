@@ -303,6 +303,8 @@ admm_status admm_batch_create(const admm_problem *probs, int32_t count, const ad
         b->max_m = std::max(b->max_m, P.m);
         b->max_q = std::max(b->max_q, P.q);
     }
+    if (tot.e > kBatchArrayMax || tot.b > kBatchArrayMax || tot.c > kBatchArrayMax)
+        return bail(bfail(ADMM_EUNSUPPORTED, "batch exceeds 2^32 - 1 elements per array: split it"));
     e = b->store.allocate(tot.e, tot.b, tot.c, tot.p, tot.s, tot.m);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_inst, sizeof(BatchInst) * count);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_order, sizeof(int) * count);

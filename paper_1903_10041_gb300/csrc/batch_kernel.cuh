@@ -51,25 +51,6 @@ template <int NT> struct Team {
     }
 };
 
-// Team-wide max of NV doubles over NT threads of one CTA (every thread gets the result).
-template <int NT, int NV> __device__ __forceinline__ void team_max(const Team<NT> &T, double *v, double *scr)
-{
-#pragma unroll
-    for (int t = 0; t < NV; ++t) v[t] = warp_max(v[t]);
-    if constexpr (NT > 32) {
-        const int lane = T.tid & 31, w = T.tid >> 5;
-        if (lane == 0)
-            for (int t = 0; t < NV; ++t) scr[w * 8 + t] = v[t];
-        __syncthreads();
-        for (int t = 0; t < NV; ++t) {
-            double r = 0.0;
-            for (int ww = 0; ww < NT / 32; ++ww) r = fmax(r, scr[ww * 8 + t]);
-            v[t] = r;
-        }
-        __syncthreads();
-    }
-}
-
 // Team-wide FP64 sum over NT threads of one CTA (fixed order), every thread gets the result.
 template <int NT> __device__ __forceinline__ double team_sum(const Team<NT> &T, double v, double *scr)
 {
@@ -143,14 +124,19 @@ template <int KIND, int NW, int M> __device__ void solve_team(const BatchArgs &a
     const int64_t npairs = (int64_t)q * nv;
     const int items = q + W - 1; // record slots: (row j, warp w) at j + w
 
-    // shared memory: scal | rec[2][items][m][4] | cmax[2][NWT][2] | part[8] | x0s[mq] | x1n | scr | uoff
+    // shared memory: scal | rec[2][items][m][4] | cmax[2][NWT][2] | part[24] | x0s[mq] | x1n | scr | uoff
+    // part: [0], [1] end-of-solve sums; [2] kappa; [3] the adaptation factor of a check; [16..19] fpar;
+    // [20..23] ipar.  Thread 0 keeps these team-wide values current so that the other threads read them
+    // instead of each converting and dividing on the FP64 pipe.
     double *scal = smem;
     double *lam = scal, *zeta = scal + mq, *hh = scal + 2 * mq, *pp = scal + 3 * mq, *nu = scal + 4 * mq;
     double *x1 = scal + 5 * mq, *rho = x1 + m, *flags = rho + 4;
     double *rec0 = smem + scal_size(m, q);
     double *cmax = rec0 + 2 * (size_t)items * m * 4;
     double *part = cmax + 4 * NWT;
-    double *x0s = part + 8;
+    float *fpar = (float *)(part + 16); // rho_1, rho_3, rho_4 and the pending mu divisor, in FP32
+    int *ipar = (int *)(part + 20);     // converged, penalties changed, cold start
+    double *x0s = part + 24;
     double *x1n = x0s + mq;
     double *scr = x1n + kMaxM;
     float *uoff = (float *)(scr + kWarpsMax * 8);
@@ -163,13 +149,21 @@ template <int KIND, int NW, int M> __device__ void solve_team(const BatchArgs &a
     for (int t = tid; t < scal_size(m, q); t += NTL) scal[t] = __ldcg(gscal + t);
     sync_local();
     for (int pr = tid; pr < mq; pr += NTL) uoff[pr] = (float)(zeta[pr] + lam[pr]);
+    if (tid == 0) {
+        part[2] = rho[1] / (rho[0] + (double)n * rho[1]); // kappa of step (b)
+        fpar[0] = (float)rho[0];
+        fpar[1] = (float)rho[2];
+        fpar[2] = (float)rho[3];
+        fpar[3] = (float)flags[1];
+        ipar[2] = flags[0] != 0.0;
+    }
     const int it0 = (int)__ldcg(out);
     sync_local();
 
-    const ElemF32 ea = {a.f2 + I.off_e, a.f1 + I.off_e, a.g2 + I.off_e, a.g1 + I.off_e, a.g0 + I.off_e,
-                        a.lo + I.off_b, a.hi + I.off_b, a.y + I.off_c,  a.x + I.off_e,  a.s + I.off_c,
-                        a.mu + I.off_c, a.s_lo + I.off_c, a.mu_lo + I.off_c, n, m, q, I.ld, a.sweep, a.xmin_mode,
-                        q, 1, a.dbg};
+    // the arrays' bases and this instance's 32-bit offsets into them (the arrays hold < 2^32 elements)
+    const ElemF32T<unsigned> ea = {a.f2, a.f1, a.g2, a.g1, a.g0, a.lo, a.hi, a.y, a.x, a.s, a.mu, a.s_lo, a.mu_lo,
+                                   n, m, q, I.ld, a.sweep, a.xmin_mode, q, 1, a.dbg,
+                                   (unsigned)I.off_e, (unsigned)I.off_b, (unsigned)I.off_c};
     const double *cc = a.c + I.off_src;
     const double *sumg0 = a.sumg0 + I.off_pair;
     unsigned esc = 0;
@@ -187,9 +181,9 @@ template <int KIND, int NW, int M> __device__ void solve_team(const BatchArgs &a
         ++it;
         const int par = it & 1;
         const bool check = (it % a.check_every == 0) || (it == a.max_iter);
-        const bool cold = flags[0] != 0.0;
-        const float mu_div = (float)flags[1];
-        const float rho1 = (float)rho[0], rho3 = (float)rho[2], rho4 = (float)rho[3];
+        const bool cold = ipar[2] != 0;
+        const float mu_div = fpar[3];
+        const float rho1 = fpar[0], rho3 = fpar[1], rho4 = fpar[2];
         const float iq = 1.0f / (float)q;
         float fcr = 0.0f, fcs = 0.0f;
         double *recs = rec0 + (size_t)par * items * m * 4;
@@ -263,11 +257,13 @@ template <int KIND, int NW, int M> __device__ void solve_team(const BatchArgs &a
                 cmax[(par * NWT + wl) * 2 + 1] = (double)ws;
             }
         }
-        if (tid == 0) flags[1] = 1.0;
         sync_team(); // every record of this iteration is complete and visible
+        if (tid == 0) { // the pending mu rescale has been applied (every thread read it before the barrier)
+            flags[1] = 1.0;
+            fpar[3] = 1.0f;
+        }
 
-        const double r1 = rho[0], r2 = rho[1], r3 = rho[2];
-        const double kappa = r2 / (r1 + (double)n * r2);
+        const double kappa = part[2];
         double r2m = 0.0, r3m = 0.0, s1m = 0.0, s2m = 0.0;
         for (int pr = tid; pr < mq; pr += NTL) {
             const int i = pr / q, j = pr - i * q;
@@ -292,11 +288,11 @@ template <int KIND, int NW, int M> __device__ void solve_team(const BatchArgs &a
             const double hn = cz < cc[i] ? cz : cc[i];
             const double pn = p0 + (hn - Z);
             if (check) {
-                r2m = fmax(r2m, fabs(lamn - lm));
-                r3m = fmax(r3m, fabs(hn - Z));
+                r2m = max_nonneg(r2m, fabs(lamn - lm));
+                r3m = max_nonneg(r3m, fabs(hn - Z));
                 const double dl = (lamn - lm) - zt;
-                s1m = fmax(s1m, fmax(fabs(dmx + dl), fabs(dmn + dl)));
-                s2m = fmax(s2m, fabs(hn - h0));
+                s1m = max_nonneg(s1m, max_nonneg(fabs(dmx + dl), fabs(dmn + dl)));
+                s2m = max_nonneg(s2m, fabs(hn - h0));
             }
             lam[pr] = lamn;
             zeta[pr] = lamn - lm;
@@ -318,50 +314,78 @@ template <int KIND, int NW, int M> __device__ void solve_team(const BatchArgs &a
             const int i = pr / q;
             const double x0 = x0s[pr], xn = x1n[i];
             nu[pr] = nu[pr] + (xn - x0);
-            if (check) r4m = fmax(r4m, fabs(x0 - xn));
+            if (check) r4m = max_nonneg(r4m, fabs(x0 - xn));
         }
         sync_local();
         if (tid < m) x1[tid] = x1n[tid];
-        if (tid == 0) flags[0] = 0.0;
+        if (tid == 0) {
+            flags[0] = 0.0;
+            ipar[2] = 0;
+        }
         sync_local();
         if (check) {
-            double c1 = 0.0, c2 = 0.0;
-            for (int r = 0; r < CL; ++r) {
-                const double *cb = cmax;
-                if constexpr (KIND == TEAM_CLUSTER) cb = cg::this_cluster().map_shared_rank(cmax, r);
-                for (int w = 0; w < NWT; ++w) {
-                    c1 = fmax(c1, cb[(par * NWT + w) * 2 + 0]);
-                    c2 = fmax(c2, cb[(par * NWT + w) * 2 + 1]);
-                }
-            }
-            double v[7] = {c1, r2m, r3m, r4m, s1m, s2m, c2};
-            team_max<NTL, 7>(T, v, scr);
+            // maxima of the residual terms: per warp, then over the team's warps and (for a cluster)
+            // the CTAs' column maxima by thread 0, which takes the stop decision and the adaptation
+            // of Sec. IV-A and passes them on; every CTA of a cluster decides the same way
+            double v[5] = {r2m, r3m, r4m, s1m, s2m};
 #pragma unroll
-            for (int t = 0; t < 7; ++t) res[t] = v[t];
-            const double r = fmax(fmax(v[0], v[1]), fmax(v[2], v[3]));
-            const double sgm = fmax(fmax(r1 * v[4], r2 * v[5]), r3 * v[6]);
-            r_last = r;
-            s_last = sgm;
-            if (r < a.r_tol && sgm < a.s_tol) {
+            for (int t = 0; t < 5; ++t) v[t] = warp_max_nonneg(v[t]);
+            if constexpr (KIND != TEAM_WARP) {
+                if (lane == 0)
+                    for (int t = 0; t < 5; ++t) scr[wl * 8 + t] = v[t];
+                sync_local();
+            }
+            if (tid == 0) {
+                double w[7] = {0.0, v[0], v[1], v[2], v[3], v[4], 0.0};
+                if constexpr (KIND != TEAM_WARP)
+                    for (int ww = 0; ww < NWT; ++ww)
+                        for (int t = 0; t < 5; ++t) w[1 + t] = max_nonneg(w[1 + t], scr[ww * 8 + t]);
+                for (int r = 0; r < CL; ++r) {
+                    const double *cb = cmax;
+                    if constexpr (KIND == TEAM_CLUSTER) cb = cg::this_cluster().map_shared_rank(cmax, r);
+                    for (int ww = 0; ww < NWT; ++ww) {
+                        w[0] = max_nonneg(w[0], cb[(par * NWT + ww) * 2 + 0]);
+                        w[6] = max_nonneg(w[6], cb[(par * NWT + ww) * 2 + 1]);
+                    }
+                }
+                for (int t = 0; t < 7; ++t) res[t] = w[t];
+                const double r = fmax(fmax(w[0], w[1]), fmax(w[2], w[3]));
+                const double sgm = fmax(fmax(rho[0] * w[4], rho[1] * w[5]), rho[2] * w[6]);
+                r_last = r;
+                s_last = sgm;
+                const bool cv = r < a.r_tol && sgm < a.s_tol;
+                double f = 1.0;
+                if (!cv && a.adapt && it < a.max_iter) { // Sec. IV-A, duals rescaled by rho_old / rho_new
+                    const double ratio = r / sgm, target = a.adapt_target;
+                    if (ratio > 1.2 * target) f = a.tau;
+                    else if (ratio < 0.8 * target) f = 1.0 / a.tau;
+                }
+                ipar[0] = cv;
+                ipar[1] = f != 1.0;
+                part[3] = f;
+            }
+            sync_local();
+            if (ipar[0]) {
                 conv = true;
                 break;
             }
-            if (a.adapt && it < a.max_iter) { // Sec. IV-A, duals rescaled by rho_old / rho_new
-                const double ratio = r / sgm, target = a.adapt_target;
-                double f = 1.0;
-                if (ratio > 1.2 * target) f = a.tau;
-                else if (ratio < 0.8 * target) f = 1.0 / a.tau;
-                if (f != 1.0) {
-                    for (int pr = tid; pr < mq; pr += NTL) {
-                        lam[pr] /= f;
-                        pp[pr] /= f;
-                        nu[pr] /= f;
-                    }
-                    sync_local();
-                    if (tid < 4) rho[tid] *= f;
-                    if (tid == 0) flags[1] = f;
-                    sync_local();
+            if (ipar[1]) {
+                const double f = part[3];
+                for (int pr = tid; pr < mq; pr += NTL) {
+                    lam[pr] /= f;
+                    pp[pr] /= f;
+                    nu[pr] /= f;
                 }
+                if (tid == 0) {
+                    for (int t = 0; t < 4; ++t) rho[t] *= f;
+                    flags[1] = f;
+                    part[2] = rho[1] / (rho[0] + (double)n * rho[1]);
+                    fpar[0] = (float)rho[0];
+                    fpar[1] = (float)rho[2];
+                    fpar[2] = (float)rho[3];
+                    fpar[3] = (float)f;
+                }
+                sync_local();
             }
         }
         for (int pr = tid; pr < mq; pr += NTL) uoff[pr] = (float)(zeta[pr] + lam[pr]);
@@ -372,13 +396,13 @@ template <int KIND, int NW, int M> __device__ void solve_team(const BatchArgs &a
     // objective (1/q) sum f(x) of eq. (2): each CTA sums its share, rank 0 adds in rank order
     double acc = 0.0;
     if (finished) {
-        const float *F2 = ea.f2, *F1 = ea.f1, *F0 = a.f0 + I.off_e;
+        const float *F2 = a.f2 + I.off_e, *F1 = a.f1 + I.off_e, *F0 = a.f0 + I.off_e, *X = a.x + I.off_e;
         const int64_t tot = (int64_t)mq * n;
         for (int64_t t = (int64_t)rank * NTL + tid; t < tot; t += (int64_t)CL * NTL) {
             const int64_t r = t / n;
             const int k = (int)(t - r * n);
             const size_t e = ADMM_IDX((size_t)r * I.ld + k, 1, ea.len_x(), a.dbg, DBG_X);
-            const double x = ea.x[e];
+            const double x = X[e];
             acc += (double)F2[e] * x * x + (double)F1[e] * x + (double)F0[e];
         }
     }

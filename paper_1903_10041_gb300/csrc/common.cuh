@@ -99,6 +99,21 @@ template <class T> __device__ __forceinline__ T warp_max(T v)
         v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
 }
+// Maxima of non-negative doubles (residual terms, absolute values): for
+// x, y >= 0 the order of their IEEE-754 bit patterns read as signed 64-bit
+// integers is the order of the values, so these run on the integer pipes
+// instead of the FP64 pipe (1/64 of the FP32 rate on this GPU).
+__device__ __forceinline__ double max_nonneg(double a, double b)
+{
+    return __longlong_as_double(max(__double_as_longlong(a), __double_as_longlong(b)));
+}
+__device__ __forceinline__ double warp_max_nonneg(double v)
+{
+    long long b = __double_as_longlong(v);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) b = max(b, __shfl_xor_sync(0xffffffffu, b, o));
+    return __longlong_as_double(b);
+}
 template <class T> __device__ __forceinline__ T warp_min(T v)
 {
 #pragma unroll

@@ -39,30 +39,55 @@ __device__ __forceinline__ FF ff_addf(FF a, float b)
 __device__ __forceinline__ FF ff_neg(FF a) { return {-a.hi, -a.lo}; }
 
 // Storage of one instance for the mixed element update (FP32 arrays with
-// row stride ld; s, mu float-float as hi and lo arrays).
-struct ElemF32 {
+// row stride ld; s, mu float-float as hi and lo arrays).  The instance's
+// ranges start at element oe (x and coefficients), ob (bounds) and oc
+// (columns) of the arrays.  IX is the index type: size_t for a single
+// instance of any size; unsigned for the batched kernel, whose arrays hold
+// at most 2^32 - 1 elements, so that an address is the array's base (a
+// kernel parameter) plus one 32-bit index and no per-instance 64-bit
+// pointers stay live in registers.
+template <class IX> struct ElemF32T {
     const float *f2, *f1, *g2, *g1, *g0, *lo, *hi, *y;
     float *x, *s, *mu, *s_lo, *mu_lo;
     int n, m, q, ld, sweep, xmin_mode;
     int cq, cj; // coefficient row of pair (i, j): i * cq + j * cj
     unsigned long long *dbg = nullptr; // bounds record (checked builds)
+    IX oe = 0, ob = 0, oc = 0;
     // lengths of the instance's ranges: columns [q][ld], x [m][q][ld],
     // coefficients [m][ld] when shared else [m][q][ld], bounds [m][ld]
     __device__ __forceinline__ size_t len_col() const { return (size_t)q * ld; }
     __device__ __forceinline__ size_t len_x() const { return (size_t)m * q * ld; }
     __device__ __forceinline__ size_t len_coef() const { return (size_t)m * (cj ? q : 1) * ld; }
     __device__ __forceinline__ size_t len_bound() const { return (size_t)m * ld; }
+    // array indices of the column pair (j, k0): column arrays, x of source i,
+    // coefficients of source i, bounds of source i (checked in the instance's range)
+    __device__ __forceinline__ IX col(int j, int k0) const
+    {
+        return oc + (IX)ADMM_IDX((IX)j * ld + k0, 2, len_col(), dbg, DBG_COL);
+    }
+    __device__ __forceinline__ IX xe(int i, int j, int k0) const
+    {
+        return oe + (IX)ADMM_IDX(((IX)i * q + j) * ld + k0, 2, len_x(), dbg, DBG_X);
+    }
+    __device__ __forceinline__ IX ce(int i, int j, int k0) const
+    {
+        return oe + (IX)ADMM_IDX(((IX)i * cq + (IX)j * cj) * ld + k0, 2, len_coef(), dbg, DBG_COEF);
+    }
+    __device__ __forceinline__ IX be(int i, int k0) const
+    {
+        return ob + (IX)ADMM_IDX((IX)i * ld + k0, 2, len_bound(), dbg, DBG_BOUND);
+    }
 };
+using ElemF32 = ElemF32T<size_t>;
 
 // L2 prefetch of everything vec32 reads for the columns (j, k0..): issued
 // one vector ahead, so the loads of the next vector hit L2 instead of
 // waiting on HBM.  Prefetches are hints and touch only rows the update reads.
 __device__ __forceinline__ void prefetch_l2(const void *p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
 
-template <int M>
-__device__ __forceinline__ void prefetch_vec32(const ElemF32 &a, int j, int k0, bool cold)
+template <int M, class EA> __device__ __forceinline__ void prefetch_vec32(const EA &a, int j, int k0, bool cold)
 {
-    const size_t col = ADMM_IDX((size_t)j * a.ld + k0, 2, a.len_col(), a.dbg, DBG_COL);
+    const auto col = a.col(j, k0);
     prefetch_l2(a.y + col);
     prefetch_l2(a.s + col);
     prefetch_l2(a.mu + col);
@@ -71,10 +96,9 @@ __device__ __forceinline__ void prefetch_vec32(const ElemF32 &a, int j, int k0, 
 #pragma unroll
     for (int i = 0; i < M; ++i)
         if (i < a.m) {
-            const size_t e = ADMM_IDX(((size_t)i * a.q + j) * a.ld + k0, 2, a.len_x(), a.dbg, DBG_X);
-            const size_t ec = ADMM_IDX(((size_t)i * a.cq + (size_t)j * a.cj) * a.ld + k0, 2, a.len_coef(), a.dbg,
-                                       DBG_COEF);
-            const size_t eb = ADMM_IDX((size_t)i * a.ld + k0, 2, a.len_bound(), a.dbg, DBG_BOUND);
+            const auto e = a.xe(i, j, k0);
+            const auto ec = a.ce(i, j, k0);
+            const auto eb = a.be(i, k0);
             prefetch_l2(a.x + e);
             prefetch_l2(a.f2 + ec);
             prefetch_l2(a.f1 + ec);
@@ -106,14 +130,13 @@ __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_g
 
 // Copies the staged arrays of the column pair (j, k0) into the lane's slots
 // (dst = stage base + lane).
-template <int M> __device__ __forceinline__ void stage_vec32(const ElemF32 &a, int j, int k0, float2 *dst)
+template <int M, class EA> __device__ __forceinline__ void stage_vec32(const EA &a, int j, int k0, float2 *dst)
 {
-    cp_async8(dst, a.y + ADMM_IDX((size_t)j * a.ld + k0, 2, a.len_col(), a.dbg, DBG_COL));
+    cp_async8(dst, a.y + a.col(j, k0));
 #pragma unroll
     for (int i = 0; i < M; ++i)
         if (i < a.m) {
-            const size_t d = ADMM_IDX(((size_t)i * a.cq + (size_t)j * a.cj) * a.ld + k0, 2, a.len_coef(), a.dbg,
-                                      DBG_COEF);
+            const auto d = a.ce(i, j, k0);
             cp_async8(dst + (1 + 4 * i) * 32, a.f2 + d);
             cp_async8(dst + (2 + 4 * i) * 32, a.f1 + d);
             cp_async8(dst + (3 + 4 * i) * 32, a.g2 + d);
@@ -123,9 +146,9 @@ template <int M> __device__ __forceinline__ void stage_vec32(const ElemF32 &a, i
 
 // L2 prefetch of what the staged element update still reads from global
 // memory: x, the bounds and the column state s, mu.
-template <int M> __device__ __forceinline__ void prefetch_mutable(const ElemF32 &a, int j, int k0)
+template <int M, class EA> __device__ __forceinline__ void prefetch_mutable(const EA &a, int j, int k0)
 {
-    const size_t col = ADMM_IDX((size_t)j * a.ld + k0, 2, a.len_col(), a.dbg, DBG_COL);
+    const auto col = a.col(j, k0);
     prefetch_l2(a.s + col);
     prefetch_l2(a.mu + col);
     prefetch_l2(a.s_lo + col);
@@ -133,8 +156,8 @@ template <int M> __device__ __forceinline__ void prefetch_mutable(const ElemF32 
 #pragma unroll
     for (int i = 0; i < M; ++i)
         if (i < a.m) {
-            prefetch_l2(a.x + ADMM_IDX(((size_t)i * a.q + j) * a.ld + k0, 2, a.len_x(), a.dbg, DBG_X));
-            const size_t eb = ADMM_IDX((size_t)i * a.ld + k0, 2, a.len_bound(), a.dbg, DBG_BOUND);
+            prefetch_l2(a.x + a.xe(i, j, k0));
+            const auto eb = a.be(i, k0);
             prefetch_l2(a.lo + eb);
             prefetch_l2(a.hi + eb);
         }
@@ -206,16 +229,16 @@ __device__ __forceinline__ void st2(float *p, float2 v) { *(float2 *)p = v; }
 // D_k extrema in dmx/dmn.  rec (if k0 == 0) receives x at k = 0.  The
 // first column is always < n; the second may be padding (k0 + 1 = n), and
 // then takes no part in the sums and residuals.
-template <int M, int VW, bool C64, bool STAGED = false>
-__device__ __forceinline__ void vec32(const ElemF32 &a, const float *uoff, const double *x1s, const double *nus,
+template <int M, int VW, bool C64, bool STAGED = false, class EA>
+__device__ __forceinline__ void vec32(const EA &a, const float *uoff, const double *x1s, const double *nus,
                                       int j, int k0, bool check, bool cold, float mu_div, float rho1, float rho3,
                                       float rho4, float iq, float2 *ghi, float2 *glo, float *dmx, float *dmn,
                                       float &cm_r, float &cm_s, unsigned &esc, double *rec,
                                       const float2 *stg = nullptr)
 {
     static_assert(VW == 2, "the element update works on column pairs");
-    const int m = a.m, q = a.q, ld = a.ld, n = a.n;
-    const size_t col = ADMM_IDX((size_t)j * ld + k0, 2, a.len_col(), a.dbg, DBG_COL);
+    const int m = a.m, q = a.q, n = a.n;
+    const auto col = a.col(j, k0);
     const float2 yv = STAGED ? stg[0] : ldg2(a.y + col);
     const float2 st = ld2(a.s + col), stl = ld2(a.s_lo + col);
     float2 mu = ld2(a.mu + col), mul = ld2(a.mu_lo + col);
@@ -228,7 +251,7 @@ __device__ __forceinline__ void vec32(const ElemF32 &a, const float *uoff, const
 #pragma unroll
     for (int i = 0; i < M; ++i)
         if (i < m) {
-            xt[i] = ld2(a.x + ADMM_IDX(((size_t)i * q + j) * ld + k0, 2, a.len_x(), a.dbg, DBG_X));
+            xt[i] = ld2(a.x + a.xe(i, j, k0));
             xs[i] = xt[i];
             xsum = add2(xsum, xt[i]);
         }
@@ -240,9 +263,8 @@ __device__ __forceinline__ void vec32(const ElemF32 &a, const float *uoff, const
 #pragma unroll
     for (int i = 0; i < M; ++i) {
         if (i < m) {
-            const size_t e = ADMM_IDX(((size_t)i * a.cq + (size_t)j * a.cj) * ld + k0, 2, a.len_coef(), a.dbg,
-                                      DBG_COEF); // coefficient element
-            const size_t eb = ADMM_IDX((size_t)i * ld + k0, 2, a.len_bound(), a.dbg, DBG_BOUND);
+            const auto e = a.ce(i, j, k0); // coefficient element
+            const auto eb = a.be(i, k0);
             const float2 a2 = STAGED ? stg[(1 + 4 * i) * 32] : ldg2(a.f2 + e);
             const float2 a1 = STAGED ? stg[(2 + 4 * i) * 32] : ldg2(a.f1 + e);
             const float2 b2 = STAGED ? stg[(3 + 4 * i) * 32] : ldg2(a.g2 + e);
@@ -314,7 +336,7 @@ __device__ __forceinline__ void vec32(const ElemF32 &a, const float *uoff, const
     }
 #pragma unroll
     for (int i = 0; i < M; ++i)
-        if (i < m) st2(a.x + ADMM_IDX(((size_t)i * q + j) * ld + k0, 2, a.len_x(), a.dbg, DBG_X), xs[i]);
+        if (i < m) st2(a.x + a.xe(i, j, k0), xs[i]);
     st2(a.s + col, sv.hi);
     st2(a.mu + col, mnew.hi);
     st2(a.s_lo + col, sv.lo);

@@ -554,6 +554,8 @@ admm_status admm_server_create(const admm_params *prm, const admm_server_config 
     if (cfg->max_active < 1 || cfg->tick_iters < 1 || cfg->store_elements < 1024 || cfg->max_m < 1 ||
         cfg->max_m > ADMM_MAX_M || cfg->max_q < 1 || (int64_t)cfg->max_m * cfg->max_q > ADMM_BATCH_MAX_PAIRS)
         return sfail(ADMM_EINVAL, "bad server configuration");
+    if (cfg->store_elements > kBatchArrayMax)
+        return sfail(ADMM_EUNSUPPORTED, "store_elements exceeds 2^32 - 1 (the kernel's 32-bit array offsets)");
     if (cfg->batch.warps_per_cta != 4 && cfg->batch.warps_per_cta != 8 && cfg->batch.warps_per_cta != 16)
         return sfail(ADMM_EINVAL, "warps_per_cta must be 4, 8 or 16");
     if (cfg->batch.cluster_size != 1 && cfg->batch.cluster_size != 2 && cfg->batch.cluster_size != 4 &&

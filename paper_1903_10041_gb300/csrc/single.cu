@@ -88,19 +88,19 @@ __device__ __forceinline__ Sm carve(double *base, int m, int q)
     return s;
 }
 
-// Block-wide max of up to 8 values; every thread gets the results in v[].
+// Block-wide max of up to 8 non-negative values; every thread gets the results in v[].
 template <int NV, int NWP> __device__ __forceinline__ void block_max(double *v, const Sm &sm)
 {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
     for (int t = 0; t < NV; ++t) {
-        double r = warp_max(v[t]);
+        double r = warp_max_nonneg(v[t]);
         if (lane == 0) sm.mx[w * 8 + t] = r;
     }
     __syncthreads();
     if (threadIdx.x < NV) {
         double r = 0.0;
-        for (int ww = 0; ww < NWP; ++ww) r = fmax(r, sm.mx[ww * 8 + threadIdx.x]);
+        for (int ww = 0; ww < NWP; ++ww) r = max_nonneg(r, sm.mx[ww * 8 + threadIdx.x]);
         sm.bc[threadIdx.x] = r;
     }
     __syncthreads();
@@ -432,6 +432,7 @@ __global__ void __launch_bounds__(NT, MINB) single_kernel(SingleArgs a)
     int it;
     double res[7] = {0, 0, 0, 0, 0, 0, 0}; // r1 r2 r3 r4 s1 s2 s3 (unscaled s)
     double r_last = INFINITY, s_last = INFINITY;
+    double kappa = sm.rho[1] / (sm.rho[0] + (double)n * sm.rho[1]); // step (b); renewed when rho changes
 
     for (it = 1; it <= a.max_iter; ++it) {
         const bool check = (it % a.check_every == 0) || (it == a.max_iter);
@@ -518,7 +519,6 @@ __global__ void __launch_bounds__(NT, MINB) single_kernel(SingleArgs a)
 
         // ---- phase 2: per-(i, j) scalar steps, redundantly in every CTA ---
         const double rho1 = sm.rho[0], rho2 = sm.rho[1], rho3 = sm.rho[2];
-        const double kappa = rho2 / (rho1 + (double)n * rho2);
         double r2m = 0.0, r3m = 0.0, s1m = 0.0, s2m = 0.0;
         for (int pr = threadIdx.x; pr < mq; pr += NT) {
             const int i = pr / q, j = pr - i * q;
@@ -544,11 +544,11 @@ __global__ void __launch_bounds__(NT, MINB) single_kernel(SingleArgs a)
             const double hn = cz < a.c[i] ? cz : a.c[i];              // (d)
             const double pn = pp + (hn - Z);                          // (i)
             if (check) {
-                r2m = fmax(r2m, fabs(lamn - lam));
-                r3m = fmax(r3m, fabs(hn - Z));
+                r2m = max_nonneg(r2m, fabs(lamn - lam));
+                r3m = max_nonneg(r3m, fabs(hn - Z));
                 const double dl = (lamn - lam) - zeta;
-                s1m = fmax(s1m, fmax(fabs(dmx + dl), fabs(dmn + dl)));
-                s2m = fmax(s2m, fabs(hn - hh));
+                s1m = max_nonneg(s1m, max_nonneg(fabs(dmx + dl), fabs(dmn + dl)));
+                s2m = max_nonneg(s2m, fabs(hn - hh));
             }
             sm.lam[pr] = lamn;
             sm.zeta[pr] = lamn - lam;
@@ -570,7 +570,7 @@ __global__ void __launch_bounds__(NT, MINB) single_kernel(SingleArgs a)
             const int i = pr / q;
             const double x0 = sm.x0[pr], x1n = sm.x1n[i];
             sm.nu[pr] = sm.nu[pr] + (x1n - x0);
-            if (check) r4m = fmax(r4m, fabs(x0 - x1n));
+            if (check) r4m = max_nonneg(r4m, fabs(x0 - x1n));
         }
         __syncthreads();
         if (threadIdx.x < m) sm.x1[threadIdx.x] = sm.x1n[threadIdx.x];
@@ -580,8 +580,8 @@ __global__ void __launch_bounds__(NT, MINB) single_kernel(SingleArgs a)
         if (check) {
             double r1 = 0.0, s3 = 0.0;
             for (int b = threadIdx.x; b < a.grid; b += NT) {
-                r1 = fmax(r1, ldcg(a.cpart + ((size_t)par * a.grid + b) * 4 + 0));
-                s3 = fmax(s3, ldcg(a.cpart + ((size_t)par * a.grid + b) * 4 + 1));
+                r1 = max_nonneg(r1, ldcg(a.cpart + ((size_t)par * a.grid + b) * 4 + 0));
+                s3 = max_nonneg(s3, ldcg(a.cpart + ((size_t)par * a.grid + b) * 4 + 1));
             }
             double v[7] = {r1, r2m, r3m, r4m, s1m, s2m, s3};
             block_max<7, NWP>(v, sm);
@@ -610,6 +610,7 @@ __global__ void __launch_bounds__(NT, MINB) single_kernel(SingleArgs a)
                     if (threadIdx.x < 4) sm.rho[threadIdx.x] *= f;
                     if (threadIdx.x == 0) sm.flags[1] = f;
                     __syncthreads();
+                    kappa = sm.rho[1] / (sm.rho[0] + (double)n * sm.rho[1]);
                 }
             }
         }
