@@ -231,8 +231,9 @@ BatchSmem batch_cta_smem(int max_m, int max_q, int warps, int cluster, bool warp
 {
     const size_t team = sizeof(double) * batch_cluster_team_doubles(max_m, max_q, warps, cluster);
     const size_t off = (team + 15) / 16 * 16;
-    // two stages of 4 m + 1 slots of 32 float2 per warp (m <= 4 kernel; see stage_vec32)
-    const size_t stages = batch_mbound(max_m) == 4 ? (size_t)warps * 2 * (4 * 4 + 1) * 32 * 2 * sizeof(float) : 0;
+    // two stages of 4 m + 1 slots of 32 float2 per warp (m <= 4 kernel; see stage_vec32), then
+    // 11 floats per thread for the check-only lane maxima
+    const size_t stages = batch_mbound(max_m) == 4 ? (size_t)warps * 2 * (4 * 4 + 1) * 32 * 2 * sizeof(float) + (size_t)warps * 32 * 11 * sizeof(float) : 0;
     size_t bytes = off + stages;
     if (warp_teams) bytes = std::max(bytes, batch_smem_bytes(warps, slice_doubles));
     return {bytes, (int)off};

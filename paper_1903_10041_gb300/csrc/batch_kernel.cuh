@@ -185,7 +185,15 @@ template <int KIND, int NW, int M> __device__ void solve_team(const BatchArgs &a
         const float mu_div = fpar[3];
         const float rho1 = fpar[0], rho3 = fpar[1], rho4 = fpar[2];
         const float iq = 1.0f / (float)q;
-        float fcr = 0.0f, fcs = 0.0f;
+        // lane maxima and minima that only check iterations use: with the staged
+        // (m <= 4) update they live in the thread's own shared-memory slots (11
+        // floats apart, no bank conflicts) instead of registers across the loop
+        float fcr_r = 0.0f, fcs_r = 0.0f;
+        float *px = (float *)(stage + NWT * 2 * stage_slots<M>() * 32) + tid * 11;
+        float &fcr = *(STG ? px + 2 * M : &fcr_r);
+        float &fcs = *(STG ? px + 2 * M + 1 : &fcs_r);
+        fcr = 0.0f;
+        fcs = 0.0f;
         double *recs = rec0 + (size_t)par * items * m * 4;
         const int64_t pend = min(npairs, (int64_t)(gw + 1) * chunk);
         for (int64_t pa = (int64_t)gw * chunk; pa < pend;) {
@@ -194,13 +202,16 @@ template <int KIND, int NW, int M> __device__ void solve_team(const BatchArgs &a
             const int v1 = (int)(min(pend, (int64_t)(j + 1) * nv) - (int64_t)j * nv);
             pa = (int64_t)j * nv + v1;
             float2 ghi[M], glo[M]; // per-lane capacity sums of the column pairs
-            float fmx[M], fmn[M];
+            float fmx_r[M], fmn_r[M];
+            float *fmx = STG ? px : fmx_r, *fmn = STG ? px + M : fmn_r;
 #pragma unroll
             for (int i = 0; i < M; ++i) {
                 ghi[i] = make_float2(0.0f, 0.0f);
                 glo[i] = make_float2(0.0f, 0.0f);
-                fmx[i] = -INFINITY;
-                fmn[i] = INFINITY;
+                if (!STG || check) {
+                    fmx[i] = -INFINITY;
+                    fmn[i] = INFINITY;
+                }
             }
             double *rec = recs + (size_t)(j + gw) * m * 4;
             if constexpr (STG) {
@@ -233,7 +244,7 @@ template <int KIND, int NW, int M> __device__ void solve_team(const BatchArgs &a
             for (int i = 0; i < M; ++i)
                 if (i < m) {
                     FF v = lanes_sum(ghi[i], glo[i]);
-                    float hi = fmx[i], lo = fmn[i];
+                    float hi = check ? fmx[i] : 0.0f, lo = check ? fmn[i] : 0.0f;
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) {
                         const FF u = {__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};

@@ -310,7 +310,10 @@ __device__ __forceinline__ void vec32(const EA &a, const float *uoff, const doub
     }
     // (e), (f) in float-float: the column state carries about 48 bits, so
     // mu's accumulation of ever smaller primal residuals is not lost to FP32
-    // rounding and the dual residual term of s settles below 1e-6.
+    // rounding and the dual residual term of s settles below 1e-6.  With
+    // d = sum_i x - y - mu, step (e) gives s = max(0, d) and step (f)
+    // mu + s - sum_i x + y = s - d = max(0, -d): one float-float chain for d
+    // gives both, and the residual mu_new - mu is formed on check iterations only.
     FF2 sx = {splat2(0.0f), splat2(0.0f)};
 #pragma unroll
     for (int i = 0; i < M; ++i)
@@ -319,9 +322,10 @@ __device__ __forceinline__ void vec32(const EA &a, const float *uoff, const doub
     const FF2 v = ff2_add(ff2_addf(sx, neg2(yv)), ff2_neg(muf));        // sum_i x - y - mu
     const FF2 sv = {make_float2(v.hi.x > 0.0f ? v.hi.x : 0.0f, v.hi.y > 0.0f ? v.hi.y : 0.0f),
                     make_float2(v.hi.x > 0.0f ? v.lo.x : 0.0f, v.hi.y > 0.0f ? v.lo.y : 0.0f)}; // (e)
-    const FF2 t = ff2_addf(ff2_add(sv, ff2_neg(sx)), yv);                // s - sum_i x + y
-    const FF2 mnew = ff2_add(muf, t);                                     // (f)
+    const FF2 mnew = {make_float2(v.hi.x < 0.0f ? -v.hi.x : 0.0f, v.hi.y < 0.0f ? -v.hi.y : 0.0f),
+                      make_float2(v.hi.x < 0.0f ? -v.lo.x : 0.0f, v.hi.y < 0.0f ? -v.lo.y : 0.0f)}; // (f)
     if (check) {
+        const FF2 t = ff2_add(mnew, ff2_neg(muf)); // s - sum_i x + y
         FF2 dx = {splat2(0.0f), splat2(0.0f)};
 #pragma unroll
         for (int i = 0; i < M; ++i)

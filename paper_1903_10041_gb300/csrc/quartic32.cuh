@@ -245,7 +245,7 @@ __device__ __forceinline__ float2 newton_polish32x2(float2 A, float2 B, float2 C
     const float2 A4 = mul2(splat2(4.0f), A), B3 = mul2(splat2(3.0f), B), C2 = add2(C, C);
     const float2 fp = fma2(fma2(fma2(A4, x, B3), x, C2), x, D);
     const float2 fpp = fma2(fma2(mul2(splat2(12.0f), A), x, mul2(splat2(6.0f), B)), x, C2);
-    const float2 r = make_float2(fpp.x > 0.0f ? rcp_fast(fpp.x) : 0.0f, fpp.y > 0.0f ? rcp_fast(fpp.y) : 0.0f);
+    const float2 r = make_float2(rcp_fast(fpp.x), rcp_fast(fpp.y)); // used only where fpp > 0
     const float2 dx = mul2(fp, r);
     const float2 xn = sub2(x, dx);
     const float2 lim = mul2(splat2(0.0625f), add2(abs2(x), splat2(1.0f)));
@@ -295,10 +295,14 @@ __device__ __forceinline__ float2 quartic_min32x2(float2 A, float2 B, float2 C, 
                                       fma2(mul2(splat2(96.0f), abs2(R)), mR, mul2(splat2(64.0f), R2))));
         const float2 bound = mul2(splat2(6.0e-8f), bsum);
         if (Dl.x > bound.x && Dl.y > bound.y) { // Cardano on both lanes
-            const float2 sq = make_float2(sqrt_fast(Dl.x), sqrt_fast(Dl.y));
+            // here Delta > bound >= 0, so sqrt(Delta) > 0, |R +- sqrt(Delta)| > 0 and S != 0: the
+            // zero guards of sqrt_fast, cbrt_fast and the T reciprocal are not needed (an S that
+            // underflows gives a non-finite x and the lane-by-lane path below)
+            const float2 sq = mul2(Dl, make_float2(rsqrtf(Dl.x), rsqrtf(Dl.y)));
             const float2 v = add2(R, make_float2(R.x >= 0.0f ? sq.x : -sq.x, R.y >= 0.0f ? sq.y : -sq.y));
-            const float2 S = make_float2(cbrt_fast(v.x), cbrt_fast(v.y));
-            const float2 rS = make_float2(S.x != 0.0f ? rcp_fast(S.x) : 0.0f, S.y != 0.0f ? rcp_fast(S.y) : 0.0f);
+            const float2 S = make_float2(copysignf(exp2f(__log2f(fabsf(v.x)) * (1.0f / 3.0f)), v.x),
+                                         copysignf(exp2f(__log2f(fabsf(v.y)) * (1.0f / 3.0f)), v.y));
+            const float2 rS = make_float2(rcp_fast(S.x), rcp_fast(S.y));
             const float2 T = mul2(neg2(Q), rS);
             const float2 x = newton_polish32x2(A, B, C, D, sub2(add2(S, T), b3));
             if (isfinite(x.x) && isfinite(x.y))
