@@ -68,20 +68,28 @@ __device__ __forceinline__ void horner_comp_step(float &s, float &c, float x, fl
 __device__ __forceinline__ float newton_polish32(float A, float B, float C, float D, float x)
 {
 #ifndef ADMM_COMPENSATED_POLISH
-    const float fp = ((4.0f * A * x + 3.0f * B) * x + 2.0f * C) * x + D;
+    // the operations and roundings of newton_polish32x2, lane for lane
+    const float C2 = __fadd_rn(C, C);
+    const float fp = __fmaf_rn(__fmaf_rn(__fmaf_rn(__fmul_rn(4.0f, A), x, __fmul_rn(3.0f, B)), x, C2), x, D);
+    const float fpp = __fmaf_rn(__fmaf_rn(__fmul_rn(12.0f, A), x, __fmul_rn(6.0f, B)), x, C2);
+    if (fpp > 0.0f) {
+        const float dx = __fmul_rn(fp, rcp_fast(fpp));
+        if (fabsf(dx) <= __fmul_rn(0.0625f, __fadd_rn(fabsf(x), 1.0f))) x = __fsub_rn(x, dx);
+    }
+    return x;
 #else
     float s = 4.0f * A, c = 0.0f;
     horner_comp_step(s, c, x, 3.0f * B);
     horner_comp_step(s, c, x, 2.0f * C);
     horner_comp_step(s, c, x, D);
     const float fp = s + c;
-#endif
     const float fpp = (12.0f * A * x + 6.0f * B) * x + 2.0f * C;
     if (fpp > 0.0f) {
         const float dx = fp * rcp_fast(fpp);
         if (fabsf(dx) <= 0.0625f * (fabsf(x) + 1.0f)) x -= dx;
     }
     return x;
+#endif
 }
 
 // Sign of F(u) - F(v) via the factored form (F' = x^3 + b x^2 + c x + d).
@@ -116,22 +124,29 @@ static __device__ __noinline__ int cubic_branch64(float A, float B, float C, flo
 __device__ __forceinline__ float quartic_min32(float A, float B, float C, float D, float lo, float hi,
                                                int paper_mode, unsigned &esc)
 {
-    if (A == 0.0f) return clampf(-D * rcp_fast(2.0f * C), lo, hi);
+    // Every operation below is rounded as the packed path (quartic_min32x2)
+    // rounds it, so a lane gets the same bits on either path.
+    if (A == 0.0f) return clampf(__fmul_rn(-D, rcp_fast(__fadd_rn(C, C))), lo, hi);
     const float inv = rcp_fast(A);
-    const float b = 0.75f * B * inv, c = 0.5f * C * inv, d = 0.25f * D * inv;
-    const float b3 = b * (1.0f / 3.0f);
-    const float Q = c * (1.0f / 3.0f) - b3 * b3;
-    const float R = b3 * (0.5f * c) - b3 * b3 * b3 - 0.5f * d;
-    const float Q3 = Q * Q * Q, R2 = R * R;
-    const float Dl = Q3 + R2;
-    // magnitudes entering Q, R (including the rounding of b, c, d)
-    const float mQ = fabsf(c) * (1.0f / 3.0f) + b3 * b3;
-    const float mR = fabsf(b3 * 0.5f * c) + fabsf(b3 * b3 * b3) + 0.5f * fabsf(d);
+    const float b = __fmul_rn(__fmul_rn(0.75f, B), inv);
+    const float c = __fmul_rn(__fmul_rn(0.5f, C), inv);
+    const float d = __fmul_rn(__fmul_rn(0.25f, D), inv);
+    const float b3 = __fmul_rn(b, 1.0f / 3.0f);
+    const float b3s = __fmul_rn(b3, b3), b3c = __fmul_rn(b3s, b3);
+    const float Q = __fmaf_rn(c, 1.0f / 3.0f, -b3s);
+    const float bhc = __fmul_rn(b3, __fmul_rn(0.5f, c));
+    const float R = __fsub_rn(__fsub_rn(bhc, b3c), __fmul_rn(0.5f, d));
+    const float Qs = __fmul_rn(Q, Q);
+    const float Dl = __fadd_rn(__fmul_rn(Qs, Q), __fmul_rn(R, R));
+    // magnitudes entering Q, R (including the rounding of b, c, d); |Q| <= mQ and |R| <= mR
+    const float mQ = __fmaf_rn(fabsf(c), 1.0f / 3.0f, b3s);
+    const float mR = __fmaf_rn(0.5f, fabsf(d), __fadd_rn(fabsf(bhc), fabsf(b3c)));
     // |fl(Delta) - Delta| <= u (78 Q^2 mQ + 12 |Q|^3 + 88 |R| mR + 4 R^2) with u = 2^-24
     // (a factor 2 over the first-order propagation of the roundings above,
-    // with a reciprocal of A off by up to 2 ulp); the constants below
-    // dominate each term.
-    const float bound = 6.0e-8f * (96.0f * Q * Q * mQ + 64.0f * fabsf(Q3) + 96.0f * fabsf(R) * mR + 64.0f * R2);
+    // with a reciprocal of A off by up to 2 ulp).  As |Q|^3 <= Q^2 mQ and
+    // R^2 <= |R| mR, that is at most 92 u (Q^2 mQ + |R| mR); the bound takes
+    // 128 u (Q^2 mQ + |R| mR), a safety factor of 1.39.
+    const float bound = __fmul_rn(7.68e-6f, __fmaf_rn(Qs, mQ, __fmul_rn(fabsf(R), mR)));
     int branch; // 0 Cardano, 1 triple, 2 trig
     if (Dl > bound) branch = 0;
     else if (Dl < -bound) branch = 2;
@@ -141,10 +156,11 @@ __device__ __forceinline__ float quartic_min32(float A, float B, float C, float 
     }
     if (branch == 1) return clampf(-b3, lo, hi);
     if (branch == 0) {
-        const float sq = sqrt_fast(Dl);
-        const float S = cbrt_fast(R >= 0.0f ? R + sq : R - sq);
-        const float T = S != 0.0f ? -Q * rcp_fast(S) : 0.0f;
-        const float x = newton_polish32(A, B, C, D, S + T - b3);
+        // Delta > 0 here (certified, or FP64 said so): as in the packed path
+        const float sq = Dl > 0.0f ? __fmul_rn(Dl, rsqrtf(Dl)) : 0.0f;
+        const float S = cbrt_fast(__fadd_rn(R, R >= 0.0f ? sq : -sq));
+        const float T = S != 0.0f ? __fmul_rn(-Q, rcp_fast(S)) : 0.0f;
+        const float x = newton_polish32(A, B, C, D, __fsub_rn(__fadd_rn(S, T), b3));
         if (!isfinite(x)) return quartic_min_fallback64(A, B, C, D, lo, hi, paper_mode);
         return clampf(x, lo, hi);
     }
@@ -232,11 +248,11 @@ __device__ __forceinline__ double quartic_min64_seeded(double A, double B, doubl
 // gives it.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 splat2(float v) { return make_float2(v, v); }
-__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 neg2(float2 a) { return __fmul2_rn(a, make_float2(-1.0f, -1.0f)); }
 __device__ __forceinline__ float2 abs2(float2 a) { return make_float2(fabsf(a.x), fabsf(a.y)); }
 
 // Newton step of newton_polish32 on both lanes.
@@ -268,11 +284,6 @@ __device__ __forceinline__ float2 quartic_min32x2(float2 A, float2 B, float2 C, 
                                                   int paper_mode, unsigned &esc)
 {
 #ifndef ADMM_COMPENSATED_POLISH
-    if (A.x == 0.0f && A.y == 0.0f) { // quadratic on both lanes
-        const float2 C2 = add2(C, C);
-        const float2 x = mul2(neg2(D), make_float2(rcp_fast(C2.x), rcp_fast(C2.y)));
-        return make_float2(clampf(x.x, lo.x, hi.x), clampf(x.y, lo.y, hi.y));
-    }
     if (A.x > 0.0f && A.y > 0.0f) {
         const float2 inv = make_float2(rcp_fast(A.x), rcp_fast(A.y));
         const float2 b = mul2(mul2(splat2(0.75f), B), inv);
@@ -290,10 +301,7 @@ __device__ __forceinline__ float2 quartic_min32x2(float2 A, float2 B, float2 C, 
         // the forward error bound of quartic_min32, on both lanes
         const float2 mQ = fma2(abs2(c), splat2(1.0f / 3.0f), b3s);
         const float2 mR = fma2(splat2(0.5f), abs2(d), add2(abs2(bhc), abs2(b3c)));
-        const float2 bsum = fma2(mul2(splat2(96.0f), Qs), mQ,
-                                 fma2(splat2(64.0f), abs2(Q3),
-                                      fma2(mul2(splat2(96.0f), abs2(R)), mR, mul2(splat2(64.0f), R2))));
-        const float2 bound = mul2(splat2(6.0e-8f), bsum);
+        const float2 bound = mul2(splat2(7.68e-6f), fma2(Qs, mQ, mul2(abs2(R), mR)));
         if (Dl.x > bound.x && Dl.y > bound.y) { // Cardano on both lanes
             // here Delta > bound >= 0, so sqrt(Delta) > 0, |R +- sqrt(Delta)| > 0 and S != 0: the
             // zero guards of sqrt_fast, cbrt_fast and the T reciprocal are not needed (an S that
@@ -308,6 +316,11 @@ __device__ __forceinline__ float2 quartic_min32x2(float2 A, float2 B, float2 C, 
             if (isfinite(x.x) && isfinite(x.y))
                 return make_float2(clampf(x.x, lo.x, hi.x), clampf(x.y, lo.y, hi.y));
         }
+    }
+    if (A.x == 0.0f && A.y == 0.0f) { // quadratic on both lanes
+        const float2 C2 = add2(C, C);
+        const float2 x = mul2(neg2(D), make_float2(rcp_fast(C2.x), rcp_fast(C2.y)));
+        return make_float2(clampf(x.x, lo.x, hi.x), clampf(x.y, lo.y, hi.y));
     }
 #endif
     return quartic_min32_lanes(A, B, C, D, lo, hi, paper_mode, &esc);
