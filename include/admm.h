@@ -106,7 +106,12 @@ typedef struct admm_params {
     int32_t adapt_rho;               /* 1: rho_i <- tau rho_i or rho_i / tau by r/sigma (Sec. IV-A) */
     int32_t rho2_over_n;             /* 1: each instance uses rho_2 = rho[1] / n (the capacity
                                         penalty acts on a sum of n terms) */
-    int32_t reserved[3];             /* must be 0 */
+    int32_t adapt_start;             /* >= 0; with adapt_rho, the adaptation applies at the check
+                                        iterations t >= adapt_start of a solve (0: from the first,
+                                        as Sec. IV-A).  A warm-started re-solve starts close to its
+                                        solution, and adapting only the ones still running after,
+                                        say, 500 iterations keeps the warm start intact for the rest */
+    int32_t reserved[2];             /* must be 0 */
 } admm_params;
 
 /* The solver state (the checkpoint).  z is not stored: after every

@@ -34,7 +34,7 @@ class _Params(C.Structure):
                 ("r_tol", C.c_double), ("s_tol", C.c_double), ("max_iter", C.c_int),
                 ("check_every", C.c_int), ("xmin_mode", C.c_int), ("sweep", C.c_int),
                 ("threads", C.c_int), ("count_differs", C.c_int),
-                ("adapt_rho", C.c_int), ("tau", C.c_double)]
+                ("adapt_rho", C.c_int), ("tau", C.c_double), ("adapt_start", C.c_int)]
 
 
 class _State(C.Structure):
@@ -130,7 +130,8 @@ def _params(par, threads: int = 1, count_differs: bool = False, n: int | None = 
         rho = (rho[0], rho[1] / n, rho[2], rho[3])
     return _Params(rho[0], rho[1], rho[2], rho[3], float(par.r_tol), float(par.s_tol), int(par.max_iter),
                    int(par.check_every), _MODES[par.xmin_mode], _SWEEPS[par.sweep], int(threads),
-                   int(count_differs), int(getattr(par, "adapt_rho", False)), float(getattr(par, "tau", 1.1)))
+                   int(count_differs), int(getattr(par, "adapt_rho", False)), float(getattr(par, "tau", 1.1)),
+                   int(getattr(par, "adapt_start", 0)))
 
 
 STATE_KEYS = ("x", "z", "lam", "s", "mu", "h", "p", "nu", "x1")

@@ -69,6 +69,7 @@ typedef struct {
     int count_differs; /* also evaluate the other x-update mode and count disagreements */
     int adapt_rho;     /* Sec. IV-A: rescale rho_1..rho_4 by tau from the r / sigma ratio */
     double tau;
+    int adapt_start;   /* the rescaling applies at check iterations t >= adapt_start (0: all) */
 } orc_params;
 
 typedef struct {
@@ -425,7 +426,7 @@ int orc_solve(const orc_problem *P, const orc_params *pr_in, orc_state *S, orc_r
                 rep->converged = 1;
                 break;
             }
-            if (pr->adapt_rho && t < pr->max_iter) {
+            if (pr->adapt_rho && t < pr->max_iter && t >= pr->adapt_start) {
                 /* Sec. IV-A: rho_i <- tau rho_i if r/sigma > 1.2 rbar/sbar,
                  * rho_i <- rho_i / tau if r/sigma < 0.8 rbar/sbar.  The scaled
                  * duals lambda, p, mu, nu carry a factor 1/rho and are rescaled

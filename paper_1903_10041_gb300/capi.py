@@ -46,7 +46,7 @@ class admm_params(C.Structure):
     _fields_ = [("rho", C.c_double * 4), ("r_tol", C.c_double), ("s_tol", C.c_double), ("tau", C.c_double),
                 ("max_iter", C.c_int32), ("check_every", C.c_int32), ("precision", C.c_int32),
                 ("xmin_mode", C.c_int32), ("sweep", C.c_int32), ("adapt_rho", C.c_int32),
-                ("rho2_over_n", C.c_int32), ("reserved", C.c_int32 * 3)]
+                ("rho2_over_n", C.c_int32), ("adapt_start", C.c_int32), ("reserved", C.c_int32 * 2)]
 
 
 class admm_state(C.Structure):
@@ -136,12 +136,12 @@ def admm_default_params() -> admm_params:
 
 def make_params(par=None, **kw) -> admm_params:
     """admm_params from a duck-typed settings object (rho, r_tol, s_tol,
-    max_iter, check_every, precision, xmin_mode, sweep, adapt_rho, tau)."""
+    max_iter, check_every, precision, xmin_mode, sweep, adapt_rho, tau, adapt_start)."""
     p = admm_default_params()
     src = {}
     if par is not None:
         for k in ("rho", "r_tol", "s_tol", "max_iter", "check_every", "precision", "xmin_mode", "sweep",
-                  "adapt_rho", "tau", "rho2_over_n"):
+                  "adapt_rho", "tau", "rho2_over_n", "adapt_start"):
             if hasattr(par, k):
                 src[k] = getattr(par, k)
     src.update(kw)
@@ -151,7 +151,7 @@ def make_params(par=None, **kw) -> admm_params:
     for k in ("r_tol", "s_tol", "tau"):
         if k in src:
             setattr(p, k, float(src[k]))
-    for k in ("max_iter", "check_every"):
+    for k in ("max_iter", "check_every", "adapt_start"):
         if k in src:
             setattr(p, k, int(src[k]))
     if "precision" in src:

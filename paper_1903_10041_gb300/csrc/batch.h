@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "internal.h"
 
 namespace admm_impl {
@@ -49,6 +51,7 @@ struct BatchArgs {
     int *lock;                // per instance: 1 while a team runs it (round-robin launches)
     double r_tol, s_tol, tau;
     double adapt_target;      // r_tol / s_tol of the settings (Sec. IV-A ratio rule)
+    int adapt_start;          // the adaptation applies at check iterations t >= adapt_start
     int max_iter, check_every, xmin_mode, sweep, adapt;
 };
 
@@ -76,6 +79,9 @@ __host__ __device__ inline float team_iter_cost(int n, int m, int q, int team_th
 // every m <= 4, else 8.  It must not depend on which instances share a
 // launch, so that an instance gives the same bits alone and in any mix.
 inline int batch_mbound(int max_m) { return max_m <= 4 ? 4 : 8; }
+
+// Settings a batch or server accepts; false with the reason in why.
+bool batch_params_ok(const admm_params *p, std::string &why);
 
 size_t batch_slice_doubles(int max_m, int max_q);
 // The persistent kernel for CTAs of 4, 8 or 16 warps and source bound mbound.

@@ -30,33 +30,6 @@ admm_status bfail(admm_status s, const std::string &msg)
                          std::string(#call) + ": " + cudaGetErrorString(e_));                             \
     } while (0)
 
-bool batch_params_ok(const admm_params *p, std::string &why)
-{
-    if (!p) {
-        why = "params is NULL";
-        return false;
-    }
-    for (int t = 0; t < 4; ++t)
-        if (!(p->rho[t] > 0.0) || !std::isfinite(p->rho[t])) {
-            why = "rho must be finite and > 0";
-            return false;
-        }
-    if (p->max_iter < 1 || p->check_every < 1) {
-        why = "max_iter and check_every must be >= 1";
-        return false;
-    }
-    if (p->precision != ADMM_MIXED) {
-        why = "the batched solver runs ADMM_MIXED only";
-        return false;
-    }
-    if ((p->xmin_mode != ADMM_XMIN_EXACT && p->xmin_mode != ADMM_XMIN_PAPER) ||
-        (p->sweep != ADMM_GAUSS_SEIDEL && p->sweep != ADMM_JACOBI) || (p->adapt_rho && !(p->tau > 1.0))) {
-        why = "bad xmin_mode, sweep or tau";
-        return false;
-    }
-    return true;
-}
-
 // Host copy of a problem whose arrays may live on the device.
 struct HostProblem {
     std::vector<double> a[10];
@@ -84,6 +57,43 @@ cudaError_t to_host(const admm_problem &in, HostProblem &out)
 }
 
 } // namespace
+
+namespace admm_impl {
+
+// Settings a batch or server accepts (the rules of admm_create, ADMM_MIXED only).
+bool batch_params_ok(const admm_params *p, std::string &why)
+{
+    if (!p) {
+        why = "params is NULL";
+        return false;
+    }
+    for (int t = 0; t < 4; ++t)
+        if (!(p->rho[t] > 0.0) || !std::isfinite(p->rho[t])) {
+            why = "rho must be finite and > 0";
+            return false;
+        }
+    if (p->max_iter < 1 || p->check_every < 1) {
+        why = "max_iter and check_every must be >= 1";
+        return false;
+    }
+    if (p->precision != ADMM_MIXED) {
+        why = "the batched solver runs ADMM_MIXED only";
+        return false;
+    }
+    if ((p->xmin_mode != ADMM_XMIN_EXACT && p->xmin_mode != ADMM_XMIN_PAPER) ||
+        (p->sweep != ADMM_GAUSS_SEIDEL && p->sweep != ADMM_JACOBI) || (p->adapt_rho && !(p->tau > 1.0)) ||
+        p->adapt_start < 0) {
+        why = "bad xmin_mode, sweep, tau or adapt_start";
+        return false;
+    }
+    if (!(p->r_tol >= 0.0) || !(p->s_tol >= 0.0) || p->reserved[0] || p->reserved[1]) {
+        why = "r_tol, s_tol must be >= 0 and reserved fields 0";
+        return false;
+    }
+    return true;
+}
+
+} // namespace admm_impl
 
 struct admm_batch {
     int count = 0, dev = 0, nsm = 0, max_m = 0, max_q = 0;
@@ -194,6 +204,7 @@ BatchArgs make_args(const admm_batch *b)
     a.r_tol = stop_r_tol(b->prm.precision, b->prm.r_tol);
     a.s_tol = stop_s_tol(b->prm.precision, b->prm.s_tol);
     a.adapt_target = b->prm.r_tol / b->prm.s_tol;
+    a.adapt_start = b->prm.adapt_start;
     a.tau = b->prm.tau;
     a.max_iter = b->prm.max_iter;
     a.check_every = b->prm.check_every;

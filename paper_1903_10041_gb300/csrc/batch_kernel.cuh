@@ -366,7 +366,7 @@ template <int KIND, int NW, int M> __device__ void solve_team(const BatchArgs &a
                 s_last = sgm;
                 const bool cv = r < a.r_tol && sgm < a.s_tol;
                 double f = 1.0;
-                if (!cv && a.adapt && it < a.max_iter) { // Sec. IV-A, duals rescaled by rho_old / rho_new
+                if (!cv && a.adapt && it < a.max_iter && it >= a.adapt_start) { // Sec. IV-A, duals rescaled
                     const double ratio = r / sgm, target = a.adapt_target;
                     if (ratio > 1.2 * target) f = a.tau;
                     else if (ratio < 0.8 * target) f = 1.0 / a.tau;

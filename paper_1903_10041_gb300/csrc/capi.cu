@@ -132,7 +132,8 @@ bool params_ok(const admm_params *p)
         return !fail(ADMM_EINVAL, "bad xmin_mode %d", p->xmin_mode);
     if (p->sweep != ADMM_GAUSS_SEIDEL && p->sweep != ADMM_JACOBI) return !fail(ADMM_EINVAL, "bad sweep %d", p->sweep);
     if (p->adapt_rho && !(p->tau > 1.0)) return !fail(ADMM_EINVAL, "tau must be > 1 with adapt_rho");
-    for (int t = 0; t < 3; ++t)
+    if (p->adapt_start < 0) return !fail(ADMM_EINVAL, "adapt_start must be >= 0");
+    for (int t = 0; t < 2; ++t)
         if (p->reserved[t]) return !fail(ADMM_EINVAL, "reserved fields must be 0");
     return true;
 }
@@ -651,6 +652,7 @@ admm_status admm_solve(admm_handle *h, const admm_state *warm, admm_result *out,
     a.r_tol = stop_r_tol(h->prm.precision, h->prm.r_tol);
     a.s_tol = stop_s_tol(h->prm.precision, h->prm.s_tol);
     a.adapt_target = h->prm.r_tol / h->prm.s_tol;
+    a.adapt_start = h->prm.adapt_start;
     a.tau = h->prm.tau;
     a.max_iter = h->prm.max_iter;
     a.check_every = h->prm.check_every;

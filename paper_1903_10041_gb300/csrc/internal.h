@@ -66,6 +66,7 @@ struct SingleArgs {
     unsigned long long *dbg;   // bounds record of checked builds (see ADMM_IDX), else unused
     double r_tol, s_tol, tau;
     double adapt_target;       // r_tol / s_tol of the settings (Sec. IV-A ratio rule)
+    int adapt_start;           // the adaptation applies at check iterations t >= adapt_start
     int max_iter, check_every, xmin_mode, sweep, adapt;
     long long spin_ns;         // bound of one barrier wait
 };

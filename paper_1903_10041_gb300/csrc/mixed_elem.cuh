@@ -246,19 +246,19 @@ __device__ __forceinline__ void vec32(const EA &a, const float *uoff, const doub
         mu = make_float2(mu.x / mu_div, mu.y / mu_div);
         mul = make_float2(mul.x / mu_div, mul.y / mu_div);
     }
-    float2 xt[M], xs[M];
+    float2 xt[M];
     float2 xsum = splat2(0.0f); // sum of x over the sources, kept current by Gauss-Seidel
 #pragma unroll
     for (int i = 0; i < M; ++i)
         if (i < m) {
             xt[i] = ld2(a.x + a.xe(i, j, k0));
-            xs[i] = xt[i];
             xsum = add2(xsum, xt[i]);
         }
     const bool v1 = k0 + 1 < n;
     const bool jac = a.sweep == ADMM_JACOBI;
     const float2 h1 = splat2(0.5f * rho1), h3 = splat2(0.5f * rho3), iq2 = splat2(iq);
     const float2 nr1 = splat2(-rho1), nr3 = splat2(-rho3), r1 = splat2(rho1);
+    FF2 sx = {splat2(0.0f), splat2(0.0f)}, dx = {splat2(0.0f), splat2(0.0f)};
 
 #pragma unroll
     for (int i = 0; i < M; ++i) {
@@ -293,7 +293,10 @@ __device__ __forceinline__ void vec32(const EA &a, const float *uoff, const doub
             else
                 xn = quartic_min32x2(A, B, C, D, L, H, a.xmin_mode, esc);
             if (!jac) xsum = add2(xsum, sub2(xn, x0));
-            xs[i] = xn;
+            sx = ff2_addf(sx, xn); // sum_i x of (e), (f) in source order
+            if (check) dx = ff2_add(dx, ff2_two_sum(xn, neg2(x0)));
+            st2(a.x + a.xe(i, j, k0), xn);
+            if (k0 == 0) rec[i * 4 + 3] = (double)xn.x;
             float2 ghh, gll;
             g_ff2(b2, b1, xn, ghh, gll);
             if (!v1) {
@@ -314,22 +317,15 @@ __device__ __forceinline__ void vec32(const EA &a, const float *uoff, const doub
     // d = sum_i x - y - mu, step (e) gives s = max(0, d) and step (f)
     // mu + s - sum_i x + y = s - d = max(0, -d): one float-float chain for d
     // gives both, and the residual mu_new - mu is formed on check iterations only.
-    FF2 sx = {splat2(0.0f), splat2(0.0f)};
-#pragma unroll
-    for (int i = 0; i < M; ++i)
-        if (i < m) sx = ff2_addf(sx, xs[i]);
     const FF2 muf = {mu, mul}, stf = {st, stl};
     const FF2 v = ff2_add(ff2_addf(sx, neg2(yv)), ff2_neg(muf));        // sum_i x - y - mu
     const FF2 sv = {make_float2(v.hi.x > 0.0f ? v.hi.x : 0.0f, v.hi.y > 0.0f ? v.hi.y : 0.0f),
                     make_float2(v.hi.x > 0.0f ? v.lo.x : 0.0f, v.hi.y > 0.0f ? v.lo.y : 0.0f)}; // (e)
-    const FF2 mnew = {make_float2(v.hi.x < 0.0f ? -v.hi.x : 0.0f, v.hi.y < 0.0f ? -v.hi.y : 0.0f),
-                      make_float2(v.hi.x < 0.0f ? -v.lo.x : 0.0f, v.hi.y < 0.0f ? -v.lo.y : 0.0f)}; // (f)
+    const FF2 nv = ff2_neg(v);
+    const FF2 mnew = {make_float2(v.hi.x < 0.0f ? nv.hi.x : 0.0f, v.hi.y < 0.0f ? nv.hi.y : 0.0f),
+                      make_float2(v.hi.x < 0.0f ? nv.lo.x : 0.0f, v.hi.y < 0.0f ? nv.lo.y : 0.0f)}; // (f)
     if (check) {
         const FF2 t = ff2_add(mnew, ff2_neg(muf)); // s - sum_i x + y
-        FF2 dx = {splat2(0.0f), splat2(0.0f)};
-#pragma unroll
-        for (int i = 0; i < M; ++i)
-            if (i < m) dx = ff2_add(dx, ff2_two_sum(xs[i], neg2(xt[i])));
         const FF2 d = ff2_add(ff2_add(sv, ff2_neg(stf)), ff2_neg(dx)); // s - s~ - sum_i (x - x~)
         cm_r = fmaxf(cm_r, fabsf(t.hi.x + t.lo.x));
         cm_s = fmaxf(cm_s, fabsf(d.hi.x + d.lo.x));
@@ -338,18 +334,10 @@ __device__ __forceinline__ void vec32(const EA &a, const float *uoff, const doub
             cm_s = fmaxf(cm_s, fabsf(d.hi.y + d.lo.y));
         }
     }
-#pragma unroll
-    for (int i = 0; i < M; ++i)
-        if (i < m) st2(a.x + a.xe(i, j, k0), xs[i]);
     st2(a.s + col, sv.hi);
     st2(a.mu + col, mnew.hi);
     st2(a.s_lo + col, sv.lo);
     st2(a.mu_lo + col, mnew.lo);
-    if (k0 == 0) {
-#pragma unroll
-        for (int i = 0; i < M; ++i)
-            if (i < m) rec[i * 4 + 3] = (double)xs[i].x;
-    }
 }
 
 // Lane sum of the per-thread capacity-sum accumulators of one source.

@@ -194,8 +194,9 @@ extern "C" admm_status admm_solve_noalloc(const admm_problem *P, const admm_para
     if (prm->max_iter < 1 || prm->check_every < 1) return nfail(ADMM_EINVAL, "max_iter and check_every must be >= 1");
     if (prm->precision != ADMM_FP64) return nfail(ADMM_EUNSUPPORTED, "only precision ADMM_FP64 is available here");
     if ((prm->xmin_mode != ADMM_XMIN_EXACT && prm->xmin_mode != ADMM_XMIN_PAPER) ||
-        (prm->sweep != ADMM_GAUSS_SEIDEL && prm->sweep != ADMM_JACOBI) || (prm->adapt_rho && !(prm->tau > 1.0)))
-        return nfail(ADMM_EINVAL, "bad xmin_mode, sweep or tau");
+        (prm->sweep != ADMM_GAUSS_SEIDEL && prm->sweep != ADMM_JACOBI) || (prm->adapt_rho && !(prm->tau > 1.0)) ||
+        prm->adapt_start < 0)
+        return nfail(ADMM_EINVAL, "bad xmin_mode, sweep, tau or adapt_start");
 
     double *scr = nullptr;
     int dev = -1;
@@ -293,6 +294,7 @@ extern "C" admm_status admm_solve_noalloc(const admm_problem *P, const admm_para
     a.r_tol = prm->r_tol;
     a.s_tol = prm->s_tol;
     a.adapt_target = prm->r_tol / prm->s_tol;
+    a.adapt_start = prm->adapt_start;
     a.tau = prm->tau;
     a.max_iter = prm->max_iter;
     a.check_every = prm->check_every;

@@ -564,8 +564,8 @@ admm_status admm_server_create(const admm_params *prm, const admm_server_config 
     if (cfg->batch.ctas_per_sm < 0 || cfg->batch.small_max_elements < 0 || cfg->batch.cluster_min_elements < 0)
         return sfail(ADMM_EINVAL, "negative setting");
     if (cfg->batch.reserved) return sfail(ADMM_EINVAL, "reserved must be 0");
-    for (int t = 0; t < 4; ++t)
-        if (!(prm->rho[t] > 0.0)) return sfail(ADMM_EINVAL, "rho must be > 0");
+    std::string why;
+    if (!batch_params_ok(prm, why)) return sfail(ADMM_EINVAL, why); // the rules of admm_batch_create
     admm_server *S = new admm_server();
     S->prm = *prm;
     S->cfg = *cfg;
@@ -662,6 +662,7 @@ admm_status admm_server_create(const admm_params *prm, const admm_server_config 
     a.r_tol = stop_r_tol(prm->precision, prm->r_tol);
     a.s_tol = stop_s_tol(prm->precision, prm->s_tol);
     a.adapt_target = prm->r_tol / prm->s_tol;
+    a.adapt_start = prm->adapt_start;
     a.tau = prm->tau;
     a.max_iter = prm->max_iter;
     a.check_every = prm->check_every;

@@ -595,7 +595,7 @@ __global__ void __launch_bounds__(NT, MINB) single_kernel(SingleArgs a)
                 conv = true;
                 break;
             }
-            if (a.adapt && it < a.max_iter) { // Sec. IV-A, duals rescaled by rho_old / rho_new
+            if (a.adapt && it < a.max_iter && it >= a.adapt_start) { // Sec. IV-A, duals rescaled
                 const double ratio = r / sg, target = a.adapt_target;
                 double f = 1.0;
                 if (ratio > 1.2 * target) f = a.tau;

@@ -124,6 +124,7 @@ class Params:
     adapt_rho: bool = False       # Sec. IV-A penalty adaptation
     tau: float = 1.1
     rho2_over_n: bool = False     # each instance uses rho_2 = rho[1] / n
+    adapt_start: int = 0          # with adapt_rho: adapt at check iterations t >= adapt_start only
 
     def replace(self, **kw) -> "Params":
         return dataclasses.replace(self, **kw)

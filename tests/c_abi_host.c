@@ -23,7 +23,7 @@ int main(void)
     CHECK(p.max_iter == 5000 && p.check_every == 10);
     CHECK(p.rho[0] == 1.0 && p.rho[3] == 1.0 && p.r_tol == 1e-6 && fabs(p.tau - 1.1) < 1e-15);
     CHECK(p.precision == ADMM_FP64 && p.xmin_mode == ADMM_XMIN_EXACT && p.sweep == ADMM_GAUSS_SEIDEL);
-    CHECK(p.reserved[0] == 0 && p.reserved[1] == 0 && p.reserved[2] == 0);
+    CHECK(p.adapt_start == 0 && p.reserved[0] == 0 && p.reserved[1] == 0);
 
     admm_handle *h = NULL;
     CHECK(admm_create(NULL, &p, &h) == ADMM_EINVAL && h == NULL);

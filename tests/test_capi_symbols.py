@@ -174,7 +174,7 @@ def test_create_refuses_bad_sizes_and_settings_on_the_host():
         return p
 
     for kw in ({"rho1": 0.0}, {"rho1": float("inf")}, {"r_tol": float("nan")}, {"max_iter": 0},
-               {"check_every": 0}, {"xmin_mode": 5}, {"sweep": 3}, {"adapt_rho": 1, "tau": 1.0},
+               {"check_every": 0}, {"xmin_mode": 5}, {"sweep": 3}, {"adapt_rho": 1, "tau": 1.0}, {"adapt_start": -1},
                {"reserved": 1}):
         assert create(P, par(**kw)) == capi.ADMM_EINVAL, kw
     assert create(P, par(precision=9)) == capi.ADMM_EUNSUPPORTED

@@ -144,6 +144,18 @@ def test_adaptive_rho_matches(capi, oracle_lib):
     compare_states(P, st_o, rep_o, st_g, res)
 
 
+def test_late_adaptation_matches(capi, oracle_lib):
+    """adapt_start: fixed penalties up to iteration 100, the Sec. IV-A rule
+    from the check at 110 on; the FP64 kernel takes the oracle's steps."""
+    P = W.random_problem(120, 3, 4, seed=31)
+    par = W.Params(rho=(1.0, 1.0 / 120, 1.0, 1.0), adapt_rho=True, adapt_start=101)
+    st_o, rep_o, st_g, res = run_both(capi, oracle_lib, P, par)
+    assert rep_o["converged"] and res["converged"]
+    assert res["iters"] == rep_o["iters"] and res["iters"] > 110
+    assert np.allclose(st_g["rho"], rep_o["rho"], rtol=1e-12, atol=0)
+    compare_states(P, st_o, rep_o, st_g, res)
+
+
 def test_config1_full_size_to_convergence(capi, oracle_lib):
     """PHEV-shaped config at full size (n = 1000, q = 50) in the launch shape
     the benchmark times."""

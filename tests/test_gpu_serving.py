@@ -119,6 +119,26 @@ def test_step_request_slides_the_horizon_on_the_device(capi, oracle_lib):
     assert abs(cold["objective"] - obj_o) <= 1e-6 * max(1.0, abs(obj_o))
 
 
+def test_step_requests_with_late_adaptation(capi, oracle_lib):
+    """The serving setting for re-solves: adaptation (Sec. IV-A) only from
+    iteration 200 on.  A batch and a server give the same bits for the same
+    problem, and a warm step re-solve reaches the oracle's optimum."""
+    par = PAR.replace(adapt_rho=True, adapt_start=200)
+    P0 = W.random_problem(400, 3, 6, seed=79)
+    P1 = W.receding_step(P0, step=1)
+    with capi.Batch([P0], par) as B:
+        B.solve()
+        rb = B.wait(want_x=True)[0]
+    with capi.Server(par, tick_iters=40) as S:
+        r0 = wait_all(S, [S.submit(P0, session=11)])[0]
+        r1 = wait_all(S, [S.submit_step(11, W.step_data(3, 6, step=1))])[0]
+    assert rb["converged"] and r0["converged"] and r1["converged"] and r1["warm"]
+    assert rb["iters"] == r0["iters"] and np.array_equal(rb["x"], r0["x"])
+    st_o, _ = oracle_lib.solve(P1, par.replace(precision="fp64"), threads=16)
+    obj_o = oracle_lib.objective(P1, st_o["x"])
+    assert abs(r1["objective"] - obj_o) <= 1e-6 * max(1.0, abs(obj_o))
+
+
 def test_step_request_without_a_resident_session_fails_cleanly(capi):
     with capi.Server(PAR) as S:
         t = S.submit_step(123, W.step_data(2, 3, step=1))

@@ -267,6 +267,31 @@ def test_adaptive_rho_reaches_the_same_solution(oracle_lib):
     assert k < 1e-7, terms
 
 
+def test_late_adaptation_is_fixed_rho_then_adaptive_continuation(oracle_lib):
+    """adapt_start = T0 + 1 (T0 a check iteration): T0 iterations at fixed
+    rho (a solve with max_iter = T0 never adapts at its last iteration), then
+    the adaptive iteration resumed from that state, give the same iterates,
+    penalties and iteration count as one solve.  adapt_start beyond the last
+    check is the fixed-rho solve; adapt_start = 0 the adaptive one."""
+    P = W.random_problem(50, 2, 3, seed=19)
+    par = W.Params(rho=(1.0, 1.0 / 50, 1.0, 1.0), r_tol=1e-8, s_tol=1e-8, max_iter=3000, adapt_rho=True)
+    T0 = 120
+    st, rep = oracle_lib.solve(P, par.replace(adapt_start=T0 + 1))
+    s1, r1 = oracle_lib.solve(P, par.replace(adapt_rho=False, max_iter=T0))
+    assert not r1["converged"]
+    s2, r2 = oracle_lib.solve(P, par.replace(max_iter=par.max_iter - T0), state=s1)
+    assert rep["converged"] and r2["converged"]
+    assert rep["iters"] == T0 + r2["iters"] and rep["rho"] == r2["rho"] and rep["rho"][0] != 1.0
+    for k in ("x", "z", "lam", "s", "mu", "h", "p", "nu", "x1"):
+        assert np.array_equal(st[k], s2[k]), k
+    sf, rf = oracle_lib.solve(P, par.replace(adapt_rho=False))
+    sl, rl = oracle_lib.solve(P, par.replace(adapt_start=par.max_iter + 1))
+    assert rl["iters"] == rf["iters"] and np.array_equal(sl["x"], sf["x"])
+    sa, ra = oracle_lib.solve(P, par)
+    s0, r0 = oracle_lib.solve(P, par.replace(adapt_start=0))
+    assert r0["iters"] == ra["iters"] and np.array_equal(s0["x"], sa["x"])
+
+
 def test_dual_residual_bounds_z_stationarity_violation(oracle_lib):
     """Stationarity of L in z asks rho1 lambda = rho2 p.  After (b), (g), (i)
     it is violated by exactly rho2 (h - h~), so sigma >= max |rho1 lambda -
