@@ -202,12 +202,12 @@ void launch_shift_state(const BatchInst *inst, const int *ids, int count, float 
 
 // Shared memory (doubles) of one team: scalar state, double-buffered records
 // of `items` work items, per-warp column maxima, x at k = 0, scratch, and
-// the FP32 zeta + lambda vector.
+// the FP32 zeta + lambda and x1 + nu vectors.
 static size_t team_doubles(int m, int q, int items, int nwt)
 {
     const int mq = m * q;
     return (size_t)scal_size(m, q) + 2 * (size_t)items * m * 4 + 4 * (size_t)nwt + 24 + mq + kMaxM + kWarpsMax * 8 +
-           (mq + 1) / 2 + 8;
+           2 * ((mq + 1) / 2) + 8;
 }
 
 size_t batch_slice_doubles(int max_m, int max_q)

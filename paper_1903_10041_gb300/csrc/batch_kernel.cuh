@@ -124,7 +124,7 @@ template <int KIND, int NW, int M> __device__ void solve_team(const BatchArgs &a
     const int64_t npairs = (int64_t)q * nv;
     const int items = q + W - 1; // record slots: (row j, warp w) at j + w
 
-    // shared memory: scal | rec[2][items][m][4] | cmax[2][NWT][2] | part[24] | x0s[mq] | x1n | scr | uoff
+    // shared memory: scal | rec[2][items][m][4] | cmax[2][NWT][2] | part[24] | x0s[mq] | x1n | scr | uoff | x1nu
     // part: [0], [1] end-of-solve sums; [2] kappa; [3] the adaptation factor of a check; [16..19] fpar;
     // [20..23] ipar.  Thread 0 keeps these team-wide values current so that the other threads read them
     // instead of each converting and dividing on the FP64 pipe.
@@ -139,7 +139,8 @@ template <int KIND, int NW, int M> __device__ void solve_team(const BatchArgs &a
     double *x0s = part + 24;
     double *x1n = x0s + mq;
     double *scr = x1n + kMaxM;
-    float *uoff = (float *)(scr + kWarpsMax * 8);
+    float *uoff = (float *)(scr + kWarpsMax * 8); // [mq] (float)(zeta + lambda)
+    float *x1nu = uoff + mq;                      // [mq] (float)(x1 + nu)
 
     double *gscal = a.scal + I.off_scal;
     double *out = a.out + (size_t)id * kInfo;
@@ -148,7 +149,10 @@ template <int KIND, int NW, int M> __device__ void solve_team(const BatchArgs &a
     if (skip) return; // every member read the same flag
     for (int t = tid; t < scal_size(m, q); t += NTL) scal[t] = __ldcg(gscal + t);
     sync_local();
-    for (int pr = tid; pr < mq; pr += NTL) uoff[pr] = (float)(zeta[pr] + lam[pr]);
+    for (int pr = tid; pr < mq; pr += NTL) {
+        uoff[pr] = (float)(zeta[pr] + lam[pr]);
+        x1nu[pr] = (float)(x1[pr / q] + nu[pr]);
+    }
     if (tid == 0) {
         part[2] = rho[1] / (rho[0] + (double)n * rho[1]); // kappa of step (b)
         fpar[0] = (float)rho[0];
@@ -229,14 +233,14 @@ template <int KIND, int NW, int M> __device__ void solve_team(const BatchArgs &a
                     }
                     cp_async_commit();
                     cp_async_wait1(); // this round's copies have landed
-                    vec32<M, VW, false, true>(ea, uoff, x1, nu, j, v * VW, check, cold, mu_div, rho1, rho3, rho4,
+                    vec32<M, VW, false, true>(ea, uoff, x1nu, j, v * VW, check, cold, mu_div, rho1, rho3, rho4,
                                               iq, ghi, glo, fmx, fmn, fcr, fcs, esc, rec, cur);
                 }
                 cp_async_wait0();
             } else {
                 for (int v = v0 + lane; v < v1; v += 32) {
                     if (v + 32 < v1) prefetch_vec32<M>(ea, j, (v + 32) * VW, cold);
-                    vec32<M, VW, false>(ea, uoff, x1, nu, j, v * VW, check, cold, mu_div, rho1, rho3, rho4, iq, ghi,
+                    vec32<M, VW, false>(ea, uoff, x1nu, j, v * VW, check, cold, mu_div, rho1, rho3, rho4, iq, ghi,
                                         glo, fmx, fmn, fcr, fcs, esc, rec);
                 }
             }
@@ -289,7 +293,7 @@ template <int KIND, int NW, int M> __device__ void solve_team(const BatchArgs &a
                     dmx = fmax(dmx, rr[1]);
                     dmn = fmin(dmn, rr[2]);
                 }
-                if (w == wf) x0 = rr[3]; // k = 0 lies in the first warp's piece
+                if (w == wf) x0 = (double)*(const float *)(rr + 3); // k = 0 lies in the first warp's piece
             }
             const double lm = lam[pr], zt = zeta[pr], h0 = hh[pr], p0 = pp[pr];
             const double Wv = (Ssum + sumg0[pr]) - (double)n * lm;
@@ -399,7 +403,10 @@ template <int KIND, int NW, int M> __device__ void solve_team(const BatchArgs &a
                 sync_local();
             }
         }
-        for (int pr = tid; pr < mq; pr += NTL) uoff[pr] = (float)(zeta[pr] + lam[pr]);
+        for (int pr = tid; pr < mq; pr += NTL) {
+            uoff[pr] = (float)(zeta[pr] + lam[pr]);
+            x1nu[pr] = (float)(x1[pr / q] + nu[pr]);
+        }
         sync_local();
     }
     const bool finished = conv || it >= a.max_iter;

@@ -223,14 +223,16 @@ __device__ __forceinline__ float2 ldg2(const float *p) { return __ldg((const flo
 __device__ __forceinline__ void st2(float *p, float2 v) { *(float2 *)p = v; }
 
 // Step (a) for all sources of the column pair (j, k0), (j, k0 + 1), then
-// (e), (f), on packed pairs.  uoff[pr] = zeta + lambda of pair pr in FP32;
-// x1 and nu are the FP64 pair scalars (read at k = 0 only).  The capacity
+// (e), (f), on packed pairs.  uoff[pr] = zeta + lambda and x1nu[pr] =
+// x1 + nu (read at k = 0 only) of pair pr, rounded to FP32 once per
+// iteration by the caller, so no FP64 operation runs per element.  The capacity
 // sums accumulate per lane in ghi/glo (the caller combines the lanes), the
-// D_k extrema in dmx/dmn.  rec (if k0 == 0) receives x at k = 0.  The
+// D_k extrema in dmx/dmn.  rec (if k0 == 0) receives x at k = 0 as an FP32
+// value in the first four bytes of its slot (the scalar phase widens it).  The
 // first column is always < n; the second may be padding (k0 + 1 = n), and
 // then takes no part in the sums and residuals.
 template <int M, int VW, bool C64, bool STAGED = false, class EA>
-__device__ __forceinline__ void vec32(const EA &a, const float *uoff, const double *x1s, const double *nus,
+__device__ __forceinline__ void vec32(const EA &a, const float *uoff, const float *x1nu,
                                       int j, int k0, bool check, bool cold, float mu_div, float rho1, float rho3,
                                       float rho4, float iq, float2 *ghi, float2 *glo, float *dmx, float *dmn,
                                       float &cm_r, float &cm_s, unsigned &esc, double *rec,
@@ -284,7 +286,7 @@ __device__ __forceinline__ void vec32(const EA &a, const float *uoff, const doub
             float2 D = fma2(a1, iq2, fma2(mul2(nr1, b1), u, mul2(nr3, phi)));
             if (k0 == 0) {
                 C.x += 0.5f * rho4;
-                D.x -= rho4 * (float)(x1s[i] + nus[pr]);
+                D.x -= rho4 * x1nu[pr];
             }
             float2 xn;
             if constexpr (C64)
@@ -296,7 +298,7 @@ __device__ __forceinline__ void vec32(const EA &a, const float *uoff, const doub
             sx = ff2_addf(sx, xn); // sum_i x of (e), (f) in source order
             if (check) dx = ff2_add(dx, ff2_two_sum(xn, neg2(x0)));
             st2(a.x + a.xe(i, j, k0), xn);
-            if (k0 == 0) rec[i * 4 + 3] = (double)xn.x;
+            if (k0 == 0) *(float *)(rec + i * 4 + 3) = xn.x; // FP32 in the slot; widened by the reader
             float2 ghh, gll;
             g_ff2(b2, b1, xn, ghh, gll);
             if (!v1) {

@@ -57,6 +57,7 @@ struct Sm {
     double *bc;   // [16] broadcast
     int *segof;   // [kSingleWarpsMax] segment (within the pass) of each warp
     float *uoff;  // [mq] zeta + lambda in FP32 (mixed variants)
+    float *x1nu;  // [mq] x1 + nu in FP32 (mixed variants)
 };
 
 __device__ __forceinline__ Sm carve(double *base, int m, int q)
@@ -85,6 +86,7 @@ __device__ __forceinline__ Sm carve(double *base, int m, int q)
     s.segof = (int *)t;
     t += kSingleWarpsMax;
     s.uoff = (float *)t;
+    s.x1nu = s.uoff + mq;
     return s;
 }
 
@@ -419,7 +421,10 @@ __global__ void __launch_bounds__(NT, MINB) single_kernel(SingleArgs a)
     for (int t = threadIdx.x; t < scal_size(m, q); t += NT) smem[t] = a.scal[t];
     __syncthreads();
     if (MIXED)
-        for (int pr = threadIdx.x; pr < mq; pr += NT) sm.uoff[pr] = (float)(sm.zeta[pr] + sm.lam[pr]);
+        for (int pr = threadIdx.x; pr < mq; pr += NT) {
+            sm.uoff[pr] = (float)(sm.zeta[pr] + sm.lam[pr]);
+            sm.x1nu[pr] = (float)(sm.x1[pr / q] + sm.nu[pr]);
+        }
     __syncthreads();
 
     int64_t c0, c1;
@@ -489,7 +494,7 @@ __global__ void __launch_bounds__(NT, MINB) single_kernel(SingleArgs a)
                 for (int k0 = kb + first * VW; k0 < kn; k0 += stride * VW) {
                     if constexpr (MINB == 2) // several vectors per thread: fetch the next one into L2
                         if (k0 + stride * VW < kn) prefetch_vec32<M>(ea, j, k0 + stride * VW, cold);
-                    vec32<M, VW, PREC == ADMM_MIXED_FP64CUBIC>(ea, sm.uoff, sm.x1, sm.nu, j, k0, check, cold,
+                    vec32<M, VW, PREC == ADMM_MIXED_FP64CUBIC>(ea, sm.uoff, sm.x1nu, j, k0, check, cold,
                                                                (float)mu_div, rho1, rho3, rho4, iq, ghi, glo, fmx,
                                                                fmn, fcr, fcs, esc, rec);
                 }
@@ -527,7 +532,8 @@ __global__ void __launch_bounds__(NT, MINB) single_kernel(SingleArgs a)
             const int stride = m * 4;
             // records of row j, in CTA order; independent loads, fixed order of the sums
             double S = 0.0, dmx = -INFINITY, dmn = INFINITY;
-            const double x0 = ldcg(rec + 3);
+            // x at k = 0: FP64 in the FP64 kernel, FP32 in the first four bytes of the slot in the mixed ones
+            const double x0 = MIXED ? (double)__ldcg((const float *)(rec + 3)) : ldcg(rec + 3);
 #pragma unroll 8
             for (int t = 0; t < nb; ++t) {
                 S += ldcg(rec + (size_t)t * stride);
@@ -615,7 +621,10 @@ __global__ void __launch_bounds__(NT, MINB) single_kernel(SingleArgs a)
             }
         }
         if (MIXED) {
-            for (int pr = threadIdx.x; pr < mq; pr += NT) sm.uoff[pr] = (float)(sm.zeta[pr] + sm.lam[pr]);
+            for (int pr = threadIdx.x; pr < mq; pr += NT) {
+                sm.uoff[pr] = (float)(sm.zeta[pr] + sm.lam[pr]);
+                sm.x1nu[pr] = (float)(sm.x1[pr / q] + sm.nu[pr]);
+            }
             __syncthreads();
         }
     }
@@ -721,7 +730,7 @@ size_t single_smem_bytes(int m, int q)
     const int mq = m * q;
     return sizeof(double) * ((size_t)scal_size(m, q) + mq + kMaxM + kSingleWarpsMax * kMaxM * 3 +
                              kSingleWarpsMax * 8 + 16 + kSingleWarpsMax) +
-           sizeof(float) * (size_t)mq + 16;
+           sizeof(float) * 2 * (size_t)mq + 16;
 }
 
 int single_blocks_per_sm(int precision, int m, int minb, size_t smem)
