@@ -88,13 +88,13 @@ def workload(cfg: int, precision: str, coef_shared: bool = False):
 # figure is reported only while the kernel's sources hash to the build it
 # was taken on (otherwise `traffic` is null).
 NCU_TRAFFIC = {
-    ("phev n=1000 q=50", "fp64"): {"bytes_per_iter": (7670528 + 57856) / 3330, "src": "8f897a19c7a6fd75"},
+    ("phev n=1000 q=50", "fp64"): {"bytes_per_iter": (7572224 + 50944) / 3330, "src": "81ac6bf6b4915e2b"},
 }
-NCU_TRAFFIC_BATCH = {"bytes_per_element_iter": (1883104666112 + 660502484224) / 76360828990.0, "src": "f5cc893436019ddd"}
+NCU_TRAFFIC_BATCH = {"bytes_per_element_iter": (1826721877760 + 617143367936) / 76330081250.0, "src": "dda501025ddee7ca"}
 # FP64 pipe utilisation (sm__pipe_fp64_cycles_active, % of peak over the active cycles) of the FP64 solve
 # kernel on the PHEV instance, from an ncu capture of the same build: the counted-flop fraction leaves out
 # the Newton steps of the FP32-seeded roots, conversions, comparisons and the per-pair scalar phase.
-NCU_FP64_PIPE = {("phev n=1000 q=50", "fp64"): {"pct": 60.85, "src": "8f897a19c7a6fd75"}}
+NCU_FP64_PIPE = {("phev n=1000 q=50", "fp64"): {"pct": 60.51, "src": "81ac6bf6b4915e2b"}}
 
 # Sources each solve kernel is compiled from.
 SINGLE_KERNEL_SOURCES = ("single.cu", "quartic32.cuh", "quartic64.cuh", "mixed_elem.cuh", "common.cuh", "internal.h")

@@ -259,7 +259,7 @@ __device__ __forceinline__ void vec32(const EA &a, const float *uoff, const floa
     const bool v1 = k0 + 1 < n;
     const bool jac = a.sweep == ADMM_JACOBI;
     const float2 h1 = splat2(0.5f * rho1), h3 = splat2(0.5f * rho3), iq2 = splat2(iq);
-    const float2 nr1 = splat2(-rho1), nr3 = splat2(-rho3), r1 = splat2(rho1);
+    const float2 nr1 = splat2(-rho1), nr3 = splat2(-rho3);
     FF2 sx = {splat2(0.0f), splat2(0.0f)}, dx = {splat2(0.0f), splat2(0.0f)};
 
 #pragma unroll
@@ -279,8 +279,9 @@ __device__ __forceinline__ void vec32(const EA &a, const float *uoff, const floa
             const float2 u = cold ? neg2(g0) : add2(gq_old, splat2(uoff[pr]));
             const float2 others = sub2(xsum, x0); // sum over l != i (x_i is still x0 here)
             const float2 phi = add2(add2(sub2(st, others), yv), mu);
-            const float2 A = mul2(mul2(h1, b2), b2);
-            const float2 B = mul2(mul2(r1, b2), b1);
+            const float2 hb2 = mul2(h1, b2); // (rho_1 / 2) b2; B = (rho_1 b2) b1 = hb2 (2 b1) exactly
+            const float2 A = mul2(hb2, b2);
+            const float2 B = mul2(hb2, add2(b1, b1));
             const float2 t = fma2(mul2(splat2(-2.0f), b2), u, mul2(b1, b1)); // b1^2 - 2 b2 u
             float2 C = fma2(a2, iq2, fma2(h1, t, h3));
             float2 D = fma2(a1, iq2, fma2(mul2(nr1, b1), u, mul2(nr3, phi)));
