@@ -90,7 +90,7 @@ def workload(cfg: int, precision: str, coef_shared: bool = False):
 NCU_TRAFFIC = {
     ("phev n=1000 q=50", "fp64"): {"bytes_per_iter": (7572224 + 50944) / 3330, "src": "81ac6bf6b4915e2b"},
 }
-NCU_TRAFFIC_BATCH = {"bytes_per_element_iter": (1826721877760 + 617143367936) / 76330081250.0, "src": "dda501025ddee7ca"}
+NCU_TRAFFIC_BATCH = {"bytes_per_element_iter": (1827028594688 + 617014689792) / 76330081250.0, "src": "8f3c010968296e10"}
 # FP64 pipe utilisation (sm__pipe_fp64_cycles_active, % of peak over the active cycles) of the FP64 solve
 # kernel on the PHEV instance, from an ncu capture of the same build: the counted-flop fraction leaves out
 # the Newton steps of the FP32-seeded roots, conversions, comparisons and the per-pair scalar phase.
@@ -625,9 +625,9 @@ def run_serving(args):
     base = rank * args.count
     shapes = [W.batch_shape(base + c) for c in range(args.count)]
     total_el = sum(((n + 3) // 4 * 4) * m * q for n, m, q in shapes)
-    # 16-warp CTA teams, no clusters (measured: p99 4.5 s against 7.4 s with 8-warp CTAs and 10 s with
-    # clusters of 2 above 1.5e5 elements, at 2000/s offered)
-    bc = dict(warps_per_cta=16, ctas_per_sm=0, small_max_elements=0, cluster_size=1, cluster_min_elements=0)
+    # 16-warp CTA teams, 2-CTA clusters for the sessions above 1e5 elements (measured at 2000/s offered:
+    # p99 0.92 s; 1.16 s above 1.5e5, 1.30 s above 2.5e5, 1.42 s without clusters)
+    bc = dict(warps_per_cta=16, ctas_per_sm=0, small_max_elements=0, cluster_size=2, cluster_min_elements=100000)
     if args.batch_config:
         w, c, sm, cl, cm = (int(v) for v in args.batch_config.split(","))
         bc = dict(warps_per_cta=w, ctas_per_sm=c, small_max_elements=sm, cluster_size=cl, cluster_min_elements=cm)
@@ -706,7 +706,7 @@ def run_serving(args):
                 "data": "synthetic (seeded receding-horizon steps per controller)",
                 "config": {"workload": f"serving: Poisson {args.rate:g}/s re-solves of {args.count} controllers "
                                        f"sized as the batched workload, {args.duration:g} s window",
-                           "tick_iters": args.tick_iters, "rho": penalty_text(args),
+                           "tick_iters": args.tick_iters, "rho": penalty_text(args), "teams": dict(bc),
                            "steps": "requests finished in the window; warmup = the controllers' cold solves",
                            "parallelism": f"replicas x{world}"},
                 "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),

@@ -61,7 +61,9 @@ struct BatchArgs {
 // works for about the same time and small instances are not held to the
 // pace of the largest one.  The host sets *tick_work to iter_budget times
 // the largest cost in the tick.  Where a tick ends does not change any
-// result: an instance resumes from its saved state bit for bit.
+// result: an instance resumes from its saved state bit for bit.  With
+// round-robin slices (below) a cluster team's instance, taken once per
+// tick, runs R slices' worth of iterations in its one pass.
 __host__ __device__ inline float team_iter_cost(int n, int m, int q, int team_threads)
 {
     return (float)((double)n * m * q / team_threads) + 4.0f; // + per-iteration fixed work

@@ -177,8 +177,14 @@ template <int KIND, int NW, int M> __device__ void solve_team(const BatchArgs &a
     double r_last = __ldcg(out + 2), s_last = __ldcg(out + 3);
     int it = it0;
     int budget = a.iter_budget;
-    if (budget > 0 && a.tick_work)
-        budget = (int)fminf(fmaxf(*a.tick_work / team_iter_cost(n, m, q, W * 32), 1.0f), 1.0e9f);
+    if (budget > 0 && a.tick_work) {
+        float cost = team_iter_cost(n, m, q, W * 32);
+        // a cluster team takes its instance once per tick: its one pass stands for the R
+        // round-robin slices a CTA team's instance gets
+        if constexpr (KIND == TEAM_CLUSTER)
+            if (a.tick_rounds) cost /= (float)max(1, *a.tick_rounds);
+        budget = (int)fminf(fmaxf(*a.tick_work / cost, 1.0f), 1.0e9f);
+    }
     const int it_end = budget > 0 ? (int)min((int64_t)a.max_iter, (int64_t)it0 + budget) : a.max_iter;
 
     while (it < it_end) {

@@ -423,11 +423,13 @@ void worker_loop(admm_server *S)
             // Round-robin slices when the CTA teams are outnumbered: the tick
             // keeps the length of ceil(A / teams) passes of the costliest
             // instance, cut into R slices per instance so no team idles in a
-            // partial last round.
+            // partial last round.  Cluster teams run their instances first
+            // (one pass each, worth R slices), so the CTAs they hold are not
+            // counted as CTA teams.
             int rounds = 1;
             float tw = (float)S->cfg.tick_iters * cmax;
-            const int teams = S->grid;
-            if (nX == 0 && nS == 0 && nL > teams) {
+            const int teams = std::max(1, S->grid - std::min(nX * S->cluster, S->grid / 2));
+            if (nS == 0 && nL > teams) {
                 rounds = 4;
                 const int passes = (nL + teams - 1) / teams;
                 tw = (float)((double)tw * passes * teams / ((double)nL * rounds));

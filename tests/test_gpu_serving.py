@@ -166,6 +166,27 @@ def test_round_robin_ticks_give_the_same_bits(capi):
         assert np.array_equal(alone[t]["x"], mix[t]["x"]), t
 
 
+def test_round_robin_ticks_with_cluster_teams_give_the_same_bits(capi, oracle_lib):
+    """Round-robin ticks while cluster teams run the largest requests: each
+    cluster instance takes one pass per tick worth the R slices of the CTA
+    teams' instances.  Every request gives the bits it gives alone."""
+    small = [W.random_problem(40 + (t % 7) * 13, 2 + t % 3, 1 + t % 4, seed=7000 + t) for t in range(700)]
+    large = [W.random_problem(600, 3, 4, seed=7900 + t) for t in range(6)]
+    cfg = dict(tick_iters=10, small_max_elements=0, cluster_size=2, cluster_min_elements=2000)
+    with capi.Server(PAR, **cfg) as S:
+        alone = [wait_all(S, [S.submit(P)])[0] for P in large[:2] + small[:2]]
+        mix = wait_all(S, [S.submit(P) for P in large + small], timeout_s=300.0)
+        stats = S.stats()
+    assert stats["instance_ticks"] / stats["ticks"] > 1.0
+    for t, u in enumerate((0, 1, 6, 7)):
+        assert alone[t]["converged"] and mix[u]["converged"], t
+        assert alone[t]["iters"] == mix[u]["iters"], t
+        assert np.array_equal(alone[t]["x"], mix[u]["x"]), t
+    st_o, _ = oracle_lib.solve(large[0], PAR.replace(precision="fp64"), threads=16)
+    obj_o = oracle_lib.objective(large[0], st_o["x"])
+    assert abs(mix[0]["objective"] - obj_o) <= 1e-6 * max(1.0, abs(obj_o))
+
+
 def test_cancel_a_queued_and_a_running_request(capi):
     long_par = PAR.replace(r_tol=0.0, s_tol=0.0, max_iter=5000)  # runs to the iteration cap
     with capi.Server(long_par, max_active=1, tick_iters=5) as S:
