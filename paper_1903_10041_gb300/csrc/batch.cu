@@ -5,15 +5,16 @@
 
 #include "batch.h"
 #include "common.cuh"
+#include "mixed_elem.cuh"
 
 namespace admm_impl {
 
-void *batch_pick(int warps, int mb)
+void *batch_pick(int warps, int mb, bool roll)
 {
     switch (warps) {
-    case 4: return batch_fn_w4(mb);
-    case 16: return batch_fn_w16(mb);
-    default: return batch_fn_w8(mb);
+    case 4: return batch_fn_w4(mb, roll);
+    case 16: return batch_fn_w16(mb, roll);
+    default: return batch_fn_w8(mb, roll);
     }
 }
 
@@ -231,17 +232,21 @@ BatchSmem batch_cta_smem(int max_m, int max_q, int warps, int cluster, bool warp
 {
     const size_t team = sizeof(double) * batch_cluster_team_doubles(max_m, max_q, warps, cluster);
     const size_t off = (team + 15) / 16 * 16;
-    // two stages of 4 m + 1 slots of 32 float2 per warp (m <= 4 kernel; see stage_vec32), then
-    // 11 floats per thread for the check-only lane maxima
-    const size_t stages = batch_mbound(max_m) == 4 ? (size_t)warps * 2 * (4 * 4 + 1) * 32 * 2 * sizeof(float) + (size_t)warps * 32 * 11 * sizeof(float) : 0;
+    // the stage region of 32-float2 slots per warp (m <= 4 kernel: the larger of the double stage,
+    // 2 (4 m + 1), and the rolling stage, 5 + 7 m; see stage_vec32, roll_issue_col), then 11
+    // floats per thread for the check-only lane maxima
+    const size_t stages = batch_mbound(max_m) == 4
+                              ? (size_t)warps * stage_region_slots<4>() * 32 * sizeof(float2) +
+                                    (size_t)warps * 32 * 11 * sizeof(float)
+                              : 0;
     size_t bytes = off + stages;
     if (warp_teams) bytes = std::max(bytes, batch_smem_bytes(warps, slice_doubles));
     return {bytes, (int)off};
 }
 
-int batch_blocks_per_sm(int warps, int mb, size_t smem)
+int batch_blocks_per_sm(int warps, int mb, size_t smem, bool roll)
 {
-    void *fn = batch_pick(warps, mb);
+    void *fn = batch_pick(warps, mb, roll);
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, warps * 32, smem) != cudaSuccess) return 0;
@@ -250,9 +255,10 @@ int batch_blocks_per_sm(int warps, int mb, size_t smem)
 
 // The kernel's shared-memory attribute is set by batch_blocks_per_sm, which
 // the host calls before launching (and before any graph capture).
-cudaError_t launch_batch(int warps, int mb, int grid, int cluster, const BatchArgs &a, size_t smem, cudaStream_t st)
+cudaError_t launch_batch(int warps, int mb, int grid, int cluster, const BatchArgs &a, size_t smem, bool roll,
+                         cudaStream_t st)
 {
-    void *fn = batch_pick(warps, mb);
+    void *fn = batch_pick(warps, mb, roll);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(warps * 32);
@@ -269,9 +275,9 @@ cudaError_t launch_batch(int warps, int mb, int grid, int cluster, const BatchAr
     return cudaLaunchKernelExC(&cfg, fn, args);
 }
 
-int batch_max_clusters(int warps, int mb, int cluster, size_t smem)
+int batch_max_clusters(int warps, int mb, int cluster, size_t smem, bool roll)
 {
-    void *fn = batch_pick(warps, mb);
+    void *fn = batch_pick(warps, mb, roll);
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
     if (cluster > 8 && cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
         return 0;

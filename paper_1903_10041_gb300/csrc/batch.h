@@ -87,9 +87,11 @@ bool batch_params_ok(const admm_params *p, std::string &why);
 
 size_t batch_slice_doubles(int max_m, int max_q);
 // The persistent kernel for CTAs of 4, 8 or 16 warps and source bound mbound.
-void *batch_fn_w4(int mbound);
-void *batch_fn_w8(int mbound);
-void *batch_fn_w16(int mbound);
+// roll: the rolling-stage instantiation (every input through cp.async; for launches whose
+// instances never move to another SM, i.e. batches; servers take the double stage).
+void *batch_fn_w4(int mbound, bool roll);
+void *batch_fn_w8(int mbound, bool roll);
+void *batch_fn_w16(int mbound, bool roll);
 // Shared memory (doubles) a CTA or cluster team needs in each of its CTAs.
 size_t batch_cluster_team_doubles(int max_m, int max_q, int warps, int cluster);
 size_t batch_smem_bytes(int warps, size_t slice_doubles);
@@ -102,12 +104,12 @@ struct BatchSmem {
     int stage_off;
 };
 BatchSmem batch_cta_smem(int max_m, int max_q, int warps, int cluster, bool warp_teams, size_t slice_doubles);
-int batch_blocks_per_sm(int warps, int mbound, size_t smem);
+int batch_blocks_per_sm(int warps, int mbound, size_t smem, bool roll = false);
 // Launch with clusters of `cluster` CTAs (1 = no clusters); grid is a multiple of it.
-cudaError_t launch_batch(int warps, int mbound, int grid, int cluster, const BatchArgs &a, size_t smem,
+cudaError_t launch_batch(int warps, int mbound, int grid, int cluster, const BatchArgs &a, size_t smem, bool roll,
                          cudaStream_t st);
 // Co-resident clusters of that size (0 if it cannot launch).
-int batch_max_clusters(int warps, int mbound, int cluster, size_t smem);
+int batch_max_clusters(int warps, int mbound, int cluster, size_t smem, bool roll = false);
 // Moves data and state of instances ids[0..count-1] one step forward,
 // writes the new last step from payload + t * payload_stride and clears the
 // result record out[id].

@@ -162,12 +162,12 @@ admm_status build_queues(admm_batch *b)
                                         b->nS > 0, b->slice);
     b->smem = bs.bytes;
     b->stage_off = bs.stage_off;
-    const int per_sm = batch_blocks_per_sm(b->cfg.warps_per_cta, mb, b->smem);
+    const int per_sm = batch_blocks_per_sm(b->cfg.warps_per_cta, mb, b->smem, true);
     if (per_sm < 1) return bfail(ADMM_EUNSUPPORTED, "batched kernel cannot be resident with this configuration");
     const int use = b->cfg.ctas_per_sm > 0 ? std::min(b->cfg.ctas_per_sm, per_sm) : per_sm;
     b->cluster = clusters ? b->cfg.cluster_size : 1;
     if (b->cluster > 1) {
-        const int nc = batch_max_clusters(b->cfg.warps_per_cta, mb, b->cluster, b->smem);
+        const int nc = batch_max_clusters(b->cfg.warps_per_cta, mb, b->cluster, b->smem, true);
         if (nc < 1) return bfail(ADMM_EUNSUPPORTED, "clusters of this size cannot be resident");
         b->grid = std::min(nc, b->nsm * use / b->cluster) * b->cluster;
         if (b->grid < b->cluster) b->grid = b->cluster;
@@ -224,7 +224,7 @@ admm_status ensure_graph(admm_batch *b)
     BTRY(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaMemsetAsync(b->d_q, 0, 4 * sizeof(int) + sizeof(unsigned long long), b->cap);
     if (e == cudaSuccess)
-        e = launch_batch(b->cfg.warps_per_cta, batch_mbound(b->max_m), b->grid, b->cluster, a, b->smem, b->cap);
+        e = launch_batch(b->cfg.warps_per_cta, batch_mbound(b->max_m), b->grid, b->cluster, a, b->smem, true, b->cap);
     cudaError_t e2 = cudaStreamEndCapture(b->cap, &g);
     if (e != cudaSuccess || e2 != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
@@ -502,7 +502,7 @@ admm_status admm_batch_autotune(admm_batch *b, int32_t trial_iters, admm_batch_c
                 const BatchArgs a = make_args(b);
                 cudaMemset(b->d_q, 0, 3 * sizeof(int));
                 cudaEventRecord(e0, b->cap);
-                cudaError_t e = launch_batch(w, batch_mbound(b->max_m), b->grid, b->cluster, a, b->smem, b->cap);
+                cudaError_t e = launch_batch(w, batch_mbound(b->max_m), b->grid, b->cluster, a, b->smem, true, b->cap);
                 cudaEventRecord(e1, b->cap);
                 if (e != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) continue;
                 float ms = 0.0f;

@@ -89,7 +89,7 @@ __host__ __device__ inline int64_t team_chunk(int W, int q, int nv)
 // column pairs, piece by piece, reducing each piece with shuffles only; one
 // team barrier; then the per-(i, j) scalar steps read the records of each
 // row in warp order.
-template <int KIND, int NW, int M> __device__ void solve_team(const BatchArgs &a, int id, double *smem)
+template <int KIND, int NW, int M, bool ROLL> __device__ void solve_team(const BatchArgs &a, int id, double *smem)
 {
     namespace cg = cooperative_groups;
     constexpr int NTL = KIND == TEAM_WARP ? 32 : NW * 32; // threads of this CTA in the team
@@ -117,7 +117,10 @@ template <int KIND, int NW, int M> __device__ void solve_team(const BatchArgs &a
     const int n = I.n, m = I.m, q = I.q, mq = m * q;
     const int nv = (n + VW - 1) / VW;
     const int W = NWT * CL, gw = rank * NWT + wl;
-    // coefficients staged in shared memory by cp.async (CTA and cluster teams of the m <= 4 kernel)
+    // inputs staged in shared memory by cp.async (CTA and cluster teams of the m <= 4 kernel): the
+    // rolling stage of every input (ROLL: batches, where an instance stays with its team), else the
+    // double stage of the read-only coefficients (serving, whose round-robin slices can bring an
+    // instance back to an SM with stale L1 lines).  Both give the same bits.
     constexpr bool STG = KIND != TEAM_WARP && M == 4;
     float2 *stage = (float2 *)((char *)smem + a.stage_off);
     const int64_t chunk = team_chunk(W, q, nv);
@@ -199,7 +202,7 @@ template <int KIND, int NW, int M> __device__ void solve_team(const BatchArgs &a
         // (m <= 4) update they live in the thread's own shared-memory slots (11
         // floats apart, no bank conflicts) instead of registers across the loop
         float fcr_r = 0.0f, fcs_r = 0.0f;
-        float *px = (float *)(stage + NWT * 2 * stage_slots<M>() * 32) + tid * 11;
+        float *px = (float *)(stage + NWT * stage_region_slots<M>() * 32) + tid * 11;
         float &fcr = *(STG ? px + 2 * M : &fcr_r);
         float &fcs = *(STG ? px + 2 * M + 1 : &fcs_r);
         fcr = 0.0f;
@@ -224,10 +227,21 @@ template <int KIND, int NW, int M> __device__ void solve_team(const BatchArgs &a
                 }
             }
             double *rec = recs + (size_t)(j + gw) * m * 4;
-            if constexpr (STG) {
+            if constexpr (STG && ROLL) {
+                // one rolling stage per warp, each slot group refilled for round r + 1 as round r reads it
+                float2 *stw = stage + (size_t)wl * stage_region_slots<M>() * 32 + lane;
+                int v = v0 + lane;
+                roll_prologue<M>(ea, j, v * VW, v < v1, stw);
+                for (; v < v1; v += 32) {
+                    const int kn = v + 32 < v1 ? (v + 32) * VW : -1;
+                    vec32<M, VW, false, STAGE_ROLL>(ea, uoff, x1nu, j, v * VW, check, cold, mu_div, rho1, rho3,
+                                                    rho4, iq, ghi, glo, fmx, fmn, fcr, fcs, esc, rec, stw, kn);
+                }
+                cp_async_wait0();
+            } else if constexpr (STG) {
                 // two stages per warp; round r of the piece reads stage r & 1
                 // while the copies of round r + 1 fill the other
-                float2 *stw = stage + (size_t)wl * 2 * stage_slots<M>() * 32 + lane;
+                float2 *stw = stage + (size_t)wl * stage_region_slots<M>() * 32 + lane;
                 int v = v0 + lane;
                 if (v < v1) stage_vec32<M>(ea, j, v * VW, stw);
                 cp_async_commit();
@@ -239,7 +253,7 @@ template <int KIND, int NW, int M> __device__ void solve_team(const BatchArgs &a
                     }
                     cp_async_commit();
                     cp_async_wait1(); // this round's copies have landed
-                    vec32<M, VW, false, true>(ea, uoff, x1nu, j, v * VW, check, cold, mu_div, rho1, rho3, rho4,
+                    vec32<M, VW, false, STAGE_DOUBLE>(ea, uoff, x1nu, j, v * VW, check, cold, mu_div, rho1, rho3, rho4,
                                               iq, ghi, glo, fmx, fmn, fcr, fcs, esc, rec, cur);
                 }
                 cp_async_wait0();
@@ -461,7 +475,7 @@ template <int KIND, int NW, int M> __device__ void solve_team(const BatchArgs &a
     sync_team(); // rank 0 has read every member's shared memory
 }
 
-template <int NW, int M> __global__ void __launch_bounds__(NW * 32, 16 / NW) batch_kernel(BatchArgs a)
+template <int NW, int M, bool ROLL> __global__ void __launch_bounds__(NW * 32, 16 / NW) batch_kernel(BatchArgs a)
 {
     extern __shared__ double smem[];
     __shared__ int s_item;
@@ -477,7 +491,7 @@ template <int NW, int M> __global__ void __launch_bounds__(NW * 32, 16 / NW) bat
             const int item = *cl.map_shared_rank(&s_item, 0);
             cl.sync();
             if (item >= nX) break;
-            solve_team<TEAM_CLUSTER, NW, M>(a, a.orderX[item], smem);
+            solve_team<TEAM_CLUSTER, NW, M, ROLL>(a, a.orderX[item], smem);
         }
     }
     const int R = a.tick_rounds ? max(1, *a.tick_rounds) : 1;
@@ -498,7 +512,7 @@ template <int NW, int M> __global__ void __launch_bounds__(NW * 32, 16 / NW) bat
         __syncthreads();
         if (id == -2) break;
         if (id < 0) continue;
-        solve_team<TEAM_CTA, NW, M>(a, id, smem);
+        solve_team<TEAM_CTA, NW, M, ROLL>(a, id, smem);
         if (R > 1) {
             __syncthreads(); // every thread's state writes precede the release
             if (threadIdx.x == 0) {
@@ -523,7 +537,7 @@ template <int NW, int M> __global__ void __launch_bounds__(NW * 32, 16 / NW) bat
         id = __shfl_sync(0xffffffffu, id, 0);
         if (id == -2) break;
         if (id < 0) continue;
-        solve_team<TEAM_WARP, NW, M>(a, id, slice);
+        solve_team<TEAM_WARP, NW, M, ROLL>(a, id, slice);
         if (R > 1) {
             __syncwarp();
             if (lane == 0) {

@@ -4,9 +4,10 @@
 
 namespace admm_impl {
 
-void *batch_fn_w8(int mb)
+void *batch_fn_w8(int mb, bool roll)
 {
-    return mb <= 4 ? (void *)batch_kernel<8, 4> : (void *)batch_kernel<8, 8>;
+    if (mb > 4) return (void *)batch_kernel<8, 8, false>; // no staging for m > 4
+    return roll ? (void *)batch_kernel<8, 4, true> : (void *)batch_kernel<8, 4, false>;
 }
 
 } // namespace admm_impl

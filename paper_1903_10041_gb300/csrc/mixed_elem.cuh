@@ -144,6 +144,64 @@ template <int M, class EA> __device__ __forceinline__ void stage_vec32(const EA 
         }
 }
 
+// Rolling staging (batched kernel, launches whose instances stay on one team):
+// every array the element update reads comes through the lane's own slots of
+// one per-warp stage, each slot group refilled for the next column pair right
+// after it is read.  Slots: 0 y, 1 s, 2 mu, 3 s_lo, 4 mu_lo, 5 + i x of source
+// i (the column group), then 5 + M + 6 i + {0..5} f2, f1, g2, g1, lo, hi of
+// source i.  A pair's copies are committed as 1 + M groups (column, then one
+// per source slot, empty past m), so the group a step needs is always the
+// oldest but M: every wait is cp.async.wait_group M.  The copies cache in L1
+// (8-byte cp.async has no L2-only form), so the mode is for launches where no
+// instance moves to another SM: its own L1 never holds lines another SM wrote.
+template <int M> __host__ __device__ constexpr int roll_slots() { return 5 + 7 * M; }
+// Slots per warp of the batched kernel's stage region (either staging mode).
+template <int M> __host__ __device__ constexpr int stage_region_slots()
+{
+    return 2 * stage_slots<M>() > roll_slots<M>() ? 2 * stage_slots<M>() : roll_slots<M>();
+}
+template <int M> __device__ __forceinline__ void cp_async_wait_m()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(M) : "memory");
+}
+template <int M, class EA> __device__ __forceinline__ void roll_issue_col(const EA &a, int j, int k0, float2 *dst)
+{
+    const auto col = a.col(j, k0);
+    cp_async8(dst + 0 * 32, a.y + col);
+    cp_async8(dst + 1 * 32, a.s + col);
+    cp_async8(dst + 2 * 32, a.mu + col);
+    cp_async8(dst + 3 * 32, a.s_lo + col);
+    cp_async8(dst + 4 * 32, a.mu_lo + col);
+#pragma unroll
+    for (int i = 0; i < M; ++i)
+        if (i < a.m) cp_async8(dst + (5 + i) * 32, a.x + a.xe(i, j, k0));
+}
+template <int M, class EA>
+__device__ __forceinline__ void roll_issue_src(const EA &a, int i, int j, int k0, float2 *dst)
+{
+    const auto d = a.ce(i, j, k0);
+    const auto eb = a.be(i, k0);
+    float2 *p = dst + (5 + M + 6 * i) * 32;
+    cp_async8(p + 0 * 32, a.f2 + d);
+    cp_async8(p + 1 * 32, a.f1 + d);
+    cp_async8(p + 2 * 32, a.g2 + d);
+    cp_async8(p + 3 * 32, a.g1 + d);
+    cp_async8(p + 4 * 32, a.lo + eb);
+    cp_async8(p + 5 * 32, a.hi + eb);
+}
+// The copies of a piece's first column pair (any: the lane has one).
+template <int M, class EA>
+__device__ __forceinline__ void roll_prologue(const EA &a, int j, int k0, bool any, float2 *stg)
+{
+    if (any) roll_issue_col<M>(a, j, k0, stg);
+    cp_async_commit();
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+        if (any && i < a.m) roll_issue_src<M>(a, i, j, k0, stg);
+        cp_async_commit();
+    }
+}
+
 // L2 prefetch of what the staged element update still reads from global
 // memory: x, the bounds and the column state s, mu.
 template <int M, class EA> __device__ __forceinline__ void prefetch_mutable(const EA &a, int j, int k0)
@@ -228,22 +286,30 @@ __device__ __forceinline__ void st2(float *p, float2 v) { *(float2 *)p = v; }
 // iteration by the caller, so no FP64 operation runs per element.  The capacity
 // sums accumulate per lane in ghi/glo (the caller combines the lanes), the
 // D_k extrema in dmx/dmn.  rec (if k0 == 0) receives x at k = 0 as an FP32
-// value in the first four bytes of its slot (the scalar phase widens it).  The
+// value in the first four bytes of its slot (the scalar phase widens it).
+// STAGE_ROLL: the inputs come from the lane's rolling stage stg, and each slot
+// group is refilled with the pair k0n (if >= 0) as soon as it is read.  The
 // first column is always < n; the second may be padding (k0 + 1 = n), and
 // then takes no part in the sums and residuals.
-template <int M, int VW, bool C64, bool STAGED = false, class EA>
+// Where vec32 reads its inputs: global memory, the double stage of
+// stage_vec32 (coefficients and y), or the rolling stage (everything).
+enum { STAGE_NONE = 0, STAGE_DOUBLE = 1, STAGE_ROLL = 2 };
+
+template <int M, int VW, bool C64, int STAGE = STAGE_NONE, class EA>
 __device__ __forceinline__ void vec32(const EA &a, const float *uoff, const float *x1nu,
                                       int j, int k0, bool check, bool cold, float mu_div, float rho1, float rho3,
                                       float rho4, float iq, float2 *ghi, float2 *glo, float *dmx, float *dmn,
                                       float &cm_r, float &cm_s, unsigned &esc, double *rec,
-                                      const float2 *stg = nullptr)
+                                      float2 *stg = nullptr, int k0n = -1)
 {
     static_assert(VW == 2, "the element update works on column pairs");
+    constexpr bool ROLL = STAGE == STAGE_ROLL;
     const int m = a.m, q = a.q, n = a.n;
     const auto col = a.col(j, k0);
-    const float2 yv = STAGED ? stg[0] : ldg2(a.y + col);
-    const float2 st = ld2(a.s + col), stl = ld2(a.s_lo + col);
-    float2 mu = ld2(a.mu + col), mul = ld2(a.mu_lo + col);
+    if constexpr (ROLL) cp_async_wait_m<M>(); // the column group of this pair
+    const float2 yv = STAGE != STAGE_NONE ? stg[0] : ldg2(a.y + col);
+    const float2 st = ROLL ? stg[1 * 32] : ld2(a.s + col), stl = ROLL ? stg[3 * 32] : ld2(a.s_lo + col);
+    float2 mu = ROLL ? stg[2 * 32] : ld2(a.mu + col), mul = ROLL ? stg[4 * 32] : ld2(a.mu_lo + col);
     if (mu_div != 1.0f) {
         mu = make_float2(mu.x / mu_div, mu.y / mu_div);
         mul = make_float2(mul.x / mu_div, mul.y / mu_div);
@@ -253,9 +319,13 @@ __device__ __forceinline__ void vec32(const EA &a, const float *uoff, const floa
 #pragma unroll
     for (int i = 0; i < M; ++i)
         if (i < m) {
-            xt[i] = ld2(a.x + a.xe(i, j, k0));
+            xt[i] = ROLL ? stg[(5 + i) * 32] : ld2(a.x + a.xe(i, j, k0));
             xsum = add2(xsum, xt[i]);
         }
+    if constexpr (ROLL) { // the column group has been read: refill it for the next pair
+        if (k0n >= 0) roll_issue_col<M>(a, j, k0n, stg);
+        cp_async_commit();
+    }
     const bool v1 = k0 + 1 < n;
     const bool jac = a.sweep == ADMM_JACOBI;
     const float2 h1 = splat2(0.5f * rho1), h3 = splat2(0.5f * rho3), iq2 = splat2(iq);
@@ -264,14 +334,20 @@ __device__ __forceinline__ void vec32(const EA &a, const float *uoff, const floa
 
 #pragma unroll
     for (int i = 0; i < M; ++i) {
+        if constexpr (ROLL) cp_async_wait_m<M>(); // source i's group of this pair
         if (i < m) {
             const auto e = a.ce(i, j, k0); // coefficient element
             const auto eb = a.be(i, k0);
-            const float2 a2 = STAGED ? stg[(1 + 4 * i) * 32] : ldg2(a.f2 + e);
-            const float2 a1 = STAGED ? stg[(2 + 4 * i) * 32] : ldg2(a.f1 + e);
-            const float2 b2 = STAGED ? stg[(3 + 4 * i) * 32] : ldg2(a.g2 + e);
-            const float2 b1 = STAGED ? stg[(4 + 4 * i) * 32] : ldg2(a.g1 + e);
-            const float2 L = ldg2(a.lo + eb), H = ldg2(a.hi + eb);
+            const float2 *sp = stg + (ROLL ? 5 + M + 6 * i : 1 + 4 * i) * 32;
+            const float2 a2 = STAGE != STAGE_NONE ? sp[0] : ldg2(a.f2 + e);
+            const float2 a1 = STAGE != STAGE_NONE ? sp[32] : ldg2(a.f1 + e);
+            const float2 b2 = STAGE != STAGE_NONE ? sp[64] : ldg2(a.g2 + e);
+            const float2 b1 = STAGE != STAGE_NONE ? sp[96] : ldg2(a.g1 + e);
+            const float2 L = ROLL ? sp[128] : ldg2(a.lo + eb), H = ROLL ? sp[160] : ldg2(a.hi + eb);
+            if constexpr (ROLL) {
+                if (k0n >= 0) roll_issue_src<M>(a, i, j, k0n, stg);
+                cp_async_commit();
+            }
             const float2 g0 = cold ? ldg2(a.g0 + e) : splat2(0.0f);
             const int pr = i * q + j;
             const float2 x0 = xt[i];
@@ -312,6 +388,8 @@ __device__ __forceinline__ void vec32(const EA &a, const float *uoff, const floa
                 dmx[i] = fmaxf(dmx[i], v1 ? fmaxf(dk.x, dk.y) : dk.x);
                 dmn[i] = fminf(dmn[i], v1 ? fminf(dk.x, dk.y) : dk.x);
             }
+        } else if constexpr (ROLL) {
+            cp_async_commit(); // the empty group of an unused source slot
         }
     }
     // (e), (f) in float-float: the column state carries about 48 bits, so

@@ -675,7 +675,7 @@ admm_status admm_server_create(const admm_params *prm, const admm_server_config 
     e = cudaStreamBeginCapture(S->st, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) e = cudaMemsetAsync(S->d_q, 0, 3 * sizeof(int), S->st);
     if (e == cudaSuccess)
-        e = launch_batch(cfg->batch.warps_per_cta, S->mbound, S->grid, S->cluster, a, S->smem, S->st);
+        e = launch_batch(cfg->batch.warps_per_cta, S->mbound, S->grid, S->cluster, a, S->smem, false, S->st);
     cudaError_t e2 = cudaStreamEndCapture(S->st, &g);
     if (e == cudaSuccess && e2 == cudaSuccess) e = cudaGraphInstantiate(&S->exec, g, 0);
     if (g) cudaGraphDestroy(g);
