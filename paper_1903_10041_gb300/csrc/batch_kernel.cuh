@@ -344,14 +344,17 @@ template <int KIND, int NW, int M, bool ROLL> __device__ void solve_team(const B
             if (lane == 0) x1n[i] = sum / (double)q;
         }
         sync_local();
+        // (h), and the FP32 offsets of the next element phase (lambda, zeta final; x1 = x1n)
         double r4m = 0.0;
         for (int pr = tid; pr < mq; pr += NTL) {
             const int i = pr / q;
             const double x0 = x0s[pr], xn = x1n[i];
-            nu[pr] = nu[pr] + (xn - x0);
+            const double nun = nu[pr] + (xn - x0);
+            nu[pr] = nun;
+            uoff[pr] = (float)(zeta[pr] + lam[pr]);
+            x1nu[pr] = (float)(xn + nun);
             if (check) r4m = max_nonneg(r4m, fabs(x0 - xn));
         }
-        sync_local();
         if (tid < m) x1[tid] = x1n[tid];
         if (tid == 0) {
             flags[0] = 0.0;
@@ -410,6 +413,8 @@ template <int KIND, int NW, int M, bool ROLL> __device__ void solve_team(const B
                     lam[pr] /= f;
                     pp[pr] /= f;
                     nu[pr] /= f;
+                    uoff[pr] = (float)(zeta[pr] + lam[pr]);
+                    x1nu[pr] = (float)(x1[pr / q] + nu[pr]);
                 }
                 if (tid == 0) {
                     for (int t = 0; t < 4; ++t) rho[t] *= f;
@@ -423,11 +428,6 @@ template <int KIND, int NW, int M, bool ROLL> __device__ void solve_team(const B
                 sync_local();
             }
         }
-        for (int pr = tid; pr < mq; pr += NTL) {
-            uoff[pr] = (float)(zeta[pr] + lam[pr]);
-            x1nu[pr] = (float)(x1[pr / q] + nu[pr]);
-        }
-        sync_local();
     }
     const bool finished = conv || it >= a.max_iter;
 
