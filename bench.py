@@ -90,7 +90,7 @@ def workload(cfg: int, precision: str, coef_shared: bool = False):
 NCU_TRAFFIC = {
     ("phev n=1000 q=50", "fp64"): {"bytes_per_iter": (7572224 + 50944) / 3330, "src": "81ac6bf6b4915e2b"},
 }
-NCU_TRAFFIC_BATCH = {"bytes_per_element_iter": (1812462231296 + 614489101056) / 76330081250.0, "src": "ef3e0b230f55ab84"}
+NCU_TRAFFIC_BATCH = {"bytes_per_element_iter": (1812820075776 + 614461865472) / 76330081250.0, "src": "228138a44e64ca53"}
 # FP64 pipe utilisation (sm__pipe_fp64_cycles_active, % of peak over the active cycles) of the FP64 solve
 # kernel on the PHEV instance, from an ncu capture of the same build: the counted-flop fraction leaves out
 # the Newton steps of the FP32-seeded roots, conversions, comparisons and the per-pair scalar phase.
