@@ -88,13 +88,14 @@ def workload(cfg: int, precision: str, coef_shared: bool = False):
 # figure is reported only while the kernel's sources hash to the build it
 # was taken on (otherwise `traffic` is null).
 NCU_TRAFFIC = {
-    ("phev n=1000 q=50", "fp64"): {"bytes_per_iter": (7662848 + 59648) / 3330, "src": "6a235cd86e95b7bb"},
+    ("phev n=1000 q=50", "fp64"): {"bytes_per_iter": (7666944 + 49920) / 3330, "src": "0f1fa41955024aab"},
+    ("plain n=1e5 m=4 q=20", "mixed"): {"bytes_per_iter": (568258408448 + 185992512000) / 2750, "src": "0f1fa41955024aab"},
 }
-NCU_TRAFFIC_BATCH = {"bytes_per_element_iter": (1812820075776 + 614461865472) / 76330081250.0, "src": "228138a44e64ca53"}
+NCU_TRAFFIC_BATCH = {"bytes_per_element_iter": (1811961266176 + 614259118080) / 76330081250.0, "src": "58bddc1cb77dc15c"}
 # FP64 pipe utilisation (sm__pipe_fp64_cycles_active, % of peak over the active cycles) of the FP64 solve
 # kernel on the PHEV instance, from an ncu capture of the same build: the counted-flop fraction leaves out
 # the Newton steps of the FP32-seeded roots, conversions, comparisons and the per-pair scalar phase.
-NCU_FP64_PIPE = {("phev n=1000 q=50", "fp64"): {"pct": 60.54, "src": "6a235cd86e95b7bb"}}
+NCU_FP64_PIPE = {("phev n=1000 q=50", "fp64"): {"pct": 60.47, "src": "0f1fa41955024aab"}}
 
 # Sources each solve kernel is compiled from.
 SINGLE_KERNEL_SOURCES = ("single.cu", "quartic32.cuh", "quartic64.cuh", "mixed_elem.cuh", "common.cuh", "internal.h")

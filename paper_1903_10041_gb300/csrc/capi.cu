@@ -503,7 +503,7 @@ admm_status admm_create(const admm_problem *P, const admm_params *prm, admm_hand
     }
 
     // launch shape: contiguous equal column chunks, all SMs busy
-    h->smem = single_smem_bytes(m, q);
+    h->smem = single_smem_bytes(m, q, prm->precision);
     h->rs = mixed ? ld : n;
     h->ncols = (int64_t)q * h->rs;
     const SingleShape sh = single_shape(prm->precision, m, q, h->rs, h->nsm, h->smem);

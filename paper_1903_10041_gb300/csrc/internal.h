@@ -95,7 +95,7 @@ inline __host__ __device__ int64_t piece_bound(int t, int64_t rs, int p, int uni
 }
 SingleShape single_shape(int precision, int m, int q, int64_t rs, int nsm, size_t smem);
 // Dynamic shared memory the single-instance kernel needs.
-size_t single_smem_bytes(int m, int q);
+size_t single_smem_bytes(int m, int q, int precision);
 // Index of the kernel variant used for m sources (template bound).
 int single_mbound(int m);
 // Threads per CTA of the single-instance kernel of a precision.

@@ -207,7 +207,7 @@ extern "C" admm_status admm_solve_noalloc(const admm_problem *P, const admm_para
     int nsm = 0;
     if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return nfail(ADMM_ECUDA, "cudaDeviceGetAttribute failed");
-    const size_t smem = single_smem_bytes(m, q);
+    const size_t smem = single_smem_bytes(m, q, ADMM_FP64);
     // the same launch shape as admm_create
     const SingleShape sh = single_shape(prm->precision, m, q, n, nsm, smem);
     if (sh.grid < 1) return nfail(ADMM_EUNSUPPORTED, "solve kernel cannot be resident");

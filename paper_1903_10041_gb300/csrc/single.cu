@@ -60,6 +60,17 @@ struct Sm {
     float *x1nu;  // [mq] x1 + nu in FP32 (mixed variants)
 };
 
+// Bytes of the shared state carve() lays out, rounded up to 16: the rolling
+// stage of the mixed kernels (m <= 4) starts there.
+__host__ __device__ inline size_t single_carve_bytes(int m, int q)
+{
+    const int mq = m * q;
+    const size_t b = sizeof(double) * ((size_t)scal_size(m, q) + mq + kMaxM + kSingleWarpsMax * kMaxM * 3 +
+                                       kSingleWarpsMax * 8 + 16 + kSingleWarpsMax) +
+                     sizeof(float) * 2 * (size_t)mq;
+    return (b + 15) / 16 * 16;
+}
+
 __device__ __forceinline__ Sm carve(double *base, int m, int q)
 {
     const int mq = m * q;
@@ -491,12 +502,28 @@ __global__ void __launch_bounds__(NT, MINB) single_kernel(SingleArgs a)
                                     a.xmin_mode,         a.cq,                a.cj,
                                     a.dbg};
                 const int kn = min(ke, n); // padding columns k >= n are skipped
-                for (int k0 = kb + first * VW; k0 < kn; k0 += stride * VW) {
-                    if constexpr (MINB == 2) // several vectors per thread: fetch the next one into L2
-                        if (k0 + stride * VW < kn) prefetch_vec32<M>(ea, j, k0 + stride * VW, cold);
-                    vec32<M, VW, PREC == ADMM_MIXED_FP64CUBIC>(ea, sm.uoff, sm.x1nu, j, k0, check, cold,
-                                                               (float)mu_div, rho1, rho3, rho4, iq, ghi, glo, fmx,
-                                                               fmn, fcr, fcs, esc, rec);
+                if constexpr (M <= 4) {
+                    // every input through the warp's rolling cp.async stage (each CTA keeps its
+                    // columns for the whole launch, so its L1 never holds another SM's lines)
+                    float2 *stw = (float2 *)((char *)smem + single_carve_bytes(m, q)) +
+                                  (size_t)(threadIdx.x >> 5) * roll_slots<M>() * 32 + (threadIdx.x & 31);
+                    const int k00 = kb + first * VW;
+                    roll_prologue<M>(ea, j, k00, k00 < kn, stw);
+                    for (int k0 = k00; k0 < kn; k0 += stride * VW) {
+                        const int k0n = k0 + stride * VW < kn ? k0 + stride * VW : -1;
+                        vec32<M, VW, PREC == ADMM_MIXED_FP64CUBIC, STAGE_ROLL>(
+                            ea, sm.uoff, sm.x1nu, j, k0, check, cold, (float)mu_div, rho1, rho3, rho4, iq, ghi, glo,
+                            fmx, fmn, fcr, fcs, esc, rec, stw, k0n);
+                    }
+                    cp_async_wait0();
+                } else {
+                    for (int k0 = kb + first * VW; k0 < kn; k0 += stride * VW) {
+                        if constexpr (MINB == 2) // several vectors per thread: fetch the next one into L2
+                            if (k0 + stride * VW < kn) prefetch_vec32<M>(ea, j, k0 + stride * VW, cold);
+                        vec32<M, VW, PREC == ADMM_MIXED_FP64CUBIC>(ea, sm.uoff, sm.x1nu, j, k0, check, cold,
+                                                                   (float)mu_div, rho1, rho3, rho4, iq, ghi, glo,
+                                                                   fmx, fmn, fcr, fcs, esc, rec);
+                    }
                 }
                 fcr_all = fmaxf(fcr_all, fcr);
                 fcs_all = fmaxf(fcs_all, fcs);
@@ -725,12 +752,13 @@ int single_mbound(int m) { return m <= 2 ? 2 : (m <= 4 ? 4 : 8); }
 // units are shared by the SM, so more warps hide more of their latency.
 int single_threads(int precision) { return precision == ADMM_FP64 ? kBlockF64 : kBlock; }
 
-size_t single_smem_bytes(int m, int q)
+size_t single_smem_bytes(int m, int q, int precision)
 {
-    const int mq = m * q;
-    return sizeof(double) * ((size_t)scal_size(m, q) + mq + kMaxM + kSingleWarpsMax * kMaxM * 3 +
-                             kSingleWarpsMax * 8 + 16 + kSingleWarpsMax) +
-           sizeof(float) * 2 * (size_t)mq + 16;
+    const int mb = single_mbound(m);
+    size_t stage = 0; // the rolling stage of the mixed kernels, one per warp
+    if (precision != ADMM_FP64 && mb <= 4)
+        stage = (size_t)(kBlock / 32) * (mb == 2 ? roll_slots<2>() : roll_slots<4>()) * 32 * sizeof(float2);
+    return single_carve_bytes(m, q) + stage;
 }
 
 int single_blocks_per_sm(int precision, int m, int minb, size_t smem)

@@ -3,6 +3,8 @@ precision): every instance matches the FP64 oracle (objective to 1e-6
 relative, KKT residual at most the oracle's plus 1e-6), gives the same bits alone and
 in the mix, and keeps doing so under every launch configuration the
 autotuner may pick."""
+import time
+
 import numpy as np
 import pytest
 
@@ -84,6 +86,36 @@ def test_batch_result_is_the_same_alone_and_in_the_mix(capi, cfg):
         assert alone["iters"] == mix[t]["iters"]
         assert np.array_equal(alone["x"], mix[t]["x"]), t
         assert alone["objective"] == mix[t]["objective"]
+
+
+@pytest.mark.parametrize("cfg", [(16, 0, 0, 1, 0), (8, 0, 0, 2, 8192)])
+def test_batch_and_server_give_the_same_bits(capi, cfg):
+    """A batch stages every input of its CTA and cluster teams through the
+    rolling cp.async stage; a server (whose round-robin slices move instances
+    between SMs) stages the coefficients only.  Both read the same values:
+    every instance gives the same iterations and bits either way."""
+    probs = small_batch(20, seed=23)
+    par = W.Params(rho=(1.0, 1.0 / 600, 1.0, 1.0), precision="mixed")
+    with capi.Batch(probs, par) as B:
+        B.set_config(*cfg)
+        B.solve()
+        res_b = B.wait(want_x=True)
+    w, c, sm, cl, cm = cfg
+    with capi.Server(par, tick_iters=25, warps_per_cta=w, ctas_per_sm=c, small_max_elements=sm, cluster_size=cl,
+                     cluster_min_elements=cm) as S:
+        tickets = [S.submit(P) for P in probs]
+        res_s, t0 = {}, time.time()
+        while len(res_s) < len(tickets):
+            for t in tickets:
+                if t not in res_s:
+                    r = S.poll(t, wait_ms=5, want_x=True)
+                    if r is not None:
+                        res_s[t] = r
+            assert time.time() - t0 < 120.0, "served requests did not finish"
+    for t, tk in enumerate(tickets):
+        assert res_b[t]["converged"] and res_s[tk]["converged"], t
+        assert res_b[t]["iters"] == res_s[tk]["iters"], t
+        assert np.array_equal(res_b[t]["x"], res_s[tk]["x"]), t
 
 
 def test_batch_autotune_picks_a_valid_config_and_still_solves(capi, oracle_lib):
