@@ -190,3 +190,38 @@ def test_server_poll_of_an_unknown_ticket_is_an_error():
     with pytest.raises(capi.AdmmError) as e:
         s.poll(12345)
     assert e.value.status == capi.ADMM_EINVAL
+
+
+def test_batch_and_server_refuse_bad_settings_before_any_device_call():
+    """Batches and servers check their settings first (the rules of
+    admm_create: adapt_start >= 0, tolerances >= 0, reserved fields 0) and a
+    server refuses a store beyond the kernel's 32-bit array offsets; none of
+    this needs a device."""
+    from paper_1903_10041_gb300 import capi
+    from paper_1903_10041_gb300 import workloads as W
+    P = W.random_problem(4, 2, 1, seed=3)
+    keep = []
+    cp = capi.make_problem(P, keep)
+
+    def mixed(**kw):
+        pp = capi.make_params(W.Params(precision="mixed"))
+        for k, v in kw.items():
+            if k == "reserved":
+                pp.reserved[0] = v
+            else:
+                setattr(pp, k, v)
+        return pp
+
+    for kw in ({"adapt_start": -1}, {"reserved": 1}, {"r_tol": -1.0}):
+        h = capi._B()
+        st = capi._lib.admm_batch_create(ctypes.byref(cp), 1, ctypes.byref(mixed(**kw)), ctypes.byref(h))
+        assert st == capi.ADMM_EINVAL and not h.value, kw
+    cfg = capi.admm_server_config()
+    capi._lib.admm_server_default_config(ctypes.byref(cfg))
+    s = capi._S()
+    assert capi._lib.admm_server_create(ctypes.byref(mixed(adapt_start=-1)), ctypes.byref(cfg),
+                                        ctypes.byref(s)) == capi.ADMM_EINVAL and not s.value
+    cfg.store_elements = 1 << 32
+    assert capi._lib.admm_server_create(ctypes.byref(mixed()), ctypes.byref(cfg),
+                                        ctypes.byref(s)) == capi.ADMM_EUNSUPPORTED and not s.value
+    assert "32-bit" in capi.admm_last_error()
