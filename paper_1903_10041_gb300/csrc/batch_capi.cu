@@ -2,11 +2,14 @@
 // packing of many instances into one store, the launch configuration and
 // its autotuner, CUDA-graph capture of the launch, and per-instance results.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <numeric>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "store.h"
@@ -326,27 +329,67 @@ admm_status admm_batch_create(const admm_problem *probs, int32_t count, const ad
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
     if (e != cudaSuccess)
         return bail(bfail(e == cudaErrorMemoryAllocation ? ADMM_ENOMEM : ADMM_ECUDA, cudaGetErrorString(e)));
-    float *pinned = nullptr;
-    e = cudaMallocHost(&pinned, sizeof(float) * std::max<size_t>(max_floats, 4));
-    if (e != cudaSuccess) return bail(bfail(ADMM_ENOMEM, "pinned staging buffer"));
+    // The store's allocator places the instances in order; then worker threads validate, stage in
+    // FP32 and upload them, each with its own stream and pinned staging buffer (the instances'
+    // ranges are disjoint). The first error stops the workers and is the one reported.
     b->inst.resize(count);
-    Staged S;
-    HostProblem H;
-    for (int t = 0; t < count && e == cudaSuccess; ++t) {
-        e = to_host(probs[t], H);
-        if (e != cudaSuccess) break;
-        if (!stage_instance(H.P, S, why)) {
-            cudaFreeHost(pinned);
-            return bail(bfail(ADMM_EINVAL, "instance " + std::to_string(t) + ": " + why));
+    for (int t = 0; t < count; ++t)
+        if (!b->store.place(probs[t].n, probs[t].m, probs[t].q, b->inst[t])) return bail(bfail(ADMM_ENOMEM, "store is full"));
+    const int hw = (int)std::thread::hardware_concurrency();
+    const int nthr = std::max(1, std::min(std::min(16, hw > 0 ? hw : 1), count));
+    std::atomic<int> next{0};
+    std::atomic<bool> failed{false};
+    std::mutex emu;
+    admm_status fst = ADMM_OK;
+    std::string fmsg;
+    auto fail_once = [&](admm_status s, const std::string &msg) {
+        std::lock_guard<std::mutex> lk(emu);
+        if (!failed.exchange(true)) {
+            fst = s;
+            fmsg = msg;
         }
-        if (!b->store.place(S.n, S.m, S.q, b->inst[t])) {
-            cudaFreeHost(pinned);
-            return bail(bfail(ADMM_ENOMEM, "store is full"));
+    };
+    auto worker = [&]() {
+        cudaStream_t st = nullptr;
+        float *pinned = nullptr;
+        cudaError_t we = cudaSetDevice(b->dev);
+        if (we == cudaSuccess) we = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+        if (we == cudaSuccess) we = cudaMallocHost(&pinned, sizeof(float) * std::max<size_t>(max_floats, 4));
+        if (we != cudaSuccess)
+            fail_once(we == cudaErrorMemoryAllocation ? ADMM_ENOMEM : ADMM_ECUDA,
+                      std::string("staging: ") + cudaGetErrorString(we));
+        Staged S;
+        HostProblem H;
+        std::string wwhy;
+        while (!failed.load()) {
+            const int t = next.fetch_add(1);
+            if (t >= count) break;
+            we = to_host(probs[t], H);
+            if (we != cudaSuccess) {
+                fail_once(ADMM_ECUDA, cudaGetErrorString(we));
+                break;
+            }
+            if (!stage_instance(H.P, S, wwhy)) {
+                fail_once(ADMM_EINVAL, "instance " + std::to_string(t) + ": " + wwhy);
+                break;
+            }
+            b->inst[t].cs = S.cs;
+            we = b->store.upload(b->inst[t], S, b->prm, pinned, max_floats, st);
+            if (we != cudaSuccess) {
+                fail_once(ADMM_ECUDA, cudaGetErrorString(we));
+                break;
+            }
         }
-        b->inst[t].cs = S.cs;
-        e = b->store.upload(b->inst[t], S, b->prm, pinned, max_floats, b->cap);
-    }
-    cudaFreeHost(pinned);
+        if (st) {
+            cudaStreamSynchronize(st);
+            cudaStreamDestroy(st);
+        }
+        if (pinned) cudaFreeHost(pinned);
+    };
+    std::vector<std::thread> pool;
+    for (int w = 0; w < nthr; ++w) pool.emplace_back(worker);
+    for (std::thread &th : pool) th.join();
+    if (failed.load()) return bail(bfail(fst, fmsg));
     if (e == cudaSuccess)
         e = cudaMemcpy(b->d_inst, b->inst.data(), sizeof(BatchInst) * count, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(b->d_out, 0, sizeof(double) * kInfo * count);
