@@ -36,10 +36,12 @@ MAX_PAIRS = 1024
 
 
 class admm_problem(C.Structure):
+    # the array pointers as c_void_p (the same ABI as const double *): they take the integer
+    # address directly, which keeps marshalling thousands of problems cheap
     _fields_ = [("n", C.c_int32), ("m", C.c_int32), ("q", C.c_int32),
-                ("f2", _dp), ("f1", _dp), ("f0", _dp), ("g2", _dp), ("g1", _dp), ("g0", _dp),
-                ("x_lo", _dp), ("x_hi", _dp), ("y", _dp), ("c", _dp), ("on_device", C.c_int32),
-                ("coef_shared", C.c_int32)]
+                ("f2", C.c_void_p), ("f1", C.c_void_p), ("f0", C.c_void_p), ("g2", C.c_void_p),
+                ("g1", C.c_void_p), ("g0", C.c_void_p), ("x_lo", C.c_void_p), ("x_hi", C.c_void_p),
+                ("y", C.c_void_p), ("c", C.c_void_p), ("on_device", C.c_int32), ("coef_shared", C.c_int32)]
 
 
 class admm_params(C.Structure):
@@ -167,12 +169,27 @@ def make_params(par=None, **kw) -> admm_params:
     return p
 
 
+def _addr(a, keep: list):
+    """Address of a float64 C-contiguous array (numpy on the host, torch on either side)."""
+    if a is None:
+        return None, None
+    if _is_torch(a):
+        import torch
+        if a.dtype != torch.float64 or not a.is_contiguous():
+            raise TypeError("torch tensors must be float64 and contiguous")
+        keep.append(a)
+        return a.data_ptr(), bool(a.is_cuda)
+    arr = np.ascontiguousarray(a, dtype=np.float64)
+    keep.append(arr)
+    return arr.ctypes.data, False
+
+
 def make_problem(prob, keep: list) -> admm_problem:
     """admm_problem pointing at the arrays of a duck-typed problem object."""
     names = ("f2", "f1", "f0", "g2", "g1", "g0", "lo", "hi", "y", "c")
     ptrs, devs = [], set()
     for nm in names:
-        p, d = _ptr(getattr(prob, nm), keep)
+        p, d = _addr(getattr(prob, nm), keep)
         ptrs.append(p)
         devs.add(d)
     if len(devs) != 1:
