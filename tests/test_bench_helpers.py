@@ -86,3 +86,19 @@ def test_paper_penalties_are_the_settings_of_the_phev_study():
     assert par.r_tol == 1e-6 * float(P.c[1]) and par.s_tol == 1e-2
     sweep = b.sweep_workloads("5,500", "fp64", False, paper=True)
     assert [q.rho for _, q in sweep] == [(1e-4, 2e-6, 5e-6, 5e-6)] * 2
+
+
+def test_penalty_settings_of_the_batched_and_served_lines():
+    """--adapt-start applies only with the adaptation, and the line's rho text
+    says so; the served line adapts from iteration 1000 (reading R16)."""
+    import argparse
+    b = _bench()
+    par = b.batch_params(argparse.Namespace(adapt=True, adapt_start=1000))
+    assert par.adapt_rho and par.adapt_start == 1000 and par.rho2_over_n and par.precision == "mixed"
+    assert b.penalty_text(argparse.Namespace(adapt=True, adapt_start=1000)).endswith("from iteration 1000")
+    par = b.batch_params(argparse.Namespace(adapt=False, adapt_start=1000))
+    assert not par.adapt_rho and par.adapt_start == 0
+    assert b.penalty_text(argparse.Namespace(adapt=True, adapt_start=0)).endswith("adapted (Sec. IV-A)")
+    src = open(os.path.join(ROOT, "bench.py")).read()
+    assert "args.adapt_start = args.adapt_start or 1000" in src
+    assert "cluster_size=2, cluster_min_elements=100000" in src
