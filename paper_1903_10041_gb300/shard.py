@@ -18,17 +18,23 @@ k = 0 (steps (c), (h)).  So an iteration is
 
 On check iterations a second, two-value maximum over the workers completes
 the residuals (the element terms |z - g(x)| and |z - z~|), and every worker
-takes the same stop decision (Alg. 2 step 3).
+takes the same stop decision (Alg. 2 step 3) and, with the penalty
+adaptation of Sec. IV-A, the same rescaling: from the same r and sigma every
+worker divides its columns' lambda, mu and the pair scalars p, nu by the
+factor and multiplies the penalties by it.
 
 This module is the protocol: the column split, the record layout, the
 exchange and the stop test.  The per-worker compute is a backend object
-with ``snapshot()``, ``phase_a(check)`` and ``phase_b(tot, check)``; the
+with ``snapshot()``, ``phase_a(check)``, ``phase_b(tot, check)`` and
+``rescale(f)``; the
 tests drive it on CPU worker processes (gloo) with their FP64 reference
 implementation of the two phases.  The device kernels for the two phases
 are not built: every machine this project runs on has one GPU, and a
 single instance fits it.
 """
 from __future__ import annotations
+
+import math
 
 import numpy as np
 
@@ -80,11 +86,21 @@ class Exchange:
         return t.cpu().numpy()
 
 
+def _div(a: float, b: float) -> float:
+    """a / b with the IEEE results for b = 0 (inf, or nan for 0 / 0)."""
+    if b != 0.0:
+        return a / b
+    return float("nan") if a == 0.0 else math.copysign(float("inf"), a)
+
+
 def run(backend, exchange, m: int, q: int, rho, r_tol: float, s_tol: float, max_iter: int,
-        check_every: int) -> dict:
+        check_every: int, adapt: bool = False, tau: float = 1.1, adapt_start: int = 0) -> dict:
     """Iterates phase A, exchange, phase B until the stop test of Alg. 2
     step 3 (r < r_tol and sigma < s_tol at a check iteration) or max_iter.
-    rho = (rho_1, rho_2, rho_3, rho_4) as the backend uses them (fixed)."""
+    rho = (rho_1, rho_2, rho_3, rho_4) as the backend uses them.  adapt:
+    the ratio rule of Sec. IV-A at check iterations t >= adapt_start (not
+    the last), rho <- rho f with f = tau or 1 / tau, duals divided by f."""
+    rho = tuple(float(v) for v in rho)
     mq = m * q
     r = sigma = float("inf")
     it = 0
@@ -100,5 +116,14 @@ def run(backend, exchange, m: int, q: int, rho, r_tol: float, s_tol: float, max_
             r = max(r1, r2, res[2], res[3])
             sigma = max(rho[0] * s1, rho[1] * res[4], rho[2] * s3)
             if r < r_tol and sigma < s_tol:
-                return {"iters": it, "converged": True, "r": r, "sigma": sigma}
-    return {"iters": it, "converged": False, "r": r, "sigma": sigma}
+                return {"iters": it, "converged": True, "r": r, "sigma": sigma, "rho": list(rho)}
+            if adapt and it < max_iter and it >= adapt_start:
+                ratio, target, f = _div(r, sigma), _div(r_tol, s_tol), 1.0
+                if ratio > 1.2 * target:
+                    f = tau
+                elif ratio < 0.8 * target:
+                    f = 1.0 / tau
+                if f != 1.0:
+                    backend.rescale(f)
+                    rho = tuple(v * f for v in rho)
+    return {"iters": it, "converged": False, "r": r, "sigma": sigma, "rho": list(rho)}

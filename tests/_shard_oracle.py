@@ -33,3 +33,9 @@ class OracleShard:
 
     def phase_b(self, tot, check):
         return oracle.shard_phase_b(self.P, self.par, self.st, self.n_total, tot, self.gx, self.zp, self.hp)
+
+    def rescale(self, f):
+        """Sec. IV-A: the scaled duals divided by f, the penalties multiplied by f."""
+        for k in ("lam", "mu", "p", "nu"):
+            self.st[k] /= f
+        self.par = self.par.replace(rho=tuple(v * f for v in self.par.rho))

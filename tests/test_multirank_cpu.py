@@ -69,7 +69,15 @@ def test_reference_arm_under_torchrun_prints_one_line_from_rank_0():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["e2e"]["h2d_bytes_per_step"] == 0
 
 
-def _shard_worker(rank, world, port, out, T, tol):
+def _shard_par(T, tol, adapt_start):
+    from paper_1903_10041_gb300 import workloads as W
+    par = W.Params(rho=(1.0, 1.0 / 97, 1.0, 1.0), r_tol=tol, s_tol=tol, max_iter=T, check_every=10)
+    if adapt_start is not None:
+        par = par.replace(adapt_rho=True, adapt_start=adapt_start)
+    return par
+
+
+def _shard_worker(rank, world, port, out, T, tol, adapt_start=None):
     os.environ.update(RANK=str(rank), WORLD_SIZE=str(world), MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     sys.path.insert(0, ROOT)
     import torch.distributed as dist
@@ -78,28 +86,33 @@ def _shard_worker(rank, world, port, out, T, tol):
     from tests._shard_oracle import OracleShard
     dist.init_process_group("gloo", rank=rank, world_size=world)
     P = W.random_problem(97, 3, 4, seed=83)
-    par = W.Params(rho=(1.0, 1.0 / 97, 1.0, 1.0), r_tol=tol, s_tol=tol, max_iter=T, check_every=10)
+    par = _shard_par(T, tol, adapt_start)
     k0, k1 = shard.column_shards(P.n, world)[rank]
     B = OracleShard(P, par, k0, k1)
-    rep = shard.run(B, shard.Exchange(), P.m, P.q, par.rho, par.r_tol, par.s_tol, par.max_iter, par.check_every)
+    rep = shard.run(B, shard.Exchange(), P.m, P.q, par.rho, par.r_tol, par.s_tol, par.max_iter, par.check_every,
+                    adapt=par.adapt_rho, tau=par.tau, adapt_start=par.adapt_start)
     out.put((rank, (k0, k1), rep, {k: v.copy() for k, v in B.st.items()}))
     dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("T,tol", [(60, 0.0), (5000, 1e-6)])
-def test_column_split_over_two_workers_reproduces_the_single_worker_iteration(oracle_lib, T, tol):
+@pytest.mark.parametrize("T,tol,adapt_start", [(60, 0.0, None), (5000, 1e-6, None), (5000, 1e-6, 0),
+                                               (5000, 1e-6, 200)])
+def test_column_split_over_two_workers_reproduces_the_single_worker_iteration(oracle_lib, T, tol, adapt_start):
     """Each worker runs the element updates of its columns (the oracle's
     phase A), one gather of the 2mq + 2 partials combines them in worker
     order, each runs the pair steps (phase B).  After T iterations, and at
     the stop test, the assembled state equals the single-worker oracle's to
     1e-12 relative (the k-sums are added in another order) with the same
-    iteration count; both workers hold the same pair scalars bit for bit."""
+    iteration count; both workers hold the same pair scalars bit for bit.
+    With the penalty adaptation of Sec. IV-A (from the first check, or from
+    iteration 200) every worker takes the oracle's rescalings: the same
+    final penalties and the same state."""
     torch = pytest.importorskip("torch")
     from paper_1903_10041_gb300 import workloads as W
     ctx = torch.multiprocessing.get_context("spawn")
     q_ = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_shard_worker, args=(r, 2, port, q_, T, tol)) for r in range(2)]
+    procs = [ctx.Process(target=_shard_worker, args=(r, 2, port, q_, T, tol, adapt_start)) for r in range(2)]
     for p in procs:
         p.start()
     got = dict((r, (b, rep, st)) for r, b, rep, st in (q_.get(timeout=300) for _ in procs))
@@ -107,7 +120,7 @@ def test_column_split_over_two_workers_reproduces_the_single_worker_iteration(or
         p.join(timeout=60)
         assert p.exitcode == 0
     P = W.random_problem(97, 3, 4, seed=83)
-    par = W.Params(rho=(1.0, 1.0 / 97, 1.0, 1.0), r_tol=tol, s_tol=tol, max_iter=T, check_every=10)
+    par = _shard_par(T, tol, adapt_start)
     st_o, rep_o = oracle_lib.solve(P, par)
     (b0, rep0, s0), (b1, rep1, s1) = got[0], got[1]
     assert b0[0] == 0 and b0[1] == b1[0] and b1[1] == P.n
@@ -123,3 +136,6 @@ def test_column_split_over_two_workers_reproduces_the_single_worker_iteration(or
     for k in ("h", "p", "nu", "x1"):
         assert rel(s0[k], st_o[k]) <= 1e-12, k
     assert abs(rep0["r"] - rep_o["r"]) <= 1e-12 and abs(rep0["sigma"] - rep_o["sigma"]) <= 1e-12
+    assert np.allclose(rep0["rho"], rep_o["rho"], rtol=1e-15, atol=0.0)
+    if adapt_start is not None:
+        assert list(rep0["rho"]) != list(par.rho)   # the rule did rescale
